@@ -1,0 +1,233 @@
+"""Plain FP64 CPU oracle of the per-track Kalman fit (arXiv 2105.01796).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the
+benchmark's CPU-baseline leg load this module; the CUDA product path never
+does.  The oracle is a small C library (``kf_oracle.c``) built with gcc by
+:func:`build` and reached through ctypes.  It shares no code with the CUDA
+path; the only thing both sides see is the synthetic input generator.
+
+Parity status of each oracle function (what pins it) is listed in the
+repository's design notes; every function here is pinned by a ``not gpu``
+test in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kf_oracle.c")
+_LIB = os.path.join(_HERE, "libkf_oracle.so")
+_lib = None
+
+OK, NO_INTERSECTION, NON_SPD, NONFINITE, BAD_INPUT = 0, 1, 2, 3, 4
+MUON_MASS = 0.1056583755  # GeV
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "kf_oracle.h"))
+    ):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", _LIB + ".tmp", _SRC, "-lm", "-lpthread"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        I, D, L = ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        lib.kfo_bound_to_free.argtypes = [P, P, P, P, P]
+        lib.kfo_rkn_step.argtypes = [P, D, P, D, P]
+        lib.kfo_propagate.argtypes = [P, P, P, P, D, D, I, P, P]
+        lib.kfo_propagate.restype = I
+        lib.kfo_transport.argtypes = [P, P, P, P, P, P, D, D, I, P, P, P]
+        lib.kfo_transport.restype = I
+        lib.kfo_highland.argtypes = [D, D, D, D]
+        lib.kfo_highland.restype = D
+        lib.kfo_update.argtypes = [P, P, P, P, P, P, P]
+        lib.kfo_update.restype = I
+        lib.kfo_rts_step.argtypes = [P] * 9
+        lib.kfo_rts_step.restype = I
+        lib.kfo_linear_fit.argtypes = [I] + [P] * 10
+        lib.kfo_linear_fit.restype = I
+        lib.kfo_fit_track.argtypes = [I, P, P, P, P, P, P, I, P, P, P, P, D, D, I] + [P] * 8
+        lib.kfo_fit_track.restype = I
+        lib.kfo_fit_batch.argtypes = [I, P, P, P, I, P, P, P, L, P, P, P, P, P, D, D, I,
+                                      P, P, P, P, P, P, I, I, I]
+        lib.kfo_fit_batch.restype = I
+        _lib = lib
+    return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def bound_to_free(c, R, x):
+    c, R, x = _f64(c, 3), _f64(R, 9), _f64(x, 6)
+    f = np.zeros(8)
+    J = np.zeros((8, 6))
+    _load().kfo_bound_to_free(_p(c), _p(R), _p(x), _p(f), _p(J))
+    return f, J
+
+
+def rkn_step(f, h, B, mass=MUON_MASS):
+    f = _f64(f, 8).copy()
+    D = np.eye(8)
+    _load().kfo_rkn_step(_p(f), float(h), _p(_f64(B, 3)), float(mass), _p(D))
+    return f, D
+
+
+def propagate(f, c, R, B, mass=MUON_MASS, h_max=50.0, n_iter=3):
+    f = _f64(f, 8).copy()
+    D = np.zeros((8, 8))
+    path = np.zeros(1)
+    st = _load().kfo_propagate(_p(f), _p(_f64(c, 3)), _p(_f64(R, 9)), _p(_f64(B, 3)),
+                               float(mass), float(h_max), int(n_iter), _p(D), _p(path))
+    return st, f, D, float(path[0])
+
+
+def transport(ca, Ra, x, cb, Rb, B, mass=MUON_MASS, h_max=50.0, n_iter=3):
+    xo = np.zeros(6)
+    F = np.zeros((6, 6))
+    path = np.zeros(1)
+    st = _load().kfo_transport(_p(_f64(ca, 3)), _p(_f64(Ra, 9)), _p(_f64(x, 6)),
+                               _p(_f64(cb, 3)), _p(_f64(Rb, 9)), _p(_f64(B, 3)),
+                               float(mass), float(h_max), int(n_iter), _p(xo), _p(F),
+                               _p(path))
+    return st, xo, F, float(path[0])
+
+
+def highland(qop, xx0, cosinc, mass=MUON_MASS):
+    return _load().kfo_highland(float(qop), float(mass), float(xx0), float(cosinc))
+
+
+def update(xp, Cp, m, V):
+    xf = np.zeros(6)
+    Cf = np.zeros((6, 6))
+    chi2 = np.zeros(1)
+    st = _load().kfo_update(_p(_f64(xp, 6)), _p(_f64(Cp, (6, 6))), _p(_f64(m, 2)),
+                            _p(_f64(V, (2, 2))), _p(xf), _p(Cf), _p(chi2))
+    return st, xf, Cf, float(chi2[0])
+
+
+def rts_step(xf, Cf, xp1, Cp1, F1, xs1, Cs1):
+    xs = np.zeros(6)
+    Cs = np.zeros((6, 6))
+    st = _load().kfo_rts_step(*[_p(_f64(a)) for a in (xf, Cf, xp1, Cp1, F1, xs1, Cs1)],
+                              _p(xs), _p(Cs))
+    return st, xs, Cs
+
+
+def linear_fit(x0, C0, F, Q, m, V, hole):
+    n = len(hole)
+    xs = np.zeros((n, 6))
+    Cs = np.zeros((n, 6, 6))
+    chi2 = np.zeros(n)
+    hole = np.ascontiguousarray(hole, dtype=np.uint8)
+    st = _load().kfo_linear_fit(n, _p(_f64(x0, 6)), _p(_f64(C0, (6, 6))),
+                                _p(_f64(F, (n, 6, 6))), _p(_f64(Q, (n, 6, 6))),
+                                _p(_f64(m, (n, 2))), _p(_f64(V, (n, 2, 2))), _p(hole),
+                                _p(xs), _p(Cs), _p(chi2))
+    return st, xs, Cs, chi2
+
+
+def fit_track(ev, t, h_max=50.0, n_iter=3, mass=MUON_MASS):
+    """Fit track ``t`` of a synthetic event; return every intermediate."""
+    o0, o1 = int(ev["offsets"][t]), int(ev["offsets"][t + 1])
+    n = o1 - o0
+    sid = np.ascontiguousarray(ev["surface_id"][o0:o1], dtype=np.int32)
+    loc = _f64(ev["loc"][:, o0:o1].T)
+    cov = _f64(ev["cov"][:, o0:o1].T)
+    hole = np.ascontiguousarray(ev["is_hole"][o0:o1], dtype=np.uint8)
+    seed = _f64(ev["seed_params"][:, t])
+    C0 = unpack_sym(ev["seed_cov"][:, t])
+    out = {k: np.zeros((n, 6)) for k in ("xp", "xf", "xs")}
+    out.update({k: np.zeros((n, 6, 6)) for k in ("Cp", "Cf", "Cs", "F")})
+    out["chi2"] = np.zeros(n)
+    S = ev["center"].shape[1]
+    center = _f64(ev["center"].T)
+    rot = _f64(np.moveaxis(ev["rot"].reshape(9, S), 0, 1))
+    st = _load().kfo_fit_track(
+        n, _p(sid), _p(loc), _p(cov), _p(hole), _p(seed), _p(C0), S, _p(center),
+        _p(rot), _p(_f64(ev["x_over_x0"])), _p(_f64(ev["bfield"], 3)), float(mass),
+        float(h_max), int(n_iter), _p(out["xp"]), _p(out["Cp"]), _p(out["xf"]),
+        _p(out["Cf"]), _p(out["xs"]), _p(out["Cs"]), _p(out["F"]), _p(out["chi2"]))
+    out["status"] = st
+    return out
+
+
+def fit_batch(ev, h_max=50.0, n_iter=3, mass=MUON_MASS, t_begin=0, t_end=None,
+              n_threads=None, with_states=False):
+    """Fit tracks [t_begin, t_end) of a synthetic event (SoA boundary layout).
+
+    Returns the outputs for the full track range (entries outside the range
+    are left NaN / zero).
+    """
+    T = int(ev["n_tracks"])
+    M = int(ev["offsets"][-1])
+    if t_end is None:
+        t_end = T
+    if n_threads is None:
+        n_threads = os.cpu_count() or 1
+    S = ev["center"].shape[1]
+    offsets = np.ascontiguousarray(ev["offsets"], dtype=np.int32)
+    sid = np.ascontiguousarray(ev["surface_id"], dtype=np.int32)
+    hole = np.ascontiguousarray(ev["is_hole"], dtype=np.uint8)
+    center = _f64(ev["center"].T)
+    rot = _f64(np.moveaxis(ev["rot"].reshape(9, S), 0, 1))
+    seed = _f64(ev["seed_params"])
+    seed_cov = _f64(ev["seed_cov"])
+    loc = _f64(ev["loc"])
+    cov = _f64(ev["cov"])
+    out = {
+        "params": np.full((6, T), np.nan),
+        "cov": np.full((21, T), np.nan),
+        "chi2": np.full(T, np.nan),
+        "ndf": np.zeros(T, dtype=np.int32),
+        "status": np.zeros(T, dtype=np.uint8),
+    }
+    states = np.full((6, M), np.nan) if with_states else None
+    rc = _load().kfo_fit_batch(
+        T, _p(offsets), _p(seed), _p(seed_cov), S, _p(center), _p(rot),
+        _p(_f64(ev["x_over_x0"])), M, _p(sid), _p(loc), _p(cov), _p(hole),
+        _p(_f64(ev["bfield"], 3)), float(mass), float(h_max), int(n_iter),
+        _p(out["params"]), _p(out["cov"]), _p(out["chi2"]), _p(out["ndf"]),
+        _p(out["status"]), _p(states), int(t_begin), int(t_end), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle rejected the batch arguments")
+    if with_states:
+        out["states"] = states
+    return out
+
+
+def unpack_sym(packed):
+    """21 packed lower-triangle values -> dense symmetric 6x6."""
+    C = np.zeros((6, 6))
+    e = 0
+    for i in range(6):
+        for j in range(i + 1):
+            C[i, j] = C[j, i] = packed[e]
+            e += 1
+    return C
+
+
+def pack_sym(C):
+    return np.array([C[i, j] for i in range(6) for j in range(i + 1)])

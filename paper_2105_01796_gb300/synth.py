@@ -1,0 +1,297 @@
+"""Seeded synthetic track events shaped like the paper's telescope workloads.
+
+This module only *simulates* inputs.  It holds none of the fit's arithmetic:
+no Runge-Kutta-Nystrom stepping, no Jacobians, no Kalman update or smoother.
+Truth trajectories are the closed-form helix of a unit charge in a constant
+field along z; multiple scattering is drawn with the Highland width at every
+crossed plane; hits are Gaussian-smeared local positions.  Both the CUDA path
+and the CPU oracle fit exactly these arrays.
+
+Stands in for the paper's Fatras single-muon samples (paper Sect. 5: a
+telescope of planes perpendicular to x, constant 2 T field along z, single
+muons, 50 um Gaussian smearing, truth-smeared seeds).
+
+Random numbers come from a counter-based generator: SplitMix64 (Steele, Lea,
+Flood 2014) applied to a key built from (seed, track, attempt, purpose,
+index), so every track is reproducible on its own and independent of batch
+size.  Normals use the Box-Muller transform.
+
+Layout of the returned event (the library's structure-of-arrays boundary):
+  offsets[T+1] int32, seed_params[6][T], seed_cov[21][T] (packed lower
+  triangle), truth_params[6][T]; center[3][S], rot[9][S] (row-major R whose
+  columns are u, v, n), x_over_x0[S]; surface_id[M] int32, loc[2][M],
+  cov[3][M] (V00, V01, V11), is_hole[M] uint8, truth_states[6][M]; bfield[3].
+State 0 of every track is the reference plane x = 0 (surface 0), which has no
+measurement and no material; the seed lives there.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+MUON_MASS = 0.1056583755  # GeV
+_KAPPA = 2.99792458e-4  # GeV / (T mm)
+_C = 299.792458  # mm / ns
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+# purposes (stream ids) of the counter-based generator
+_P_PHI, _P_THETA, _P_CHARGE, _P_MOM, _P_NHIT = 0, 1, 2, 3, 4
+_P_SEED, _P_HIT, _P_MS, _P_HOLE = 5, 6, 7, 8
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A synthetic workload: geometry, field, kinematics and smearing."""
+    name: str
+    n_tracks: int
+    plane_x: tuple            # x positions of the measurement planes (mm)
+    x_over_x0: float          # material per plane (fraction of X0)
+    bz: float                 # field along z (T)
+    sigma: float              # hit resolution per axis (mm)
+    p_range: tuple            # log-uniform momentum range (GeV)
+    nhit_range: tuple | None = None   # planes crossed ~ U{lo..hi}; None = all
+    hole_prob: float = 0.0    # probability that a crossed plane has no hit
+    seed: int = 0
+    phi_half: float = 0.3     # phi ~ U(-phi_half, phi_half)
+    theta_half: float = 0.3   # theta ~ U(pi/2 - theta_half, pi/2 + theta_half)
+    half_width: float = 500.0 # planes are 1 m x 1 m in the simulation
+    min_cos_incidence: float = 0.1
+    min_meas: int = 3         # resample tracks left with fewer measurements
+
+
+def _planes(n, step):
+    return tuple(step * (i + 1) for i in range(n))
+
+
+# Workloads shaped like the paper's telescope (Sect. 5) at the sizes the
+# benchmark and the parity tests use.
+WORKLOADS = {
+    "tel10_1k": Workload("tel10_1k", 1000, _planes(10, 30.0), 0.005, 2.0, 0.050,
+                         (1.0, 10.0), seed=0),
+    "tel30_100k": Workload("tel30_100k", 100_000, _planes(30, 25.0), 0.01, 2.0,
+                           0.030, (0.5, 100.0), seed=1),
+    "uneven30_1m": Workload("uneven30_1m", 1_000_000, _planes(30, 25.0), 0.01, 2.0,
+                            0.050, (1.0, 50.0), nhit_range=(5, 30), hole_prob=0.05,
+                            seed=2),
+    "tel30_4m": Workload("tel30_4m", 4_000_000, _planes(30, 25.0), 0.01, 2.0, 0.050,
+                         (1.0, 100.0), seed=4),
+}
+
+
+def scaled(w: Workload, n_tracks: int, **kw) -> Workload:
+    """The same workload with another track count (and optional overrides)."""
+    return dataclasses.replace(w, n_tracks=int(n_tracks), **kw)
+
+
+# ---------------------------------------------------------------------------
+# counter-based random numbers
+# ---------------------------------------------------------------------------
+
+def _splitmix64(z):
+    with np.errstate(over="ignore"):
+        z = (z + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def _uniform(seed, tracks, attempt, purpose, index):
+    """U(0,1) (open) for each track id; attempt may be an array."""
+    t = np.asarray(tracks, dtype=np.uint64)
+    a = np.asarray(attempt, dtype=np.uint64)
+    stream = (a << np.uint64(32)) | np.uint64((purpose << 16) | index)
+    k = _splitmix64(_splitmix64(np.uint64(seed) ^ _splitmix64(t)) ^ stream)
+    return ((k >> np.uint64(11)).astype(np.float64) + 0.5) * (2.0 ** -53)
+
+
+def _normal(seed, tracks, attempt, purpose, index):
+    u1 = _uniform(seed, tracks, attempt, purpose, 2 * index)
+    u2 = _uniform(seed, tracks, attempt, purpose, 2 * index + 1)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# ---------------------------------------------------------------------------
+# simulation
+# ---------------------------------------------------------------------------
+
+def _highland_width(qop, xx0, cos_inc, mass):
+    """Highland/PDG projected scattering width for a unit charge."""
+    p = 1.0 / np.abs(qop)
+    beta2 = p * p / (p * p + mass * mass)
+    eps = xx0 / np.abs(cos_inc)
+    return 0.0136 / (np.sqrt(beta2) * p) * np.sqrt(eps) * (1.0 + 0.038 * np.log(eps / beta2))
+
+
+def _simulate(w: Workload, ids, attempt, mass):
+    """Simulate tracks `ids` (attempt per track); return arrays + ok mask."""
+    n = len(ids)
+    npl = len(w.plane_x)
+    s = w.seed
+    phi0 = -w.phi_half + 2 * w.phi_half * _uniform(s, ids, attempt, _P_PHI, 0)
+    th0 = (math.pi / 2 - w.theta_half) + 2 * w.theta_half * _uniform(s, ids, attempt, _P_THETA, 0)
+    q = np.where(_uniform(s, ids, attempt, _P_CHARGE, 0) < 0.5, -1.0, 1.0)
+    lo, hi = math.log(w.p_range[0]), math.log(w.p_range[1])
+    p = np.exp(lo + (hi - lo) * _uniform(s, ids, attempt, _P_MOM, 0))
+    qop = q / p
+    if w.nhit_range is None:
+        nhit = np.full(n, npl, dtype=np.int64)
+    else:
+        a, b = w.nhit_range
+        nhit = a + np.minimum((_uniform(s, ids, attempt, _P_NHIT, 0) * (b - a + 1)).astype(np.int64), b - a)
+    omega = qop * _KAPPA * w.bz  # turning rate: dphi/ds = -omega
+    gam = np.sqrt(1.0 + mass * mass * qop * qop) / _C  # dt/ds
+    x0 = np.zeros(n); y0 = np.zeros(n); z0 = np.zeros(n); t0 = np.zeros(n)
+    phi = phi0.copy(); th = th0.copy()
+    ok = np.ones(n, dtype=bool)
+    loc = np.zeros((2, npl, n)); meas = np.zeros((2, npl, n))
+    leave = np.zeros((4, npl, n))  # phi, theta (leaving), t, unused
+    hole = np.zeros((npl, n), dtype=bool)
+    for j, xp in enumerate(w.plane_x):
+        crossed = j < nhit
+        st = np.sin(th)
+        dx = xp - x0
+        arg = np.sin(phi) - omega * dx / st
+        ok &= ~crossed | (np.abs(arg) < 1.0)
+        arg = np.clip(arg, -1.0, 1.0)
+        psi = np.arcsin(arg)
+        small = np.abs(omega) < 1e-12
+        om_safe = np.where(small, 1.0, omega)
+        # exact helix: path length and transverse displacement to the plane
+        s_path = np.where(small, dx / (np.cos(phi) * st), (phi - psi) / om_safe)
+        dy = np.where(small, dx * np.tan(phi),
+                      -2.0 * st / om_safe * np.sin(0.5 * (psi + phi)) * np.sin(0.5 * (psi - phi)))
+        y1 = y0 + dy
+        z1 = z0 + s_path * np.cos(th)
+        t1 = t0 + s_path * gam
+        phi1 = np.where(small, phi, psi)
+        cos_inc = np.cos(phi1) * st
+        ok &= ~crossed | ((cos_inc > w.min_cos_incidence) & (np.abs(y1) <= w.half_width)
+                          & (np.abs(z1) <= w.half_width) & (s_path > 0))
+        loc[0, j] = y1; loc[1, j] = z1
+        meas[0, j] = y1 + w.sigma * _normal(s, ids, attempt, _P_HIT, 2 * j)
+        meas[1, j] = z1 + w.sigma * _normal(s, ids, attempt, _P_HIT, 2 * j + 1)
+        hole[j] = _uniform(s, ids, attempt, _P_HOLE, j) < w.hole_prob
+        # multiple scattering in plane j, after the hit (state j leaves it)
+        if w.x_over_x0 > 0:
+            th0w = _highland_width(qop, w.x_over_x0, np.maximum(np.abs(cos_inc), 1e-3), mass)
+            dphi = th0w / st * _normal(s, ids, attempt, _P_MS, 2 * j)
+            dth = th0w * _normal(s, ids, attempt, _P_MS, 2 * j + 1)
+        else:
+            dphi = dth = 0.0
+        phi = phi1 + dphi
+        th = th + dth
+        leave[0, j] = phi; leave[1, j] = th; leave[2, j] = t1
+        x0 = np.full(n, xp, dtype=np.float64); y0 = y1; z0 = z1; t0 = t1
+    nmeas = np.sum(~hole & (np.arange(npl)[:, None] < nhit[None, :]), axis=0)
+    ok &= nmeas >= w.min_meas
+    return dict(phi0=phi0, th0=th0, qop=qop, nhit=nhit, loc=loc, meas=meas,
+                leave=leave, hole=hole, ok=ok)
+
+
+def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200) -> dict:
+    """Simulate workload `w` and return the event dict (see module doc)."""
+    T = w.n_tracks
+    npl = len(w.plane_x)
+    ids_all = np.arange(T, dtype=np.uint64)
+    attempt = np.zeros(T, dtype=np.uint64)
+    sim = _simulate(w, ids_all, attempt, mass)
+    rejected = 0
+    for _ in range(max_attempts):
+        bad = np.nonzero(~sim["ok"])[0]
+        if bad.size == 0:
+            break
+        rejected += bad.size
+        attempt[bad] += 1
+        sub = _simulate(w, ids_all[bad], attempt[bad], mass)
+        for k, v in sub.items():
+            if isinstance(v, np.ndarray):
+                sim[k][..., bad] = v
+    else:
+        raise RuntimeError("track simulation did not converge")
+
+    nhit = sim["nhit"]
+    nstates = nhit + 1
+    offsets = np.zeros(T + 1, dtype=np.int64)
+    np.cumsum(nstates, out=offsets[1:])
+    M = int(offsets[-1])
+    if M >= 2 ** 31:
+        raise ValueError("too many states for int32 offsets")
+    # scatter per-plane arrays into the ragged state list
+    k_idx = np.arange(npl)
+    valid = k_idx[:, None] < nhit[None, :]               # [npl, T]
+    pos = offsets[:-1][None, :] + 1 + k_idx[:, None]      # state index of plane j
+    sel = pos[valid]
+    surface_id = np.zeros(M, dtype=np.int32)
+    loc = np.zeros((2, M)); cov = np.zeros((3, M)); is_hole = np.ones(M, dtype=np.uint8)
+    truth_states = np.zeros((6, M))
+    surface_id[sel] = np.broadcast_to(k_idx[:, None] + 1, valid.shape)[valid]
+    hole = sim["hole"][valid]
+    loc[0, sel] = np.where(hole, 0.0, sim["meas"][0][valid])
+    loc[1, sel] = np.where(hole, 0.0, sim["meas"][1][valid])
+    cov[0, sel] = w.sigma ** 2
+    cov[2, sel] = w.sigma ** 2
+    is_hole[sel] = hole.astype(np.uint8)
+    qop_b = np.broadcast_to(sim["qop"][None, :], valid.shape)
+    truth_states[0, sel] = sim["loc"][0][valid]
+    truth_states[1, sel] = sim["loc"][1][valid]
+    truth_states[2, sel] = sim["leave"][0][valid]
+    truth_states[3, sel] = sim["leave"][1][valid]
+    truth_states[4, sel] = qop_b[valid]
+    truth_states[5, sel] = sim["leave"][2][valid]
+    # state 0: reference plane, no measurement
+    s0 = offsets[:-1]
+    surface_id[s0] = 0
+    is_hole[s0] = 1
+    cov[0, s0] = 1.0
+    cov[2, s0] = 1.0
+    truth = np.stack([np.zeros(T), np.zeros(T), sim["phi0"], sim["th0"], sim["qop"], np.zeros(T)])
+    truth_states[:, s0] = truth
+    # seed: truth smeared with a consistent diagonal prior
+    ids = ids_all
+    sig_seed = np.stack([
+        np.full(T, 10 * w.sigma), np.full(T, 10 * w.sigma),
+        np.full(T, 10 * w.sigma / 100.0), np.full(T, 10 * w.sigma / 100.0),
+        0.1 * np.abs(sim["qop"]), np.full(T, 1.0)])
+    seed_params = truth + sig_seed * np.stack(
+        [_normal(w.seed, ids, attempt, _P_SEED, i) for i in range(6)])
+    seed_cov = np.zeros((21, T))
+    for i in range(6):
+        seed_cov[i * (i + 1) // 2 + i] = sig_seed[i] ** 2
+    # geometry: surface 0 = reference plane at x = 0, then the telescope
+    S = npl + 1
+    center = np.zeros((3, S))
+    center[0, 1:] = np.asarray(w.plane_x)
+    Rn = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])  # u=y, v=z, n=x
+    rot = np.repeat(Rn.reshape(9, 1), S, axis=1)
+    x_over_x0 = np.full(S, w.x_over_x0)
+    x_over_x0[0] = 0.0
+    return dict(
+        name=w.name, n_tracks=T, offsets=offsets.astype(np.int32),
+        seed_params=seed_params, seed_cov=seed_cov, truth_params=truth,
+        center=center, rot=rot, x_over_x0=x_over_x0,
+        bfield=np.array([0.0, 0.0, w.bz]), surface_id=surface_id, loc=loc,
+        cov=cov, is_hole=is_hole, truth_states=truth_states,
+        sigma=w.sigma, rejected=rejected,
+    )
+
+
+def subset(ev: dict, tracks) -> dict:
+    """Event restricted to the given track indices (renumbered 0..k-1)."""
+    tracks = np.asarray(tracks, dtype=np.int64)
+    o = ev["offsets"].astype(np.int64)
+    lens = o[tracks + 1] - o[tracks]
+    new_off = np.zeros(len(tracks) + 1, dtype=np.int64)
+    np.cumsum(lens, out=new_off[1:])
+    idx = np.concatenate([np.arange(o[t], o[t + 1]) for t in tracks]) if len(tracks) else np.zeros(0, np.int64)
+    out = dict(ev)
+    out["n_tracks"] = len(tracks)
+    out["offsets"] = new_off.astype(np.int32)
+    for k in ("seed_params", "seed_cov", "truth_params"):
+        out[k] = np.ascontiguousarray(ev[k][:, tracks])
+    for k in ("loc", "cov", "truth_states"):
+        out[k] = np.ascontiguousarray(ev[k][:, idx])
+    for k in ("surface_id", "is_hole"):
+        out[k] = np.ascontiguousarray(ev[k][idx])
+    return out

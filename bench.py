@@ -1,0 +1,325 @@
+"""Benchmark: tracks fitted per second on one GB300, mixed vs FP64 fit.
+
+Workload: 100,000 synthetic muon tracks through a telescope of 30 planes
+(25 mm spacing, 1 % X0 each), Bz = 2 T, p log-uniform 0.5-100 GeV, 30 um hits
+(one state on the reference plane plus 30 measured states per track).
+A step is one complete fit of the batch: forward filter + RTS smoother of
+every track.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 C fitter) on the host
+cores on a bounded sample of the same workload.  Under torchrun every rank
+fits its own 100k-track batch (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "tel30_100k"
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Roofline denominators for plain ALU work, from the unit counts and clocks of
+# the part: 152 SMs at 2070 MHz; FP64 1.25 TFLOP/s nominal = 2 DFMA lanes per
+# SM per clock; FP32 128 lanes per SM per clock.
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12      # 1.259
+FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tracks", type=int, default=None, help="override the track count")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_tracks_per_s(ev, n_sample, cores):
+    """Oracle (plain FP64 C, POSIX threads) over the first n_sample tracks."""
+    import oracle
+    from paper_2105_01796_gb300 import synth
+    sub = synth.subset(ev, np.arange(min(n_sample, ev["n_tracks"])))
+    t0 = time.perf_counter()
+    oracle.fit_batch(sub, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return sub["n_tracks"] / dt, dt, sub["n_tracks"]
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: each step fits a bounded sample on the host cores."""
+    if rank != 0:
+        return
+    from paper_2105_01796_gb300 import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    if args.tracks:
+        w = synth.scaled(w, args.tracks)
+    ev = synth.make_event(w)
+    cores = os.cpu_count() or 1
+    sample = min(20000, ev["n_tracks"])
+    for _ in range(args.warmup):
+        oracle_tracks_per_s(ev, min(sample, 2000), cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt, n = oracle_tracks_per_s(ev, sample, cores)
+        times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    value = sample / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": "tracks_fitted_per_s", "value": value,
+        "unit": "tracks/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tracks": int(ev["n_tracks"]), "planes": 30,
+                   "sample_tracks_per_step": sample, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                         "sample": "first %d of %d tracks per step" % (sample, ev["n_tracks"])},
+        "e2e": {"value": value, "unit": "tracks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2105_01796_gb300 as kf
+    from paper_2105_01796_gb300 import _build, roofline, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    w = synth.WORKLOADS[WORKLOAD]
+    if args.tracks:
+        w = synth.scaled(w, args.tracks)
+    w = synth.scaled(w, w.n_tracks, seed=w.seed + 1000 * rank)
+    ev = synth.make_event(w)
+    T = int(ev["n_tracks"])
+    M = int(ev["surface_id"].shape[0])
+    dev = kf.event_to_device(ev)
+    h = kf.Handle()
+    stream = torch.cuda.current_stream()
+    prec_id = {"mixed": kf.KF_PRECISION_MIXED, "fp64": kf.KF_PRECISION_FP64}
+    l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(prec, steps, warmup):
+        opt = kf.kf_default_options(prec_id[prec])
+        out = kf.alloc_outputs(T)
+        for _ in range(warmup):
+            kf.kf_fit_ex(h, dev, out, opt, stream)
+        torch.cuda.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        launches = 0
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(steps):
+            l2_flush.zero_()                       # flush L2 between timed steps
+            ev0[i].record(stream)
+            kf.kf_fit_ex(h, dev, out, opt, stream)
+            ev1[i].record(stream)
+            launches += h.last_launch_count()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if dist is not None:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        st = out["status"].cpu().numpy()
+        return ms, launches, wall, st
+
+    # the precision not being headlined is timed first, untimed for clocks
+    other = "fp64" if args.precision == "mixed" else "mixed"
+    ms_other, _, _, st_other = timed(other, max(3, args.steps // 2), args.warmup)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms, launches, wall, st = timed(args.precision, args.steps, args.warmup)
+    clocks = sampler.stop() if sampler else None
+    step_ms = float(np.mean(ms))
+    if dist is not None:
+        t = torch.tensor([step_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * T / (step_ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        host = kf.host_event(ev)
+        pinned = {}
+        for k in kf._HOST_DTYPES:
+            t_ = torch.from_numpy(host[k]).pin_memory()
+            pinned[k] = t_.numpy()
+        hev = dict(host)
+        hev.update(pinned)
+        hev["max_states"] = kf.max_states_of(ev["offsets"])
+        outs = {"params": torch.empty((6, T), dtype=torch.float64).pin_memory().numpy(),
+                "cov": torch.empty((21, T), dtype=torch.float64).pin_memory().numpy(),
+                "chi2": torch.empty((T,), dtype=torch.float64).pin_memory().numpy(),
+                "ndf": torch.empty((T,), dtype=torch.int32).pin_memory().numpy(),
+                "status": torch.empty((T,), dtype=torch.uint8).pin_memory().numpy(),
+                "states": None}
+        opt = kf.kf_default_options(prec_id[args.precision])
+        for _ in range(args.warmup):
+            kf.kf_fit_host(h, hev, opt, out=outs, stream=stream)
+        torch.cuda.synchronize()
+        e_ms = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            kf.kf_fit_host(h, hev, opt, out=outs, stream=stream)   # synchronous
+            e_ms.append(1e3 * (time.perf_counter() - t0))
+        h2d = sum(hev[k].nbytes for k in kf._HOST_DTYPES)
+        d2h = sum(v.nbytes for v in outs.values() if v is not None)
+        e2e_ms = float(np.mean(e_ms))
+        if dist is not None:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * T / (e2e_ms / 1e3), "unit": "tracks/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    f64, f32 = roofline.batch_flops(ev["offsets"], ev["is_hole"], prec_id[args.precision])
+    kern_s = step_ms / 1e3
+    if args.precision == "mixed":
+        achieved = f64 / kern_s / 1e12
+        t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
+    else:
+        achieved = f64 / kern_s / 1e12
+        t_roof = f64 / (FP64_PEAK_TFLOPS * 1e12)
+    traffic = None
+    cpu = None
+    if not args.no_cpu:
+        cores = os.cpu_count() or 1
+        # warm the oracle build, then time a bounded sample
+        oracle_tracks_per_s(ev, 500, cores)
+        v, dt, n = oracle_tracks_per_s(ev, T, cores)
+        cpu = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+               "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt)}
+    other_ms = float(np.mean(ms_other))
+    line = {
+        "metric": "tracks_fitted_per_s", "value": value, "unit": "tracks/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tracks_per_gpu": T, "planes": 30, "states": M,
+                   "precision": args.precision, "field_T": 2.0, "x_over_x0": 0.01,
+                   "sigma_um": 30, "p_GeV": [0.5, 100],
+                   "l2": "flushed between timed steps (256 MiB write); inputs 165 MB > L2",
+                   "parallelism": "one independent batch per GPU" if world > 1 else "single GPU"},
+        "fp64_path" if args.precision == "mixed" else "mixed_path": {
+            "value": world * T / (other_ms / 1e3), "ms_per_step": other_ms,
+            "ok_tracks": int((st_other == 0).sum())},
+        "ok_tracks": int((st == 0).sum()),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "kernel": "kf_fit_kernel", "pipe": "fp64",
+                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2070 MHz",
+                     "t_roof_ms": 1e3 * t_roof, "roof_frac": 1e3 * t_roof / step_ms,
+                     "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * kf.h -- C ABI of the GB300 (sm_103a) Kalman-filter track fitter.
+ *
+ * Method: "A GPU-based Kalman Filter for Track Fitting" (arXiv 2105.01796).
+ *   Sect. 2, Kalman filter step list: predict the state to the next measurement
+ *     surface, then combine it with the measurement (gain-matrix formalism);
+ *     repeat to the end of the trajectory.
+ *   Sect. 2, smoother paragraph: Rauch-Tung-Striebel smoother using the
+ *     Jacobians stored during the forward filter.
+ *   Sect. 2, parameter list: bound parameters (loc0, loc1, phi, theta, q/p, t).
+ *   Sect. 4.1: adaptive Runge-Kutta-Nystrom transport of the parameters; the
+ *     covariance is transported with the transport Jacobian and the
+ *     local<->global Jacobians at both surfaces.
+ *   Sect. 4.2: the smoother's matrix inverse is done in double precision.
+ *   Sect. 4.3: surfaces with geometry and material; a constant 3-vector field;
+ *     four sets of per-track data (measurements, starting parameters, fitting
+ *     configuration, fitted results with a status); boundless surfaces.
+ *
+ * Units: mm, GeV, tesla, ns.  |q| = 1.
+ *
+ * Memory: every array pointer passed to kf_fit / kf_fit_ex is a DEVICE pointer
+ * on the current CUDA device, owned by the caller; kf_fit_host takes HOST
+ * pointers.  The library never frees caller memory.  A kf_handle owns its
+ * workspace (the per-state record the smoother reads back) and staging
+ * buffers.
+ *
+ * Layouts (structure of arrays; T tracks, S surfaces, M states in total):
+ *   offsets[T+1]         int32, states of track t are [offsets[t], offsets[t+1]);
+ *                        state 0 of a track is the surface its seed lives on.
+ *   seed_params[6][T]    double, bound parameters of the seed on state 0.
+ *   seed_cov[21][T]      double, seed covariance, packed lower triangle in
+ *                        row-major order: (0,0) (1,0) (1,1) (2,0) (2,1) ...
+ *   center[3][S]         double, plane centre.
+ *   rot[9][S]            double, row-major 3x3 R whose columns are the local
+ *                        axes u, v and the normal n; point = c + loc0 u + loc1 v.
+ *   x_over_x0[S]         double, material thickness in radiation lengths.
+ *   surface_id[M]        int32 in [0, S).
+ *   loc[2][M]            double, measured (loc0, loc1).
+ *   cov[3][M]            double, measurement covariance (V00, V01, V11).
+ *   is_hole[M]           uint8, 1 = surface crossed without a measurement.
+ *   out_params[6][T]     double, smoothed parameters on state 0.
+ *   out_cov[21][T]       double, smoothed covariance on state 0 (packed).
+ *   out_chi2[T]          double, sum over measured states of r^T S^-1 r of
+ *                        the predicted residual.
+ *   out_ndf[T]           int32, 2 x number of measured states.
+ *   out_status[T]        uint8, kf_track_status.
+ *   out_states[6][M]     double, smoothed parameters on every state (optional).
+ *
+ * Errors: functions return 0 or a negative kf_error.  A per-track failure
+ * does not fail the call: it sets out_status[t] and writes NaN parameters,
+ * covariance and chi2 (ndf 0) for that track.  No device assert or trap is
+ * ever used.  Calls on a handle are asynchronous on the given stream and a
+ * handle must not be used from two host threads at once.
+ */
+#ifndef KF_H
+#define KF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KF_ABI_VERSION 1
+
+typedef enum {
+  KF_SUCCESS = 0,
+  KF_EINVAL = -1,       /* null pointer, bad size or inconsistent arguments */
+  KF_ECUDA = -2,        /* a CUDA call failed; kf_last_cuda_error() has it */
+  KF_ENOMEM = -3,       /* device or pinned allocation failed */
+  KF_EUNSUPPORTED = -4, /* option outside what this build supports */
+  KF_EDEVICE = -5       /* a kernel reported an internal wait timeout */
+} kf_error;
+
+typedef enum {
+  KF_TRACK_OK = 0,
+  KF_TRACK_NO_INTERSECTION = 1, /* track (nearly) parallel to a plane */
+  KF_TRACK_NON_SPD = 2,         /* non-positive innovation or Cholesky pivot */
+  KF_TRACK_NONFINITE = 3,       /* NaN/Inf in the result */
+  KF_TRACK_BAD_INPUT = 4        /* empty track, too many states, bad surface id */
+} kf_track_status;
+
+typedef enum {
+  KF_PRECISION_FP64 = 0, /* every step in double precision */
+  KF_PRECISION_MIXED = 1 /* propagation, Jacobians, covariance transport and
+                            gain in float; Joseph covariance update, the
+                            smoother's Cholesky solve and chi2 in double */
+} kf_precision;
+
+typedef struct {
+  int32_t n_tracks;
+  int32_t max_states;          /* upper bound on offsets[t+1]-offsets[t] */
+  const int32_t* offsets;      /* [n_tracks + 1] */
+  const double* seed_params;   /* [6][n_tracks] */
+  const double* seed_cov;      /* [21][n_tracks] */
+} kf_tracks;
+
+typedef struct {
+  int32_t n_surfaces;
+  const double* center;        /* [3][n_surfaces] */
+  const double* rot;           /* [9][n_surfaces] */
+  const double* x_over_x0;     /* [n_surfaces] */
+} kf_surfaces;
+
+typedef struct {
+  int64_t n_states;
+  const int32_t* surface_id;   /* [n_states] */
+  const double* loc;           /* [2][n_states] */
+  const double* cov;           /* [3][n_states] */
+  const uint8_t* is_hole;      /* [n_states] */
+} kf_measurements;
+
+typedef struct {
+  double b[3];                 /* constant field (Bx, By, Bz) in tesla */
+} kf_field;
+
+typedef struct {
+  double* params;              /* [6][n_tracks], required */
+  double* cov;                 /* [21][n_tracks], required */
+  double* chi2;                /* [n_tracks], required */
+  int32_t* ndf;                /* [n_tracks], optional (NULL) */
+  uint8_t* status;             /* [n_tracks], optional (NULL) */
+  double* states;              /* [6][n_states], optional (NULL) */
+} kf_outputs;
+
+typedef struct {
+  int32_t precision;           /* kf_precision */
+  double mass;                 /* particle mass in GeV (default: muon) */
+  double h_max;                /* longest RKN step in mm (default 50) */
+  int32_t n_iter;              /* Newton corrections onto each plane (default 3) */
+  int32_t block;               /* threads per CTA (0 = default 128) */
+  int64_t workspace_bytes;     /* cap on the handle's workspace (0 = 4 GiB);
+                                  larger batches are fitted in chunks */
+} kf_options;
+
+typedef struct kf_handle kf_handle;
+
+/* Fill *opt with the defaults: FP64, muon mass, h_max 50 mm, 3 corrections. */
+void kf_default_options(kf_options* opt);
+
+/* Create a handle bound to the current CUDA device.  Returns 0 or kf_error. */
+int kf_create(kf_handle** handle);
+
+/* Release the handle's workspace.  Safe on NULL. */
+void kf_destroy(kf_handle* handle);
+
+/* Fit with default options on the legacy default stream, using a library-
+ * owned handle for the current device (created on first use).  Device
+ * pointers.  Waits for completion before returning. */
+int kf_fit(const kf_tracks* tracks, const kf_surfaces* surfaces,
+           const kf_measurements* meas, const kf_field* field,
+           double* out_params, double* out_cov, double* out_chi2);
+
+/* Fit with explicit options on `stream` (a cudaStream_t, NULL = legacy
+ * default stream).  Device pointers.  Asynchronous: the call returns after
+ * the launches are queued.  opt may be NULL (defaults). */
+int kf_fit_ex(kf_handle* handle, const kf_tracks* tracks,
+              const kf_surfaces* surfaces, const kf_measurements* meas,
+              const kf_field* field, const kf_options* opt,
+              const kf_outputs* out, void* stream);
+
+/* Same as kf_fit_ex but every pointer in tracks, surfaces, meas and out is a
+ * HOST pointer: the handle copies the inputs to its device buffers, fits, and
+ * copies the outputs back before returning (synchronous). */
+int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
+                const kf_surfaces* surfaces, const kf_measurements* meas,
+                const kf_field* field, const kf_options* opt,
+                const kf_outputs* out, void* stream);
+
+/* Bytes of device workspace kf_fit_ex would use for this batch shape. */
+int64_t kf_workspace_size(int32_t n_tracks, int32_t max_states,
+                          const kf_options* opt);
+
+/* Number of kernel launches the last kf_fit_ex / kf_fit_host on this handle
+ * queued (for launch accounting). */
+int32_t kf_last_launch_count(const kf_handle* handle);
+
+/* Human-readable text of a kf_error. */
+const char* kf_strerror(int code);
+
+/* Text of the last CUDA error seen by the library on this host thread. */
+const char* kf_last_cuda_error(void);
+
+/* ABI version of the loaded library (KF_ABI_VERSION). */
+int kf_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KF_H */

@@ -1,0 +1,63 @@
+// Internal interface between the C ABI (kf_api.cu) and the kernels
+// (kf_kernels.cu).  Not part of the public header.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kfgb {
+
+// Packed surface record staged into shared memory: 16 doubles (128 B, so the
+// table is a whole number of 16-byte units for the bulk copy):
+//   [0..2] centre, [3..11] R row-major (columns u, v, n), [12] x/X0, [13..15] 0
+constexpr int kSurfStride = 16;
+constexpr int kMaxSurfaces = 1536;  // 192 KiB of shared memory
+
+// Per-state record the forward pass writes and the RTS pass reads back.
+// FP64 path, all in ws64:  xp 6 | xf 6 | Cp 21 | Cf 21 | Bm 36   (90 doubles)
+// Mixed path, ws64:        xp 6 | xf 6 | Cp 21                   (33 doubles)
+//             ws32:        Cf 21 | Bm 36                         (57 floats)
+// Bm = F_k * Cf_{k-1}: the right-hand side of the smoother-gain solve.
+constexpr int kRec64Fp64 = 90;
+constexpr int kRec64Mixed = 33;
+constexpr int kRec32Mixed = 57;
+
+struct FitParams {
+  int32_t n_tracks;        // tracks in this launch (chunk)
+  int32_t track0;          // global index of the chunk's first track
+  int32_t n_tracks_total;  // row stride of [k][n_tracks_total] inputs/outputs
+  int32_t max_states;      // states per track the workspace holds
+  const int32_t* offsets;
+  const double* seed_params;
+  const double* seed_cov;
+  int32_t n_surfaces;
+  const double* surf;      // packed [n_surfaces][kSurfStride]
+  int64_t n_states;
+  const int32_t* surface_id;
+  const double* loc;
+  const double* cov;
+  const uint8_t* is_hole;
+  double bfield[3];
+  double mass;
+  double h_max;
+  int32_t n_iter;
+  double* out_params;
+  double* out_cov;
+  double* out_chi2;
+  int32_t* out_ndf;
+  uint8_t* out_status;
+  double* out_states;
+  double* ws64;            // [max_states][rec64][n_tracks]
+  float* ws32;             // [max_states][rec32][n_tracks] (mixed only)
+  int32_t* error_flag;     // set to 1 when a bounded device wait gives up
+};
+
+// Pack the SoA surface table into [S][kSurfStride] doubles.
+cudaError_t launch_pack_surfaces(int n_surfaces, const double* center,
+                                 const double* rot, const double* x_over_x0,
+                                 double* packed, cudaStream_t stream);
+
+// One fused filter + smoother launch over p.n_tracks tracks.
+cudaError_t launch_fit(const FitParams& p, int precision, int block,
+                       cudaStream_t stream);
+
+}  // namespace kfgb

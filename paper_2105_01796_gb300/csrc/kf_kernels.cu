@@ -1,0 +1,703 @@
+// kf_kernels.cu -- sm_103a kernels of the Kalman-filter track fit
+// (arXiv 2105.01796): forward filter (Runge-Kutta-Nystrom propagation in a
+// constant field, Jacobian transport, multiple-scattering noise, gain-matrix
+// update with the Joseph covariance form, chi2) and the Rauch-Tung-Striebel
+// smoother, fused into one launch with one track per thread.
+//
+// Precision modes (template PREC):
+//   0 = FP64: every step in double precision.
+//   1 = mixed: propagation, Jacobian and covariance transport and the gain in
+//       float; the Joseph covariance update, the smoother's Cholesky solve and
+//       chi2 in double.  Positions, directions, time and the parameter vector
+//       are double-precision accumulators that receive float increments.
+// Paper references: Sect. 2 (filter step list, RTS smoother with the stored
+// Jacobians), Sect. 4.1 (RKN transport; local<->global Jacobians at both
+// surfaces), Sect. 4.2 (double-precision inverter), Sect. 4.3 (surfaces in
+// global memory accessed once; constant field).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "kf_internal.h"
+
+namespace kfgb {
+namespace {
+
+constexpr double kKappa = 2.99792458e-4;   // GeV / (T mm)
+constexpr double kInvC = 1.0 / 299.792458;  // ns / mm
+
+enum : int { ST_OK = 0, ST_NO_INTERSECTION = 1, ST_NON_SPD = 2, ST_NONFINITE = 3, ST_BAD_INPUT = 4 };
+
+// packed lower-triangle index, i >= j
+__host__ __device__ constexpr int sy(int i, int j) { return i * (i + 1) / 2 + j; }
+__device__ __forceinline__ int sym(int i, int j) { return i >= j ? sy(i, j) : sy(j, i); }
+
+template <int PREC> struct Prec;
+template <> struct Prec<0> { using R = double; };
+template <> struct Prec<1> { using R = float; };
+
+// ---------------------------------------------------------------------------
+// surface table staging: one bulk (TMA) copy global -> shared per CTA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Every thread of the CTA must call this.  Returns false if the bounded wait
+// on the copy's mbarrier gave up (the error flag is then set).
+__device__ bool stage_surfaces(double* s_surf, const double* g_surf, uint32_t nbytes,
+                               uint64_t* mbar, int32_t* error_flag) {
+  const uint32_t bar = smem_addr(mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nbytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(s_surf)),
+        "l"(g_surf), "r"(nbytes), "r"(bar)
+        : "memory");
+  }
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 20) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(0u)
+        : "memory");
+  }
+  if (!done) {
+    atomicExch(error_flag, 1);
+    return false;
+  }
+  return true;
+}
+
+struct Surf {
+  const double* d;  // points into shared memory
+  __device__ double c(int i) const { return d[i]; }
+  __device__ double R(int i, int j) const { return d[3 + 3 * i + j]; }
+  __device__ double u(int i) const { return R(i, 0); }
+  __device__ double v(int i) const { return R(i, 1); }
+  __device__ double n(int i) const { return R(i, 2); }
+  __device__ double xx0() const { return d[12]; }
+};
+
+// out = v x bs, where bs = (q/p) * kappa * B; this is the operator A of the
+// equation of motion dT/ds = A T.
+template <typename R, bool BZ>
+__device__ __forceinline__ void applyA(const R bs[3], const R v[3], R out[3]) {
+  if (BZ) {
+    out[0] = v[1] * bs[2];
+    out[1] = -v[0] * bs[2];
+    out[2] = R(0);
+  } else {
+    out[0] = v[1] * bs[2] - v[2] * bs[1];
+    out[1] = v[2] * bs[0] - v[0] * bs[2];
+    out[2] = v[0] * bs[1] - v[1] * bs[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// propagation state: free parameters (double accumulators) plus the columns
+// of G = D * J_bf that vary along the path.  Columns: 0 phi, 1 theta, 2 q/p.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Prop {
+  double r[3], T[3], t;
+  double lam;
+  R gr[3][3];  // position rows, column c
+  R gT[3][3];  // direction rows, column c
+  R gtl;       // time row, q/p column
+};
+
+// One 4-stage Nystrom step of length h in the constant field.  With
+// A v = (q/p) kappa (v x B) the four stages give
+//   T' = (I + hA + h^2A^2/2 + h^3A^3/6 + h^4A^4/24) T = Stt T
+//   r' = r + (hI + h^2A/2 + h^3A^2/6 + h^4A^3/24) T  = r + Srt T
+// (the classic RKN4 combination k1+2k2+2k3+k4 and k1+k2+k3 of the stage
+// accelerations).  G advances by the exact derivative of this step:
+//   position rows += Srt * direction rows (+ dSrt/dlam T on the q/p column)
+//   direction rows = Stt * direction rows (+ dStt/dlam T on the q/p column)
+//   time row (q/p column) += h m^2 lam / (c sqrt(1 + m^2 lam^2)).
+template <typename R, bool BZ>
+__device__ __forceinline__ void rkn_step(Prop<R>& s, double h, const double B[3], double mass) {
+  const R hr = (R)h;
+  const R h2 = hr * hr * R(0.5);
+  const R h3 = hr * hr * hr * R(1.0 / 6.0);
+  const R h4 = hr * hr * hr * hr * R(1.0 / 24.0);
+  const R lk = (R)(s.lam * kKappa);
+  const R bs[3] = {lk * (R)B[0], lk * (R)B[1], lk * (R)B[2]};
+  const R kB[3] = {(R)(kKappa * B[0]), (R)(kKappa * B[1]), (R)(kKappa * B[2])};
+  // value
+  const R Tr[3] = {(R)s.T[0], (R)s.T[1], (R)s.T[2]};
+  R a1[3], a2[3], a3[3], a4[3];
+  applyA<R, BZ>(bs, Tr, a1);
+  applyA<R, BZ>(bs, a1, a2);
+  applyA<R, BZ>(bs, a2, a3);
+  applyA<R, BZ>(bs, a3, a4);
+  // q/p derivative seed: u = kappa (T x B)
+  R u0[3], u1[3], u2[3], u3[3];
+  applyA<R, BZ>(kB, Tr, u0);
+  applyA<R, BZ>(bs, u0, u1);
+  applyA<R, BZ>(bs, u1, u2);
+  applyA<R, BZ>(bs, u2, u3);
+  // Jacobian columns
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R g[3] = {s.gT[0][c], s.gT[1][c], s.gT[2][c]};
+    R b1[3], b2[3], b3[3], b4[3];
+    applyA<R, BZ>(bs, g, b1);
+    applyA<R, BZ>(bs, b1, b2);
+    applyA<R, BZ>(bs, b2, b3);
+    applyA<R, BZ>(bs, b3, b4);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R dr = hr * g[i] + h2 * b1[i] + h3 * b2[i] + h4 * b3[i];
+      R nt = g[i] + hr * b1[i] + h2 * b2[i] + h3 * b3[i] + h4 * b4[i];
+      if (c == 2) {
+        dr += h2 * u0[i] + hr * hr * hr * R(1.0 / 3.0) * u1[i] + hr * hr * hr * hr * R(0.125) * u2[i];
+        nt += hr * u0[i] + hr * hr * u1[i] + hr * hr * hr * R(0.5) * u2[i] +
+              hr * hr * hr * hr * R(1.0 / 6.0) * u3[i];
+      }
+      s.gr[i][c] += dr;
+      s.gT[i][c] = nt;
+    }
+  }
+  const double g2 = 1.0 + mass * mass * s.lam * s.lam;
+  const R gam = (R)sqrt(g2);
+  s.gtl += hr * (R)(mass * mass * s.lam * kInvC) / gam;
+  // advance the double accumulators with float (mixed) increments
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const R dr = h2 * a1[i] + h3 * a2[i] + h4 * a3[i];
+    const R dT = hr * a1[i] + h2 * a2[i] + h3 * a3[i] + h4 * a4[i];
+    s.r[i] = fma(h, s.T[i], s.r[i]) + (double)dr;
+    s.T[i] += (double)dT;
+  }
+  s.t += (double)(hr * gam * (R)kInvC);
+}
+
+// signed straight-line distance along T from r to the plane (c, n)
+template <typename R>
+__device__ __forceinline__ bool plane_step(const Prop<R>& s, const Surf& sb, double& out) {
+  const double d = sb.n(0) * (sb.c(0) - s.r[0]) + sb.n(1) * (sb.c(1) - s.r[1]) + sb.n(2) * (sb.c(2) - s.r[2]);
+  const double nT = sb.n(0) * s.T[0] + sb.n(1) * s.T[1] + sb.n(2) * s.T[2];
+  if (!(fabs(nT) > 1e-9)) return false;
+  out = d / nT;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// transport x (bound, on surface a) to surface b.  Returns the bound
+// prediction xp, the 6x6 Jacobian F (row 4 = e4 and column 5 = e5 implied),
+// and the unit-direction quantities the noise needs.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Jac {
+  R f[4][5];   // rows loc0, loc1, phi, theta over columns 0..4
+  R ft[5];     // time row over columns 0..4 (column 5 of that row is 1)
+};
+
+template <typename R, bool BZ>
+__device__ int transport(const Surf& sa, const Surf& sb, const double x[6], const double B[3],
+                         double mass, double h_max, int n_iter, double xp[6], Jac<R>& J,
+                         R& sin_theta, R& cos_inc) {
+  Prop<R> s;
+  double sp, cp, st, ct;
+  sincos(x[2], &sp, &cp);
+  sincos(x[3], &st, &ct);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.r[i] = sa.c(i) + x[0] * sa.u(i) + x[1] * sa.v(i);
+  s.T[0] = cp * st;
+  s.T[1] = sp * st;
+  s.T[2] = ct;
+  s.t = x[5];
+  s.lam = x[4];
+  // G columns phi, theta: direction rows = dT/dphi, dT/dtheta; q/p column 0
+  s.gT[0][0] = (R)(-sp * st); s.gT[1][0] = (R)(cp * st); s.gT[2][0] = R(0);
+  s.gT[0][1] = (R)(cp * ct);  s.gT[1][1] = (R)(sp * ct); s.gT[2][1] = (R)(-st);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    s.gT[i][2] = R(0);
+    s.gr[i][0] = s.gr[i][1] = s.gr[i][2] = R(0);
+  }
+  s.gtl = R(0);
+
+  double s0;
+  if (!plane_step(s, sb, s0)) return ST_NO_INTERSECTION;
+  const double nsub_d = ceil(fabs(s0) / h_max);
+  if (!(nsub_d <= 64.0)) return ST_NO_INTERSECTION;
+  const int nsub = nsub_d < 1.0 ? 1 : (int)nsub_d;
+  const double h = s0 / nsub;
+  for (int k = 0; k < nsub; ++k) rkn_step<R, BZ>(s, h, B, mass);
+  for (int it = 0; it < n_iter; ++it) {
+    double si;
+    if (!plane_step(s, sb, si)) return ST_NO_INTERSECTION;
+    rkn_step<R, BZ>(s, si, B, mass);
+  }
+
+  // end point: unit direction and bound angles
+  const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
+  const double phi = atan2(s.T[1], s.T[0]);
+  const double theta = atan2(sqrt(rho2), s.T[2]);
+  const R Tr[3] = {(R)s.T[0], (R)s.T[1], (R)s.T[2]};
+  const R rho = (R)sqrt(rho2);
+  const R tn = (R)sqrt(rho2 + s.T[2] * s.T[2]);
+  const R cph = Tr[0] / rho, sph = Tr[1] / rho;
+  const R sth = rho / tn, cth = Tr[2] / tn;
+  const R nb[3] = {(R)sb.n(0), (R)sb.n(1), (R)sb.n(2)};
+  const R nT = nb[0] * Tr[0] + nb[1] * Tr[1] + nb[2] * Tr[2];
+
+  // path correction: dfree += F' w, w = -(n . position rows) / (n . T),
+  // F' = (T, dt/ds, A T, 0) at the end point.
+  const R lk = (R)(s.lam * kKappa);
+  const R bs[3] = {lk * (R)B[0], lk * (R)B[1], lk * (R)B[2]};
+  R AT[3];
+  applyA<R, BZ>(bs, Tr, AT);
+  const R dtds = (R)(sqrt(1.0 + mass * mass * s.lam * s.lam) * kInvC);
+  const R inv_nT = R(1) / nT;
+  // columns 0..4: loc0, loc1, phi, theta, q/p; full G columns after correction
+  R Gr[3][5], GT[3][5], Gt[5];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Gr[i][0] = (R)sa.u(i);
+    Gr[i][1] = (R)sa.v(i);
+    Gr[i][2] = s.gr[i][0];
+    Gr[i][3] = s.gr[i][1];
+    Gr[i][4] = s.gr[i][2];
+    GT[i][0] = R(0);
+    GT[i][1] = R(0);
+    GT[i][2] = s.gT[i][0];
+    GT[i][3] = s.gT[i][1];
+    GT[i][4] = s.gT[i][2];
+  }
+  Gt[0] = Gt[1] = Gt[2] = Gt[3] = R(0);
+  Gt[4] = s.gtl;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const R w = -(nb[0] * Gr[0][c] + nb[1] * Gr[1][c] + nb[2] * Gr[2][c]) * inv_nT;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Gr[i][c] += Tr[i] * w;
+      GT[i][c] += AT[i] * w;
+    }
+    Gt[c] += dtds * w;
+  }
+  // free -> bound at b
+  const R ub[3] = {(R)sb.u(0), (R)sb.u(1), (R)sb.u(2)};
+  const R vb[3] = {(R)sb.v(0), (R)sb.v(1), (R)sb.v(2)};
+  const R inv_sth = R(1) / sth;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    J.f[0][c] = ub[0] * Gr[0][c] + ub[1] * Gr[1][c] + ub[2] * Gr[2][c];
+    J.f[1][c] = vb[0] * Gr[0][c] + vb[1] * Gr[1][c] + vb[2] * Gr[2][c];
+    J.f[2][c] = (-sph * GT[0][c] + cph * GT[1][c]) * inv_sth;
+    J.f[3][c] = cph * cth * GT[0][c] + sph * cth * GT[1][c] - sth * GT[2][c];
+    J.ft[c] = Gt[c];
+  }
+  const double d0 = s.r[0] - sb.c(0), d1 = s.r[1] - sb.c(1), d2 = s.r[2] - sb.c(2);
+  xp[0] = d0 * sb.u(0) + d1 * sb.u(1) + d2 * sb.u(2);
+  xp[1] = d0 * sb.v(0) + d1 * sb.v(1) + d2 * sb.v(2);
+  xp[2] = phi;
+  xp[3] = theta;
+  xp[4] = s.lam;
+  xp[5] = s.t;
+  sin_theta = sth;
+  cos_inc = nT / tn;
+  return ST_OK;
+}
+
+// Highland width for |q| = 1: theta0 = 13.6 MeV/(beta p) sqrt(eps)
+// (1 + 0.038 ln(eps/beta^2)), eps = (x/X0)/|cos incidence|.
+template <typename R>
+__device__ __forceinline__ R highland(double lam, double mass, R xx0, R cos_inc) {
+  const R l = (R)fabs(lam);
+  const R g2 = R(1) + (R)(mass * mass) * l * l;  // 1/beta^2
+  const R eps = xx0 / fabs(cos_inc);
+  return R(0.0136) * l * sqrt(g2) * sqrt(eps) * (R(1) + R(0.038) * log(eps * g2));
+}
+
+// ---------------------------------------------------------------------------
+// workspace access: record element e of state k for chunk track i
+// ---------------------------------------------------------------------------
+struct WS {
+  double* w64;
+  float* w32;
+  size_t nt;
+  int rec64, rec32;
+  int i;
+  __device__ double& d(int k, int e) const { return w64[((size_t)k * rec64 + e) * nt + i]; }
+  __device__ float& f(int k, int e) const { return w32[((size_t)k * rec32 + e) * nt + i]; }
+};
+
+// Storage of the record fields whose precision depends on the path.
+template <int PREC> struct Rec;
+template <> struct Rec<0> {
+  static constexpr int XP = 0, XF = 6, CP = 12, CF = 33, BM = 54;
+  __device__ static void put_cf(const WS& w, int k, int e, double v) { w.d(k, CF + e) = v; }
+  __device__ static double get_cf(const WS& w, int k, int e) { return w.d(k, CF + e); }
+  __device__ static void put_bm(const WS& w, int k, int e, double v) { w.d(k, BM + e) = v; }
+  __device__ static double get_bm(const WS& w, int k, int e) { return w.d(k, BM + e); }
+};
+template <> struct Rec<1> {
+  static constexpr int XP = 0, XF = 6, CP = 12, CF = 0, BM = 21;
+  __device__ static void put_cf(const WS& w, int k, int e, float v) { w.f(k, CF + e) = v; }
+  __device__ static float get_cf(const WS& w, int k, int e) { return w.f(k, CF + e); }
+  __device__ static void put_bm(const WS& w, int k, int e, float v) { w.f(k, BM + e) = v; }
+  __device__ static float get_bm(const WS& w, int k, int e) { return w.f(k, BM + e); }
+};
+
+// ---------------------------------------------------------------------------
+// gain-matrix update with the Joseph covariance form (double precision for
+// the covariance and chi2; the gain in R).  Cp, Cf packed lower triangles.
+//   S = V + H Cp H^T, K = Cp H^T S^-1, xf = xp + K r
+//   Cf = (I-KH) Cp (I-KH)^T + K V K^T
+//      = Cp + K W - (H Cp)^T K^T,  W = S K^T - H Cp   (expanded, exact for any K)
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int kalman_update(const double xp[6], const double Cp[21], const double m[2],
+                                             const double V[3], double xf[6], double Cf[21],
+                                             double& chi2) {
+  const double S00 = V[0] + Cp[sy(0, 0)], S01 = V[1] + Cp[sy(1, 0)], S11 = V[2] + Cp[sy(1, 1)];
+  const double det = S00 * S11 - S01 * S01;
+  if (!(det > 0.0) || !(S00 > 0.0)) return ST_NON_SPD;
+  const double idet = 1.0 / det;
+  const double r0 = m[0] - xp[0], r1 = m[1] - xp[1];
+  chi2 = (S11 * r0 * r0 - 2.0 * S01 * r0 * r1 + S00 * r1 * r1) * idet;
+  // gain in R
+  const R i00 = (R)(S11 * idet), i01 = (R)(-S01 * idet), i11 = (R)(S00 * idet);
+  double K[6][2];
+  const R rr0 = (R)r0, rr1 = (R)r1;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const R c0 = (R)Cp[sym(i, 0)], c1 = (R)Cp[sym(i, 1)];
+    const R k0 = c0 * i00 + c1 * i01;
+    const R k1 = c0 * i01 + c1 * i11;
+    K[i][0] = (double)k0;
+    K[i][1] = (double)k1;
+    xf[i] = xp[i] + (double)(k0 * rr0 + k1 * rr1);
+  }
+  double W[2][6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    W[0][j] = S00 * K[j][0] + S01 * K[j][1] - Cp[sym(0, j)];
+    W[1][j] = S01 * K[j][0] + S11 * K[j][1] - Cp[sym(1, j)];
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      double v = Cp[sy(i, j)];
+      v = fma(K[i][0], W[0][j], v);
+      v = fma(K[i][1], W[1][j], v);
+      v = fma(-Cp[sym(0, i)], K[j][0], v);
+      v = fma(-Cp[sym(1, i)], K[j][1], v);
+      Cf[sy(i, j)] = v;
+    }
+  return ST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the fused fit kernel
+// ---------------------------------------------------------------------------
+template <int PREC, bool BZ>
+__global__ void __launch_bounds__(128) kf_fit_kernel(const FitParams p) {
+  using R = typename Prec<PREC>::R;
+  using RC = Rec<PREC>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* s_surf = reinterpret_cast<double*>(smem_raw);
+  __shared__ __align__(8) uint64_t s_mbar;
+  const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8),
+                                     &s_mbar, p.error_flag);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!staged || i >= p.n_tracks) return;
+  const int t = p.track0 + i;
+  const size_t TT = (size_t)p.n_tracks_total;
+  const WS ws{p.ws64, p.ws32, (size_t)p.n_tracks, PREC == 0 ? kRec64Fp64 : kRec64Mixed,
+              PREC == 0 ? 0 : kRec32Mixed, i};
+  const int64_t o0 = p.offsets[t], o1 = p.offsets[t + 1];
+  const int n = (int)(o1 - o0);
+  int status = ST_OK;
+  if (!(o1 > o0) || o0 < 0 || o1 > p.n_states || n > p.max_states) status = ST_BAD_INPUT;
+  if (status == ST_OK)
+    for (int k = 0; k < n; ++k) {
+      const int sid = p.surface_id[o0 + k];
+      if (sid < 0 || sid >= p.n_surfaces) status = ST_BAD_INPUT;
+    }
+
+  double xs[6], Cs[21];
+  double chi2sum = 0.0;
+  int nmeas = 0;
+  if (status == ST_OK) {
+    // ------------------------------------------------ forward filter
+    double x[6], C[21];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TT + t];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) C[e] = p.seed_cov[e * TT + t];
+    int sid_prev = p.surface_id[o0];
+    for (int k = 0; k < n && status == ST_OK; ++k) {
+      const int sid = p.surface_id[o0 + k];
+      double xp[6], Cp[21];
+      if (k == 0) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) xp[e] = x[e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cp[e] = C[e];
+      } else {
+        const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
+        Jac<R> J;
+        R sin_th, cos_inc;
+        status = transport<R, BZ>(sa, sb, x, p.bfield, p.mass, p.h_max, p.n_iter, xp, J, sin_th, cos_inc);
+        if (status != ST_OK) break;
+        // Bm = F Cf_{k-1}; Cp = Bm F^T + Q.  F rows 0..3 and 5 over columns
+        // 0..4 are J; row 4 = e4; column 5 = e5.
+        R Cr[21];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cr[e] = (R)C[e];
+        R Cpr[21];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          R brow[6];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            R v;
+            if (r == 4) {
+              v = Cr[sym(4, j)];
+            } else {
+              const R* fr = (r == 5) ? J.ft : J.f[r];
+              v = fr[0] * Cr[sym(0, j)] + fr[1] * Cr[sym(1, j)] + fr[2] * Cr[sym(2, j)] +
+                  fr[3] * Cr[sym(3, j)] + fr[4] * Cr[sym(4, j)];
+              if (r == 5) v += Cr[sym(5, j)];
+            }
+            brow[j] = v;
+            RC::put_bm(ws, k, r * 6 + j, brow[j]);
+          }
+#pragma unroll
+          for (int c = 0; c <= r; ++c) {
+            R v;
+            if (c == 4) {
+              v = brow[4];
+            } else {
+              const R* fc = (c == 5) ? J.ft : J.f[c];
+              v = brow[0] * fc[0] + brow[1] * fc[1] + brow[2] * fc[2] + brow[3] * fc[3] + brow[4] * fc[4];
+              if (c == 5) v += brow[5];
+            }
+            Cpr[sy(r, c)] = v;
+          }
+        }
+        // multiple scattering of surface k (added before the update)
+        const R xx0 = (R)sb.xx0();
+        if (xx0 > R(0)) {
+          const R th0 = highland<R>(x[4], p.mass, xx0, cos_inc);
+          const R q = th0 * th0;
+          Cpr[sy(2, 2)] += q / (sin_th * sin_th);
+          Cpr[sy(3, 3)] += q;
+        }
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cp[e] = (double)Cpr[e];
+      }
+      // record the prediction
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ws.d(k, RC::XP + e) = xp[e];
+#pragma unroll
+      for (int e = 0; e < 21; ++e) ws.d(k, RC::CP + e) = Cp[e];
+      // update
+      if (!p.is_hole[o0 + k]) {
+        const double m[2] = {p.loc[o0 + k], p.loc[p.n_states + o0 + k]};
+        const double V[3] = {p.cov[o0 + k], p.cov[p.n_states + o0 + k], p.cov[2 * p.n_states + o0 + k]};
+        double c2 = 0.0;
+        status = kalman_update<R>(xp, Cp, m, V, x, C, c2);
+        if (status != ST_OK) break;
+        chi2sum += c2;
+        ++nmeas;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) x[e] = xp[e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) C[e] = Cp[e];
+      }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ws.d(k, RC::XF + e) = x[e];
+#pragma unroll
+      for (int e = 0; e < 21; ++e) RC::put_cf(ws, k, e, (R)C[e]);
+      sid_prev = sid;
+    }
+
+    // ------------------------------------------------ RTS smoother
+    if (status == ST_OK) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) xs[e] = x[e];
+#pragma unroll
+      for (int e = 0; e < 21; ++e) Cs[e] = C[e];
+      if (p.out_states)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + n - 1] = xs[e];
+      for (int k = n - 2; k >= 0 && status == ST_OK; --k) {
+        // dC = Cs_{k+1} - Cp_{k+1}; L = chol(Cp_{k+1})
+        double L[21], dC[21];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) {
+          L[e] = ws.d(k + 1, RC::CP + e);
+          dC[e] = Cs[e] - L[e];
+        }
+        double idg[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          double dj = L[sy(j, j)];
+#pragma unroll
+          for (int q = 0; q < j; ++q) dj -= L[sy(j, q)] * L[sy(j, q)];
+          if (!(dj > 0.0)) status = ST_NON_SPD;
+          const double ljj = sqrt(dj);
+          idg[j] = 1.0 / ljj;
+          L[sy(j, j)] = ljj;
+#pragma unroll
+          for (int r = j + 1; r < 6; ++r) {
+            double v = L[sy(r, j)];
+#pragma unroll
+            for (int q = 0; q < j; ++q) v -= L[sy(r, q)] * L[sy(j, q)];
+            L[sy(r, j)] = v * idg[j];
+          }
+        }
+        if (status != ST_OK) break;
+        // X = Cp^-1 Bm (column by column); the smoother gain is A = X^T
+        double X[6][6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          double y[6];
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            double v = (double)RC::get_bm(ws, k + 1, r * 6 + c);
+#pragma unroll
+            for (int q = 0; q < r; ++q) v -= L[sy(r, q)] * y[q];
+            y[r] = v * idg[r];
+          }
+#pragma unroll
+          for (int r = 5; r >= 0; --r) {
+            double v = y[r];
+#pragma unroll
+            for (int q = r + 1; q < 6; ++q) v -= L[sy(q, r)] * X[q][c];
+            X[r][c] = v * idg[r];
+          }
+        }
+        // xs_k = xf_k + A (xs_{k+1} - xp_{k+1})
+        double d[6];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) d[e] = xs[e] - ws.d(k + 1, RC::XP + e);
+        R Ar[6][6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) Ar[r][c] = (R)X[c][r];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          R acc = R(0);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) acc += Ar[r][c] * (R)d[c];
+          xs[r] = ws.d(k, RC::XF + r) + (double)acc;
+        }
+        // Cs_k = Cf_k + A dC A^T
+        R dCr[21];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) dCr[e] = (R)dC[e];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          R z[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            R acc = R(0);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc += Ar[r][q] * dCr[sym(q, c)];
+            z[c] = acc;
+          }
+#pragma unroll
+          for (int c = 0; c <= r; ++c) {
+            R acc = R(0);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc += z[q] * Ar[c][q];
+            Cs[sy(r, c)] = (double)(RC::get_cf(ws, k, sy(r, c)) + acc);
+          }
+        }
+        if (p.out_states)
+#pragma unroll
+          for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + k] = xs[e];
+      }
+    }
+    if (status == ST_OK) {
+      bool fin = isfinite(chi2sum);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) fin = fin && isfinite(xs[e]);
+#pragma unroll
+      for (int e = 0; e < 21; ++e) fin = fin && isfinite(Cs[e]);
+      if (!fin) status = ST_NONFINITE;
+    }
+  }
+  if (status != ST_OK) {
+    const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) xs[e] = nan;
+#pragma unroll
+    for (int e = 0; e < 21; ++e) Cs[e] = nan;
+    chi2sum = nan;
+    nmeas = 0;
+    if (p.out_states && n >= 1 && o0 >= 0 && o1 <= p.n_states && n <= p.max_states)
+      for (int k = 0; k < n; ++k)
+        for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + k] = nan;
+  }
+#pragma unroll
+  for (int e = 0; e < 6; ++e) p.out_params[e * TT + t] = xs[e];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) p.out_cov[e * TT + t] = Cs[e];
+  p.out_chi2[t] = chi2sum;
+  if (p.out_ndf) p.out_ndf[t] = 2 * nmeas;
+  if (p.out_status) p.out_status[t] = (uint8_t)status;
+}
+
+__global__ void pack_surfaces_kernel(int n, const double* __restrict__ center, const double* __restrict__ rot,
+                                     const double* __restrict__ xx0, double* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double* o = out + (size_t)s * kSurfStride;
+  for (int i = 0; i < 3; ++i) o[i] = center[(size_t)i * n + s];
+  for (int i = 0; i < 9; ++i) o[3 + i] = rot[(size_t)i * n + s];
+  o[12] = xx0[s];
+  o[13] = o[14] = o[15] = 0.0;
+}
+
+template <int PREC, bool BZ>
+cudaError_t launch_t(const FitParams& p, int block, cudaStream_t stream) {
+  const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);
+  auto kern = kf_fit_kernel<PREC, BZ>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = (p.n_tracks + block - 1) / block;
+  kern<<<grid, block, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_pack_surfaces(int n_surfaces, const double* center, const double* rot,
+                                 const double* x_over_x0, double* packed, cudaStream_t stream) {
+  const int block = 128;
+  pack_surfaces_kernel<<<(n_surfaces + block - 1) / block, block, 0, stream>>>(n_surfaces, center, rot,
+                                                                              x_over_x0, packed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const FitParams& p, int precision, int block, cudaStream_t stream) {
+  if (p.n_tracks <= 0) return cudaSuccess;
+  if (block <= 0) block = 128;
+  const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
+  if (precision == 0) return bz ? launch_t<0, true>(p, block, stream) : launch_t<0, false>(p, block, stream);
+  return bz ? launch_t<1, true>(p, block, stream) : launch_t<1, false>(p, block, stream);
+}
+
+}  // namespace kfgb

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA fit (through the C ABI) against the CPU oracle.
+
+Tolerances are those the fit is specified to: FP64 path within 1e-9
+relative; mixed path within 1e-4 on parameters and 1e-3 on covariances
+(metrics in tests/metrics.py).  Inputs are seeded synthetic telescope events.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2105_01796_gb300 as kf
+from paper_2105_01796_gb300 import synth
+from tests.metrics import chi2_err, cov_err, param_err
+
+pytestmark = pytest.mark.gpu
+
+FP64, MIXED = kf.KF_PRECISION_FP64, kf.KF_PRECISION_MIXED
+TOL = {FP64: (1e-9, 1e-9, 1e-9), MIXED: (1e-4, 1e-3, 1e-4)}
+
+
+@pytest.fixture(scope="module")
+def handle():
+    import torch
+    assert torch.cuda.is_available()
+    import __graft_entry__
+    __graft_entry__.build()
+    h = kf.Handle()
+    yield h
+    h.close()
+
+
+def gpu_fit(handle, ev, prec, with_states=False, **opt):
+    import torch
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(int(ev["n_tracks"]), int(ev["surface_id"].shape[0]),
+                           with_states=with_states)
+    kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(prec, **opt))
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+def compare(g, r, prec, tracks=None):
+    tp, tc, tx = TOL[prec]
+    if tracks is None:
+        tracks = np.arange(g["params"].shape[1])
+    st_g, st_r = g["status"][tracks], r["status"][tracks]
+    assert np.array_equal(st_g, st_r), (np.bincount(st_g), np.bincount(st_r))
+    ok = tracks[st_r == 0]
+    assert np.array_equal(g["ndf"][ok], r["ndf"][ok])
+    pe = param_err(g["params"][:, ok], r["params"][:, ok], r["cov"][:, ok])
+    ce = cov_err(g["cov"][:, ok], r["cov"][:, ok])
+    xe = chi2_err(g["chi2"][ok], r["chi2"][ok])
+    assert pe.max() < tp, ("params", pe.max(), np.unravel_index(pe.argmax(), pe.shape))
+    assert ce.max() < tc, ("cov", ce.max(), np.unravel_index(ce.argmax(), ce.shape))
+    assert xe.max() < tx, ("chi2", xe.max())
+    bad = tracks[st_r != 0]
+    assert np.all(np.isnan(g["params"][:, bad])) and np.all(np.isnan(g["chi2"][bad]))
+    return pe.max(), ce.max()
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_tel10_1k_full(handle, prec):
+    ev = synth.make_event(synth.WORKLOADS["tel10_1k"])
+    compare(gpu_fit(handle, ev, prec), oracle.fit_batch(ev), prec)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_tel30_several_tiles_ragged_tail(handle, prec):
+    # 3001 tracks = 23 full CTAs of 128 plus a ragged tail
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel30_100k"], 3001))
+    compare(gpu_fit(handle, ev, prec), oracle.fit_batch(ev), prec)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_uneven_tracks_with_holes_and_all_states(handle, prec):
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 2000))
+    g = gpu_fit(handle, ev, prec, with_states=True)
+    r = oracle.fit_batch(ev, with_states=True)
+    compare(g, r, prec)
+    # smoothed parameters on every state (uncertainty floor: the state-0 sigma)
+    tp = TOL[prec][0]
+    o = ev["offsets"].astype(np.int64)
+    track_of = np.repeat(np.arange(ev["n_tracks"]), np.diff(o))
+    sd = np.sqrt(np.stack([r["cov"][i * (i + 1) // 2 + i] for i in range(6)]))[:, track_of]
+    err = np.abs(g["states"] - r["states"]) / np.maximum(np.abs(r["states"]), sd)
+    assert err.max() < 10 * tp
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_general_constant_field(handle, prec):
+    w = synth.scaled(synth.WORKLOADS["tel10_1k"], 700)
+    ev = dict(synth.make_event(w))
+    ev["bfield"] = np.array([0.3, -0.2, 2.0])  # the fit's field differs from the simulation's
+    compare(gpu_fit(handle, ev, prec), oracle.fit_batch(ev), prec)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_tilted_planes(handle, prec):
+    ev = dict(synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 500)))
+    rng = np.random.default_rng(11)
+    S = ev["center"].shape[1]
+    rot = ev["rot"].copy()
+    center = ev["center"].copy()
+    for s in range(1, S):
+        a, b, c = rng.normal(size=3) * 0.02
+        Rx = np.array([[1, 0, 0], [0, np.cos(a), -np.sin(a)], [0, np.sin(a), np.cos(a)]])
+        Ry = np.array([[np.cos(b), 0, np.sin(b)], [0, 1, 0], [-np.sin(b), 0, np.cos(b)]])
+        Rz = np.array([[np.cos(c), -np.sin(c), 0], [np.sin(c), np.cos(c), 0], [0, 0, 1]])
+        rot[:, s] = (Rz @ Ry @ Rx @ rot[:, s].reshape(3, 3)).ravel()
+        center[:, s] += rng.normal(size=3) * 0.1
+    ev["rot"], ev["center"] = rot, center
+    compare(gpu_fit(handle, ev, prec), oracle.fit_batch(ev), prec)
+
+
+def _edge_event():
+    """Tracks of 1..11 states, holes first/last/everywhere-but-3, a bad
+    surface id, a non-positive measurement variance."""
+    base = synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 12))
+    lengths = [1, 2, 11, 11, 11, 5, 11, 3, 11, 11, 7, 11]
+    keep = []
+    o = base["offsets"]
+    for t, L in enumerate(lengths):
+        keep.append(np.arange(o[t], o[t] + L))
+    idx = np.concatenate(keep)
+    ev = dict(base)
+    ev["offsets"] = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int32)
+    for k in ("loc", "cov", "truth_states"):
+        ev[k] = np.ascontiguousarray(base[k][:, idx])
+    for k in ("surface_id", "is_hole"):
+        ev[k] = np.ascontiguousarray(base[k][idx]).copy()
+    off = ev["offsets"]
+    ev["is_hole"][off[3] + 1] = 1            # first measurement plane is a hole
+    ev["is_hole"][off[4] + 10] = 1           # last state is a hole
+    ev["is_hole"][off[6] + 1:off[6] + 9] = 1  # only 2 measured planes left
+    ev["surface_id"][off[8] + 4] = 77        # surface that does not exist
+    ev["cov"][0, off[9] + 5] = -1e-4         # non-positive variance -> S not SPD
+    ev["is_hole"][off[1] + 1] = 0
+    return ev
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_edge_cases(handle, prec):
+    ev = _edge_event()
+    g = gpu_fit(handle, ev, prec, with_states=True)
+    r = oracle.fit_batch(ev, with_states=True)
+    assert r["status"][8] == oracle.BAD_INPUT and r["status"][9] == oracle.NON_SPD
+    compare(g, r, prec)
+    assert g["ndf"][0] == 0 and g["chi2"][0] == 0.0  # seed only: x_s = seed
+    assert np.array_equal(g["params"][:, 0], ev["seed_params"][:, 0])
+
+
+def test_empty_batch(handle):
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 3))
+    ev = synth.subset(ev, [])
+    ev["offsets"] = np.zeros(1, dtype=np.int32)
+    dev = kf.event_to_device(ev)
+    dev["max_states"] = 1
+    out = kf.alloc_outputs(0)
+    kf.kf_fit_ex(handle, dev, out)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_chunked_equals_single_launch(handle, prec):
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel30_100k"], 1500))
+    a = gpu_fit(handle, ev, prec)
+    per_track = 31 * (720 if prec == FP64 else 33 * 8 + 57 * 4)
+    b = gpu_fit(handle, ev, prec, workspace_bytes=per_track * 400)  # 4 chunks
+    assert handle.last_launch_count() == 1 + 4
+    for k in ("params", "cov", "chi2", "ndf", "status"):
+        assert np.array_equal(a[k], b[k])
+
+
+def test_fit_host_and_default_entry(handle):
+    import torch
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 300))
+    a = gpu_fit(handle, ev, FP64)
+    hb = kf.kf_fit_host(handle, ev, kf.kf_default_options(FP64))
+    for k in ("params", "cov", "chi2", "ndf", "status"):
+        assert np.array_equal(a[k], hb[k])
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(300)
+    kf.kf_fit(dev, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out["params"].cpu().numpy(), a["params"])
+    assert np.array_equal(out["cov"].cpu().numpy(), a["cov"])
+
+
+def test_invalid_arguments(handle):
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 4))
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(4)
+    with pytest.raises(kf.KfError, match="unsupported"):
+        kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(7))
+    with pytest.raises(kf.KfError, match="invalid"):
+        kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(FP64, h_max=-1.0))
+    bad = dict(out)
+    bad["params"] = None
+    with pytest.raises(kf.KfError, match="invalid"):
+        kf.kf_fit_ex(handle, dev, bad)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_full_size_tel30_100k_sampled(handle, prec):
+    """The benchmark workload at full size, in the benchmark's launch
+    configuration; the oracle checks a random sample of 1500 tracks."""
+    ev = synth.make_event(synth.WORKLOADS["tel30_100k"])
+    g = gpu_fit(handle, ev, prec)
+    rng = np.random.default_rng(5)
+    sample = np.sort(rng.choice(ev["n_tracks"], 1500, replace=False))
+    r = oracle.fit_batch(synth.subset(ev, sample))
+    gs = {k: (v[..., sample] if v is not None else None) for k, v in g.items()}
+    compare(gs, r, prec)
+    assert np.all(g["status"] == 0)

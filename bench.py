@@ -265,13 +265,11 @@ def run_ours(args, rank, world, local):
         return
 
     f64, f32 = roofline.batch_flops(ev["offsets"], ev["is_hole"], prec_id[args.precision])
+    nbytes = roofline.algorithmic_bytes(ev["offsets"], ev["is_hole"])
+    hbm = json.load(open(MEASURED_PEAKS)).get("hbm_gbs", 6780.0) if os.path.exists(MEASURED_PEAKS) else 6780.0
     kern_s = step_ms / 1e3
-    if args.precision == "mixed":
-        achieved = f64 / kern_s / 1e12
-        t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12))
-    else:
-        achieved = f64 / kern_s / 1e12
-        t_roof = f64 / (FP64_PEAK_TFLOPS * 1e12)
+    achieved = f64 / kern_s / 1e12
+    t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12), nbytes / (hbm * 1e9))
     traffic = None
     cpu = None
     if not args.no_cpu:
@@ -298,10 +296,12 @@ def run_ours(args, rank, world, local):
         "ok_tracks": int((st == 0).sum()),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                     "kernel": "kf_fit_kernel", "pipe": "fp64",
+                     "kernel": "kf_fit_mixed_kernel" if args.precision == "mixed" else "kf_fit_kernel",
+                     "pipe": "fp64",
                      "peak_source": "derived: 152 SM x 2 DFMA/clk x 2070 MHz",
                      "t_roof_ms": 1e3 * t_roof, "roof_frac": 1e3 * t_roof / step_ms,
-                     "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32},
+                     "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
+                     "algorithmic_bytes_per_launch": nbytes},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

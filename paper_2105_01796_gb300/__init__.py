@@ -28,7 +28,7 @@ MUON_MASS = 0.1056583755
 # exported symbols of include/kf.h
 EXPORTS = ("kf_default_options", "kf_create", "kf_destroy", "kf_fit", "kf_fit_ex",
            "kf_fit_host", "kf_workspace_size", "kf_last_launch_count", "kf_strerror",
-           "kf_last_cuda_error", "kf_abi_version")
+           "kf_last_cuda_error", "kf_abi_version", "kf_selftest")
 
 
 class KfTracks(ctypes.Structure):
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
         lib.kf_last_cuda_error.restype = ctypes.c_char_p
         lib.kf_abi_version.argtypes = []
         lib.kf_abi_version.restype = ctypes.c_int
+        lib.kf_selftest.argtypes = [ctypes.c_int64, ctypes.c_void_p]
+        lib.kf_selftest.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -239,6 +241,13 @@ def kf_fit_ex(handle: Handle, dev_ev, out, opt: KfOptions | None = None, stream=
                             ctypes.byref(fi), ctypes.byref(opt) if opt is not None else None,
                             ctypes.byref(o), ctypes.c_void_p(int(stream))))
     return out
+
+
+def kf_selftest(n_patterns=1 << 22):
+    """Device self-check of the numeric helpers; returns the 5 mismatch counts."""
+    counts = np.zeros(5, dtype=np.uint64)
+    _check(load().kf_selftest(int(n_patterns), counts.ctypes.data_as(ctypes.c_void_p)))
+    return [int(c) for c in counts]
 
 
 def kf_fit(dev_ev, out):

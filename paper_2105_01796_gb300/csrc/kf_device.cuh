@@ -1,0 +1,167 @@
+// kf_device.cuh -- device helpers shared by the FP64 and mixed fit kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "kf_internal.h"
+
+namespace kfgb {
+namespace dev {
+
+constexpr double kKappa = 2.99792458e-4;   // GeV / (T mm): curvature = kappa B q/p
+constexpr double kInvC = 1.0 / 299.792458;  // ns / mm
+
+enum : int { ST_OK = 0, ST_NO_INTERSECTION = 1, ST_NON_SPD = 2, ST_NONFINITE = 3, ST_BAD_INPUT = 4 };
+
+// packed lower-triangle index
+__host__ __device__ constexpr int sy(int i, int j) { return i * (i + 1) / 2 + j; }
+__host__ __device__ constexpr int sym(int i, int j) { return i >= j ? sy(i, j) : sy(j, i); }
+
+// ---------------------------------------------------------------------------
+// surface table staging: one bulk (TMA) copy global -> shared per CTA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Every thread of the CTA calls this.  Returns false if the bounded wait on
+// the copy's mbarrier gave up (the error flag is then set).
+__device__ __forceinline__ bool stage_surfaces(double* s_surf, const double* g_surf, uint32_t nbytes,
+                                               uint64_t* mbar, int32_t* error_flag) {
+  const uint32_t bar = smem_addr(mbar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nbytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(s_surf)),
+        "l"(g_surf), "r"(nbytes), "r"(bar)
+        : "memory");
+  }
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 20) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(0u)
+        : "memory");
+  }
+  if (!done) {
+    atomicExch(error_flag, 1);
+    return false;
+  }
+  return true;
+}
+
+struct Surf {
+  const double* d;  // points into shared memory
+  __device__ double c(int i) const { return d[i]; }
+  __device__ double R(int i, int j) const { return d[3 + 3 * i + j]; }
+  __device__ double u(int i) const { return R(i, 0); }
+  __device__ double v(int i) const { return R(i, 1); }
+  __device__ double n(int i) const { return R(i, 2); }
+  __device__ double xx0() const { return d[12]; }
+  __device__ double nc() const { return d[13]; }  // n . c
+  __device__ double uc() const { return d[14]; }  // u . c
+  __device__ double vc() const { return d[15]; }  // v . c
+};
+
+// out = v x bs, with bs = (q/p) kappa B: the operator A of dT/ds = A T
+template <typename R, bool BZ>
+__device__ __forceinline__ void applyA(const R bs[3], const R v[3], R out[3]) {
+  if (BZ) {
+    out[0] = v[1] * bs[2];
+    out[1] = -v[0] * bs[2];
+    out[2] = R(0);
+  } else {
+    out[0] = v[1] * bs[2] - v[2] * bs[1];
+    out[1] = v[2] * bs[0] - v[0] * bs[2];
+    out[2] = v[0] * bs[1] - v[1] * bs[0];
+  }
+}
+
+// Highland width for |q| = 1:
+//   theta0 = 13.6 MeV/(beta p) sqrt(eps) (1 + 0.038 ln(eps/beta^2)),
+//   eps = (x/X0)/|cos incidence|, 1/(beta p) = |q/p| sqrt(1 + m^2 (q/p)^2).
+template <typename R>
+__device__ __forceinline__ R highland(R lam_abs, R m2, R xx0, R cos_inc) {
+  const R g2 = R(1) + m2 * lam_abs * lam_abs;  // 1/beta^2
+  const R eps = xx0 / fabs(cos_inc);
+  return R(0.0136) * lam_abs * sqrt(g2) * sqrt(eps) * (R(1) + R(0.038) * log(eps * g2));
+}
+
+// ---------------------------------------------------------------------------
+// float <-> double conversions on the integer pipe.  On this part the
+// hardware F2F conversions issue on the (narrow) FP64 pipe; these use plain
+// 32-bit integer operations instead.
+//   f2d: exact for normal floats and zero; float subnormals become 0;
+//        Inf/NaN preserved.
+//   d2f: round to nearest even; |x| < 2^-126 becomes 0 (no float subnormals);
+//        overflow gives Inf; NaN preserved.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint32_t sign = b & 0x80000000u;
+  const uint32_t m = b & 0x7fffffu;
+  uint32_t hi = sign | (((e + 896u) << 20) + (m >> 3));
+  uint32_t lo = b << 29;
+  if (e == 0u) {
+    hi = sign;
+    lo = 0u;
+  }
+  if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ float d2f(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t ex = (hi >> 20) & 0x7ffu;
+  const int e = (int)ex - 896;
+  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1fffffffu;
+  uint32_t r = ((uint32_t)e << 23) + m;
+  r += (uint32_t)((rem > 0x10000000u) | ((rem == 0x10000000u) & (m & 1u)));
+  if (e <= 0) r = 0u;
+  if (e >= 255) r = 0x7f800000u | ((ex == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
+  return __uint_as_float(sign | r);
+}
+
+// Double-precision 1/sqrt(x) and 1/x for positive normal x within the float
+// range: a float seed refined by Newton-Raphson steps in double,
+//   rsqrt: y <- y + y (1 - x y^2) / 2,   rcp: y <- y + y (1 - x y).
+// One step leaves a relative error below 1e-13 (the seed is accurate to a few
+// float ulps and each step squares the error); two steps reach double
+// rounding level.
+template <int STEPS>
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y = f2d(rsqrtf(d2f(x)));
+#pragma unroll
+  for (int i = 0; i < STEPS; ++i) {
+    const double e = fma(-x * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+
+template <int STEPS>
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y = f2d(__frcp_rn(d2f(x)));
+#pragma unroll
+  for (int i = 0; i < STEPS; ++i) {
+    const double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+  }
+  return y;
+}
+
+__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ULL); }
+
+}  // namespace dev
+}  // namespace kfgb

@@ -8,18 +8,22 @@ namespace kfgb {
 
 // Packed surface record staged into shared memory: 16 doubles (128 B, so the
 // table is a whole number of 16-byte units for the bulk copy):
-//   [0..2] centre, [3..11] R row-major (columns u, v, n), [12] x/X0, [13..15] 0
+//   [0..2] centre c, [3..11] R row-major (columns u, v, n), [12] x/X0,
+//   [13] n.c, [14] u.c, [15] v.c
 constexpr int kSurfStride = 16;
 constexpr int kMaxSurfaces = 1536;  // 192 KiB of shared memory
 
 // Per-state record the forward pass writes and the RTS pass reads back.
 // FP64 path, all in ws64:  xp 6 | xf 6 | Cp 21 | Cf 21 | Bm 36   (90 doubles)
+//   Bm = F_k * Cf_{k-1}: the right-hand side of the smoother-gain solve.
 // Mixed path, ws64:        xp 6 | xf 6 | Cp 21                   (33 doubles)
-//             ws32:        Cf 21 | Bm 36                         (57 floats)
-// Bm = F_k * Cf_{k-1}: the right-hand side of the smoother-gain solve.
+//             ws32:        F 25 | q_phi | q_theta                (27 floats)
+//   F_k: rows loc0, loc1, phi, theta over columns 0..4 (20), then the time
+//   row over columns 0..4 (5); q = the multiple-scattering variances added to
+//   Var(phi) and Var(theta) at state k.
 constexpr int kRec64Fp64 = 90;
 constexpr int kRec64Mixed = 33;
-constexpr int kRec32Mixed = 57;
+constexpr int kRec32Mixed = 27;
 
 struct FitParams {
   int32_t n_tracks;        // tracks in this launch (chunk)
@@ -55,6 +59,10 @@ struct FitParams {
 cudaError_t launch_pack_surfaces(int n_surfaces, const double* center,
                                  const double* rot, const double* x_over_x0,
                                  double* packed, cudaStream_t stream);
+
+// Check the integer-pipe conversions and the Newton 1/sqrt, 1/x helpers on n
+// patterns; counters[0..4] receive the mismatch counts.
+cudaError_t launch_selftest(long long n, unsigned long long* counters, cudaStream_t stream);
 
 // One fused filter + smoother launch over p.n_tracks tracks.
 cudaError_t launch_fit(const FitParams& p, int precision, int block,

@@ -18,89 +18,16 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "kf_device.cuh"
 #include "kf_internal.h"
 
 namespace kfgb {
 namespace {
+using namespace dev;
 
-constexpr double kKappa = 2.99792458e-4;   // GeV / (T mm)
-constexpr double kInvC = 1.0 / 299.792458;  // ns / mm
-
-enum : int { ST_OK = 0, ST_NO_INTERSECTION = 1, ST_NON_SPD = 2, ST_NONFINITE = 3, ST_BAD_INPUT = 4 };
-
-// packed lower-triangle index, i >= j
-__host__ __device__ constexpr int sy(int i, int j) { return i * (i + 1) / 2 + j; }
-__device__ __forceinline__ int sym(int i, int j) { return i >= j ? sy(i, j) : sy(j, i); }
-
+// this file holds the FP64 path; the mixed path is in kf_mixed.cu
 template <int PREC> struct Prec;
 template <> struct Prec<0> { using R = double; };
-template <> struct Prec<1> { using R = float; };
-
-// ---------------------------------------------------------------------------
-// surface table staging: one bulk (TMA) copy global -> shared per CTA
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Every thread of the CTA must call this.  Returns false if the bounded wait
-// on the copy's mbarrier gave up (the error flag is then set).
-__device__ bool stage_surfaces(double* s_surf, const double* g_surf, uint32_t nbytes,
-                               uint64_t* mbar, int32_t* error_flag) {
-  const uint32_t bar = smem_addr(mbar);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nbytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(s_surf)),
-        "l"(g_surf), "r"(nbytes), "r"(bar)
-        : "memory");
-  }
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 20) && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(0u)
-        : "memory");
-  }
-  if (!done) {
-    atomicExch(error_flag, 1);
-    return false;
-  }
-  return true;
-}
-
-struct Surf {
-  const double* d;  // points into shared memory
-  __device__ double c(int i) const { return d[i]; }
-  __device__ double R(int i, int j) const { return d[3 + 3 * i + j]; }
-  __device__ double u(int i) const { return R(i, 0); }
-  __device__ double v(int i) const { return R(i, 1); }
-  __device__ double n(int i) const { return R(i, 2); }
-  __device__ double xx0() const { return d[12]; }
-};
-
-// out = v x bs, where bs = (q/p) * kappa * B; this is the operator A of the
-// equation of motion dT/ds = A T.
-template <typename R, bool BZ>
-__device__ __forceinline__ void applyA(const R bs[3], const R v[3], R out[3]) {
-  if (BZ) {
-    out[0] = v[1] * bs[2];
-    out[1] = -v[0] * bs[2];
-    out[2] = R(0);
-  } else {
-    out[0] = v[1] * bs[2] - v[2] * bs[1];
-    out[1] = v[2] * bs[0] - v[0] * bs[2];
-    out[2] = v[0] * bs[1] - v[1] * bs[0];
-  }
-}
 
 // ---------------------------------------------------------------------------
 // propagation state: free parameters (double accumulators) plus the columns
@@ -312,15 +239,6 @@ __device__ int transport(const Surf& sa, const Surf& sb, const double x[6], cons
   return ST_OK;
 }
 
-// Highland width for |q| = 1: theta0 = 13.6 MeV/(beta p) sqrt(eps)
-// (1 + 0.038 ln(eps/beta^2)), eps = (x/X0)/|cos incidence|.
-template <typename R>
-__device__ __forceinline__ R highland(double lam, double mass, R xx0, R cos_inc) {
-  const R l = (R)fabs(lam);
-  const R g2 = R(1) + (R)(mass * mass) * l * l;  // 1/beta^2
-  const R eps = xx0 / fabs(cos_inc);
-  return R(0.0136) * l * sqrt(g2) * sqrt(eps) * (R(1) + R(0.038) * log(eps * g2));
-}
 
 // ---------------------------------------------------------------------------
 // workspace access: record element e of state k for chunk track i
@@ -343,13 +261,6 @@ template <> struct Rec<0> {
   __device__ static double get_cf(const WS& w, int k, int e) { return w.d(k, CF + e); }
   __device__ static void put_bm(const WS& w, int k, int e, double v) { w.d(k, BM + e) = v; }
   __device__ static double get_bm(const WS& w, int k, int e) { return w.d(k, BM + e); }
-};
-template <> struct Rec<1> {
-  static constexpr int XP = 0, XF = 6, CP = 12, CF = 0, BM = 21;
-  __device__ static void put_cf(const WS& w, int k, int e, float v) { w.f(k, CF + e) = v; }
-  __device__ static float get_cf(const WS& w, int k, int e) { return w.f(k, CF + e); }
-  __device__ static void put_bm(const WS& w, int k, int e, float v) { w.f(k, BM + e) = v; }
-  __device__ static float get_bm(const WS& w, int k, int e) { return w.f(k, BM + e); }
 };
 
 // ---------------------------------------------------------------------------
@@ -494,7 +405,7 @@ __global__ void __launch_bounds__(128) kf_fit_kernel(const FitParams p) {
         // multiple scattering of surface k (added before the update)
         const R xx0 = (R)sb.xx0();
         if (xx0 > R(0)) {
-          const R th0 = highland<R>(x[4], p.mass, xx0, cos_inc);
+          const R th0 = highland<R>((R)fabs(x[4]), (R)(p.mass * p.mass), xx0, cos_inc);
           const R q = th0 * th0;
           Cpr[sy(2, 2)] += q / (sin_th * sin_th);
           Cpr[sy(3, 3)] += q;
@@ -638,7 +549,7 @@ __global__ void __launch_bounds__(128) kf_fit_kernel(const FitParams p) {
     }
   }
   if (status != ST_OK) {
-    const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+    const double nan = qnan();
 #pragma unroll
     for (int e = 0; e < 6; ++e) xs[e] = nan;
 #pragma unroll
@@ -666,7 +577,8 @@ __global__ void pack_surfaces_kernel(int n, const double* __restrict__ center, c
   for (int i = 0; i < 3; ++i) o[i] = center[(size_t)i * n + s];
   for (int i = 0; i < 9; ++i) o[3 + i] = rot[(size_t)i * n + s];
   o[12] = xx0[s];
-  o[13] = o[14] = o[15] = 0.0;
+  // n.c, u.c, v.c (column j of R is o[3 + 3 i + j], i = 0..2)
+  for (int j = 0; j < 3; ++j) o[13 + (j + 1) % 3] = o[3 + j] * o[0] + o[6 + j] * o[1] + o[9 + j] * o[2];
 }
 
 template <int PREC, bool BZ>
@@ -692,12 +604,14 @@ cudaError_t launch_pack_surfaces(int n_surfaces, const double* center, const dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_fit_mixed(const FitParams& p, int block, cudaStream_t stream);
+
 cudaError_t launch_fit(const FitParams& p, int precision, int block, cudaStream_t stream) {
   if (p.n_tracks <= 0) return cudaSuccess;
   if (block <= 0) block = 128;
   const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
   if (precision == 0) return bz ? launch_t<0, true>(p, block, stream) : launch_t<0, false>(p, block, stream);
-  return bz ? launch_t<1, true>(p, block, stream) : launch_t<1, false>(p, block, stream);
+  return launch_fit_mixed(p, block, stream);
 }
 
 }  // namespace kfgb

@@ -1,0 +1,807 @@
+// kf_mixed.cu -- the mixed-precision fit kernel (sm_103a).
+//
+// Same method as the FP64 kernel (paper Sect. 2 filter step list and RTS
+// smoother; Sect. 4.1 RKN transport with local<->global Jacobians; Sect. 4.2
+// double-precision inverter), arranged for a part whose FP64 pipe is a
+// small fraction of its FP32 pipe:
+//   * FP32: RKN stages, the step Jacobians, path correction, the 6x6
+//     transport F C F^T, the Highland noise, the gain K, the smoother gain
+//     algebra and the smoothed covariance.
+//   * FP64: the Joseph covariance update, chi2, the Cholesky factorisation
+//     of the predicted covariance and its solves (the smoother's inverse),
+//     and the accumulators of position, direction, time and the parameter
+//     vector, which receive FP32 increments.
+//   * float<->double conversions run on the integer pipe (dev::f2d/d2f);
+//     FP64 1/sqrt and 1/x come from float seeds refined by a Newton step.
+//   * The direction is carried as FP64 (phi, theta) with their cosines and
+//     sines; propagation and updates change them by small rotations, so no
+//     FP64 trigonometry runs after the seed.
+//
+// Smoother in noise-rank form.  With Cp' = F Cf F^T + Q (Q non-zero only in
+// the (phi, theta) block) the RTS gain A = Cf F^T Cp'^-1 equals
+//   A = F^-1 (I - Q Cp'^-1),
+// and the smoothed covariance Cs = Cf + A (Cs' - Cp') A^T equals
+//   Cs = F^-1 (Q - Q Cp'^-1 Q) F^-T + A Cs' A^T,
+// a sum of two positive semi-definite terms (no cancellation against Cf).
+// Only the (phi, theta) columns of Cp'^-1 are needed: one FP64 Cholesky
+// factorisation and two FP64 triangular-solve pairs per state.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "kf_device.cuh"
+#include "kf_internal.h"
+
+namespace kfgb {
+namespace {
+using namespace dev;
+
+constexpr int XP = 0, XF = 6, CP = 12;  // ws64 record fields
+constexpr int FJ = 0, QPHI = 25, QTH = 26;  // ws32 record fields
+
+struct WSM {
+  double* w64;
+  float* w32;
+  size_t nt;
+  int i;
+  __device__ double& d(int k, int e) const { return w64[((size_t)k * kRec64Mixed + e) * nt + i]; }
+  __device__ float& f(int k, int e) const { return w32[((size_t)k * kRec32Mixed + e) * nt + i]; }
+};
+
+// direction: angles and their cosines / sines, all FP64
+struct Dir {
+  double phi, theta, cp, sp, ct, st;
+};
+
+// FP32 Jacobian columns along the path (G = D J_bf): phi, theta, q/p
+struct Cols {
+  float gr[3][3], gT[3][3], gtl;
+};
+
+struct JacF {
+  float f[4][5];  // rows loc0, loc1, phi, theta over columns loc0..q/p
+  float ft[5];    // time row over columns loc0..q/p
+};
+
+// G advance for one RKN4 step of length h (FP32): direction rows <- Stt g,
+// position rows += Srt g, plus the q/p column's dStt/dlam T, dSrt/dlam T.
+template <bool BZ>
+__device__ __forceinline__ void cols_step(Cols& g, float h, const float bs[3], const float kB[3],
+                                          const float T[3], float dtl) {
+  const float h2 = h * h * 0.5f, h3 = h * h * h * (1.0f / 6.0f), h4 = h * h * h * h * (1.0f / 24.0f);
+  float u0[3], u1[3], u2[3], u3[3];
+  applyA<float, BZ>(kB, T, u0);
+  applyA<float, BZ>(bs, u0, u1);
+  applyA<float, BZ>(bs, u1, u2);
+  applyA<float, BZ>(bs, u2, u3);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float v[3] = {g.gT[0][c], g.gT[1][c], g.gT[2][c]};
+    float b1[3], b2[3], b3[3], b4[3];
+    applyA<float, BZ>(bs, v, b1);
+    applyA<float, BZ>(bs, b1, b2);
+    applyA<float, BZ>(bs, b2, b3);
+    applyA<float, BZ>(bs, b3, b4);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float dr = h * v[i] + h2 * b1[i] + h3 * b2[i] + h4 * b3[i];
+      float nt = v[i] + h * b1[i] + h2 * b2[i] + h3 * b3[i] + h4 * b4[i];
+      if (c == 2) {
+        dr += h2 * u0[i] + h * h * h * (1.0f / 3.0f) * u1[i] + h * h * h * h * 0.125f * u2[i];
+        nt += h * u0[i] + h * h * u1[i] + h * h * h * 0.5f * u2[i] + h * h * h * h * (1.0f / 6.0f) * u3[i];
+      }
+      g.gr[i][c] += dr;
+      g.gT[i][c] = nt;
+    }
+  }
+  g.gtl += h * dtl;
+}
+
+// value increments of one RKN4 step: dr_curv = (Srt - hI) T, dT = (Stt - I) T
+template <bool BZ>
+__device__ __forceinline__ void value_step(float h, const float bs[3], const float T[3], float dr[3],
+                                           float dT[3]) {
+  const float h2 = h * h * 0.5f, h3 = h * h * h * (1.0f / 6.0f), h4 = h * h * h * h * (1.0f / 24.0f);
+  float a1[3], a2[3], a3[3], a4[3];
+  applyA<float, BZ>(bs, T, a1);
+  applyA<float, BZ>(bs, a1, a2);
+  applyA<float, BZ>(bs, a2, a3);
+  applyA<float, BZ>(bs, a3, a4);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    dr[i] = h2 * a1[i] + h3 * a2[i] + h4 * a3[i];
+    dT[i] = h * a1[i] + h2 * a2[i] + h3 * a3[i] + h4 * a4[i];
+  }
+}
+
+// asin(s) - s for |s| <= 0.1 (series to s^9; truncation < 2e-13)
+__device__ __forceinline__ float asin_tail(float s) {
+  const float s2 = s * s;
+  return s * s2 * (1.0f / 6.0f + s2 * (3.0f / 40.0f + s2 * (5.0f / 112.0f + s2 * (35.0f / 1152.0f))));
+}
+
+// new angle = old + asin(sin_delta), the delta being the small rotation from
+// the old to the new direction; a large rotation falls back to atan2.
+__device__ __forceinline__ double angle_step(double old, double sin_delta, float cos_delta, double y, double x) {
+  const float sf = d2f(sin_delta);
+  if (fabsf(sf) <= 0.1f && cos_delta > 0.0f) return (old + sin_delta) + f2d(asin_tail(sf));
+  return atan2(y, x);
+}
+
+// rotate (c, s) of an angle by a small float increment delta
+__device__ __forceinline__ void rotate(double& c, double& s, float delta) {
+  float sh, ch;
+  sincosf(0.5f * delta, &sh, &ch);
+  const float sd = 2.0f * sh * ch, cm1 = -2.0f * sh * sh;
+  const float cf = d2f(c), sf = d2f(s);
+  const float dc = cf * cm1 - sf * sd, ds = sf * cm1 + cf * sd;
+  c += f2d(dc);
+  s += f2d(ds);
+}
+
+// Transport the filtered state (x, d) on surface a to surface b.
+template <bool BZ>
+__device__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6], const Dir& d,
+                               const double B[3], float m2, float h_max, int n_iter, double xp[6], Dir& dp,
+                               JacF& J, float& sin_th, float& cos_inc) {
+  // start point (FP64 accumulators)
+  double r[3], T[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) r[i] = fma(x[1], sa.v(i), fma(x[0], sa.u(i), sa.c(i)));
+  T[0] = d.cp * d.st;
+  T[1] = d.sp * d.st;
+  T[2] = d.ct;
+  double t = x[5];
+  const float lam = d2f(x[4]);
+  const float lk = lam * (float)kKappa;
+  const float bs[3] = {lk * (float)B[0], lk * (float)B[1], lk * (float)B[2]};
+  const float kB[3] = {(float)(kKappa * B[0]), (float)(kKappa * B[1]), (float)(kKappa * B[2])};
+  const float gam = sqrtf(1.0f + m2 * lam * lam);
+  const float dtds = gam * (float)kInvC;
+  const float dtl = m2 * lam * (float)kInvC / gam;  // d(dt/ds)/dlam
+  Cols g;
+  {
+    const float cpf = d2f(d.cp), spf = d2f(d.sp), ctf = d2f(d.ct), stf = d2f(d.st);
+    g.gT[0][0] = -spf * stf; g.gT[1][0] = cpf * stf; g.gT[2][0] = 0.0f;
+    g.gT[0][1] = cpf * ctf;  g.gT[1][1] = spf * ctf; g.gT[2][1] = -stf;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      g.gT[i][2] = 0.0f;
+      g.gr[i][0] = g.gr[i][1] = g.gr[i][2] = 0.0f;
+    }
+    g.gtl = 0.0f;
+  }
+  const float nb[3] = {(float)sb.n(0), (float)sb.n(1), (float)sb.n(2)};
+  // main steps over the straight-line distance
+  float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
+  {
+    const double dist = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
+    const float nT = nb[0] * Tf[0] + nb[1] * Tf[1] + nb[2] * Tf[2];
+    if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
+    const float s0 = d2f(dist) / nT;
+    const float nsub_f = ceilf(fabsf(s0) / h_max);
+    if (!(nsub_f <= 64.0f)) return ST_NO_INTERSECTION;
+    const int nsub = nsub_f < 1.0f ? 1 : (int)nsub_f;
+    const float h = s0 / (float)nsub;
+    const double hd = f2d(h);
+    for (int k = 0; k < nsub; ++k) {
+      if (k > 0) {
+        Tf[0] = d2f(T[0]); Tf[1] = d2f(T[1]); Tf[2] = d2f(T[2]);
+      }
+      cols_step<BZ>(g, h, bs, kB, Tf, dtl);
+      float dr[3], dT[3];
+      value_step<BZ>(h, bs, Tf, dr, dT);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        r[i] = fma(hd, T[i], r[i]) + f2d(dr[i]);
+        T[i] += f2d(dT[i]);
+      }
+      t += f2d(h * dtds);
+    }
+  }
+  // Newton corrections onto the plane, as float offsets from the main end
+  {
+    const double dm = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
+    const float dmf = d2f(dm);
+    const float T0[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
+    float orr[3] = {0.0f, 0.0f, 0.0f}, oT[3] = {0.0f, 0.0f, 0.0f}, ot = 0.0f;
+    for (int it = 0; it < n_iter; ++it) {
+      const float Tc[3] = {T0[0] + oT[0], T0[1] + oT[1], T0[2] + oT[2]};
+      const float dist = dmf - (nb[0] * orr[0] + nb[1] * orr[1] + nb[2] * orr[2]);
+      const float nT = nb[0] * Tc[0] + nb[1] * Tc[1] + nb[2] * Tc[2];
+      if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
+      const float si = dist / nT;
+      cols_step<BZ>(g, si, bs, kB, Tc, dtl);
+      float dr[3], dT[3];
+      value_step<BZ>(si, bs, Tc, dr, dT);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        orr[i] += si * Tc[i] + dr[i];
+        oT[i] += dT[i];
+      }
+      ot += si * dtds;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      r[i] += f2d(orr[i]);
+      T[i] += f2d(oT[i]);
+    }
+    t += f2d(ot);
+  }
+  // end frame: unit direction, angles by small rotations, local position
+  const double rho2 = fma(T[1], T[1], T[0] * T[0]);
+  const double irho = rsqrt_nr<1>(rho2);
+  dp.cp = T[0] * irho;
+  dp.sp = T[1] * irho;
+  const double rho = rho2 * irho;
+  const double inn = rsqrt_nr<1>(fma(T[2], T[2], rho2));
+  dp.st = rho * inn;
+  dp.ct = T[2] * inn;
+  {
+    const double sdp = fma(d.cp, dp.sp, -d.sp * dp.cp);
+    const float cdp = d2f(d.cp) * d2f(dp.cp) + d2f(d.sp) * d2f(dp.sp);
+    double phi = angle_step(d.phi, sdp, cdp, dp.sp, dp.cp);
+    const double pi = 3.141592653589793;
+    if (phi > pi) phi -= 2.0 * pi;
+    if (phi <= -pi) phi += 2.0 * pi;
+    dp.phi = phi;
+    const double sdt = fma(dp.st, d.ct, -dp.ct * d.st);
+    const float cdt = d2f(dp.st) * d2f(d.st) + d2f(dp.ct) * d2f(d.ct);
+    dp.theta = angle_step(d.theta, sdt, cdt, dp.st, dp.ct);
+  }
+  xp[0] = fma(sb.u(2), r[2], fma(sb.u(1), r[1], fma(sb.u(0), r[0], -sb.uc())));
+  xp[1] = fma(sb.v(2), r[2], fma(sb.v(1), r[1], fma(sb.v(0), r[0], -sb.vc())));
+  xp[2] = dp.phi;
+  xp[3] = dp.theta;
+  xp[4] = x[4];
+  xp[5] = t;
+
+  // path correction and free -> bound Jacobian (FP32)
+  const float cph = d2f(dp.cp), sph = d2f(dp.sp), cth = d2f(dp.ct), sth = d2f(dp.st);
+  const float Tu[3] = {cph * sth, sph * sth, cth};
+  const float nT = nb[0] * Tu[0] + nb[1] * Tu[1] + nb[2] * Tu[2];
+  float AT[3];
+  applyA<float, BZ>(bs, Tu, AT);
+  const float inv_nT = 1.0f / nT;
+  float Gr[3][5], GT[3][5], Gt[5];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Gr[i][0] = (float)sa.u(i);
+    Gr[i][1] = (float)sa.v(i);
+    Gr[i][2] = g.gr[i][0];
+    Gr[i][3] = g.gr[i][1];
+    Gr[i][4] = g.gr[i][2];
+    GT[i][0] = 0.0f;
+    GT[i][1] = 0.0f;
+    GT[i][2] = g.gT[i][0];
+    GT[i][3] = g.gT[i][1];
+    GT[i][4] = g.gT[i][2];
+  }
+  Gt[0] = Gt[1] = Gt[2] = Gt[3] = 0.0f;
+  Gt[4] = g.gtl;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const float w = -(nb[0] * Gr[0][c] + nb[1] * Gr[1][c] + nb[2] * Gr[2][c]) * inv_nT;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Gr[i][c] += Tu[i] * w;
+      GT[i][c] += AT[i] * w;
+    }
+    Gt[c] += dtds * w;
+  }
+  const float ub[3] = {(float)sb.u(0), (float)sb.u(1), (float)sb.u(2)};
+  const float vb[3] = {(float)sb.v(0), (float)sb.v(1), (float)sb.v(2)};
+  const float inv_sth = 1.0f / sth;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    J.f[0][c] = ub[0] * Gr[0][c] + ub[1] * Gr[1][c] + ub[2] * Gr[2][c];
+    J.f[1][c] = vb[0] * Gr[0][c] + vb[1] * Gr[1][c] + vb[2] * Gr[2][c];
+    J.f[2][c] = (-sph * GT[0][c] + cph * GT[1][c]) * inv_sth;
+    J.f[3][c] = cph * cth * GT[0][c] + sph * cth * GT[1][c] - sth * GT[2][c];
+    J.ft[c] = Gt[c];
+  }
+  sin_th = sth;
+  cos_inc = nT;
+  return ST_OK;
+}
+
+// 6x6 inverse of the transport Jacobian F in FP32, using its structure
+// (q/p row = e4, time column = e5):  with F11 the loc/angle 4x4 block,
+//   F^-1 = [[F11^-1, -F11^-1 f12, 0], [0, 1, 0], [-ft F11^-1, ft F11^-1 f12 - ft4, 1]].
+// F11^-1 by 2x2 blocks (the loc-loc and angle-angle blocks are near identity):
+//   F11 = [[P, Qb], [Rb, S]], Z = (S - Rb P^-1 Qb)^-1,
+//   F11^-1 = [[P^-1 + P^-1 Qb Z Rb P^-1, -P^-1 Qb Z], [-Z Rb P^-1, Z]].
+__device__ __forceinline__ void inv2(const float a[2][2], float o[2][2]) {
+  const float id = 1.0f / (a[0][0] * a[1][1] - a[0][1] * a[1][0]);
+  o[0][0] = a[1][1] * id;
+  o[0][1] = -a[0][1] * id;
+  o[1][0] = -a[1][0] * id;
+  o[1][1] = a[0][0] * id;
+}
+
+__device__ __forceinline__ void mul2(const float a[2][2], const float b[2][2], float o[2][2]) {
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) o[i][j] = a[i][0] * b[0][j] + a[i][1] * b[1][j];
+}
+
+__device__ void invert_F(const float F[25], float Fi[6][6]) {
+  float P[2][2], Qb[2][2], Rb[2][2], S[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      P[i][j] = F[i * 5 + j];
+      Qb[i][j] = F[i * 5 + 2 + j];
+      Rb[i][j] = F[(2 + i) * 5 + j];
+      S[i][j] = F[(2 + i) * 5 + 2 + j];
+    }
+  float Pi[2][2], PiQ[2][2], RPi[2][2], Sc[2][2], Z[2][2], t1[2][2], t2[2][2];
+  inv2(P, Pi);
+  mul2(Pi, Qb, PiQ);
+  mul2(Rb, Pi, RPi);
+  mul2(Rb, PiQ, t1);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) Sc[i][j] = S[i][j] - t1[i][j];
+  inv2(Sc, Z);
+  float M[4][4];
+  mul2(PiQ, Z, t1);  // P^-1 Qb Z
+  mul2(t1, RPi, t2);  // P^-1 Qb Z Rb P^-1
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      M[i][j] = Pi[i][j] + t2[i][j];
+      M[i][2 + j] = -t1[i][j];
+      M[2 + i][2 + j] = Z[i][j];
+    }
+  mul2(Z, RPi, t2);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) M[2 + i][j] = -t2[i][j];
+  // assemble
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float mf = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      Fi[i][j] = M[i][j];
+      mf += M[i][j] * F[j * 5 + 4];
+    }
+    Fi[i][4] = -mf;
+    Fi[i][5] = 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < 6; ++j) Fi[4][j] = (j == 4) ? 1.0f : 0.0f;
+  float tf = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float v = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v += F[20 + q] * M[q][j];
+    Fi[5][j] = -v;
+    tf += v * F[j * 5 + 4];
+  }
+  Fi[5][4] = tf - F[24];
+  Fi[5][5] = 1.0f;
+}
+
+template <bool BZ>
+__global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* s_surf = reinterpret_cast<double*>(smem_raw);
+  __shared__ __align__(8) uint64_t s_mbar;
+  const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
+                                     p.error_flag);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!staged || i >= p.n_tracks) return;
+  const int t = p.track0 + i;
+  const size_t TT = (size_t)p.n_tracks_total;
+  const WSM ws{p.ws64, p.ws32, (size_t)p.n_tracks, i};
+  const int64_t o0 = p.offsets[t], o1 = p.offsets[t + 1];
+  const int n = (int)(o1 - o0);
+  int status = ST_OK;
+  if (!(o1 > o0) || o0 < 0 || o1 > p.n_states || n > p.max_states) status = ST_BAD_INPUT;
+  if (status == ST_OK)
+    for (int k = 0; k < n; ++k) {
+      const int sid = p.surface_id[o0 + k];
+      if (sid < 0 || sid >= p.n_surfaces) status = ST_BAD_INPUT;
+    }
+  const float m2 = (float)(p.mass * p.mass);
+  const float h_max = (float)p.h_max;
+
+  double xs[6];
+  double Cs_out[21];
+  double chi2sum = 0.0;
+  int nmeas = 0;
+  if (status == ST_OK) {
+    // ------------------------------------------------ forward filter
+    double x[6], C[21];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TT + t];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) C[e] = p.seed_cov[e * TT + t];
+    Dir d;
+    d.phi = x[2];
+    d.theta = x[3];
+    sincos(x[2], &d.sp, &d.cp);  // the only FP64 trigonometry of the track
+    sincos(x[3], &d.st, &d.ct);
+    int sid_prev = p.surface_id[o0];
+    for (int k = 0; k < n && status == ST_OK; ++k) {
+      const int sid = p.surface_id[o0 + k];
+      double xp[6], Cp[21];
+      float Cpf[21];
+      Dir dp;
+      if (k == 0) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) xp[e] = x[e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) {
+          Cp[e] = C[e];
+          Cpf[e] = d2f(C[e]);
+        }
+        dp = d;
+      } else {
+        const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
+        JacF J;
+        float sin_th, cos_inc;
+        status = transport_mixed<BZ>(sa, sb, x, d, p.bfield, m2, h_max, p.n_iter, xp, dp, J, sin_th, cos_inc);
+        if (status != ST_OK) break;
+        float Cr[21];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cr[e] = d2f(C[e]);
+        // Cp = F Cf F^T, rows of Bm = F Cf formed on the fly
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          float brow[6];
+#pragma unroll
+          for (int j = 0; j < 6; ++j) {
+            float v;
+            if (r == 4) {
+              v = Cr[sym(4, j)];
+            } else {
+              const float* fr = (r == 5) ? J.ft : J.f[r];
+              v = fr[0] * Cr[sym(0, j)] + fr[1] * Cr[sym(1, j)] + fr[2] * Cr[sym(2, j)] + fr[3] * Cr[sym(3, j)] +
+                  fr[4] * Cr[sym(4, j)];
+              if (r == 5) v += Cr[sym(5, j)];
+            }
+            brow[j] = v;
+          }
+#pragma unroll
+          for (int c = 0; c <= r; ++c) {
+            float v;
+            if (c == 4) {
+              v = brow[4];
+            } else {
+              const float* fc = (c == 5) ? J.ft : J.f[c];
+              v = brow[0] * fc[0] + brow[1] * fc[1] + brow[2] * fc[2] + brow[3] * fc[3] + brow[4] * fc[4];
+              if (c == 5) v += brow[5];
+            }
+            Cpf[sy(r, c)] = v;
+          }
+        }
+        // multiple scattering of surface k, added before the update
+        float qphi = 0.0f, qth = 0.0f;
+        const float xx0 = (float)sb.xx0();
+        if (xx0 > 0.0f) {
+          const float th0 = highland<float>(fabsf(d2f(x[4])), m2, xx0, cos_inc);
+          qth = th0 * th0;
+          qphi = qth / (sin_th * sin_th);
+          Cpf[sy(2, 2)] += qphi;
+          Cpf[sy(3, 3)] += qth;
+        }
+#pragma unroll
+        for (int e = 0; e < 20; ++e) ws.f(k, FJ + e) = J.f[e / 5][e % 5];
+#pragma unroll
+        for (int e = 0; e < 5; ++e) ws.f(k, FJ + 20 + e) = J.ft[e];
+        ws.f(k, QPHI) = qphi;
+        ws.f(k, QTH) = qth;
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cp[e] = f2d(Cpf[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ws.d(k, XP + e) = xp[e];
+#pragma unroll
+      for (int e = 0; e < 21; ++e) ws.d(k, CP + e) = Cp[e];
+      if (!p.is_hole[o0 + k]) {
+        // gain-matrix update: gain in FP32, Joseph covariance and chi2 in FP64
+        const double m0 = p.loc[o0 + k], m1 = p.loc[p.n_states + o0 + k];
+        const double V0 = p.cov[o0 + k], V1 = p.cov[p.n_states + o0 + k], V2 = p.cov[2 * p.n_states + o0 + k];
+        const double S00 = V0 + Cp[sy(0, 0)], S01 = V1 + Cp[sy(1, 0)], S11 = V2 + Cp[sy(1, 1)];
+        const double det = fma(S00, S11, -S01 * S01);
+        if (!(det > 0.0) || !(S00 > 0.0)) {
+          status = ST_NON_SPD;
+          break;
+        }
+        const double idet = rcp_nr<1>(det);
+        const double r0 = m0 - xp[0], r1 = m1 - xp[1];
+        const double u = fma(S11, r0, -S01 * r1), v = fma(S00, r1, -S01 * r0);
+        chi2sum += fma(r0, u, r1 * v) * idet;
+        ++nmeas;
+        const float idf = d2f(idet);
+        const float i00 = d2f(S11) * idf, i01 = -d2f(S01) * idf, i11 = d2f(S00) * idf;
+        const float r0f = d2f(r0), r1f = d2f(r1);
+        double K[6][2];
+        float dx[6];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+          const float c0 = Cpf[sym(e, 0)], c1 = Cpf[sym(e, 1)];
+          const float k0 = c0 * i00 + c1 * i01, k1 = c0 * i01 + c1 * i11;
+          K[e][0] = f2d(k0);
+          K[e][1] = f2d(k1);
+          dx[e] = k0 * r0f + k1 * r1f;
+          x[e] = xp[e] + f2d(dx[e]);
+        }
+        // Joseph form, expanded: Cf = Cp + K W - (H Cp)^T K^T, W = S K^T - H Cp
+        double W[2][6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          W[0][j] = fma(S00, K[j][0], fma(S01, K[j][1], -Cp[sym(0, j)]));
+          W[1][j] = fma(S01, K[j][0], fma(S11, K[j][1], -Cp[sym(1, j)]));
+        }
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+          for (int b = 0; b <= a; ++b) {
+            double v = Cp[sy(a, b)];
+            v = fma(K[a][0], W[0][b], v);
+            v = fma(K[a][1], W[1][b], v);
+            v = fma(-Cp[sym(0, a)], K[b][0], v);
+            v = fma(-Cp[sym(1, a)], K[b][1], v);
+            C[sy(a, b)] = v;
+          }
+        d = dp;
+        d.phi = x[2];
+        d.theta = x[3];
+        rotate(d.cp, d.sp, dx[2]);
+        rotate(d.ct, d.st, dx[3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) x[e] = xp[e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) C[e] = Cp[e];
+        d = dp;
+      }
+#pragma unroll
+      for (int e = 0; e < 6; ++e) ws.d(k, XF + e) = x[e];
+      sid_prev = sid;
+    }
+
+    // ------------------------------------------------ RTS smoother
+    if (status == ST_OK) {
+      float Cs[21];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) xs[e] = x[e];
+#pragma unroll
+      for (int e = 0; e < 21; ++e) Cs[e] = d2f(C[e]);
+      if (p.out_states)
+#pragma unroll
+        for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + n - 1] = xs[e];
+      for (int k = n - 2; k >= 0 && status == ST_OK; --k) {
+        // FP64 Cholesky of Cp_{k+1} and the (phi, theta) columns of its inverse
+        double L[21], idg[6];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) L[e] = ws.d(k + 1, CP + e);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+          double dj = L[sy(j, j)];
+#pragma unroll
+          for (int q = 0; q < j; ++q) dj = fma(-L[sy(j, q)], L[sy(j, q)], dj);
+          if (!(dj > 0.0)) {
+            status = ST_NON_SPD;
+            dj = 1.0;
+          }
+          idg[j] = rsqrt_nr<1>(dj);
+#pragma unroll
+          for (int r = j + 1; r < 6; ++r) {
+            double v = L[sy(r, j)];
+#pragma unroll
+            for (int q = 0; q < j; ++q) v = fma(-L[sy(r, q)], L[sy(j, q)], v);
+            L[sy(r, j)] = v * idg[j];
+          }
+        }
+        if (status != ST_OK) break;
+        double w[2][6];
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int c = 2 + cc;
+          double y[6];
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            if (r < c) {
+              y[r] = 0.0;
+            } else {
+              double v = (r == c) ? 1.0 : 0.0;
+#pragma unroll
+              for (int q = c; q < r; ++q) v = fma(-L[sy(r, q)], y[q], v);
+              y[r] = v * idg[r];
+            }
+          }
+#pragma unroll
+          for (int r = 5; r >= 0; --r) {
+            double v = y[r];
+#pragma unroll
+            for (int q = r + 1; q < 6; ++q) v = fma(-L[sy(q, r)], w[cc][q], v);
+            w[cc][r] = v * idg[r];
+          }
+        }
+        // noise-rank pieces: Q Cp^-1 rows (phi, theta) and N = Q - Q Cp^-1 Q
+        const float qp = ws.f(k + 1, QPHI), qt = ws.f(k + 1, QTH);
+        const double qpd = f2d(qp), qtd = f2d(qt);
+        float qw[2][6];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+          qw[0][e] = qp * d2f(w[0][e]);
+          qw[1][e] = qt * d2f(w[1][e]);
+        }
+        const float Npp = d2f(qpd * fma(-qpd, w[0][2], 1.0));
+        const float Ntt = d2f(qtd * fma(-qtd, w[1][3], 1.0));
+        const float Npt = d2f(-qpd * qtd * w[1][2]);
+        // F^-1 and the gain A = F^-1 - F^-1[:,phi] qw_phi^T - F^-1[:,theta] qw_theta^T
+        float Fr[25];
+#pragma unroll
+        for (int e = 0; e < 25; ++e) Fr[e] = ws.f(k + 1, FJ + e);
+        float Fi[6][6];
+        invert_F(Fr, Fi);
+        float A[6][6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int c = 0; c < 6; ++c) A[r][c] = Fi[r][c] - Fi[r][2] * qw[0][c] - Fi[r][3] * qw[1][c];
+        // xs_k = xf_k + A (xs_{k+1} - xp_{k+1})
+        float df[6];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) df[e] = d2f(xs[e] - ws.d(k + 1, XP + e));
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) acc += A[r][c] * df[c];
+          xs[r] = ws.d(k, XF + r) + f2d(acc);
+        }
+        // Cs_k = F^-1 N F^-T (N on the (phi, theta) block) + A Cs_{k+1} A^T
+        float Cn[21];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          float z[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc += A[r][q] * Cs[sym(q, c)];
+            z[c] = acc;
+          }
+          const float a2 = Fi[r][2] * Npp + Fi[r][3] * Npt, a3 = Fi[r][2] * Npt + Fi[r][3] * Ntt;
+#pragma unroll
+          for (int c = 0; c <= r; ++c) {
+            float acc = a2 * Fi[c][2] + a3 * Fi[c][3];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc += z[q] * A[c][q];
+            Cn[sy(r, c)] = acc;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cs[e] = Cn[e];
+        if (p.out_states)
+#pragma unroll
+          for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + k] = xs[e];
+      }
+      if (n == 1) {
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cs_out[e] = C[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cs_out[e] = f2d(Cs[e]);
+      }
+    }
+    if (status == ST_OK) {
+      bool fin = isfinite(chi2sum);
+#pragma unroll
+      for (int e = 0; e < 6; ++e) fin = fin && isfinite(xs[e]);
+#pragma unroll
+      for (int e = 0; e < 21; ++e) fin = fin && isfinite(Cs_out[e]);
+      if (!fin) status = ST_NONFINITE;
+    }
+  }
+  if (status != ST_OK) {
+    const double nan = qnan();
+#pragma unroll
+    for (int e = 0; e < 6; ++e) xs[e] = nan;
+#pragma unroll
+    for (int e = 0; e < 21; ++e) Cs_out[e] = nan;
+    chi2sum = nan;
+    nmeas = 0;
+    if (p.out_states && n >= 1 && o0 >= 0 && o1 <= p.n_states && n <= p.max_states)
+      for (int k = 0; k < n; ++k)
+        for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + k] = nan;
+  }
+#pragma unroll
+  for (int e = 0; e < 6; ++e) p.out_params[e * TT + t] = xs[e];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) p.out_cov[e * TT + t] = Cs_out[e];
+  p.out_chi2[t] = chi2sum;
+  if (p.out_ndf) p.out_ndf[t] = 2 * nmeas;
+  if (p.out_status) p.out_status[t] = (uint8_t)status;
+}
+
+template <bool BZ>
+cudaError_t launch_m(const FitParams& p, int block, cudaStream_t stream) {
+  const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);
+  auto kern = kf_fit_mixed_kernel<BZ>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = (p.n_tracks + block - 1) / block;
+  kern<<<grid, block, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fit_mixed(const FitParams& p, int block, cudaStream_t stream) {
+  const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
+  return bz ? launch_m<true>(p, block, stream) : launch_m<false>(p, block, stream);
+}
+
+}  // namespace kfgb
+
+// ---------------------------------------------------------------------------
+// self-check of the numeric helpers against the hardware conversions and
+// CUDA's double-precision sqrt / division (no fit involved)
+// ---------------------------------------------------------------------------
+namespace kfgb {
+namespace {
+using namespace dev;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// counters: [0] f2d mismatches, [1] d2f mismatches, [2] rsqrt_nr<1> beyond
+// 1e-13 relative, [3] rcp_nr<1> beyond 1e-13, [4] rsqrt_nr<2>/rcp_nr<2> beyond
+// 4 ulp (2^-50 relative)
+__global__ void selftest_kernel(long long n, unsigned long long* counters) {
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long c[5] = {0, 0, 0, 0, 0};
+  for (long long i = i0; i < n; i += stride) {
+    const uint64_t z = mix64((uint64_t)i);
+    // f2d over random float bit patterns (subnormals excluded by design)
+    const float f = __uint_as_float((uint32_t)z);
+    const uint32_t fe = ((uint32_t)z >> 23) & 0xffu;
+    if (fe != 0u) {
+      const double a = f2d(f), b = (double)f;
+      if (__double_as_longlong(a) != __double_as_longlong(b) && !(a != a && b != b)) ++c[0];
+    }
+    // d2f over doubles in and around the float range
+    const double x = __longlong_as_double((long long)((z & 0x800fffffffffffffULL) |
+                                                      ((uint64_t)(896 - 8 + (int)((z >> 52) % 272)) << 52)));
+    const float g1 = d2f(x);
+    const float g2 = __double2float_rn(x);
+    const bool sub = fabs(x) < 1.1754943508222875e-38;  // float subnormal range flushes to 0
+    if (!sub && __float_as_uint(g1) != __float_as_uint(g2)) ++c[1];
+    // Newton helpers on positive values across 1e-30 .. 1e30
+    const double y = exp2((double)((int)(z % 180) - 90)) * (1.0 + (double)((z >> 20) & 0xfffff) / 1048576.0);
+    const double rs_ref = 1.0 / sqrt(y), rc_ref = 1.0 / y;
+    if (fabs(rsqrt_nr<1>(y) - rs_ref) > 1e-13 * rs_ref) ++c[2];
+    if (fabs(rcp_nr<1>(y) - rc_ref) > 1e-13 * rc_ref) ++c[3];
+    if (fabs(rsqrt_nr<2>(y) - rs_ref) > 8.9e-16 * rs_ref || fabs(rcp_nr<2>(y) - rc_ref) > 8.9e-16 * rc_ref) ++c[4];
+  }
+  for (int k = 0; k < 5; ++k)
+    if (c[k]) atomicAdd(&counters[k], c[k]);
+}
+}  // namespace
+
+cudaError_t launch_selftest(long long n, unsigned long long* counters, cudaStream_t stream) {
+  selftest_kernel<<<152 * 4, 256, 0, stream>>>(n, counters);
+  return cudaGetLastError();
+}
+}  // namespace kfgb

@@ -70,7 +70,9 @@ typedef enum {
   KF_ECUDA = -2,        /* a CUDA call failed; kf_last_cuda_error() has it */
   KF_ENOMEM = -3,       /* device or pinned allocation failed */
   KF_EUNSUPPORTED = -4, /* option outside what this build supports */
-  KF_EDEVICE = -5       /* a kernel reported an internal wait timeout */
+  KF_EDEVICE = -5,      /* a kernel reported an internal wait timeout */
+  KF_ESIZE = -6         /* kf_fit_static: the batch does not fit its fixed
+                           device block */
 } kf_error;
 
 typedef enum {
@@ -167,6 +169,25 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
                 const kf_surfaces* surfaces, const kf_measurements* meas,
                 const kf_field* field, const kf_options* opt,
                 const kf_outputs* out, void* stream);
+
+/* kf_fit_ex without any device allocation, for callers that cannot allocate:
+ * code running inside a CUDA stream capture, real-time loops that must not
+ * wait on the allocator, hosts with a fixed memory budget.  (The paper has no
+ * counterpart; it is an addition of this library.)
+ * Scratch space is one fixed 64 MiB block of device memory per GPU, reserved
+ * for the whole life of the process once the library is loaded.  It holds
+ * the packed surface table (up to 1536 surfaces) and the per-state records;
+ * larger batches run as several launches on `stream`.  Returns KF_ESIZE when
+ * n_surfaces > 1536 or when one track's records (max_states x 720 B in FP64,
+ * max_states x 372 B in mixed precision) do not fit the block.  Device
+ * pointers, asynchronous on `stream`, same outputs as kf_fit_ex.
+ * The first call on a device looks up the block's device address; make it
+ * before capturing a stream.  Every call reuses the same block, which keeps
+ * the previous call's contents: calls whose GPU work overlaps (other streams
+ * or host threads) race on it and must be serialised by the caller. */
+int kf_fit_static(const kf_tracks* tracks, const kf_surfaces* surfaces,
+                  const kf_measurements* meas, const kf_field* field,
+                  const kf_options* opt, const kf_outputs* out, void* stream);
 
 /* Bytes of device workspace kf_fit_ex would use for this batch shape. */
 int64_t kf_workspace_size(int32_t n_tracks, int32_t max_states,

@@ -28,7 +28,7 @@ MUON_MASS = 0.1056583755
 # exported symbols of include/kf.h
 EXPORTS = ("kf_default_options", "kf_create", "kf_destroy", "kf_fit", "kf_fit_ex",
            "kf_fit_host", "kf_workspace_size", "kf_last_launch_count", "kf_strerror",
-           "kf_last_cuda_error", "kf_abi_version", "kf_selftest")
+           "kf_last_cuda_error", "kf_abi_version", "kf_selftest", "kf_fit_static")
 
 
 class KfTracks(ctypes.Structure):
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH):
         lib.kf_last_cuda_error.restype = ctypes.c_char_p
         lib.kf_abi_version.argtypes = []
         lib.kf_abi_version.restype = ctypes.c_int
+        lib.kf_fit_static.argtypes = base + [ctypes.POINTER(KfOptions), ctypes.POINTER(KfOutputs), P]
+        lib.kf_fit_static.restype = ctypes.c_int
         lib.kf_selftest.argtypes = [ctypes.c_int64, ctypes.c_void_p]
         lib.kf_selftest.restype = ctypes.c_int
         _lib = lib
@@ -248,6 +250,25 @@ def kf_selftest(n_patterns=1 << 22):
     counts = np.zeros(5, dtype=np.uint64)
     _check(load().kf_selftest(int(n_patterns), counts.ctypes.data_as(ctypes.c_void_p)))
     return [int(c) for c in counts]
+
+
+def kf_fit_static(dev_ev, out, opt: KfOptions | None = None, stream=None):
+    """Fit without any device allocation: scratch lives in the library's fixed
+    per-GPU block (for callers that cannot allocate, e.g. inside a stream
+    capture).  Same inputs, outputs and results as :func:`kf_fit_ex`; calls
+    that overlap on the GPU share the block and must be serialised."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    tr, su, me, fi = _structs(dev_ev, dev_ev["max_states"])
+    o = KfOutputs(_ptr(out["params"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out.get("ndf")),
+                  _ptr(out.get("status")), _ptr(out.get("states")))
+    _check(load().kf_fit_static(ctypes.byref(tr), ctypes.byref(su), ctypes.byref(me), ctypes.byref(fi),
+                                ctypes.byref(opt) if opt is not None else None, ctypes.byref(o),
+                                ctypes.c_void_p(int(stream))))
+    return out
 
 
 def kf_fit(dev_ev, out):

@@ -134,6 +134,7 @@ const char* kf_strerror(int code) {
     case KF_ENOMEM: return "out of memory";
     case KF_EUNSUPPORTED: return "unsupported option";
     case KF_EDEVICE: return "device-side wait timed out";
+    case KF_ESIZE: return "batch does not fit the fixed device block of kf_fit_static";
     default: return "unknown error";
   }
 }

@@ -131,14 +131,29 @@ typedef struct {
   double mass;                 /* particle mass in GeV (default: muon) */
   double h_max;                /* longest RKN step in mm (default 50) */
   int32_t n_iter;              /* Newton corrections onto each plane (default 3) */
-  int32_t block;               /* threads per CTA (0 = default 128) */
+  int32_t block;               /* threads per CTA: 32, 64, 96 or 128 (0 = 128) */
   int64_t workspace_bytes;     /* cap on the handle's workspace (0 = 4 GiB);
                                   larger batches are fitted in chunks */
+  int32_t schedule;            /* kf_schedule (default KF_SCHEDULE_PERSISTENT) */
+  int32_t min_blocks;          /* register-cap variant: minimum resident CTAs
+                                  per SM the kernel is compiled for (0 = the
+                                  default variant; 3 and 4 cap registers) */
 } kf_options;
+
+typedef enum {
+  KF_SCHEDULE_GRID = 0,        /* one thread per track, one CTA per block of
+                                  tracks */
+  KF_SCHEDULE_PERSISTENT = 1,  /* resident CTAs; each warp takes 32-track
+                                  units from a work counter until done */
+  KF_SCHEDULE_SORTED = 2       /* persistent, tracks taken longest first
+                                  (counting sort by state count; for uneven
+                                  tracks) */
+} kf_schedule;
 
 typedef struct kf_handle kf_handle;
 
-/* Fill *opt with the defaults: FP64, muon mass, h_max 50 mm, 3 corrections. */
+/* Fill *opt with the defaults: FP64, muon mass, h_max 50 mm, 3 corrections,
+ * 128 threads per CTA, persistent schedule, default register variant. */
 void kf_default_options(kf_options* opt);
 
 /* Create a handle bound to the current CUDA device.  Returns 0 or kf_error. */
@@ -176,9 +191,9 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
  * counterpart; it is an addition of this library.)
  * Scratch space is one fixed 64 MiB block of device memory per GPU, reserved
  * for the whole life of the process once the library is loaded.  It holds
- * the packed surface table (up to 1536 surfaces) and the per-state records;
+ * the packed surface table (up to 1024 surfaces) and the per-state records;
  * larger batches run as several launches on `stream`.  Returns KF_ESIZE when
- * n_surfaces > 1536 or when one track's records (max_states x 720 B in FP64,
+ * n_surfaces > 1024 or when one track's records (max_states x 720 B in FP64,
  * max_states x 372 B in mixed precision) do not fit the block.  Device
  * pointers, asynchronous on `stream`, same outputs as kf_fit_ex.
  * The first call on a device looks up the block's device address; make it

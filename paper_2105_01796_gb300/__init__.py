@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libkfgb.so")
 
 KF_PRECISION_FP64 = 0
 KF_PRECISION_MIXED = 1
+KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED = 0, 1, 2
 TRACK_STATUS = {0: "ok", 1: "no_intersection", 2: "non_spd", 3: "nonfinite", 4: "bad_input"}
 MUON_MASS = 0.1056583755
 
@@ -61,7 +62,8 @@ class KfOutputs(ctypes.Structure):
 class KfOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mass", ctypes.c_double),
                 ("h_max", ctypes.c_double), ("n_iter", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64)]
+                ("block", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
+                ("schedule", ctypes.c_int32), ("min_blocks", ctypes.c_int32)]
 
 
 _lib = None

@@ -20,6 +20,13 @@ struct kf_handle {
   double* surf = nullptr;
   int surf_cap = 0;
   int32_t* error_flag = nullptr;
+  // work counters (one per chunk launch) and the length-sort buffers
+  int32_t* counters = nullptr;
+  int counters_cap = 0;
+  int32_t* order = nullptr;
+  int64_t order_cap = 0;
+  int32_t* hist = nullptr;
+  int hist_cap = 0;
   // device copies for kf_fit_host
   void* dev_io = nullptr;
   size_t dev_io_bytes = 0;
@@ -91,6 +98,8 @@ int validate(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* 
   if (opt->precision != KF_PRECISION_FP64 && opt->precision != KF_PRECISION_MIXED) return KF_EUNSUPPORTED;
   if (!(opt->mass >= 0.0) || !(opt->h_max > 0.0) || opt->n_iter < 0 || opt->n_iter > 16) return KF_EINVAL;
   if (opt->block < 0 || opt->block > 128 || (opt->block % 32) != 0) return KF_EUNSUPPORTED;
+  if (opt->schedule < KF_SCHEDULE_GRID || opt->schedule > KF_SCHEDULE_SORTED) return KF_EUNSUPPORTED;
+  if (opt->min_blocks < 0 || opt->min_blocks > 4) return KF_EUNSUPPORTED;
   for (int i = 0; i < 3; ++i)
     if (!(fi->b[i] == fi->b[i])) return KF_EINVAL;
   return KF_SUCCESS;
@@ -109,6 +118,8 @@ void kf_default_options(kf_options* opt) {
   opt->n_iter = 3;
   opt->block = 128;
   opt->workspace_bytes = 0;
+  opt->schedule = KF_SCHEDULE_PERSISTENT;
+  opt->min_blocks = 0;
 }
 
 int kf_abi_version(void) { return KF_ABI_VERSION; }
@@ -172,6 +183,9 @@ void kf_destroy(kf_handle* h) {
   if (h->surf) cudaFree(h->surf);
   if (h->error_flag) cudaFree(h->error_flag);
   if (h->dev_io) cudaFree(h->dev_io);
+  if (h->counters) cudaFree(h->counters);
+  if (h->order) cudaFree(h->order);
+  if (h->hist) cudaFree(h->hist);
   delete h;
 }
 
@@ -202,9 +216,45 @@ int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf
       opt.precision == KF_PRECISION_FP64 ? 0 : align_up(kRec32Mixed * sizeof(float) * tr->max_states * chunk, 256);
   if ((rc = ensure_ws(h, bytes64 + bytes32))) return rc;
   if ((rc = ensure_surf(h, su->n_surfaces))) return rc;
+  const int n_chunks = (int)((tr->n_tracks + chunk - 1) / chunk);
+  if (opt.schedule != KF_SCHEDULE_GRID && h->counters_cap < n_chunks) {
+    if (h->counters) cudaFree(h->counters);
+    h->counters = nullptr;
+    h->counters_cap = 0;
+    cudaError_t e = cudaMalloc(&h->counters, sizeof(int32_t) * n_chunks);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(counters)");
+    h->counters_cap = n_chunks;
+  }
+  if (opt.schedule == KF_SCHEDULE_SORTED) {
+    if (h->order_cap < tr->n_tracks) {
+      if (h->order) cudaFree(h->order);
+      h->order = nullptr;
+      h->order_cap = 0;
+      cudaError_t e = cudaMalloc(&h->order, sizeof(int32_t) * (size_t)tr->n_tracks);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(order)");
+      h->order_cap = tr->n_tracks;
+    }
+    if (h->hist_cap < tr->max_states + 2) {
+      if (h->hist) cudaFree(h->hist);
+      h->hist = nullptr;
+      h->hist_cap = 0;
+      cudaError_t e = cudaMalloc(&h->hist, sizeof(int32_t) * (size_t)(tr->max_states + 2));
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(hist)");
+      h->hist_cap = tr->max_states + 2;
+    }
+  }
   cudaError_t e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
   if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
   int launches = 1;
+  if (opt.schedule != KF_SCHEDULE_GRID) {
+    e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * n_chunks, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+  }
+  if (opt.schedule == KF_SCHEDULE_SORTED) {
+    e = launch_length_order(tr->n_tracks, tr->max_states, tr->offsets, h->hist, h->order, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "length order launch");
+    launches += 3;
+  }
   FitParams p;
   memset(&p, 0, sizeof(p));
   p.n_tracks_total = tr->n_tracks;
@@ -232,10 +282,13 @@ int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf
   p.ws64 = (double*)h->ws;
   p.ws32 = opt.precision == KF_PRECISION_FP64 ? nullptr : (float*)((char*)h->ws + bytes64);
   p.error_flag = h->error_flag;
-  for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk) {
+  p.order = opt.schedule == KF_SCHEDULE_SORTED ? h->order : nullptr;
+  int c = 0;
+  for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk, ++c) {
     p.track0 = (int32_t)t0;
     p.n_tracks = (int32_t)((tr->n_tracks - t0) < chunk ? (tr->n_tracks - t0) : chunk);
-    e = launch_fit(p, opt.precision, opt.block, stream);
+    p.work_counter = opt.schedule == KF_SCHEDULE_GRID ? nullptr : h->counters + c;
+    e = launch_fit(p, opt.precision, opt.block, opt.min_blocks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "fit launch");
     ++launches;
   }

@@ -69,6 +69,11 @@ struct Surf {
   __device__ double nc() const { return d[13]; }  // n . c
   __device__ double uc() const { return d[14]; }  // u . c
   __device__ double vc() const { return d[15]; }  // v . c
+  __device__ const float* f() const { return reinterpret_cast<const float*>(d + 16); }
+  __device__ float nf(int i) const { return f()[i]; }
+  __device__ float uf(int i) const { return f()[3 + i]; }
+  __device__ float vf(int i) const { return f()[6 + i]; }
+  __device__ float xx0f() const { return f()[9]; }
 };
 
 // out = v x bs, with bs = (q/p) kappa B: the operator A of dT/ds = A T
@@ -139,15 +144,28 @@ __device__ __forceinline__ float d2f(double x) {
 // One step leaves a relative error below 1e-13 (the seed is accurate to a few
 // float ulps and each step squares the error); two steps reach double
 // rounding level.
+// y / 2 for a positive normal double, by decrementing the exponent field on
+// the integer pipe
+__device__ __forceinline__ double half_pos(double y) {
+  return __hiloint2double(__double2hiint(y) - 0x00100000, __double2loint(y));
+}
+
 template <int STEPS>
 __device__ __forceinline__ double rsqrt_nr(double x) {
   double y = f2d(rsqrtf(d2f(x)));
 #pragma unroll
   for (int i = 0; i < STEPS; ++i) {
     const double e = fma(-x * y, y, 1.0);
-    y = fma(0.5 * y, e, y);
+    y = fma(half_pos(y), e, y);
   }
   return y;
+}
+
+// x > 0 (false for NaN), decided on the integer pipe: positive doubles order
+// like their bit patterns, and NaNs lie above +Inf
+__device__ __forceinline__ bool dpos(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
 }
 
 template <int STEPS>
@@ -162,6 +180,65 @@ __device__ __forceinline__ double rcp_nr(double x) {
 }
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000ULL); }
+
+// track fitted by slot i of a launch
+__device__ __forceinline__ int track_of(const FitParams& p, int i) {
+  return p.order ? p.order[p.track0 + i] : p.track0 + i;
+}
+
+// The fit kernel: stage the surface table once per CTA, then either one
+// track per thread over the grid (work_counter == nullptr) or a persistent
+// loop in which every warp takes 32-track units from a global counter until
+// the batch is exhausted (balances uneven tracks and removes the wave tail).
+// Body::run(p, s_surf, i) fits slot i.
+template <class Body, int MINB>
+__global__ void __launch_bounds__(128, MINB) fit_kernel(const FitParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* s_surf = reinterpret_cast<double*>(smem_raw);
+  __shared__ __align__(8) uint64_t s_mbar;
+  const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
+                                     p.error_flag);
+  if (!staged) return;
+  if (p.work_counter == nullptr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < p.n_tracks) Body::run(p, s_surf, i);
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int unit = 0;
+    if (lane == 0) unit = atomicAdd(p.work_counter, 1);
+    unit = __shfl_sync(0xffffffffu, unit, 0);
+    const int base = unit * 32;
+    if (base >= p.n_tracks) break;
+    if (base + lane < p.n_tracks) Body::run(p, s_surf, base + lane);
+    __syncwarp();
+  }
+}
+
+// launch with the persistent grid (resident CTAs on every SM) or one thread
+// per track
+template <class Body, int MINB>
+cudaError_t launch_body(const FitParams& p, int block, cudaStream_t stream) {
+  const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);
+  auto kern = fit_kernel<Body, MINB>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int grid = (p.n_tracks + block - 1) / block;
+  if (p.work_counter) {
+    int dev = 0, nsm = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem);
+    if (e != cudaSuccess) return e;
+    const long long resident = (long long)nsm * (occ > 0 ? occ : 1);
+    if (grid > resident) grid = (int)resident;
+  }
+  kern<<<grid, block, smem, stream>>>(p);
+  return cudaGetLastError();
+}
 
 }  // namespace dev
 }  // namespace kfgb

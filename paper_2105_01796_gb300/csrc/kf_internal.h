@@ -6,12 +6,14 @@
 
 namespace kfgb {
 
-// Packed surface record staged into shared memory: 16 doubles (128 B, so the
-// table is a whole number of 16-byte units for the bulk copy):
-//   [0..2] centre c, [3..11] R row-major (columns u, v, n), [12] x/X0,
-//   [13] n.c, [14] u.c, [15] v.c
-constexpr int kSurfStride = 16;
-constexpr int kMaxSurfaces = 1536;  // 192 KiB of shared memory
+// Packed surface record staged into shared memory: 24 doubles (192 B, a
+// whole number of 16-byte units for the bulk copy):
+//   doubles [0..2] centre c, [3..11] R row-major (columns u, v, n), [12] x/X0,
+//           [13] n.c, [14] u.c, [15] v.c
+//   floats at double offset 16: [0..2] n, [3..5] u, [6..8] v, [9] x/X0
+//           (float copies, so the mixed kernel converts nothing per step)
+constexpr int kSurfStride = 24;
+constexpr int kMaxSurfaces = 1024;  // 192 KiB of shared memory
 
 // Per-state record the forward pass writes and the RTS pass reads back.
 // FP64 path, all in ws64:  xp 6 | xf 6 | Cp 21 | Cf 21 | Bm 36   (90 doubles)
@@ -53,6 +55,9 @@ struct FitParams {
   double* ws64;            // [max_states][rec64][n_tracks]
   float* ws32;             // [max_states][rec32][n_tracks] (mixed only)
   int32_t* error_flag;     // set to 1 when a bounded device wait gives up
+  int32_t* work_counter;   // non-null: persistent launch, warps take 32-track
+                           // units from this counter (zeroed before launch)
+  const int32_t* order;    // non-null: slot s fits track order[s]
 };
 
 // Pack the SoA surface table into [S][kSurfStride] doubles.
@@ -64,8 +69,15 @@ cudaError_t launch_pack_surfaces(int n_surfaces, const double* center,
 // patterns; counters[0..4] receive the mismatch counts.
 cudaError_t launch_selftest(long long n, unsigned long long* counters, cudaStream_t stream);
 
-// One fused filter + smoother launch over p.n_tracks tracks.
-cudaError_t launch_fit(const FitParams& p, int precision, int block,
+// One fused filter + smoother launch over p.n_tracks tracks.  min_blocks
+// selects the register-cap variant (__launch_bounds__ minimum CTAs per SM;
+// 0 = the default variant).
+cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks,
                        cudaStream_t stream);
+
+// Counting sort of the tracks by state count, longest first:
+// order[0..n_tracks) receives track indices.  hist needs max_states + 2 ints.
+cudaError_t launch_length_order(int n_tracks, int max_states, const int32_t* offsets,
+                                int32_t* hist, int32_t* order, cudaStream_t stream);
 
 }  // namespace kfgb

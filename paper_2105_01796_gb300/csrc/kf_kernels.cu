@@ -131,7 +131,7 @@ struct Jac {
 };
 
 template <typename R, bool BZ>
-__device__ int transport(const Surf& sa, const Surf& sb, const double x[6], const double B[3],
+__device__ __forceinline__ int transport(const Surf& sa, const Surf& sb, const double x[6], const double B[3],
                          double mass, double h_max, int n_iter, double xp[6], Jac<R>& J,
                          R& sin_theta, R& cos_inc) {
   Prop<R> s;
@@ -316,18 +316,12 @@ __device__ __forceinline__ int kalman_update(const double xp[6], const double Cp
 // ---------------------------------------------------------------------------
 // the fused fit kernel
 // ---------------------------------------------------------------------------
-template <int PREC, bool BZ>
-__global__ void __launch_bounds__(128) kf_fit_kernel(const FitParams p) {
+template <bool BZ>
+__device__ __forceinline__ void fit_one_fp64(const FitParams& p, const double* s_surf, int i) {
+  constexpr int PREC = 0;
   using R = typename Prec<PREC>::R;
   using RC = Rec<PREC>;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  double* s_surf = reinterpret_cast<double*>(smem_raw);
-  __shared__ __align__(8) uint64_t s_mbar;
-  const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8),
-                                     &s_mbar, p.error_flag);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!staged || i >= p.n_tracks) return;
-  const int t = p.track0 + i;
+  const int t = track_of(p, i);
   const size_t TT = (size_t)p.n_tracks_total;
   const WS ws{p.ws64, p.ws32, (size_t)p.n_tracks, PREC == 0 ? kRec64Fp64 : kRec64Mixed,
               PREC == 0 ? 0 : kRec32Mixed, i};
@@ -364,7 +358,10 @@ __global__ void __launch_bounds__(128) kf_fit_kernel(const FitParams p) {
         const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
         Jac<R> J;
         R sin_th, cos_inc;
-        status = transport<R, BZ>(sa, sb, x, p.bfield, p.mass, p.h_max, p.n_iter, xp, J, sin_th, cos_inc);
+        // field copied to registers: taking the address of a kernel parameter
+        // would move the parameter block to local memory
+        const double Bf[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
+        status = transport<R, BZ>(sa, sb, x, Bf, p.mass, p.h_max, p.n_iter, xp, J, sin_th, cos_inc);
         if (status != ST_OK) break;
         // Bm = F Cf_{k-1}; Cp = Bm F^T + Q.  F rows 0..3 and 5 over columns
         // 0..4 are J; row 4 = e4; column 5 = e5.
@@ -579,19 +576,59 @@ __global__ void pack_surfaces_kernel(int n, const double* __restrict__ center, c
   o[12] = xx0[s];
   // n.c, u.c, v.c (column j of R is o[3 + 3 i + j], i = 0..2)
   for (int j = 0; j < 3; ++j) o[13 + (j + 1) % 3] = o[3 + j] * o[0] + o[6 + j] * o[1] + o[9 + j] * o[2];
+  // float copies of n, u, v and x/X0
+  float* f = reinterpret_cast<float*>(o + 16);
+  for (int i = 0; i < 3; ++i) {
+    f[i] = (float)o[3 + 3 * i + 2];
+    f[3 + i] = (float)o[3 + 3 * i + 0];
+    f[6 + i] = (float)o[3 + 3 * i + 1];
+  }
+  f[9] = (float)o[12];
+  for (int i = 10; i < 16; ++i) f[i] = 0.0f;
 }
 
-template <int PREC, bool BZ>
-cudaError_t launch_t(const FitParams& p, int block, cudaStream_t stream) {
-  const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);
-  auto kern = kf_fit_kernel<PREC, BZ>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+template <bool BZ>
+struct Fp64Body {
+  static __device__ __forceinline__ void run(const FitParams& p, const double* s_surf, int i) {
+    fit_one_fp64<BZ>(p, s_surf, i);
   }
-  const int grid = (p.n_tracks + block - 1) / block;
-  kern<<<grid, block, smem, stream>>>(p);
-  return cudaGetLastError();
+};
+
+template <bool BZ>
+cudaError_t launch_fp64(const FitParams& p, int block, int min_blocks, cudaStream_t stream) {
+  (void)min_blocks;  // a register cap below 255 spills this kernel heavily
+  return launch_body<Fp64Body<BZ>, 1>(p, block, stream);
+}
+
+// counting sort of tracks by state count (longest first)
+__global__ void length_hist_kernel(int n, int max_states, const int32_t* __restrict__ offsets,
+                                   int32_t* __restrict__ hist) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int len = offsets[t + 1] - offsets[t];
+  len = len < 0 ? 0 : (len > max_states ? max_states + 1 : len);
+  atomicAdd(&hist[max_states + 1 - len], 1);  // bin 0 = longest
+}
+
+__global__ void length_scan_kernel(int nbins, int32_t* hist) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < nbins; ++b) {
+      const int c = hist[b];
+      hist[b] = acc;
+      acc += c;
+    }
+  }
+}
+
+__global__ void length_scatter_kernel(int n, int max_states, const int32_t* __restrict__ offsets,
+                                      int32_t* __restrict__ hist, int32_t* __restrict__ order) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int len = offsets[t + 1] - offsets[t];
+  len = len < 0 ? 0 : (len > max_states ? max_states + 1 : len);
+  const int slot = atomicAdd(&hist[max_states + 1 - len], 1);
+  order[slot] = t;
 }
 
 }  // namespace
@@ -604,14 +641,28 @@ cudaError_t launch_pack_surfaces(int n_surfaces, const double* center, const dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_fit_mixed(const FitParams& p, int block, cudaStream_t stream);
+cudaError_t launch_fit_mixed(const FitParams& p, int block, int min_blocks, cudaStream_t stream);
 
-cudaError_t launch_fit(const FitParams& p, int precision, int block, cudaStream_t stream) {
+cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks, cudaStream_t stream) {
   if (p.n_tracks <= 0) return cudaSuccess;
   if (block <= 0) block = 128;
   const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
-  if (precision == 0) return bz ? launch_t<0, true>(p, block, stream) : launch_t<0, false>(p, block, stream);
-  return launch_fit_mixed(p, block, stream);
+  if (precision == 0) return bz ? launch_fp64<true>(p, block, min_blocks, stream)
+                                : launch_fp64<false>(p, block, min_blocks, stream);
+  return launch_fit_mixed(p, block, min_blocks, stream);
+}
+
+cudaError_t launch_length_order(int n_tracks, int max_states, const int32_t* offsets, int32_t* hist,
+                                int32_t* order, cudaStream_t stream) {
+  if (n_tracks <= 0) return cudaSuccess;
+  const int nbins = max_states + 2;
+  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * nbins, stream);
+  if (e != cudaSuccess) return e;
+  const int block = 256, grid = (n_tracks + block - 1) / block;
+  length_hist_kernel<<<grid, block, 0, stream>>>(n_tracks, max_states, offsets, hist);
+  length_scan_kernel<<<1, 32, 0, stream>>>(nbins, hist);
+  length_scatter_kernel<<<grid, block, 0, stream>>>(n_tracks, max_states, offsets, hist, order);
+  return cudaGetLastError();
 }
 
 }  // namespace kfgb

@@ -141,8 +141,8 @@ __device__ __forceinline__ void rotate(double& c, double& s, float delta) {
 
 // Transport the filtered state (x, d) on surface a to surface b.
 template <bool BZ>
-__device__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6], const Dir& d,
-                               const double B[3], float m2, float h_max, int n_iter, double xp[6], Dir& dp,
+__device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6], const Dir& d,
+                               const float Bf[3], float m2, float h_max, int n_iter, double xp[6], Dir& dp,
                                JacF& J, float& sin_th, float& cos_inc) {
   // start point (FP64 accumulators)
   double r[3], T[3];
@@ -154,8 +154,8 @@ __device__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6]
   double t = x[5];
   const float lam = d2f(x[4]);
   const float lk = lam * (float)kKappa;
-  const float bs[3] = {lk * (float)B[0], lk * (float)B[1], lk * (float)B[2]};
-  const float kB[3] = {(float)(kKappa * B[0]), (float)(kKappa * B[1]), (float)(kKappa * B[2])};
+  const float bs[3] = {lk * Bf[0], lk * Bf[1], lk * Bf[2]};
+  const float kB[3] = {(float)kKappa * Bf[0], (float)kKappa * Bf[1], (float)kKappa * Bf[2]};
   const float gam = sqrtf(1.0f + m2 * lam * lam);
   const float dtds = gam * (float)kInvC;
   const float dtl = m2 * lam * (float)kInvC / gam;  // d(dt/ds)/dlam
@@ -171,7 +171,7 @@ __device__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6]
     }
     g.gtl = 0.0f;
   }
-  const float nb[3] = {(float)sb.n(0), (float)sb.n(1), (float)sb.n(2)};
+  const float nb[3] = {sb.nf(0), sb.nf(1), sb.nf(2)};
   // main steps over the straight-line distance
   float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
   {
@@ -241,9 +241,12 @@ __device__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6]
     const double sdp = fma(d.cp, dp.sp, -d.sp * dp.cp);
     const float cdp = d2f(d.cp) * d2f(dp.cp) + d2f(d.sp) * d2f(dp.sp);
     double phi = angle_step(d.phi, sdp, cdp, dp.sp, dp.cp);
+    // keep phi in (-pi, pi]; compared on the integer pipe (doubles of one
+    // sign order like their magnitudes' bit patterns)
     const double pi = 3.141592653589793;
-    if (phi > pi) phi -= 2.0 * pi;
-    if (phi <= -pi) phi += 2.0 * pi;
+    const long long bp = __double_as_longlong(phi), bpi = __double_as_longlong(pi);
+    if (bp > bpi) phi -= 2.0 * pi;
+    else if (bp < 0 && (bp & 0x7fffffffffffffffLL) >= bpi) phi += 2.0 * pi;
     dp.phi = phi;
     const double sdt = fma(dp.st, d.ct, -dp.ct * d.st);
     const float cdt = d2f(dp.st) * d2f(d.st) + d2f(dp.ct) * d2f(d.ct);
@@ -266,8 +269,8 @@ __device__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6]
   float Gr[3][5], GT[3][5], Gt[5];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    Gr[i][0] = (float)sa.u(i);
-    Gr[i][1] = (float)sa.v(i);
+    Gr[i][0] = sa.uf(i);
+    Gr[i][1] = sa.vf(i);
     Gr[i][2] = g.gr[i][0];
     Gr[i][3] = g.gr[i][1];
     Gr[i][4] = g.gr[i][2];
@@ -289,8 +292,8 @@ __device__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6]
     }
     Gt[c] += dtds * w;
   }
-  const float ub[3] = {(float)sb.u(0), (float)sb.u(1), (float)sb.u(2)};
-  const float vb[3] = {(float)sb.v(0), (float)sb.v(1), (float)sb.v(2)};
+  const float ub[3] = {sb.uf(0), sb.uf(1), sb.uf(2)};
+  const float vb[3] = {sb.vf(0), sb.vf(1), sb.vf(2)};
   const float inv_sth = 1.0f / sth;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
@@ -326,7 +329,7 @@ __device__ __forceinline__ void mul2(const float a[2][2], const float b[2][2], f
     for (int j = 0; j < 2; ++j) o[i][j] = a[i][0] * b[0][j] + a[i][1] * b[1][j];
 }
 
-__device__ void invert_F(const float F[25], float Fi[6][6]) {
+__device__ __forceinline__ void invert_F(const float F[25], float Fi[6][6]) {
   float P[2][2], Qb[2][2], Rb[2][2], S[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -391,15 +394,8 @@ __device__ void invert_F(const float F[25], float Fi[6][6]) {
 }
 
 template <bool BZ>
-__global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  double* s_surf = reinterpret_cast<double*>(smem_raw);
-  __shared__ __align__(8) uint64_t s_mbar;
-  const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
-                                     p.error_flag);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (!staged || i >= p.n_tracks) return;
-  const int t = p.track0 + i;
+__device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* s_surf, int i) {
+  const int t = track_of(p, i);
   const size_t TT = (size_t)p.n_tracks_total;
   const WSM ws{p.ws64, p.ws32, (size_t)p.n_tracks, i};
   const int64_t o0 = p.offsets[t], o1 = p.offsets[t + 1];
@@ -413,6 +409,10 @@ __global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
     }
   const float m2 = (float)(p.mass * p.mass);
   const float h_max = (float)p.h_max;
+  // the field as floats, once per track (copied to registers: taking the
+  // address of a kernel parameter would move the parameter block to local
+  // memory)
+  const float Bf[3] = {(float)p.bfield[0], (float)p.bfield[1], (float)p.bfield[2]};
 
   double xs[6];
   double Cs_out[21];
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
         const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
         JacF J;
         float sin_th, cos_inc;
-        status = transport_mixed<BZ>(sa, sb, x, d, p.bfield, m2, h_max, p.n_iter, xp, dp, J, sin_th, cos_inc);
+        status = transport_mixed<BZ>(sa, sb, x, d, Bf, m2, h_max, p.n_iter, xp, dp, J, sin_th, cos_inc);
         if (status != ST_OK) break;
         float Cr[21];
 #pragma unroll
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
         }
         // multiple scattering of surface k, added before the update
         float qphi = 0.0f, qth = 0.0f;
-        const float xx0 = (float)sb.xx0();
+        const float xx0 = sb.xx0f();
         if (xx0 > 0.0f) {
           const float th0 = highland<float>(fabsf(d2f(x[4])), m2, xx0, cos_inc);
           qth = th0 * th0;
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
         const double V0 = p.cov[o0 + k], V1 = p.cov[p.n_states + o0 + k], V2 = p.cov[2 * p.n_states + o0 + k];
         const double S00 = V0 + Cp[sy(0, 0)], S01 = V1 + Cp[sy(1, 0)], S11 = V2 + Cp[sy(1, 1)];
         const double det = fma(S00, S11, -S01 * S01);
-        if (!(det > 0.0) || !(S00 > 0.0)) {
+        if (!dpos(det) || !dpos(S00)) {
           status = ST_NON_SPD;
           break;
         }
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
           double dj = L[sy(j, j)];
 #pragma unroll
           for (int q = 0; q < j; ++q) dj = fma(-L[sy(j, q)], L[sy(j, q)], dj);
-          if (!(dj > 0.0)) {
+          if (!dpos(dj)) {
             status = ST_NON_SPD;
             dj = 1.0;
           }
@@ -729,23 +729,26 @@ __global__ void __launch_bounds__(128) kf_fit_mixed_kernel(const FitParams p) {
 }
 
 template <bool BZ>
-cudaError_t launch_m(const FitParams& p, int block, cudaStream_t stream) {
-  const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);
-  auto kern = kf_fit_mixed_kernel<BZ>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+struct MixedBody {
+  static __device__ __forceinline__ void run(const FitParams& p, const double* s_surf, int i) {
+    fit_one_mixed<BZ>(p, s_surf, i);
   }
-  const int grid = (p.n_tracks + block - 1) / block;
-  kern<<<grid, block, smem, stream>>>(p);
-  return cudaGetLastError();
+};
+
+template <bool BZ>
+cudaError_t launch_m(const FitParams& p, int block, int min_blocks, cudaStream_t stream) {
+  switch (min_blocks) {
+    case 4: return launch_body<MixedBody<BZ>, 4>(p, block, stream);
+    case 3: return launch_body<MixedBody<BZ>, 3>(p, block, stream);
+    default: return launch_body<MixedBody<BZ>, 1>(p, block, stream);
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_fit_mixed(const FitParams& p, int block, cudaStream_t stream) {
+cudaError_t launch_fit_mixed(const FitParams& p, int block, int min_blocks, cudaStream_t stream) {
   const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
-  return bz ? launch_m<true>(p, block, stream) : launch_m<false>(p, block, stream);
+  return bz ? launch_m<true>(p, block, min_blocks, stream) : launch_m<false>(p, block, min_blocks, stream);
 }
 
 }  // namespace kfgb

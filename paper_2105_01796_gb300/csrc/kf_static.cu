@@ -85,6 +85,8 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   if (opt.precision != KF_PRECISION_FP64 && opt.precision != KF_PRECISION_MIXED) return KF_EUNSUPPORTED;
   if (!(opt.mass >= 0.0) || !(opt.h_max > 0.0) || opt.n_iter < 0 || opt.n_iter > 16) return KF_EINVAL;
   if (opt.block < 0 || opt.block > 128 || (opt.block % 32) != 0) return KF_EUNSUPPORTED;
+  if (opt.schedule < KF_SCHEDULE_GRID || opt.schedule > KF_SCHEDULE_PERSISTENT) return KF_EUNSUPPORTED;
+  if (opt.min_blocks < 0 || opt.min_blocks > 4) return KF_EUNSUPPORTED;
   // size limits of the static block
   if (su->n_surfaces > kMaxSurfaces) return KF_ESIZE;
   // one track's records (both precisions' parts, each 256-byte aligned) must fit
@@ -106,7 +108,7 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   const size_t n64 = opt.precision == KF_PRECISION_FP64 ? kRec64Fp64 : kRec64Mixed;
   const size_t bytes64 = (n64 * sizeof(double) * tr->max_states * chunk + 255) / 256 * 256;
 
-  e = cudaMemsetAsync(flag, 0, sizeof(int32_t), stream);  // the flag must start at zero
+  e = cudaMemsetAsync(flag, 0, 2 * sizeof(int32_t), stream);  // flag and work counter start at zero
   if (e != cudaSuccess) return KF_ECUDA;
   e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, surf, stream);
   if (e != cudaSuccess) return KF_ECUDA;
@@ -137,10 +139,17 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   p.ws64 = (double*)rec;
   p.ws32 = opt.precision == KF_PRECISION_FP64 ? nullptr : (float*)(rec + bytes64);
   p.error_flag = flag;
+  // persistent launches share one work counter, re-zeroed before each chunk
+  const bool persistent = opt.schedule != KF_SCHEDULE_GRID;
   for (size_t t0 = 0; t0 < (size_t)tr->n_tracks; t0 += chunk) {
     p.track0 = (int32_t)t0;
     p.n_tracks = (int32_t)(((size_t)tr->n_tracks - t0) < chunk ? ((size_t)tr->n_tracks - t0) : chunk);
-    e = launch_fit(p, opt.precision, opt.block, stream);
+    p.work_counter = persistent ? flag + 1 : nullptr;
+    if (persistent && t0 > 0) {
+      e = cudaMemsetAsync(flag + 1, 0, sizeof(int32_t), stream);
+      if (e != cudaSuccess) return KF_ECUDA;
+    }
+    e = launch_fit(p, opt.precision, opt.block, opt.min_blocks, stream);
     if (e != cudaSuccess) return KF_ECUDA;
   }
   return KF_SUCCESS;

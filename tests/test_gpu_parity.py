@@ -217,3 +217,23 @@ def test_numeric_helpers_selftest(handle):
     """Integer-pipe float<->double conversions match the hardware ones bit for
     bit; the Newton-refined 1/sqrt and 1/x meet their stated error bounds."""
     assert kf.kf_selftest(1 << 22) == [0, 0, 0, 0, 0]
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_every_launch_variant_agrees(handle, prec):
+    """All schedules, block sizes and register-cap variants a tuner may pick:
+    FP64 results identical bit for bit, mixed results within tolerance of the
+    oracle (uneven tracks with holes, so the sorted schedule reorders)."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 3001))
+    r = oracle.fit_batch(ev)
+    base = None
+    for sched in (kf.KF_SCHEDULE_GRID, kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED):
+        for block in (64, 128):
+            for mb in ((0,) if prec == FP64 else (0, 3, 4)):
+                g = gpu_fit(handle, ev, prec, schedule=sched, block=block, min_blocks=mb)
+                compare(g, r, prec)
+                if prec == FP64:
+                    if base is None:
+                        base = g
+                    for k in ("params", "cov", "chi2", "ndf", "status"):
+                        assert np.array_equal(g[k], base[k]), (sched, block, k)

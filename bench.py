@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--tracks", type=int, default=None, help="override the track count")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="plain launches instead of graph replay")
     return ap.parse_args()
 
 
@@ -176,13 +177,21 @@ def run_ours(args, rank, world, local):
     M = int(ev["surface_id"].shape[0])
     dev = kf.event_to_device(ev)
     h = kf.Handle()
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()          # graphs need a non-default stream
+    torch.cuda.set_stream(stream)
     prec_id = {"mixed": kf.KF_PRECISION_MIXED, "fp64": kf.KF_PRECISION_FP64}
     l2_flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    tuned = {}
+
     def timed(prec, steps, warmup):
-        opt = kf.kf_default_options(prec_id[prec])
         out = kf.alloc_outputs(T)
+        # launch shape from the autotuner (untimed), then CUDA-graph replay
+        best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(prec_id[prec]), stream)
+        opt = kf.kf_default_options(prec_id[prec], schedule=best.schedule, block=best.block,
+                                    min_blocks=best.min_blocks, use_graph=0 if args.no_graph else 1)
+        tuned[prec] = {"schedule": ["grid", "persistent", "sorted"][best.schedule], "block": best.block,
+                       "min_blocks": best.min_blocks, "cuda_graph": not args.no_graph}
         for _ in range(warmup):
             kf.kf_fit_ex(h, dev, out, opt, stream)
         torch.cuda.synchronize()
@@ -239,7 +248,9 @@ def run_ours(args, rank, world, local):
                 "ndf": torch.empty((T,), dtype=torch.int32).pin_memory().numpy(),
                 "status": torch.empty((T,), dtype=torch.uint8).pin_memory().numpy(),
                 "states": None}
-        opt = kf.kf_default_options(prec_id[args.precision])
+        sh = tuned[args.precision]
+        opt = kf.kf_default_options(prec_id[args.precision], block=sh["block"], min_blocks=sh["min_blocks"],
+                                    schedule=["grid", "persistent", "sorted"].index(sh["schedule"]))
         for _ in range(args.warmup):
             kf.kf_fit_host(h, hev, opt, out=outs, stream=stream)
         torch.cuda.synchronize()
@@ -294,6 +305,7 @@ def run_ours(args, rank, world, local):
             "value": world * T / (other_ms / 1e3), "ms_per_step": other_ms,
             "ok_tracks": int((st_other == 0).sum())},
         "ok_tracks": int((st == 0).sum()),
+        "launch_shape": tuned,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "kf_fit_mixed_kernel" if args.precision == "mixed" else "kf_fit_kernel",

@@ -132,15 +132,21 @@ typedef struct {
   double h_max;                /* longest RKN step in mm (default 50) */
   int32_t n_iter;              /* Newton corrections onto each plane (default 3) */
   int32_t block;               /* threads per CTA: 32, 64, 96 or 128 (0 = 128) */
-  int64_t workspace_bytes;     /* cap on the handle's workspace (0 = 4 GiB);
+  int64_t workspace_bytes;     /* cap on the handle's workspace (0 = 32 GiB);
                                   larger batches are fitted in chunks */
   int32_t schedule;            /* kf_schedule (default KF_SCHEDULE_PERSISTENT) */
   int32_t min_blocks;          /* register-cap variant: minimum resident CTAs
                                   per SM the kernel is compiled for (0 = the
                                   default variant; 3 and 4 cap registers) */
+  int32_t use_graph;           /* 1: kf_fit_ex captures its launches into a
+                                  CUDA graph held by the handle and replays it
+                                  while every argument is unchanged (needs a
+                                  non-NULL stream) */
 } kf_options;
 
 typedef enum {
+  KF_SCHEDULE_AUTO = -1,       /* kf_fit_ex asks kf_autotune (cached per
+                                  batch shape in the handle) */
   KF_SCHEDULE_GRID = 0,        /* one thread per track, one CTA per block of
                                   tracks */
   KF_SCHEDULE_PERSISTENT = 1,  /* resident CTAs; each warp takes 32-track
@@ -203,6 +209,21 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
 int kf_fit_static(const kf_tracks* tracks, const kf_surfaces* surfaces,
                   const kf_measurements* meas, const kf_field* field,
                   const kf_options* opt, const kf_outputs* out, void* stream);
+
+/* Autotuner: time every launch shape (schedule x threads per CTA x register
+ * variant) on this batch, on `stream`, and return the fastest in *best
+ * (other fields copied from *base; base may be NULL for the defaults) and
+ * its median time in *best_ms (optional).  Results are cached in the handle
+ * per (precision, n_tracks, max_states, n_surfaces, field along z); a cached
+ * shape returns at once.  Runs the fit about 30-60 times, overwriting *out,
+ * and synchronises the stream; inside a stream capture it returns the
+ * defaults without timing.  The paper scans grid, block and register counts
+ * by hand (Sect. 5.3.5); this automates that scan. */
+int kf_autotune(kf_handle* handle, const kf_tracks* tracks,
+                const kf_surfaces* surfaces, const kf_measurements* meas,
+                const kf_field* field, const kf_options* base,
+                const kf_outputs* out, void* stream, kf_options* best,
+                double* best_ms);
 
 /* Bytes of device workspace kf_fit_ex would use for this batch shape. */
 int64_t kf_workspace_size(int32_t n_tracks, int32_t max_states,

@@ -22,14 +22,15 @@ LIB_PATH = os.path.join(_HERE, "libkfgb.so")
 
 KF_PRECISION_FP64 = 0
 KF_PRECISION_MIXED = 1
-KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED = 0, 1, 2
+KF_SCHEDULE_AUTO, KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED = -1, 0, 1, 2
 TRACK_STATUS = {0: "ok", 1: "no_intersection", 2: "non_spd", 3: "nonfinite", 4: "bad_input"}
 MUON_MASS = 0.1056583755
 
 # exported symbols of include/kf.h
 EXPORTS = ("kf_default_options", "kf_create", "kf_destroy", "kf_fit", "kf_fit_ex",
            "kf_fit_host", "kf_workspace_size", "kf_last_launch_count", "kf_strerror",
-           "kf_last_cuda_error", "kf_abi_version", "kf_selftest", "kf_fit_static")
+           "kf_last_cuda_error", "kf_abi_version", "kf_selftest", "kf_fit_static",
+           "kf_autotune")
 
 
 class KfTracks(ctypes.Structure):
@@ -63,7 +64,8 @@ class KfOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mass", ctypes.c_double),
                 ("h_max", ctypes.c_double), ("n_iter", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
-                ("schedule", ctypes.c_int32), ("min_blocks", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
 
 
 _lib = None
@@ -106,6 +108,9 @@ def load(path: str = LIB_PATH):
         lib.kf_last_cuda_error.restype = ctypes.c_char_p
         lib.kf_abi_version.argtypes = []
         lib.kf_abi_version.restype = ctypes.c_int
+        lib.kf_autotune.argtypes = [P] + base + [ctypes.POINTER(KfOptions), ctypes.POINTER(KfOutputs), P,
+                                                 ctypes.POINTER(KfOptions), ctypes.POINTER(ctypes.c_double)]
+        lib.kf_autotune.restype = ctypes.c_int
         lib.kf_fit_static.argtypes = base + [ctypes.POINTER(KfOptions), ctypes.POINTER(KfOutputs), P]
         lib.kf_fit_static.restype = ctypes.c_int
         lib.kf_selftest.argtypes = [ctypes.c_int64, ctypes.c_void_p]
@@ -252,6 +257,26 @@ def kf_selftest(n_patterns=1 << 22):
     counts = np.zeros(5, dtype=np.uint64)
     _check(load().kf_selftest(int(n_patterns), counts.ctypes.data_as(ctypes.c_void_p)))
     return [int(c) for c in counts]
+
+
+def kf_autotune(handle: Handle, dev_ev, out, opt: KfOptions | None = None, stream=None):
+    """Time every launch shape on this batch; return (best options, median ms).
+    The choice is cached in the handle per batch shape."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    tr, su, me, fi = _structs(dev_ev, dev_ev["max_states"])
+    o = KfOutputs(_ptr(out["params"]), _ptr(out["cov"]), _ptr(out["chi2"]), _ptr(out.get("ndf")),
+                  _ptr(out.get("status")), _ptr(out.get("states")))
+    best = KfOptions()
+    ms = ctypes.c_double(0.0)
+    _check(load().kf_autotune(handle.ptr, ctypes.byref(tr), ctypes.byref(su), ctypes.byref(me),
+                              ctypes.byref(fi), ctypes.byref(opt) if opt is not None else None,
+                              ctypes.byref(o), ctypes.c_void_p(int(stream)), ctypes.byref(best),
+                              ctypes.byref(ms)))
+    return best, ms.value
 
 
 def kf_fit_static(dev_ev, out, opt: KfOptions | None = None, stream=None):

@@ -27,6 +27,18 @@ struct kf_handle {
   int64_t order_cap = 0;
   int32_t* hist = nullptr;
   int hist_cap = 0;
+  // autotuner cache: best launch options per batch shape
+  struct Tuned {
+    int32_t precision, n_tracks, max_states, n_surfaces, bz;
+    kf_options best;
+    double ms;
+  };
+  Tuned tuned[16];
+  int n_tuned = 0;
+  // cached CUDA graph of the last captured fit and the call it replays
+  cudaGraphExec_t graph_exec = nullptr;
+  alignas(8) unsigned char graph_key[512];
+  int32_t graph_launches = 0;
   // device copies for kf_fit_host
   void* dev_io = nullptr;
   size_t dev_io_bytes = 0;
@@ -43,7 +55,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 
 constexpr double kMuonMass = 0.1056583755;
-constexpr int64_t kDefaultWorkspace = int64_t(4) << 30;
+constexpr int64_t kDefaultWorkspace = int64_t(32) << 30;
 
 size_t record_bytes(int precision) {
   return precision == KF_PRECISION_FP64 ? kRec64Fp64 * sizeof(double)
@@ -98,7 +110,7 @@ int validate(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* 
   if (opt->precision != KF_PRECISION_FP64 && opt->precision != KF_PRECISION_MIXED) return KF_EUNSUPPORTED;
   if (!(opt->mass >= 0.0) || !(opt->h_max > 0.0) || opt->n_iter < 0 || opt->n_iter > 16) return KF_EINVAL;
   if (opt->block < 0 || opt->block > 128 || (opt->block % 32) != 0) return KF_EUNSUPPORTED;
-  if (opt->schedule < KF_SCHEDULE_GRID || opt->schedule > KF_SCHEDULE_SORTED) return KF_EUNSUPPORTED;
+  if (opt->schedule < KF_SCHEDULE_AUTO || opt->schedule > KF_SCHEDULE_SORTED) return KF_EUNSUPPORTED;
   if (opt->min_blocks < 0 || opt->min_blocks > 4) return KF_EUNSUPPORTED;
   for (int i = 0; i < 3; ++i)
     if (!(fi->b[i] == fi->b[i])) return KF_EINVAL;
@@ -120,6 +132,7 @@ void kf_default_options(kf_options* opt) {
   opt->workspace_bytes = 0;
   opt->schedule = KF_SCHEDULE_PERSISTENT;
   opt->min_blocks = 0;
+  opt->use_graph = 0;
 }
 
 int kf_abi_version(void) { return KF_ABI_VERSION; }
@@ -186,6 +199,7 @@ void kf_destroy(kf_handle* h) {
   if (h->counters) cudaFree(h->counters);
   if (h->order) cudaFree(h->order);
   if (h->hist) cudaFree(h->hist);
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   delete h;
 }
 
@@ -199,16 +213,20 @@ int64_t kf_workspace_size(int32_t n_tracks, int32_t max_states, const kf_options
 
 int32_t kf_last_launch_count(const kf_handle* h) { return h ? h->last_launches : 0; }
 
-int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
-              const kf_field* fi, const kf_options* opt_in, const kf_outputs* out, void* stream_v) {
-  if (!h) return KF_EINVAL;
-  kf_options opt;
-  if (opt_in) opt = *opt_in; else kf_default_options(&opt);
-  int rc = validate(tr, su, me, fi, &opt, out);
-  if (rc) return rc;
-  h->last_launches = 0;
-  if (tr->n_tracks == 0) return KF_SUCCESS;
-  cudaStream_t stream = (cudaStream_t)stream_v;
+}  // extern "C"
+
+namespace {
+
+// Everything kf_fit_ex computes before it queues work: chunking and the
+// handle's buffers (allocations cannot happen inside a stream capture).
+struct FitPlan {
+  int64_t chunk;
+  size_t bytes64;
+  int n_chunks;
+};
+
+int prepare_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_options& opt, FitPlan* plan) {
+  int rc;
   const int64_t chunk = chunk_tracks(tr->n_tracks, tr->max_states, opt);
   const size_t n64 = opt.precision == KF_PRECISION_FP64 ? kRec64Fp64 : kRec64Mixed;
   const size_t bytes64 = align_up(n64 * sizeof(double) * tr->max_states * chunk, 256);
@@ -243,11 +261,22 @@ int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf
       h->hist_cap = tr->max_states + 2;
     }
   }
+  plan->chunk = chunk;
+  plan->bytes64 = bytes64;
+  plan->n_chunks = n_chunks;
+  return KF_SUCCESS;
+}
+
+// Queue the fit on `stream` (no allocation, no synchronisation).
+int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
+                const kf_field* fi, const kf_options& opt, const kf_outputs* out, cudaStream_t stream,
+                const FitPlan& plan, int* launches_out) {
+  const int64_t chunk = plan.chunk;
   cudaError_t e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
   if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
   int launches = 1;
   if (opt.schedule != KF_SCHEDULE_GRID) {
-    e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * n_chunks, stream);
+    e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * plan.n_chunks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
   }
   if (opt.schedule == KF_SCHEDULE_SORTED) {
@@ -280,7 +309,7 @@ int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf
   p.out_status = out->status;
   p.out_states = out->states;
   p.ws64 = (double*)h->ws;
-  p.ws32 = opt.precision == KF_PRECISION_FP64 ? nullptr : (float*)((char*)h->ws + bytes64);
+  p.ws32 = opt.precision == KF_PRECISION_FP64 ? nullptr : (float*)((char*)h->ws + plan.bytes64);
   p.error_flag = h->error_flag;
   p.order = opt.schedule == KF_SCHEDULE_SORTED ? h->order : nullptr;
   int c = 0;
@@ -292,7 +321,181 @@ int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf
     if (e != cudaSuccess) return cuda_fail(e, "fit launch");
     ++launches;
   }
-  h->last_launches = launches;
+  *launches_out = launches;
+  return KF_SUCCESS;
+}
+
+// Everything that identifies a queued fit, for the graph cache.
+struct GraphKey {
+  kf_tracks tr;
+  kf_surfaces su;
+  kf_measurements me;
+  kf_field fi;
+  kf_options opt;
+  kf_outputs out;
+  void* stream;
+  // the handle's buffers the graph's kernels point into
+  const void* bufs[5];
+};
+static_assert(sizeof(GraphKey) <= 512, "graph key storage");
+
+GraphKey make_key(const kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
+                  const kf_field* fi, const kf_options& opt, const kf_outputs* out, void* stream) {
+  GraphKey k;
+  memset(&k, 0, sizeof(k));  // padding bytes take part in the comparison
+  k.tr = *tr;
+  k.su = *su;
+  k.me = *me;
+  k.fi = *fi;
+  k.opt = opt;
+  k.out = *out;
+  k.stream = stream;
+  k.bufs[0] = h->ws;
+  k.bufs[1] = h->surf;
+  k.bufs[2] = h->counters;
+  k.bufs[3] = h->order;
+  k.bufs[4] = h->hist;
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
+              const kf_field* fi, const kf_options* opt_in, const kf_outputs* out, void* stream_v) {
+  if (!h) return KF_EINVAL;
+  kf_options opt;
+  if (opt_in) opt = *opt_in; else kf_default_options(&opt);
+  int rc = validate(tr, su, me, fi, &opt, out);
+  if (rc) return rc;
+  h->last_launches = 0;
+  if (tr->n_tracks == 0) return KF_SUCCESS;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  if (opt.schedule == KF_SCHEDULE_AUTO) {
+    kf_options best;
+    if ((rc = kf_autotune(h, tr, su, me, fi, &opt, out, stream_v, &best, nullptr))) return rc;
+    opt.schedule = best.schedule;
+    opt.block = best.block;
+    opt.min_blocks = best.min_blocks;
+  }
+  FitPlan plan;
+  if ((rc = prepare_fit(h, tr, su, opt, &plan))) return rc;
+  if (!opt.use_graph) return enqueue_fit(h, tr, su, me, fi, opt, out, stream, plan, &h->last_launches);
+  // CUDA graph: replay when every argument matches the captured call
+  if (stream == nullptr) return KF_EUNSUPPORTED;  // the legacy stream cannot be captured
+  GraphKey key = make_key(h, tr, su, me, fi, opt, out, stream_v);
+  if (!h->graph_exec || memcmp(&key, h->graph_key, sizeof(key)) != 0) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    int launches = 0;
+    rc = enqueue_fit(h, tr, su, me, fi, opt, out, stream, plan, &launches);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->graph_exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    memcpy(h->graph_key, &key, sizeof(key));
+    h->graph_launches = launches;
+  }
+  cudaError_t e = cudaGraphLaunch(h->graph_exec, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  h->last_launches = h->graph_launches;
+  return KF_SUCCESS;
+}
+
+int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
+                const kf_field* fi, const kf_options* base_in, const kf_outputs* out, void* stream_v,
+                kf_options* best_out, double* best_ms) {
+  if (!h || !best_out) return KF_EINVAL;
+  kf_options base;
+  if (base_in) base = *base_in; else kf_default_options(&base);
+  base.schedule = KF_SCHEDULE_PERSISTENT;  // a valid placeholder for validation
+  int rc = validate(tr, su, me, fi, &base, out);
+  if (rc) return rc;
+  const int bz = fi->b[0] == 0.0 && fi->b[1] == 0.0;
+  for (int k = 0; k < h->n_tuned; ++k) {
+    const kf_handle::Tuned& c = h->tuned[k];
+    if (c.precision == base.precision && c.n_tracks == tr->n_tracks && c.max_states == tr->max_states &&
+        c.n_surfaces == su->n_surfaces && c.bz == bz) {
+      *best_out = base;
+      best_out->schedule = c.best.schedule;
+      best_out->block = c.best.block;
+      best_out->min_blocks = c.best.min_blocks;
+      if (best_ms) *best_ms = c.ms;
+      return KF_SUCCESS;
+    }
+  }
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    *best_out = base;  // no timing inside a capture: the default launch
+    if (best_ms) *best_ms = -1.0;
+    return KF_SUCCESS;
+  }
+  // candidate launch shapes: schedule x threads per CTA x register variant
+  const int schedules[3] = {KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED};
+  const int blocks[3] = {32, 64, 128};
+  const int mbs_mixed[2] = {0, 3};
+  const int n_mb = base.precision == KF_PRECISION_FP64 ? 1 : 2;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  }
+  kf_options best = base;
+  double best_t = 1e300;
+  for (int si = 0; si < 3 && rc == KF_SUCCESS; ++si)
+    for (int bi = 0; bi < 3 && rc == KF_SUCCESS; ++bi)
+      for (int mi = 0; mi < n_mb && rc == KF_SUCCESS; ++mi) {
+        kf_options o = base;
+        o.schedule = schedules[si];
+        o.block = blocks[bi];
+        o.min_blocks = base.precision == KF_PRECISION_FP64 ? 0 : mbs_mixed[mi];
+        o.use_graph = 0;
+        float times[3];
+        for (int r = -1; r < 3 && rc == KF_SUCCESS; ++r) {  // one warm-up, three timed
+          cudaEventRecord(e0, stream);
+          rc = kf_fit_ex(h, tr, su, me, fi, &o, out, stream_v);
+          cudaEventRecord(e1, stream);
+          cudaError_t e = cudaEventSynchronize(e1);
+          if (e != cudaSuccess) rc = cuda_fail(e, "autotune");
+          if (r >= 0 && rc == KF_SUCCESS) cudaEventElapsedTime(&times[r], e0, e1);
+        }
+        if (rc) break;
+        // median of three
+        float a = times[0], b = times[1], c = times[2];
+        const float med = a > b ? (b > c ? b : (a > c ? c : a)) : (a > c ? a : (b > c ? c : b));
+        if (med < best_t) {
+          best_t = med;
+          best = o;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  best.use_graph = base_in ? base_in->use_graph : 0;
+  kf_handle::Tuned& slot = h->tuned[h->n_tuned < 16 ? h->n_tuned++ : 15];
+  slot.precision = base.precision;
+  slot.n_tracks = tr->n_tracks;
+  slot.max_states = tr->max_states;
+  slot.n_surfaces = su->n_surfaces;
+  slot.bz = bz;
+  slot.best = best;
+  slot.ms = best_t;
+  *best_out = best;
+  if (best_ms) *best_ms = best_t;
   return KF_SUCCESS;
 }
 

@@ -130,6 +130,11 @@ struct Jac {
   R ft[5];     // time row over columns 0..4 (column 5 of that row is 1)
 };
 
+// element (r, c) of F for r in {0..3, 5}, c in 0..4 (a value select, so the
+// struct stays in registers when r and c are compile-time constants)
+template <typename R>
+__device__ __forceinline__ R jf(const Jac<R>& J, int r, int c) { return r == 5 ? J.ft[c] : J.f[r][c]; }
+
 template <typename R, bool BZ>
 __device__ __forceinline__ int transport(const Surf& sa, const Surf& sb, const double x[6], const double B[3],
                          double mass, double h_max, int n_iter, double xp[6], Jac<R>& J,
@@ -302,7 +307,7 @@ __device__ __forceinline__ int kalman_update(const double xp[6], const double Cp
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j) {
+    for (int j = 0; j < 6; ++j) if (j <= i) {
       double v = Cp[sy(i, j)];
       v = fma(K[i][0], W[0][j], v);
       v = fma(K[i][1], W[1][j], v);
@@ -378,22 +383,21 @@ __device__ __forceinline__ void fit_one_fp64(const FitParams& p, const double* s
             if (r == 4) {
               v = Cr[sym(4, j)];
             } else {
-              const R* fr = (r == 5) ? J.ft : J.f[r];
-              v = fr[0] * Cr[sym(0, j)] + fr[1] * Cr[sym(1, j)] + fr[2] * Cr[sym(2, j)] +
-                  fr[3] * Cr[sym(3, j)] + fr[4] * Cr[sym(4, j)];
+              v = jf(J, r, 0) * Cr[sym(0, j)] + jf(J, r, 1) * Cr[sym(1, j)] + jf(J, r, 2) * Cr[sym(2, j)] +
+                  jf(J, r, 3) * Cr[sym(3, j)] + jf(J, r, 4) * Cr[sym(4, j)];
               if (r == 5) v += Cr[sym(5, j)];
             }
             brow[j] = v;
             RC::put_bm(ws, k, r * 6 + j, brow[j]);
           }
 #pragma unroll
-          for (int c = 0; c <= r; ++c) {
+          for (int c = 0; c < 6; ++c) if (c <= r) {
             R v;
             if (c == 4) {
               v = brow[4];
             } else {
-              const R* fc = (c == 5) ? J.ft : J.f[c];
-              v = brow[0] * fc[0] + brow[1] * fc[1] + brow[2] * fc[2] + brow[3] * fc[3] + brow[4] * fc[4];
+              v = brow[0] * jf(J, c, 0) + brow[1] * jf(J, c, 1) + brow[2] * jf(J, c, 2) + brow[3] * jf(J, c, 3) +
+                  brow[4] * jf(J, c, 4);
               if (c == 5) v += brow[5];
             }
             Cpr[sy(r, c)] = v;
@@ -459,16 +463,16 @@ __device__ __forceinline__ void fit_one_fp64(const FitParams& p, const double* s
         for (int j = 0; j < 6; ++j) {
           double dj = L[sy(j, j)];
 #pragma unroll
-          for (int q = 0; q < j; ++q) dj -= L[sy(j, q)] * L[sy(j, q)];
+          for (int q = 0; q < 6; ++q) if (q < j) dj -= L[sy(j, q)] * L[sy(j, q)];
           if (!(dj > 0.0)) status = ST_NON_SPD;
           const double ljj = sqrt(dj);
           idg[j] = 1.0 / ljj;
           L[sy(j, j)] = ljj;
 #pragma unroll
-          for (int r = j + 1; r < 6; ++r) {
+          for (int r = 0; r < 6; ++r) if (r > j) {
             double v = L[sy(r, j)];
 #pragma unroll
-            for (int q = 0; q < j; ++q) v -= L[sy(r, q)] * L[sy(j, q)];
+            for (int q = 0; q < 6; ++q) if (q < j) v -= L[sy(r, q)] * L[sy(j, q)];
             L[sy(r, j)] = v * idg[j];
           }
         }
@@ -482,14 +486,14 @@ __device__ __forceinline__ void fit_one_fp64(const FitParams& p, const double* s
           for (int r = 0; r < 6; ++r) {
             double v = (double)RC::get_bm(ws, k + 1, r * 6 + c);
 #pragma unroll
-            for (int q = 0; q < r; ++q) v -= L[sy(r, q)] * y[q];
+            for (int q = 0; q < 6; ++q) if (q < r) v -= L[sy(r, q)] * y[q];
             y[r] = v * idg[r];
           }
 #pragma unroll
           for (int r = 5; r >= 0; --r) {
             double v = y[r];
 #pragma unroll
-            for (int q = r + 1; q < 6; ++q) v -= L[sy(q, r)] * X[q][c];
+            for (int q = 0; q < 6; ++q) if (q > r) v -= L[sy(q, r)] * X[q][c];
             X[r][c] = v * idg[r];
           }
         }
@@ -524,7 +528,7 @@ __device__ __forceinline__ void fit_one_fp64(const FitParams& p, const double* s
             z[c] = acc;
           }
 #pragma unroll
-          for (int c = 0; c <= r; ++c) {
+          for (int c = 0; c < 6; ++c) if (c <= r) {
             R acc = R(0);
 #pragma unroll
             for (int q = 0; q < 6; ++q) acc += z[q] * Ar[c][q];

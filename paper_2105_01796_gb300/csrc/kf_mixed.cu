@@ -63,6 +63,10 @@ struct JacF {
   float ft[5];    // time row over columns loc0..q/p
 };
 
+// element (r, c) of F for r in {0..3, 5}, c in 0..4 (a value select, so the
+// struct stays in registers when r and c are compile-time constants)
+__device__ __forceinline__ float jf(const JacF& J, int r, int c) { return r == 5 ? J.ft[c] : J.f[r][c]; }
+
 // G advance for one RKN4 step of length h (FP32): direction rows <- Stt g,
 // position rows += Srt g, plus the q/p column's dStt/dlam T, dSrt/dlam T.
 template <bool BZ>
@@ -464,21 +468,20 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
             if (r == 4) {
               v = Cr[sym(4, j)];
             } else {
-              const float* fr = (r == 5) ? J.ft : J.f[r];
-              v = fr[0] * Cr[sym(0, j)] + fr[1] * Cr[sym(1, j)] + fr[2] * Cr[sym(2, j)] + fr[3] * Cr[sym(3, j)] +
-                  fr[4] * Cr[sym(4, j)];
+              v = jf(J, r, 0) * Cr[sym(0, j)] + jf(J, r, 1) * Cr[sym(1, j)] + jf(J, r, 2) * Cr[sym(2, j)] +
+                  jf(J, r, 3) * Cr[sym(3, j)] + jf(J, r, 4) * Cr[sym(4, j)];
               if (r == 5) v += Cr[sym(5, j)];
             }
             brow[j] = v;
           }
 #pragma unroll
-          for (int c = 0; c <= r; ++c) {
+          for (int c = 0; c < 6; ++c) if (c <= r) {
             float v;
             if (c == 4) {
               v = brow[4];
             } else {
-              const float* fc = (c == 5) ? J.ft : J.f[c];
-              v = brow[0] * fc[0] + brow[1] * fc[1] + brow[2] * fc[2] + brow[3] * fc[3] + brow[4] * fc[4];
+              v = brow[0] * jf(J, c, 0) + brow[1] * jf(J, c, 1) + brow[2] * jf(J, c, 2) + brow[3] * jf(J, c, 3) +
+                  brow[4] * jf(J, c, 4);
               if (c == 5) v += brow[5];
             }
             Cpf[sy(r, c)] = v;
@@ -546,7 +549,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
 #pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-          for (int b = 0; b <= a; ++b) {
+          for (int b = 0; b < 6; ++b) if (b <= a) {
             double v = Cp[sy(a, b)];
             v = fma(K[a][0], W[0][b], v);
             v = fma(K[a][1], W[1][b], v);
@@ -590,17 +593,17 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         for (int j = 0; j < 6; ++j) {
           double dj = L[sy(j, j)];
 #pragma unroll
-          for (int q = 0; q < j; ++q) dj = fma(-L[sy(j, q)], L[sy(j, q)], dj);
+          for (int q = 0; q < 6; ++q) if (q < j) dj = fma(-L[sy(j, q)], L[sy(j, q)], dj);
           if (!dpos(dj)) {
             status = ST_NON_SPD;
             dj = 1.0;
           }
           idg[j] = rsqrt_nr<1>(dj);
 #pragma unroll
-          for (int r = j + 1; r < 6; ++r) {
+          for (int r = 0; r < 6; ++r) if (r > j) {
             double v = L[sy(r, j)];
 #pragma unroll
-            for (int q = 0; q < j; ++q) v = fma(-L[sy(r, q)], L[sy(j, q)], v);
+            for (int q = 0; q < 6; ++q) if (q < j) v = fma(-L[sy(r, q)], L[sy(j, q)], v);
             L[sy(r, j)] = v * idg[j];
           }
         }
@@ -617,7 +620,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
             } else {
               double v = (r == c) ? 1.0 : 0.0;
 #pragma unroll
-              for (int q = c; q < r; ++q) v = fma(-L[sy(r, q)], y[q], v);
+              for (int q = 0; q < 6; ++q) if (q >= c && q < r) v = fma(-L[sy(r, q)], y[q], v);
               y[r] = v * idg[r];
             }
           }
@@ -625,7 +628,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           for (int r = 5; r >= 0; --r) {
             double v = y[r];
 #pragma unroll
-            for (int q = r + 1; q < 6; ++q) v = fma(-L[sy(q, r)], w[cc][q], v);
+            for (int q = 0; q < 6; ++q) if (q > r) v = fma(-L[sy(q, r)], w[cc][q], v);
             w[cc][r] = v * idg[r];
           }
         }
@@ -677,7 +680,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           }
           const float a2 = Fi[r][2] * Npp + Fi[r][3] * Npt, a3 = Fi[r][2] * Npt + Fi[r][3] * Ntt;
 #pragma unroll
-          for (int c = 0; c <= r; ++c) {
+          for (int c = 0; c < 6; ++c) if (c <= r) {
             float acc = a2 * Fi[c][2] + a3 * Fi[c][3];
 #pragma unroll
             for (int q = 0; q < 6; ++q) acc += z[q] * A[c][q];

@@ -237,3 +237,64 @@ def test_every_launch_variant_agrees(handle, prec):
                         base = g
                     for k in ("params", "cov", "chi2", "ndf", "status"):
                         assert np.array_equal(g[k], base[k]), (sched, block, k)
+
+
+def test_graph_capture_and_replay(handle):
+    """use_graph: the first call captures the launches into a CUDA graph, the
+    next identical call replays it; results equal the plain launches bit for
+    bit; changing an argument re-captures."""
+    import torch
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 2500))
+    dev = kf.event_to_device(ev)
+    s = torch.cuda.Stream()
+    ref = gpu_fit(handle, ev, MIXED, schedule=kf.KF_SCHEDULE_SORTED)
+    opt = kf.kf_default_options(MIXED, schedule=kf.KF_SCHEDULE_SORTED, use_graph=1)
+    outs = [kf.alloc_outputs(ev["n_tracks"]) for _ in range(2)]
+    for out in (outs[0], outs[0], outs[1], outs[0]):   # capture, replay, re-capture, re-capture
+        for v in out.values():
+            if v is not None:
+                v.zero_()
+        with torch.cuda.stream(s):
+            kf.kf_fit_ex(handle, dev, out, opt, s)
+        s.synchronize()
+        assert handle.last_launch_count() == 5   # pack + 3 sort kernels + fit
+        for k in ("params", "cov", "chi2", "ndf", "status"):
+            assert np.array_equal(out[k].cpu().numpy(), ref[k])
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_autotuner_choice_is_valid_and_cached(handle, prec):
+    import time
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 20000))
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(ev["n_tracks"])
+    best, ms = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
+    assert ms > 0 and best.precision == prec
+    assert best.schedule in (0, 1, 2) and best.block in (32, 64, 128)
+    t0 = time.perf_counter()
+    best2, ms2 = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
+    assert time.perf_counter() - t0 < 0.05 and ms2 == ms       # cached
+    assert (best2.schedule, best2.block, best2.min_blocks) == (best.schedule, best.block, best.min_blocks)
+    # the fit with the tuned shape, and the AUTO schedule, agree with the oracle
+    rng = np.random.default_rng(3)
+    sample = np.sort(rng.choice(ev["n_tracks"], 1500, replace=False))
+    r = oracle.fit_batch(synth.subset(ev, sample))
+    for o in (best, kf.kf_default_options(prec, schedule=kf.KF_SCHEDULE_AUTO)):
+        g = gpu_fit(handle, ev, prec, schedule=o.schedule, block=o.block, min_blocks=o.min_blocks)
+        compare({k: (v[..., sample] if v is not None else None) for k, v in g.items()}, r, prec)
+
+
+def test_full_size_uneven_1m_sampled(handle):
+    """1,000,000 uneven tracks with holes in one persistent launch with the
+    autotuner's launch shape (mixed precision); oracle on a 1500-track sample."""
+    ev = synth.make_event(synth.WORKLOADS["uneven30_1m"])
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(ev["n_tracks"])
+    best, _ = kf.kf_autotune(handle, dev, out, kf.kf_default_options(MIXED))
+    g = gpu_fit(handle, ev, MIXED, schedule=best.schedule, block=best.block, min_blocks=best.min_blocks)
+    assert handle.last_launch_count() <= 5       # pack (+ sort) + one fit launch
+    rng = np.random.default_rng(9)
+    sample = np.sort(rng.choice(ev["n_tracks"], 1500, replace=False))
+    r = oracle.fit_batch(synth.subset(ev, sample))
+    compare({k: (v[..., sample] if v is not None else None) for k, v in g.items()}, r, MIXED)
+    assert np.all(g["status"] == 0)

@@ -36,8 +36,8 @@ namespace kfgb {
 namespace {
 using namespace dev;
 
-constexpr int XP = 0, XF = 6, CP = 12;  // ws64 record fields
-constexpr int FJ = 0, QPHI = 25, QTH = 26;  // ws32 record fields
+constexpr int XP = 0, CP = 6;  // ws64 record fields
+constexpr int FJ = 0, QPHI = 25, QTH = 26, DXF = 27;  // ws32 record fields
 
 struct WSM {
   double* w64;
@@ -145,13 +145,11 @@ __device__ __forceinline__ void rotate(double& c, double& s, float delta) {
 
 // Transport the filtered state (x, d) on surface a to surface b.
 template <bool BZ>
-__device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, const double x[6], const Dir& d,
-                               const float Bf[3], float m2, float h_max, int n_iter, double xp[6], Dir& dp,
-                               JacF& J, float& sin_th, float& cos_inc) {
-  // start point (FP64 accumulators)
-  double r[3], T[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) r[i] = fma(x[1], sa.v(i), fma(x[0], sa.u(i), sa.c(i)));
+__device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, const double r0[3], const double x[6],
+                               const Dir& d, const float Bf[3], float m2, float h_max, int n_iter, double xp[6],
+                               double rp[3], Dir& dp, JacF& J, float& sin_th, float& cos_inc) {
+  // start point (FP64 accumulators): the filtered point on surface a
+  double r[3] = {r0[0], r0[1], r0[2]}, T[3];
   T[0] = d.cp * d.st;
   T[1] = d.sp * d.st;
   T[2] = d.ct;
@@ -256,6 +254,9 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     const float cdt = d2f(dp.st) * d2f(d.st) + d2f(dp.ct) * d2f(d.ct);
     dp.theta = angle_step(d.theta, sdt, cdt, dp.st, dp.ct);
   }
+  rp[0] = r[0];
+  rp[1] = r[1];
+  rp[2] = r[2];
   xp[0] = fma(sb.u(2), r[2], fma(sb.u(1), r[1], fma(sb.u(0), r[0], -sb.uc())));
   xp[1] = fma(sb.v(2), r[2], fma(sb.v(1), r[1], fma(sb.v(0), r[0], -sb.vc())));
   xp[2] = dp.phi;
@@ -397,6 +398,88 @@ __device__ __forceinline__ void invert_F(const float F[25], float Fi[6][6]) {
   Fi[5][5] = 1.0f;
 }
 
+// Columns phi and theta of Cp^-1 in FP64, by block elimination with the
+// angle block last: a = (loc0, loc1, q/p, t), b = (phi, theta).
+//   X = Caa^-1 Cab (4x4 Cholesky, two solves), Sig = Cbb - Cab^T X (the 2x2
+//   Schur complement), then (Cp^-1)[b][b] = Sig^-1, (Cp^-1)[a][b] = -X Sig^-1.
+// Cp is SPD iff the four pivots of Caa and Sig are positive.  Returns false
+// otherwise.  w[0] = Cp^-1 e_phi, w[1] = Cp^-1 e_theta (6 each).
+__device__ __forceinline__ bool angle_columns_of_inverse(const double Cp[21], double w[2][6]) {
+  constexpr int ia[4] = {0, 1, 4, 5};
+  double L[4][4], idg[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) L[r][c] = Cp[sym(ia[r], ia[c])];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    double dj = L[j][j];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < j) dj = fma(-L[j][q], L[j][q], dj);
+    if (!dpos(dj)) {
+      ok = false;
+      dj = 1.0;
+    }
+    idg[j] = rsqrt_nr<1>(dj);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (r > j) {
+        double v = L[r][j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < j) v = fma(-L[r][q], L[j][q], v);
+        L[r][j] = v * idg[j];
+      }
+    }
+  }
+  double X[4][2];
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    double y[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      double v = Cp[sym(ia[r], 2 + m)];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < r) v = fma(-L[r][q], y[q], v);
+      y[r] = v * idg[r];
+    }
+#pragma unroll
+    for (int r = 3; r >= 0; --r) {
+      double v = y[r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q > r) v = fma(-L[q][r], X[q][m], v);
+      X[r][m] = v * idg[r];
+    }
+  }
+  double s00 = Cp[sy(2, 2)], s01 = Cp[sy(3, 2)], s11 = Cp[sy(3, 3)];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    s00 = fma(-Cp[sym(ia[r], 2)], X[r][0], s00);
+    s01 = fma(-Cp[sym(ia[r], 2)], X[r][1], s01);
+    s11 = fma(-Cp[sym(ia[r], 3)], X[r][1], s11);
+  }
+  const double det = fma(s00, s11, -s01 * s01);
+  if (!dpos(det) || !dpos(s00)) {
+    ok = false;
+  }
+  const double idet = rcp_nr<1>(det);
+  const double i00 = s11 * idet, i01 = -s01 * idet, i11 = s00 * idet;
+  w[0][2] = i00;
+  w[0][3] = i01;
+  w[1][2] = i01;
+  w[1][3] = i11;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    w[0][ia[r]] = -fma(X[r][0], i00, X[r][1] * i01);
+    w[1][ia[r]] = -fma(X[r][0], i01, X[r][1] * i11);
+  }
+  return ok;
+}
+
 template <bool BZ>
 __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* s_surf, int i) {
   const int t = track_of(p, i);
@@ -424,7 +507,11 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
   int nmeas = 0;
   if (status == ST_OK) {
     // ------------------------------------------------ forward filter
-    double x[6], C[21];
+    // x[2..5] (phi, theta, q/p, t) are FP64 accumulators; the position is
+    // carried as the FP64 point r on the current surface (loc0/loc1 of the
+    // filtered state are r's local coordinates).
+    double x[6], C[21], r[3];
+    float dx[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // x_f - x_p of the last state
 #pragma unroll
     for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TT + t];
 #pragma unroll
@@ -435,9 +522,14 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
     sincos(x[2], &d.sp, &d.cp);  // the only FP64 trigonometry of the track
     sincos(x[3], &d.st, &d.ct);
     int sid_prev = p.surface_id[o0];
+    {
+      const Surf s0{s_surf + sid_prev * kSurfStride};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r[c] = fma(x[1], s0.v(c), fma(x[0], s0.u(c), s0.c(c)));
+    }
     for (int k = 0; k < n && status == ST_OK; ++k) {
       const int sid = p.surface_id[o0 + k];
-      double xp[6], Cp[21];
+      double xp[6], Cp[21], rp[3];
       float Cpf[21];
       Dir dp;
       if (k == 0) {
@@ -448,44 +540,47 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           Cp[e] = C[e];
           Cpf[e] = d2f(C[e]);
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rp[c] = r[c];
         dp = d;
       } else {
         const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
         JacF J;
         float sin_th, cos_inc;
-        status = transport_mixed<BZ>(sa, sb, x, d, Bf, m2, h_max, p.n_iter, xp, dp, J, sin_th, cos_inc);
+        status = transport_mixed<BZ>(sa, sb, r, x, d, Bf, m2, h_max, p.n_iter, xp, rp, dp, J, sin_th, cos_inc);
         if (status != ST_OK) break;
         float Cr[21];
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cr[e] = d2f(C[e]);
         // Cp = F Cf F^T, rows of Bm = F Cf formed on the fly
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
+        for (int a = 0; a < 6; ++a) {
           float brow[6];
 #pragma unroll
           for (int j = 0; j < 6; ++j) {
             float v;
-            if (r == 4) {
+            if (a == 4) {
               v = Cr[sym(4, j)];
             } else {
-              v = jf(J, r, 0) * Cr[sym(0, j)] + jf(J, r, 1) * Cr[sym(1, j)] + jf(J, r, 2) * Cr[sym(2, j)] +
-                  jf(J, r, 3) * Cr[sym(3, j)] + jf(J, r, 4) * Cr[sym(4, j)];
-              if (r == 5) v += Cr[sym(5, j)];
+              v = jf(J, a, 0) * Cr[sym(0, j)] + jf(J, a, 1) * Cr[sym(1, j)] + jf(J, a, 2) * Cr[sym(2, j)] +
+                  jf(J, a, 3) * Cr[sym(3, j)] + jf(J, a, 4) * Cr[sym(4, j)];
+              if (a == 5) v += Cr[sym(5, j)];
             }
             brow[j] = v;
           }
 #pragma unroll
-          for (int c = 0; c < 6; ++c) if (c <= r) {
-            float v;
-            if (c == 4) {
-              v = brow[4];
-            } else {
-              v = brow[0] * jf(J, c, 0) + brow[1] * jf(J, c, 1) + brow[2] * jf(J, c, 2) + brow[3] * jf(J, c, 3) +
-                  brow[4] * jf(J, c, 4);
-              if (c == 5) v += brow[5];
+          for (int c = 0; c < 6; ++c)
+            if (c <= a) {
+              float v;
+              if (c == 4) {
+                v = brow[4];
+              } else {
+                v = brow[0] * jf(J, c, 0) + brow[1] * jf(J, c, 1) + brow[2] * jf(J, c, 2) +
+                    brow[3] * jf(J, c, 3) + brow[4] * jf(J, c, 4);
+                if (c == 5) v += brow[5];
+              }
+              Cpf[sy(a, c)] = v;
             }
-            Cpf[sy(r, c)] = v;
-          }
         }
         // multiple scattering of surface k, added before the update
         float qphi = 0.0f, qth = 0.0f;
@@ -510,6 +605,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
       for (int e = 0; e < 6; ++e) ws.d(k, XP + e) = xp[e];
 #pragma unroll
       for (int e = 0; e < 21; ++e) ws.d(k, CP + e) = Cp[e];
+      const Surf sk{s_surf + sid * kSurfStride};
       if (!p.is_hole[o0 + k]) {
         // gain-matrix update: gain in FP32, Joseph covariance and chi2 in FP64
         const double m0 = p.loc[o0 + k], m1 = p.loc[p.n_states + o0 + k];
@@ -529,7 +625,6 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         const float i00 = d2f(S11) * idf, i01 = -d2f(S01) * idf, i11 = d2f(S00) * idf;
         const float r0f = d2f(r0), r1f = d2f(r1);
         double K[6][2];
-        float dx[6];
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
           const float c0 = Cpf[sym(e, 0)], c1 = Cpf[sym(e, 1)];
@@ -537,7 +632,6 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           K[e][0] = f2d(k0);
           K[e][1] = f2d(k1);
           dx[e] = k0 * r0f + k1 * r1f;
-          x[e] = xp[e] + f2d(dx[e]);
         }
         // Joseph form, expanded: Cf = Cp + K W - (H Cp)^T K^T, W = S K^T - H Cp
         double W[2][6];
@@ -549,14 +643,21 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
 #pragma unroll
         for (int a = 0; a < 6; ++a)
 #pragma unroll
-          for (int b = 0; b < 6; ++b) if (b <= a) {
-            double v = Cp[sy(a, b)];
-            v = fma(K[a][0], W[0][b], v);
-            v = fma(K[a][1], W[1][b], v);
-            v = fma(-Cp[sym(0, a)], K[b][0], v);
-            v = fma(-Cp[sym(1, a)], K[b][1], v);
-            C[sy(a, b)] = v;
-          }
+          for (int b = 0; b < 6; ++b)
+            if (b <= a) {
+              double v = Cp[sy(a, b)];
+              v = fma(K[a][0], W[0][b], v);
+              v = fma(K[a][1], W[1][b], v);
+              v = fma(-Cp[sym(0, a)], K[b][0], v);
+              v = fma(-Cp[sym(1, a)], K[b][1], v);
+              C[sy(a, b)] = v;
+            }
+        // the filtered point: the predicted point moved in the plane by
+        // (dx0, dx1); angles, q/p and t receive their increments
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = rp[c] + f2d(dx[0] * sk.uf(c) + dx[1] * sk.vf(c));
+#pragma unroll
+        for (int e = 2; e < 6; ++e) x[e] = xp[e] + f2d(dx[e]);
         d = dp;
         d.phi = x[2];
         d.theta = x[3];
@@ -564,73 +665,43 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         rotate(d.ct, d.st, dx[3]);
       } else {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) x[e] = xp[e];
+        for (int e = 0; e < 6; ++e) {
+          x[e] = xp[e];
+          dx[e] = 0.0f;
+        }
 #pragma unroll
         for (int e = 0; e < 21; ++e) C[e] = Cp[e];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = rp[c];
         d = dp;
       }
 #pragma unroll
-      for (int e = 0; e < 6; ++e) ws.d(k, XF + e) = x[e];
+      for (int e = 0; e < 6; ++e) ws.f(k, DXF + e) = dx[e];
       sid_prev = sid;
     }
 
     // ------------------------------------------------ RTS smoother
+    // The recursion runs on FP32 offsets: with dxf_k = x_f,k - x_p,k (the
+    // filter increment) and off_k = x_s,k - x_f,k,
+    //   x_s,k+1 - x_p,k+1 = dxf_{k+1} + off_{k+1},  off_k = A_k (that),
+    // and x_s,k = x_p,k + dxf_k + off_k is formed in FP64 only for output.
     if (status == ST_OK) {
       float Cs[21];
-#pragma unroll
-      for (int e = 0; e < 6; ++e) xs[e] = x[e];
+      float off[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int e = 0; e < 21; ++e) Cs[e] = d2f(C[e]);
       if (p.out_states)
 #pragma unroll
-        for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + n - 1] = xs[e];
+        for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + n - 1] = ws.d(n - 1, XP + e) + f2d(dx[e]);
       for (int k = n - 2; k >= 0 && status == ST_OK; --k) {
-        // FP64 Cholesky of Cp_{k+1} and the (phi, theta) columns of its inverse
-        double L[21], idg[6];
+        // FP64: the (phi, theta) columns of Cp_{k+1}^-1
+        double Cp1[21];
 #pragma unroll
-        for (int e = 0; e < 21; ++e) L[e] = ws.d(k + 1, CP + e);
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          double dj = L[sy(j, j)];
-#pragma unroll
-          for (int q = 0; q < 6; ++q) if (q < j) dj = fma(-L[sy(j, q)], L[sy(j, q)], dj);
-          if (!dpos(dj)) {
-            status = ST_NON_SPD;
-            dj = 1.0;
-          }
-          idg[j] = rsqrt_nr<1>(dj);
-#pragma unroll
-          for (int r = 0; r < 6; ++r) if (r > j) {
-            double v = L[sy(r, j)];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) if (q < j) v = fma(-L[sy(r, q)], L[sy(j, q)], v);
-            L[sy(r, j)] = v * idg[j];
-          }
-        }
-        if (status != ST_OK) break;
+        for (int e = 0; e < 21; ++e) Cp1[e] = ws.d(k + 1, CP + e);
         double w[2][6];
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int c = 2 + cc;
-          double y[6];
-#pragma unroll
-          for (int r = 0; r < 6; ++r) {
-            if (r < c) {
-              y[r] = 0.0;
-            } else {
-              double v = (r == c) ? 1.0 : 0.0;
-#pragma unroll
-              for (int q = 0; q < 6; ++q) if (q >= c && q < r) v = fma(-L[sy(r, q)], y[q], v);
-              y[r] = v * idg[r];
-            }
-          }
-#pragma unroll
-          for (int r = 5; r >= 0; --r) {
-            double v = y[r];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) if (q > r) v = fma(-L[sy(q, r)], w[cc][q], v);
-            w[cc][r] = v * idg[r];
-          }
+        if (!angle_columns_of_inverse(Cp1, w)) {
+          status = ST_NON_SPD;
+          break;
         }
         // noise-rank pieces: Q Cp^-1 rows (phi, theta) and N = Q - Q Cp^-1 Q
         const float qp = ws.f(k + 1, QPHI), qt = ws.f(k + 1, QTH);
@@ -652,48 +723,64 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         invert_F(Fr, Fi);
         float A[6][6];
 #pragma unroll
-        for (int r = 0; r < 6; ++r)
+        for (int a = 0; a < 6; ++a)
 #pragma unroll
-          for (int c = 0; c < 6; ++c) A[r][c] = Fi[r][c] - Fi[r][2] * qw[0][c] - Fi[r][3] * qw[1][c];
-        // xs_k = xf_k + A (xs_{k+1} - xp_{k+1})
-        float df[6];
+          for (int c = 0; c < 6; ++c) A[a][c] = Fi[a][c] - Fi[a][2] * qw[0][c] - Fi[a][3] * qw[1][c];
+        // off_k = A (dxf_{k+1} + off_{k+1})
+        float dd[6];
 #pragma unroll
-        for (int e = 0; e < 6; ++e) df[e] = d2f(xs[e] - ws.d(k + 1, XP + e));
+        for (int e = 0; e < 6; ++e) dd[e] = ws.f(k + 1, DXF + e) + off[e];
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
+        for (int a = 0; a < 6; ++a) {
           float acc = 0.0f;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) acc += A[r][c] * df[c];
-          xs[r] = ws.d(k, XF + r) + f2d(acc);
+          for (int c = 0; c < 6; ++c) acc += A[a][c] * dd[c];
+          off[a] = acc;
         }
         // Cs_k = F^-1 N F^-T (N on the (phi, theta) block) + A Cs_{k+1} A^T
         float Cn[21];
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
+        for (int a = 0; a < 6; ++a) {
           float z[6];
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
             float acc = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc += A[r][q] * Cs[sym(q, c)];
+            for (int q = 0; q < 6; ++q) acc += A[a][q] * Cs[sym(q, c)];
             z[c] = acc;
           }
-          const float a2 = Fi[r][2] * Npp + Fi[r][3] * Npt, a3 = Fi[r][2] * Npt + Fi[r][3] * Ntt;
+          const float a2 = Fi[a][2] * Npp + Fi[a][3] * Npt, a3 = Fi[a][2] * Npt + Fi[a][3] * Ntt;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) if (c <= r) {
-            float acc = a2 * Fi[c][2] + a3 * Fi[c][3];
+          for (int c = 0; c < 6; ++c)
+            if (c <= a) {
+              float acc = a2 * Fi[c][2] + a3 * Fi[c][3];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) acc += z[q] * A[c][q];
-            Cn[sy(r, c)] = acc;
-          }
+              for (int q = 0; q < 6; ++q) acc += z[q] * A[c][q];
+              Cn[sy(a, c)] = acc;
+            }
         }
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cs[e] = Cn[e];
-        if (p.out_states)
+        if (p.out_states || k == 0) {
+          float tot[6];
 #pragma unroll
-          for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + k] = xs[e];
+          for (int e = 0; e < 6; ++e) tot[e] = ws.f(k, DXF + e) + off[e];
+#pragma unroll
+          for (int e = 0; e < 6; ++e) xs[e] = ws.d(k, XP + e) + f2d(tot[e]);
+          if (p.out_states)
+#pragma unroll
+            for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + k] = xs[e];
+        }
       }
       if (n == 1) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) xs[e] = x[e];
+        xs[0] = p.seed_params[0 * TT + t];
+        xs[1] = p.seed_params[1 * TT + t];
+        if (!p.is_hole[o0]) {
+          xs[0] += f2d(dx[0]);
+          xs[1] += f2d(dx[1]);
+        }
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cs_out[e] = C[e];
       } else {

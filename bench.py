@@ -161,6 +161,7 @@ def run_ours(args, rank, world, local):
     import torch
     import paper_2105_01796_gb300 as kf
     from paper_2105_01796_gb300 import _build, roofline, synth
+    from paper_2105_01796_gb300 import dist as kdist
 
     torch.cuda.set_device(local)
     dist = None
@@ -224,11 +225,7 @@ def run_ours(args, rank, world, local):
         sampler.start()
     ms, launches, wall, st = timed(args.precision, args.steps, args.warmup)
     clocks = sampler.stop() if sampler else None
-    step_ms = float(np.mean(ms))
-    if dist is not None:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = kdist.max_over_ranks(float(np.mean(ms)), device="cuda")
     value = world * T / (step_ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -261,11 +258,7 @@ def run_ours(args, rank, world, local):
             e_ms.append(1e3 * (time.perf_counter() - t0))
         h2d = sum(hev[k].nbytes for k in kf._HOST_DTYPES)
         d2h = sum(v.nbytes for v in outs.values() if v is not None)
-        e2e_ms = float(np.mean(e_ms))
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = kdist.max_over_ranks(float(np.mean(e_ms)), device="cuda")
         e2e = {"value": world * T / (e2e_ms / 1e3), "unit": "tracks/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e2e_ms}

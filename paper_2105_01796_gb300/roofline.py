@@ -27,8 +27,10 @@ FP64 path (everything in double precision):
 
 Mixed path: the double-precision part the method requires is
     per measured state   JOSEPH + CHI2
-    per smoother step    CHOL + SOLVE2 + NRANK   (the (phi, theta) columns of
-                         Cp^-1 and N = Q - Q Cp^-1 Q)
+    per smoother step    INV_COLS + NRANK   (the (phi, theta) columns of
+                         Cp^-1 by a 4x4 Cholesky of the loc/q/p/t block, two
+                         solves and the 2x2 Schur complement of the angle
+                         block; N = Q - Q Cp^-1 Q)
 and everything else runs in FP32 (counted as fp32 work).
 """
 
@@ -42,6 +44,10 @@ CHI2 = 16
 CHOL = 2 * 35 + 15 + 6
 SOLVE6 = 6 * 2 * 36
 SOLVE2 = 48 + 42
+# 4x4 Cholesky (6 FMA, 4 rsqrt, 4 FMA + 6 mul), two solve pairs (2 x 32),
+# Schur complement (12 FMA), its inverse (det 3, 1/det 1, 3 mul), off-block
+# columns (8 x (FMA + mul) + 8 negations folded) -> flops
+INV_COLS = (2 * 6 + 4 + 2 * 4 + 6) + 2 * 32 + 2 * 12 + 7 + 8 * 3
 NRANK = 7
 RTS_UPD = 84 + 21 + 2 * 216 + 2 * 126 + 21
 # FP32 side of the mixed smoother: F^-1 (block form), gain A, xs, Cs
@@ -65,7 +71,7 @@ def batch_flops(offsets, is_hole, precision, steps_per_transition=4):
     prop = tr * (steps_per_transition * RKN_STEP + FRAME + TRANSPORT + NOISE)
     if precision == 0:
         return prop + M * (GAIN + JOSEPH) + tr * (CHOL + SOLVE6 + RTS_UPD), 0
-    f64 = M * (JOSEPH + CHI2) + tr * (CHOL + SOLVE2 + NRANK)
+    f64 = M * (JOSEPH + CHI2) + tr * (INV_COLS + NRANK)
     f32 = prop + M * (GAIN - CHI2) + tr * MIXED_SMOOTH_FP32
     return f64, f32
 

@@ -225,6 +225,29 @@ int kf_autotune(kf_handle* handle, const kf_tracks* tracks,
                 const kf_outputs* out, void* stream, kf_options* best,
                 double* best_ms);
 
+/* Gradient of the summed chi2 (the adjoint of the filter).
+ * L = sum_t w_t chi2_t with w_t = dl_dchi2[t] (NULL: all 1); chi2_t as
+ * returned by kf_fit (predicted-residual chi2, which the smoother does not
+ * change).  Computed in FP64 whatever opt->precision says.
+ *   align[6][S]       alignment of every surface (NULL: all zero): shifts
+ *                     (du, dv, dn) along the surface's local axes, then
+ *                     rotations (alpha, beta, gamma) about them:
+ *                     c' = c + R (du, dv, dn), R' = R Ru(alpha) Rv(beta) Rn(gamma).
+ *   out_chi2[T]       chi2 per track at this alignment (optional).
+ *   grad_seed[6][T]   dL/d seed_params (optional).
+ *   grad_align[6][S]  dL/d align (optional); overwritten.
+ * Method: reverse sweep over the states with the filtered states recomputed
+ * from checkpoints every 8 states; inside each transport, forward-mode dual
+ * numbers give the sensitivities of the prediction, of F and of the
+ * scattering noise.  Device pointers; asynchronous on `stream`.  Tracks that
+ * fail get NaN chi2 and gradients and do not contribute to grad_align. */
+int kf_chi2_grad(kf_handle* handle, const kf_tracks* tracks,
+                 const kf_surfaces* surfaces, const double* align,
+                 const kf_measurements* meas, const kf_field* field,
+                 const kf_options* opt, const double* dl_dchi2,
+                 double* out_chi2, double* grad_seed, double* grad_align,
+                 void* stream);
+
 /* Bytes of device workspace kf_fit_ex would use for this batch shape. */
 int64_t kf_workspace_size(int32_t n_tracks, int32_t max_states,
                           const kf_options* opt);

@@ -231,3 +231,69 @@ def unpack_sym(packed):
 
 def pack_sym(C):
     return np.array([C[i, j] for i in range(6) for j in range(i + 1)])
+
+
+# ---------------------------------------------------------------------------
+# alignment and the gradient of the summed chi2 (finite differences)
+# ---------------------------------------------------------------------------
+
+def apply_alignment(center, rot, align):
+    """Aligned geometry: c' = c + R (du, dv, dn) and
+    R' = R Ru(alpha) Rv(beta) Rn(gamma), rotations about the plane's own
+    local axes u, v, n.  center [3][S], rot [9][S], align [6][S]."""
+    center = np.asarray(center, dtype=np.float64)
+    rot = np.asarray(rot, dtype=np.float64)
+    S = center.shape[1]
+    c2 = np.empty_like(center)
+    r2 = np.empty_like(rot)
+    for s in range(S):
+        R = rot[:, s].reshape(3, 3)
+        du, dv, dn, al, be, ga = [float(v) for v in align[:, s]]
+        Ru = np.array([[1.0, 0.0, 0.0], [0.0, np.cos(al), -np.sin(al)], [0.0, np.sin(al), np.cos(al)]])
+        Rv = np.array([[np.cos(be), 0.0, np.sin(be)], [0.0, 1.0, 0.0], [-np.sin(be), 0.0, np.cos(be)]])
+        Rn = np.array([[np.cos(ga), -np.sin(ga), 0.0], [np.sin(ga), np.cos(ga), 0.0], [0.0, 0.0, 1.0]])
+        c2[:, s] = center[:, s] + R @ np.array([du, dv, dn])
+        r2[:, s] = (R @ Ru @ Rv @ Rn).ravel()
+    return c2, r2
+
+
+def chi2_per_track(ev, align=None, seed_params=None, **kw):
+    """chi2 of every track with the geometry aligned by `align` [6][S]."""
+    e = dict(ev)
+    if align is not None:
+        e["center"], e["rot"] = apply_alignment(ev["center"], ev["rot"], align)
+    if seed_params is not None:
+        e["seed_params"] = seed_params
+    return fit_batch(e, **kw)["chi2"]
+
+
+def chi2_gradient_fd(ev, align=None, weights=None, h_shift=1e-6, h_rot=1e-6, h_seed=1e-6, n_threads=None):
+    """Gradient of L = sum_t w_t chi2_t by central finite differences of the
+    oracle (the plain definition of the derivative).  Returns
+    (grad_seed [6][T], grad_align [6][S]).  Steps are in the parameters'
+    units (mm, rad, GeV^-1, ns); the q/p step is relative to |q/p|."""
+    T = int(ev["n_tracks"])
+    S = ev["center"].shape[1]
+    a0 = np.zeros((6, S)) if align is None else np.asarray(align, dtype=np.float64)
+    w = np.ones(T) if weights is None else np.asarray(weights, dtype=np.float64)
+    seeds = np.asarray(ev["seed_params"], dtype=np.float64)
+    gs = np.zeros((6, T))
+    for i in range(6):
+        hv = np.full(T, h_seed)
+        if i == 4:
+            hv = h_seed * np.abs(seeds[4])
+        sp = seeds.copy(); sp[i] += hv
+        sm = seeds.copy(); sm[i] -= hv
+        cp = chi2_per_track(ev, a0, sp, n_threads=n_threads)
+        cm = chi2_per_track(ev, a0, sm, n_threads=n_threads)
+        gs[i] = w * (cp - cm) / (2 * hv)
+    ga = np.zeros((6, S))
+    for s in range(S):
+        for e in range(6):
+            h = h_shift if e < 3 else h_rot
+            ap = a0.copy(); ap[e, s] += h
+            am = a0.copy(); am[e, s] -= h
+            cp = chi2_per_track(ev, ap, n_threads=n_threads)
+            cm = chi2_per_track(ev, am, n_threads=n_threads)
+            ga[e, s] = np.sum(w * (cp - cm)) / (2 * h)
+    return gs, ga

@@ -30,7 +30,7 @@ MUON_MASS = 0.1056583755
 EXPORTS = ("kf_default_options", "kf_create", "kf_destroy", "kf_fit", "kf_fit_ex",
            "kf_fit_host", "kf_workspace_size", "kf_last_launch_count", "kf_strerror",
            "kf_last_cuda_error", "kf_abi_version", "kf_selftest", "kf_fit_static",
-           "kf_autotune")
+           "kf_autotune", "kf_chi2_grad")
 
 
 class KfTracks(ctypes.Structure):
@@ -108,6 +108,10 @@ def load(path: str = LIB_PATH):
         lib.kf_last_cuda_error.restype = ctypes.c_char_p
         lib.kf_abi_version.argtypes = []
         lib.kf_abi_version.restype = ctypes.c_int
+        lib.kf_chi2_grad.argtypes = [P, ctypes.POINTER(KfTracks), ctypes.POINTER(KfSurfaces), P,
+                                     ctypes.POINTER(KfMeasurements), ctypes.POINTER(KfField),
+                                     ctypes.POINTER(KfOptions), P, P, P, P, P]
+        lib.kf_chi2_grad.restype = ctypes.c_int
         lib.kf_autotune.argtypes = [P] + base + [ctypes.POINTER(KfOptions), ctypes.POINTER(KfOutputs), P,
                                                  ctypes.POINTER(KfOptions), ctypes.POINTER(ctypes.c_double)]
         lib.kf_autotune.restype = ctypes.c_int
@@ -326,3 +330,64 @@ def kf_fit_host(handle: Handle, ev, opt: KfOptions | None = None, out=None, stre
                               ctypes.byref(fi), ctypes.byref(opt) if opt is not None else None,
                               ctypes.byref(o), ctypes.c_void_p(int(stream or 0))))
     return out
+
+
+def kf_chi2_grad(handle: Handle, dev_ev, align=None, dl_dchi2=None, out_chi2=None, grad_seed=None,
+                 grad_align=None, opt: KfOptions | None = None, stream=None):
+    """chi2 per track and the gradient of sum_t w_t chi2_t (w = dl_dchi2, default
+    1) with respect to the seeds (grad_seed [6][T]) and the per-surface
+    alignment (grad_align [6][S]).  Device tensors; None outputs are skipped."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    tr, su, me, fi = _structs(dev_ev, dev_ev["max_states"])
+    _check(load().kf_chi2_grad(handle.ptr, ctypes.byref(tr), ctypes.byref(su), _ptr(align), ctypes.byref(me),
+                               ctypes.byref(fi), ctypes.byref(opt) if opt is not None else None,
+                               _ptr(dl_dchi2), _ptr(out_chi2), _ptr(grad_seed), _ptr(grad_align),
+                               ctypes.c_void_p(int(stream))))
+
+
+def _chi2_function():
+    import torch
+
+    class KalmanChi2(torch.autograd.Function):
+        """chi2 per track of the Kalman fit as a differentiable function of
+        the seed parameters [6][T] and the surface alignment [6][S]; the
+        backward pass is the library's adjoint kernel (kf_chi2_grad)."""
+
+        @staticmethod
+        def forward(ctx, seed_params, align, dev_ev, handle):
+            ev = dict(dev_ev)
+            ev["seed_params"] = seed_params.detach().contiguous()
+            chi2 = torch.empty(int(ev["n_tracks"]), dtype=torch.float64, device=seed_params.device)
+            kf_chi2_grad(handle, ev, align=align.detach().contiguous(), out_chi2=chi2)
+            ctx.save_for_backward(seed_params.detach(), align.detach())
+            ctx.ev = dev_ev
+            ctx.handle = handle
+            return chi2
+
+        @staticmethod
+        def backward(ctx, g):
+            seed_params, align = ctx.saved_tensors
+            ev = dict(ctx.ev)
+            ev["seed_params"] = seed_params.contiguous()
+            gs = torch.empty_like(seed_params) if ctx.needs_input_grad[0] else None
+            ga = torch.empty_like(align) if ctx.needs_input_grad[1] else None
+            kf_chi2_grad(ctx.handle, ev, align=align.contiguous(), dl_dchi2=g.contiguous().to(torch.float64),
+                         grad_seed=gs, grad_align=ga)
+            return gs, ga, None, None
+
+    return KalmanChi2
+
+
+_CHI2_FN = None
+
+
+def chi2_autograd(seed_params, align, dev_ev, handle):
+    """Differentiable chi2 per track (torch.autograd), see KalmanChi2."""
+    global _CHI2_FN
+    if _CHI2_FN is None:
+        _CHI2_FN = _chi2_function()
+    return _CHI2_FN.apply(seed_params, align, dev_ev, handle)

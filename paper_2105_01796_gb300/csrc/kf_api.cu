@@ -27,6 +27,9 @@ struct kf_handle {
   int64_t order_cap = 0;
   int32_t* hist = nullptr;
   int hist_cap = 0;
+  // adjoint checkpoints
+  double* ckpt = nullptr;
+  size_t ckpt_bytes = 0;
   // autotuner cache: best launch options per batch shape
   struct Tuned {
     int32_t precision, n_tracks, max_states, n_surfaces, bz;
@@ -200,6 +203,7 @@ void kf_destroy(kf_handle* h) {
   if (h->order) cudaFree(h->order);
   if (h->hist) cudaFree(h->hist);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->ckpt) cudaFree(h->ckpt);
   delete h;
 }
 
@@ -496,6 +500,65 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   slot.ms = best_t;
   *best_out = best;
   if (best_ms) *best_ms = best_t;
+  return KF_SUCCESS;
+}
+
+int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const double* align,
+                 const kf_measurements* me, const kf_field* fi, const kf_options* opt_in, const double* dl_dchi2,
+                 double* out_chi2, double* grad_seed, double* grad_align, void* stream_v) {
+  if (!h) return KF_EINVAL;
+  kf_options opt;
+  if (opt_in) opt = *opt_in; else kf_default_options(&opt);
+  opt.precision = KF_PRECISION_FP64;
+  opt.schedule = KF_SCHEDULE_GRID;
+  kf_outputs dummy;
+  memset(&dummy, 0, sizeof(dummy));
+  double one = 0.0;  // non-null placeholders for the output checks of validate()
+  dummy.params = dummy.cov = dummy.chi2 = &one;
+  int rc = validate(tr, su, me, fi, &opt, &dummy);
+  if (rc) return rc;
+  cudaStream_t stream = (cudaStream_t)stream_v;
+  if (grad_align) {
+    cudaError_t e = cudaMemsetAsync(grad_align, 0, sizeof(double) * 6 * (size_t)su->n_surfaces, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(grad_align)");
+  }
+  if (tr->n_tracks == 0) return KF_SUCCESS;
+  const int n_ckpt = (tr->max_states + grad_segment_length() - 1) / grad_segment_length();
+  const size_t need = sizeof(double) * 27 * (size_t)n_ckpt * (size_t)tr->n_tracks;
+  if (h->ckpt_bytes < need) {
+    if (h->ckpt) cudaFree(h->ckpt);
+    h->ckpt = nullptr;
+    h->ckpt_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->ckpt, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(checkpoints)");
+    h->ckpt_bytes = need;
+  }
+  if ((rc = ensure_surf(h, su->n_surfaces))) return rc;
+  cudaError_t e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
+  FitParams p;
+  memset(&p, 0, sizeof(p));
+  p.n_tracks = tr->n_tracks;
+  p.n_tracks_total = tr->n_tracks;
+  p.max_states = tr->max_states;
+  p.offsets = tr->offsets;
+  p.seed_params = tr->seed_params;
+  p.seed_cov = tr->seed_cov;
+  p.n_surfaces = su->n_surfaces;
+  p.surf = h->surf;
+  p.n_states = me->n_states;
+  p.surface_id = me->surface_id;
+  p.loc = me->loc;
+  p.cov = me->cov;
+  p.is_hole = me->is_hole;
+  for (int i = 0; i < 3; ++i) p.bfield[i] = fi->b[i];
+  p.mass = opt.mass;
+  p.h_max = opt.h_max;
+  p.n_iter = opt.n_iter;
+  p.error_flag = h->error_flag;
+  e = launch_grad(p, align, dl_dchi2, out_chi2, grad_seed, grad_align, h->ckpt, n_ckpt, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "grad launch");
+  h->last_launches = 2;
   return KF_SUCCESS;
 }
 

@@ -76,6 +76,13 @@ cudaError_t launch_selftest(long long n, unsigned long long* counters, cudaStrea
 cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks,
                        cudaStream_t stream);
 
+// Gradients of sum_t w_t chi2_t with respect to the seeds and the
+// per-surface alignment (kf_adjoint.cu).  ckpt holds n_ckpt checkpoints of 27
+// doubles per track; n_ckpt = ceil(max_states / grad_segment_length()).
+cudaError_t launch_grad(const FitParams& f, const double* align, const double* dl_dchi2, double* chi2,
+                        double* grad_seed, double* grad_align, double* ckpt, int n_ckpt, cudaStream_t stream);
+int grad_segment_length();
+
 // Counting sort of the tracks by state count, longest first:
 // order[0..n_tracks) receives track indices.  hist needs max_states + 2 ints.
 cudaError_t launch_length_order(int n_tracks, int max_states, const int32_t* offsets,

@@ -59,6 +59,9 @@ class Workload:
     half_width: float = 500.0 # planes are 1 m x 1 m in the simulation
     min_cos_incidence: float = 0.1
     min_meas: int = 3         # resample tracks left with fewer measurements
+    misalign: tuple | None = None  # (shift sigma mm, rotation sigma rad) of the
+                                   # true planes; the event keeps the nominal
+                                   # geometry and records align_true
 
 
 def _planes(n, step):
@@ -77,6 +80,8 @@ WORKLOADS = {
                             seed=2),
     "tel30_4m": Workload("tel30_4m", 4_000_000, _planes(30, 25.0), 0.01, 2.0, 0.050,
                          (1.0, 100.0), seed=4),
+    "align20_100k": Workload("align20_100k", 100_000, _planes(20, 30.0), 0.005, 2.0, 0.050,
+                             (1.0, 10.0), seed=3, misalign=(0.100, 0.001)),
 }
 
 
@@ -124,6 +129,55 @@ def _highland_width(qop, xx0, cos_inc, mass):
     return 0.0136 / (np.sqrt(beta2) * p) * np.sqrt(eps) * (1.0 + 0.038 * np.log(eps / beta2))
 
 
+_P_ALIGN = 9
+
+
+def alignment_draw(w: Workload):
+    """Per-surface misalignment (du, dv, dn, alpha, beta, gamma) of the true
+    planes, [6][S]; surface 0 (the reference plane) stays nominal."""
+    S = len(w.plane_x) + 1
+    a = np.zeros((6, S))
+    if w.misalign is None:
+        return a
+    ss, rs = w.misalign
+    sid = np.arange(1, S, dtype=np.uint64)
+    for e in range(6):
+        a[e, 1:] = (ss if e < 3 else rs) * _normal(w.seed, sid, np.zeros(S - 1, dtype=np.uint64), _P_ALIGN, e)
+    return a
+
+
+def aligned_planes(center, rot, align):
+    """Apply alignment: c' = c + R (du, dv, dn), R' = R Ru(alpha) Rv(beta) Rn(gamma)
+    (rotations about the plane's local axes).  center [3][S], rot [9][S]."""
+    S = center.shape[1]
+    c2 = np.empty_like(center)
+    r2 = np.empty_like(rot)
+    for s in range(S):
+        R = rot[:, s].reshape(3, 3)
+        a = align[:, s]
+        ca, sa, cb, sb, cg, sg = (np.cos(a[3]), np.sin(a[3]), np.cos(a[4]), np.sin(a[4]),
+                                  np.cos(a[5]), np.sin(a[5]))
+        Ru = np.array([[1, 0, 0], [0, ca, -sa], [0, sa, ca]])
+        Rv = np.array([[cb, 0, sb], [0, 1, 0], [-sb, 0, cb]])
+        Rn = np.array([[cg, -sg, 0], [sg, cg, 0], [0, 0, 1]])
+        c2[:, s] = center[:, s] + R @ a[:3]
+        r2[:, s] = (R @ Ru @ Rv @ Rn).ravel()
+    return c2, r2
+
+
+def _helix_at(x0, y0, z0, phi, st, ct, omega, s):
+    """Position and azimuth after path s on the helix (stable as omega -> 0)."""
+    half = 0.5 * omega * s
+    small = np.abs(half) < 1e-9
+    sinc = np.where(small, 1.0 - half * half / 6.0, np.sin(half) / np.where(small, 1.0, half))
+    chord = s * sinc                                   # 2 sin(omega s / 2) / omega
+    mid = phi - half
+    x = x0 + st * chord * np.cos(mid)
+    y = y0 + st * chord * np.sin(mid)
+    z = z0 + s * ct
+    return x, y, z, phi - omega * s
+
+
 def _simulate(w: Workload, ids, attempt, mass):
     """Simulate tracks `ids` (attempt per track); return arrays + ok mask."""
     n = len(ids)
@@ -141,6 +195,16 @@ def _simulate(w: Workload, ids, attempt, mass):
         a, b = w.nhit_range
         nhit = a + np.minimum((_uniform(s, ids, attempt, _P_NHIT, 0) * (b - a + 1)).astype(np.int64), b - a)
     omega = qop * _KAPPA * w.bz  # turning rate: dphi/ds = -omega
+    true_planes = None
+    if w.misalign is not None:
+        S = npl + 1
+        c_nom = np.zeros((3, S)); c_nom[0, 1:] = np.asarray(w.plane_x)
+        r_nom = np.repeat(np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]).reshape(9, 1), S, axis=1)
+        c_true, r_true = aligned_planes(c_nom, r_nom, alignment_draw(w))
+        true_planes = []
+        for j in range(npl):
+            R = r_true[:, j + 1].reshape(3, 3)
+            true_planes.append((c_true[:, j + 1], R[:, 2], R[:, 0], R[:, 1]))
     gam = np.sqrt(1.0 + mass * mass * qop * qop) / _C  # dt/ds
     x0 = np.zeros(n); y0 = np.zeros(n); z0 = np.zeros(n); t0 = np.zeros(n)
     phi = phi0.copy(); th = th0.copy()
@@ -164,11 +228,30 @@ def _simulate(w: Workload, ids, attempt, mass):
                       -2.0 * st / om_safe * np.sin(0.5 * (psi + phi)) * np.sin(0.5 * (psi - phi)))
         y1 = y0 + dy
         z1 = z0 + s_path * np.cos(th)
-        t1 = t0 + s_path * gam
         phi1 = np.where(small, phi, psi)
         cos_inc = np.cos(phi1) * st
+        if true_planes is not None:
+            # crossing of the true (shifted, rotated) plane: Newton on the
+            # signed distance n'.(r(s) - c') along the helix
+            cT, nT, uT, vT = true_planes[j]
+            ct_ = np.cos(th)
+            for _ in range(8):
+                xh, yh, zh, ph = _helix_at(x0, y0, z0, phi, st, ct_, omega, s_path)
+                g = nT[0] * (xh - cT[0]) + nT[1] * (yh - cT[1]) + nT[2] * (zh - cT[2])
+                dg = nT[0] * st * np.cos(ph) + nT[1] * st * np.sin(ph) + nT[2] * ct_
+                s_path = s_path - g / dg
+            xh, yh, zh, ph = _helix_at(x0, y0, z0, phi, st, ct_, omega, s_path)
+            dr = np.stack([xh - cT[0], yh - cT[1], zh - cT[2]])
+            y1 = uT @ dr        # local coordinates on the true plane
+            z1 = vT @ dr
+            phi1 = ph
+            cos_inc = nT[0] * st * np.cos(ph) + nT[1] * st * np.sin(ph) + nT[2] * ct_
+            xt, yt, zt = xh, yh, zh
+        t1 = t0 + s_path * gam
         ok &= ~crossed | ((cos_inc > w.min_cos_incidence) & (np.abs(y1) <= w.half_width)
                           & (np.abs(z1) <= w.half_width) & (s_path > 0))
+        if true_planes is None:
+            xt, yt, zt = np.full(n, xp, dtype=np.float64), y1, z1
         loc[0, j] = y1; loc[1, j] = z1
         meas[0, j] = y1 + w.sigma * _normal(s, ids, attempt, _P_HIT, 2 * j)
         meas[1, j] = z1 + w.sigma * _normal(s, ids, attempt, _P_HIT, 2 * j + 1)
@@ -183,7 +266,7 @@ def _simulate(w: Workload, ids, attempt, mass):
         phi = phi1 + dphi
         th = th + dth
         leave[0, j] = phi; leave[1, j] = th; leave[2, j] = t1
-        x0 = np.full(n, xp, dtype=np.float64); y0 = y1; z0 = z1; t0 = t1
+        x0 = xt; y0 = yt; z0 = zt; t0 = t1
     nmeas = np.sum(~hole & (np.arange(npl)[:, None] < nhit[None, :]), axis=0)
     ok &= nmeas >= w.min_meas
     return dict(phi0=phi0, th0=th0, qop=qop, nhit=nhit, loc=loc, meas=meas,
@@ -273,7 +356,7 @@ def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200) ->
         center=center, rot=rot, x_over_x0=x_over_x0,
         bfield=np.array([0.0, 0.0, w.bz]), surface_id=surface_id, loc=loc,
         cov=cov, is_hole=is_hole, truth_states=truth_states,
-        sigma=w.sigma, rejected=rejected,
+        sigma=w.sigma, rejected=rejected, align_true=alignment_draw(w),
     )
 
 

@@ -510,12 +510,13 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
     // x[2..5] (phi, theta, q/p, t) are FP64 accumulators; the position is
     // carried as the FP64 point r on the current surface (loc0/loc1 of the
     // filtered state are r's local coordinates).
-    double x[6], C[21], r[3];
+    // the filtered covariance is kept in FP32 between states: it only feeds
+    // the FP32 transport F Cf F^T (the Joseph update produces it in FP64)
+    double x[6], r[3];
+    float Cf[21];
     float dx[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // x_f - x_p of the last state
 #pragma unroll
     for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TT + t];
-#pragma unroll
-    for (int e = 0; e < 21; ++e) C[e] = p.seed_cov[e * TT + t];
     Dir d;
     d.phi = x[2];
     d.theta = x[3];
@@ -537,8 +538,8 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         for (int e = 0; e < 6; ++e) xp[e] = x[e];
 #pragma unroll
         for (int e = 0; e < 21; ++e) {
-          Cp[e] = C[e];
-          Cpf[e] = d2f(C[e]);
+          Cp[e] = p.seed_cov[e * TT + t];
+          Cpf[e] = d2f(Cp[e]);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) rp[c] = r[c];
@@ -549,9 +550,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         float sin_th, cos_inc;
         status = transport_mixed<BZ>(sa, sb, r, x, d, Bf, m2, h_max, p.n_iter, xp, rp, dp, J, sin_th, cos_inc);
         if (status != ST_OK) break;
-        float Cr[21];
-#pragma unroll
-        for (int e = 0; e < 21; ++e) Cr[e] = d2f(C[e]);
+        const float* Cr = Cf;
         // Cp = F Cf F^T, rows of Bm = F Cf formed on the fly
 #pragma unroll
         for (int a = 0; a < 6; ++a) {
@@ -650,7 +649,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
               v = fma(K[a][1], W[1][b], v);
               v = fma(-Cp[sym(0, a)], K[b][0], v);
               v = fma(-Cp[sym(1, a)], K[b][1], v);
-              C[sy(a, b)] = v;
+              Cf[sy(a, b)] = d2f(v);
             }
         // the filtered point: the predicted point moved in the plane by
         // (dx0, dx1); angles, q/p and t receive their increments
@@ -670,7 +669,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           dx[e] = 0.0f;
         }
 #pragma unroll
-        for (int e = 0; e < 21; ++e) C[e] = Cp[e];
+        for (int e = 0; e < 21; ++e) Cf[e] = Cpf[e];
 #pragma unroll
         for (int c = 0; c < 3; ++c) r[c] = rp[c];
         d = dp;
@@ -689,7 +688,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
       float Cs[21];
       float off[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-      for (int e = 0; e < 21; ++e) Cs[e] = d2f(C[e]);
+      for (int e = 0; e < 21; ++e) Cs[e] = Cf[e];
       if (p.out_states)
 #pragma unroll
         for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + o0 + n - 1] = ws.d(n - 1, XP + e) + f2d(dx[e]);
@@ -782,7 +781,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           xs[1] += f2d(dx[1]);
         }
 #pragma unroll
-        for (int e = 0; e < 21; ++e) Cs_out[e] = C[e];
+        for (int e = 0; e < 21; ++e) Cs_out[e] = f2d(Cf[e]);
       } else {
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cs_out[e] = f2d(Cs[e]);

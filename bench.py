@@ -190,9 +190,11 @@ def run_ours(args, rank, world, local):
         # launch shape from the autotuner (untimed), then CUDA-graph replay
         best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(prec_id[prec]), stream)
         opt = kf.kf_default_options(prec_id[prec], schedule=best.schedule, block=best.block,
-                                    min_blocks=best.min_blocks, use_graph=0 if args.no_graph else 1)
+                                    min_blocks=best.min_blocks, resident_warps=best.resident_warps,
+                                    use_graph=0 if args.no_graph else 1)
         tuned[prec] = {"schedule": ["grid", "persistent", "sorted"][best.schedule], "block": best.block,
-                       "min_blocks": best.min_blocks, "cuda_graph": not args.no_graph}
+                       "min_blocks": best.min_blocks, "resident_warps": best.resident_warps,
+                       "cuda_graph": not args.no_graph}
         for _ in range(warmup):
             kf.kf_fit_ex(h, dev, out, opt, stream)
         torch.cuda.synchronize()
@@ -247,6 +249,7 @@ def run_ours(args, rank, world, local):
                 "states": None}
         sh = tuned[args.precision]
         opt = kf.kf_default_options(prec_id[args.precision], block=sh["block"], min_blocks=sh["min_blocks"],
+                                    resident_warps=sh["resident_warps"],
                                     schedule=["grid", "persistent", "sorted"].index(sh["schedule"]))
         for _ in range(args.warmup):
             kf.kf_fit_host(h, hev, opt, out=outs, stream=stream)

@@ -62,7 +62,7 @@
 extern "C" {
 #endif
 
-#define KF_ABI_VERSION 1
+#define KF_ABI_VERSION 2
 
 typedef enum {
   KF_SUCCESS = 0,
@@ -142,6 +142,12 @@ typedef struct {
                                   CUDA graph held by the handle and replays it
                                   while every argument is unchanged (needs a
                                   non-NULL stream) */
+  int32_t resident_warps;      /* persistent schedules: warps kept resident on
+                                  each SM (0 = as many as fit).  With U
+                                  32-track units and W resident warps the
+                                  launch takes ceil(U / W) rounds; fewer
+                                  warps that still fill the FP64 pipe can
+                                  remove a part-filled last round */
 } kf_options;
 
 typedef enum {
@@ -211,7 +217,8 @@ int kf_fit_static(const kf_tracks* tracks, const kf_surfaces* surfaces,
                   const kf_options* opt, const kf_outputs* out, void* stream);
 
 /* Autotuner: time every launch shape (schedule x threads per CTA x register
- * variant) on this batch, on `stream`, and return the fastest in *best
+ * variant, and persistent launches of one-warp CTAs with the resident_warps
+ * values that best fill the last round of 32-track units) on this batch, on `stream`, and return the fastest in *best
  * (other fields copied from *base; base may be NULL for the defaults) and
  * its median time in *best_ms (optional).  Results are cached in the handle
  * per (precision, n_tracks, max_states, n_surfaces, field along z); a cached

@@ -65,7 +65,7 @@ class KfOptions(ctypes.Structure):
                 ("h_max", ctypes.c_double), ("n_iter", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
                 ("schedule", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("resident_warps", ctypes.c_int32)]
 
 
 _lib = None

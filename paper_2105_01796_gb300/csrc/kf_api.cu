@@ -115,6 +115,7 @@ int validate(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* 
   if (opt->block < 0 || opt->block > 128 || (opt->block % 32) != 0) return KF_EUNSUPPORTED;
   if (opt->schedule < KF_SCHEDULE_AUTO || opt->schedule > KF_SCHEDULE_SORTED) return KF_EUNSUPPORTED;
   if (opt->min_blocks < 0 || opt->min_blocks > 4) return KF_EUNSUPPORTED;
+  if (opt->resident_warps < 0 || opt->resident_warps > 64) return KF_EINVAL;
   for (int i = 0; i < 3; ++i)
     if (!(fi->b[i] == fi->b[i])) return KF_EINVAL;
   return KF_SUCCESS;
@@ -136,6 +137,7 @@ void kf_default_options(kf_options* opt) {
   opt->schedule = KF_SCHEDULE_PERSISTENT;
   opt->min_blocks = 0;
   opt->use_graph = 0;
+  opt->resident_warps = 0;
 }
 
 int kf_abi_version(void) { return KF_ABI_VERSION; }
@@ -316,6 +318,7 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   p.ws32 = opt.precision == KF_PRECISION_FP64 ? nullptr : (float*)((char*)h->ws + plan.bytes64);
   p.error_flag = h->error_flag;
   p.order = opt.schedule == KF_SCHEDULE_SORTED ? h->order : nullptr;
+  p.resident_warps = opt.resident_warps;
   int c = 0;
   for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk, ++c) {
     p.track0 = (int32_t)t0;
@@ -342,6 +345,41 @@ struct GraphKey {
   const void* bufs[5];
 };
 static_assert(sizeof(GraphKey) <= 512, "graph key storage");
+
+// Resident warps per SM (at least 4, at most 16) for which the
+// ceil(n_tracks / 32) units of a persistent launch fill every round but the
+// last nearly completely: for each round count r the fewest warps that finish
+// in r rounds, ranked by the filled fraction U / (r * nsm * w).  Writes up to
+// 3 values to w_out and returns how many.
+int round_filling_warps(int64_t n_tracks, int nsm, int* w_out) {
+  const double U = (double)((n_tracks + 31) / 32);
+  int ws[16];
+  double fill[16];
+  int n = 0;
+  for (int r = 1; r <= 4096 && n < 16; ++r) {
+    const int w = (int)((U + (double)r * nsm - 1.0) / ((double)r * nsm));
+    if (w < 4) break;
+    if (w > 16) continue;
+    if (n > 0 && ws[n - 1] == w) continue;
+    ws[n] = w;
+    fill[n] = U / ((double)r * nsm * w);
+    ++n;
+  }
+  int m = 0;
+  for (; m < 3 && m < n; ++m) {  // partial selection sort, best fill first
+    int b = m;
+    for (int j = m + 1; j < n; ++j)
+      if (fill[j] > fill[b]) b = j;
+    const int tw = ws[m];
+    const double tf = fill[m];
+    ws[m] = ws[b];
+    fill[m] = fill[b];
+    ws[b] = tw;
+    fill[b] = tf;
+    w_out[m] = ws[m];
+  }
+  return m;
+}
 
 GraphKey make_key(const kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
                   const kf_field* fi, const kf_options& opt, const kf_outputs* out, void* stream) {
@@ -382,6 +420,7 @@ int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf
     opt.schedule = best.schedule;
     opt.block = best.block;
     opt.min_blocks = best.min_blocks;
+    opt.resident_warps = best.resident_warps;
   }
   FitPlan plan;
   if ((rc = prepare_fit(h, tr, su, opt, &plan))) return rc;
@@ -436,6 +475,7 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
       best_out->schedule = c.best.schedule;
       best_out->block = c.best.block;
       best_out->min_blocks = c.best.min_blocks;
+      best_out->resident_warps = c.best.resident_warps;
       if (best_ms) *best_ms = c.ms;
       return KF_SUCCESS;
     }
@@ -447,11 +487,45 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     if (best_ms) *best_ms = -1.0;
     return KF_SUCCESS;
   }
-  // candidate launch shapes: schedule x threads per CTA x register variant
+  // candidate launch shapes: schedule x threads per CTA x register variant,
+  // then persistent launches with fewer resident warps chosen so that the
+  // 32-track units fill their last round (see resident_warps in kf.h)
   const int schedules[3] = {KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED};
   const int blocks[3] = {32, 64, 128};
   const int mbs_mixed[2] = {0, 3};
   const int n_mb = base.precision == KF_PRECISION_FP64 ? 1 : 2;
+  kf_options cand[64];
+  int n_cand = 0;
+  for (int si = 0; si < 3; ++si)
+    for (int bi = 0; bi < 3; ++bi)
+      for (int mi = 0; mi < n_mb; ++mi) {
+        kf_options o = base;
+        o.schedule = schedules[si];
+        o.block = blocks[bi];
+        o.min_blocks = base.precision == KF_PRECISION_FP64 ? 0 : mbs_mixed[mi];
+        o.resident_warps = 0;
+        o.use_graph = 0;
+        cand[n_cand++] = o;
+      }
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0) {
+      int wps[3];
+      const int n_w = round_filling_warps(tr->n_tracks, nsm, wps);
+      for (int wi = 0; wi < n_w; ++wi)
+        for (int si = 1; si < 3; ++si)
+          for (int mi = 0; mi < n_mb; ++mi) {
+            kf_options o = base;
+            o.schedule = schedules[si];
+            o.block = 32;
+            o.min_blocks = base.precision == KF_PRECISION_FP64 ? 0 : mbs_mixed[mi];
+            o.resident_warps = wps[wi];
+            o.use_graph = 0;
+            cand[n_cand++] = o;
+          }
+    }
+  }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -460,32 +534,26 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   }
   kf_options best = base;
   double best_t = 1e300;
-  for (int si = 0; si < 3 && rc == KF_SUCCESS; ++si)
-    for (int bi = 0; bi < 3 && rc == KF_SUCCESS; ++bi)
-      for (int mi = 0; mi < n_mb && rc == KF_SUCCESS; ++mi) {
-        kf_options o = base;
-        o.schedule = schedules[si];
-        o.block = blocks[bi];
-        o.min_blocks = base.precision == KF_PRECISION_FP64 ? 0 : mbs_mixed[mi];
-        o.use_graph = 0;
-        float times[3];
-        for (int r = -1; r < 3 && rc == KF_SUCCESS; ++r) {  // one warm-up, three timed
-          cudaEventRecord(e0, stream);
-          rc = kf_fit_ex(h, tr, su, me, fi, &o, out, stream_v);
-          cudaEventRecord(e1, stream);
-          cudaError_t e = cudaEventSynchronize(e1);
-          if (e != cudaSuccess) rc = cuda_fail(e, "autotune");
-          if (r >= 0 && rc == KF_SUCCESS) cudaEventElapsedTime(&times[r], e0, e1);
-        }
-        if (rc) break;
-        // median of three
-        float a = times[0], b = times[1], c = times[2];
-        const float med = a > b ? (b > c ? b : (a > c ? c : a)) : (a > c ? a : (b > c ? c : b));
-        if (med < best_t) {
-          best_t = med;
-          best = o;
-        }
-      }
+  for (int ci = 0; ci < n_cand && rc == KF_SUCCESS; ++ci) {
+    const kf_options& o = cand[ci];
+    float times[3];
+    for (int r = -1; r < 3 && rc == KF_SUCCESS; ++r) {  // one warm-up, three timed
+      cudaEventRecord(e0, stream);
+      rc = kf_fit_ex(h, tr, su, me, fi, &o, out, stream_v);
+      cudaEventRecord(e1, stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) rc = cuda_fail(e, "autotune");
+      if (r >= 0 && rc == KF_SUCCESS) cudaEventElapsedTime(&times[r], e0, e1);
+    }
+    if (rc) break;
+    // median of three
+    float a = times[0], b = times[1], c = times[2];
+    const float med = a > b ? (b > c ? b : (a > c ? c : a)) : (a > c ? a : (b > c ? c : b));
+    if (med < best_t) {
+      best_t = med;
+      best = o;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;

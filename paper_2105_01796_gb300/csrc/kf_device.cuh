@@ -233,7 +233,11 @@ cudaError_t launch_body(const FitParams& p, int block, cudaStream_t stream) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem);
     if (e != cudaSuccess) return e;
-    const long long resident = (long long)nsm * (occ > 0 ? occ : 1);
+    long long resident = (long long)nsm * (occ > 0 ? occ : 1);
+    if (p.resident_warps > 0) {
+      const long long want = ((long long)nsm * p.resident_warps * 32 + block - 1) / block;
+      if (want < resident) resident = want;
+    }
     if (grid > resident) grid = (int)resident;
   }
   kern<<<grid, block, smem, stream>>>(p);

@@ -59,6 +59,7 @@ struct FitParams {
   int32_t* work_counter;   // non-null: persistent launch, warps take 32-track
                            // units from this counter (zeroed before launch)
   const int32_t* order;    // non-null: slot s fits track order[s]
+  int32_t resident_warps;  // persistent launch: warps per SM (0 = occupancy)
 };
 
 // Pack the SoA surface table into [S][kSurfStride] doubles.

@@ -87,6 +87,7 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   if (opt.block < 0 || opt.block > 128 || (opt.block % 32) != 0) return KF_EUNSUPPORTED;
   if (opt.schedule < KF_SCHEDULE_GRID || opt.schedule > KF_SCHEDULE_PERSISTENT) return KF_EUNSUPPORTED;
   if (opt.min_blocks < 0 || opt.min_blocks > 4) return KF_EUNSUPPORTED;
+  if (opt.resident_warps < 0 || opt.resident_warps > 64) return KF_EINVAL;
   // size limits of the static block
   if (su->n_surfaces > kMaxSurfaces) return KF_ESIZE;
   // one track's records (both precisions' parts, each 256-byte aligned) must fit
@@ -114,6 +115,7 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   if (e != cudaSuccess) return KF_ECUDA;
   FitParams p;
   memset(&p, 0, sizeof(p));
+  p.resident_warps = opt.resident_warps;
   p.n_tracks_total = tr->n_tracks;
   p.max_states = tr->max_states;
   p.offsets = tr->offsets;

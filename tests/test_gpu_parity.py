@@ -237,6 +237,15 @@ def test_every_launch_variant_agrees(handle, prec):
                         base = g
                     for k in ("params", "cov", "chi2", "ndf", "status"):
                         assert np.array_equal(g[k], base[k]), (sched, block, k)
+    # persistent launches of one-warp CTAs with a few resident warps per SM
+    # (fewer warps than units: every warp takes several units)
+    for sched in (kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED):
+        for w in (1, 5, 7):
+            g = gpu_fit(handle, ev, prec, schedule=sched, block=32, resident_warps=w)
+            compare(g, r, prec)
+            if prec == FP64:
+                for k in ("params", "cov", "chi2", "ndf", "status"):
+                    assert np.array_equal(g[k], base[k]), (sched, w, k)
 
 
 def test_graph_capture_and_replay(handle):

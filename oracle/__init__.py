@@ -25,6 +25,69 @@ _lib = None
 
 OK, NO_INTERSECTION, NON_SPD, NONFINITE, BAD_INPUT = 0, 1, 2, 3, 4
 MUON_MASS = 0.1056583755  # GeV
+SMOOTHER_RTS, SMOOTHER_BACKWARD_FILTER = 0, 1
+
+
+class FieldMap(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("origin", ctypes.c_double * 3), ("spacing", ctypes.c_double * 3),
+                ("b", ctypes.c_void_p)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("z_over_a", ctypes.c_double), ("i_exc", ctypes.c_double),
+                ("x0_rho", ctypes.c_double), ("sh_cbar", ctypes.c_double),
+                ("sh_x0", ctypes.c_double), ("sh_x1", ctypes.c_double),
+                ("sh_a", ctypes.c_double), ("sh_k", ctypes.c_double),
+                ("sh_delta0", ctypes.c_double)]
+
+
+class Method(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("bf_scale", ctypes.c_double),
+                ("energy_loss", ctypes.c_int), ("mat", Material),
+                ("map", ctypes.c_void_p)]
+
+
+def silicon() -> Material:
+    """Silicon: Z/A, mean excitation energy, radiation length and the
+    Sternheimer density-effect parameters as tabulated by the PDG (atomic
+    and nuclear properties of materials)."""
+    return Material(0.49848, 173.0e-9, 21.82, 4.4355, 0.2015, 2.8716, 0.1492, 3.2546, 0.14)
+
+
+def field_map_struct(fm):
+    """ctypes FieldMap for a map dict {origin[3], spacing[3], b[nz][ny][nx][3]};
+    returns (struct, the contiguous value array that must stay alive)."""
+    b = np.ascontiguousarray(fm["b"], dtype=np.float64)
+    nz, ny, nx, three = b.shape
+    assert three == 3
+    st = FieldMap(nx, ny, nz, (ctypes.c_double * 3)(*[float(v) for v in fm["origin"]]),
+                  (ctypes.c_double * 3)(*[float(v) for v in fm["spacing"]]),
+                  b.ctypes.data_as(ctypes.c_void_p))
+    return st, b
+
+
+def method_struct(method=None, field_map=None):
+    """Build the kfo_method for a dict {smoother: 'rts'|'backward',
+    bf_scale, energy_loss, material} and an optional field-map dict.
+    Returns (struct or None, objects to keep alive)."""
+    if method is None and field_map is None:
+        return None, []
+    method = dict(method or {})
+    keep = []
+    m = Method()
+    m.smoother = SMOOTHER_BACKWARD_FILTER if method.get("smoother", "rts") == "backward" else SMOOTHER_RTS
+    m.bf_scale = float(method.get("bf_scale", 1e4))
+    m.energy_loss = 1 if method.get("energy_loss", False) else 0
+    m.mat = method.get("material") or silicon()
+    if field_map is not None:
+        fm, b = field_map_struct(field_map)
+        keep += [fm, b]
+        m.map = ctypes.cast(ctypes.pointer(fm), ctypes.c_void_p)
+    else:
+        m.map = None
+    keep.append(m)
+    return m, keep
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +128,25 @@ def _load():
         lib.kfo_fit_batch.argtypes = [I, P, P, P, I, P, P, P, L, P, P, P, P, P, D, D, I,
                                       P, P, P, P, P, P, I, I, I]
         lib.kfo_fit_batch.restype = I
+        lib.kfo_field_at.argtypes = [P, P, P, P]
+        lib.kfo_rkn_step_field.argtypes = [P, D, P, P, D, P]
+        lib.kfo_transport_field.argtypes = [P, P, P, P, P, P, P, D, D, I, P, P, P]
+        lib.kfo_transport_field.restype = I
+        lib.kfo_density_effect.argtypes = [D, P]
+        lib.kfo_density_effect.restype = D
+        lib.kfo_bethe.argtypes = [D, D, P]
+        lib.kfo_bethe.restype = D
+        lib.kfo_landau_xi.argtypes = [D, D, P]
+        lib.kfo_landau_xi.restype = D
+        lib.kfo_energy_loss.argtypes = [P, D, D, D, P, I, P, P]
+        lib.kfo_energy_loss.restype = I
+        lib.kfo_linear_fit_ex.argtypes = [I] + [P] * 7 + [I, D] + [P] * 3
+        lib.kfo_linear_fit_ex.restype = I
+        lib.kfo_fit_track_ex.argtypes = [I, P, P, P, P, P, P, I, P, P, P, P, D, D, I] + [P] * 9
+        lib.kfo_fit_track_ex.restype = I
+        lib.kfo_fit_batch_ex.argtypes = [I, P, P, P, I, P, P, P, L, P, P, P, P, P, D, D, I,
+                                         P, P, P, P, P, P, P, I, I, I]
+        lib.kfo_fit_batch_ex.restype = I
         _lib = lib
     return _lib
 
@@ -115,6 +197,63 @@ def transport(ca, Ra, x, cb, Rb, B, mass=MUON_MASS, h_max=50.0, n_iter=3):
     return st, xo, F, float(path[0])
 
 
+def field_at(B, r, field_map=None):
+    out = np.zeros(3)
+    if field_map is None:
+        _load().kfo_field_at(_p(_f64(B, 3)), None, _p(_f64(r, 3)), _p(out))
+    else:
+        fm, keep = field_map_struct(field_map)
+        _load().kfo_field_at(_p(_f64(B, 3)), ctypes.byref(fm), _p(_f64(r, 3)), _p(out))
+    return out
+
+
+def rkn_step_field(f, h, B, field_map, mass=MUON_MASS):
+    f = _f64(f, 8).copy()
+    D = np.eye(8)
+    fm, keep = field_map_struct(field_map)
+    _load().kfo_rkn_step_field(_p(f), float(h), _p(_f64(B, 3)), ctypes.byref(fm), float(mass), _p(D))
+    return f, D
+
+
+def transport_field(ca, Ra, x, cb, Rb, B, field_map, mass=MUON_MASS, h_max=50.0, n_iter=3):
+    xo = np.zeros(6)
+    F = np.zeros((6, 6))
+    path = np.zeros(1)
+    fm, keep = field_map_struct(field_map)
+    st = _load().kfo_transport_field(_p(_f64(ca, 3)), _p(_f64(Ra, 9)), _p(_f64(x, 6)),
+                                     _p(_f64(cb, 3)), _p(_f64(Rb, 9)), _p(_f64(B, 3)),
+                                     ctypes.byref(fm), float(mass), float(h_max), int(n_iter),
+                                     _p(xo), _p(F), _p(path))
+    return st, xo, F, float(path[0])
+
+
+def density_effect(bg, material=None):
+    m = material or silicon()
+    return _load().kfo_density_effect(float(bg), ctypes.byref(m))
+
+
+def bethe(bg, mass=MUON_MASS, material=None):
+    """Mean stopping power in GeV cm^2/g."""
+    m = material or silicon()
+    return _load().kfo_bethe(float(bg), float(mass), ctypes.byref(m))
+
+
+def landau_xi(beta, thick, material=None):
+    m = material or silicon()
+    return _load().kfo_landau_xi(float(beta), float(thick), ctypes.byref(m))
+
+
+def energy_loss(qop, xx0, cosinc, direction=1, mass=MUON_MASS, material=None):
+    """Returns (status, new q/p, Jacobian factor, downstream q/p variance)."""
+    m = material or silicon()
+    q = np.array([float(qop)])
+    jac = np.zeros(1)
+    var = np.zeros(1)
+    st = _load().kfo_energy_loss(_p(q), float(mass), float(xx0), float(cosinc), ctypes.byref(m),
+                                 int(direction), _p(jac), _p(var))
+    return st, float(q[0]), float(jac[0]), float(var[0])
+
+
 def highland(qop, xx0, cosinc, mass=MUON_MASS):
     return _load().kfo_highland(float(qop), float(mass), float(xx0), float(cosinc))
 
@@ -136,21 +275,24 @@ def rts_step(xf, Cf, xp1, Cp1, F1, xs1, Cs1):
     return st, xs, Cs
 
 
-def linear_fit(x0, C0, F, Q, m, V, hole):
+def linear_fit(x0, C0, F, Q, m, V, hole, smoother="rts", bf_scale=1e4):
     n = len(hole)
     xs = np.zeros((n, 6))
     Cs = np.zeros((n, 6, 6))
     chi2 = np.zeros(n)
     hole = np.ascontiguousarray(hole, dtype=np.uint8)
-    st = _load().kfo_linear_fit(n, _p(_f64(x0, 6)), _p(_f64(C0, (6, 6))),
-                                _p(_f64(F, (n, 6, 6))), _p(_f64(Q, (n, 6, 6))),
-                                _p(_f64(m, (n, 2))), _p(_f64(V, (n, 2, 2))), _p(hole),
-                                _p(xs), _p(Cs), _p(chi2))
+    sm = SMOOTHER_BACKWARD_FILTER if smoother == "backward" else SMOOTHER_RTS
+    st = _load().kfo_linear_fit_ex(n, _p(_f64(x0, 6)), _p(_f64(C0, (6, 6))),
+                                   _p(_f64(F, (n, 6, 6))), _p(_f64(Q, (n, 6, 6))),
+                                   _p(_f64(m, (n, 2))), _p(_f64(V, (n, 2, 2))), _p(hole),
+                                   sm, float(bf_scale), _p(xs), _p(Cs), _p(chi2))
     return st, xs, Cs, chi2
 
 
-def fit_track(ev, t, h_max=50.0, n_iter=3, mass=MUON_MASS):
-    """Fit track ``t`` of a synthetic event; return every intermediate."""
+def fit_track(ev, t, h_max=50.0, n_iter=3, mass=MUON_MASS, method=None):
+    """Fit track ``t`` of a synthetic event; return every intermediate.
+    ``method``: None (the baseline) or a dict of variants (see
+    :func:`method_struct`); a field map is taken from ``ev['field_map']``."""
     o0, o1 = int(ev["offsets"][t]), int(ev["offsets"][t + 1])
     n = o1 - o0
     sid = np.ascontiguousarray(ev["surface_id"][o0:o1], dtype=np.int32)
@@ -165,18 +307,22 @@ def fit_track(ev, t, h_max=50.0, n_iter=3, mass=MUON_MASS):
     S = ev["center"].shape[1]
     center = _f64(ev["center"].T)
     rot = _f64(np.moveaxis(ev["rot"].reshape(9, S), 0, 1))
-    st = _load().kfo_fit_track(
+    meth, keep = method_struct(method, ev.get("field_map"))
+    st = _load().kfo_fit_track_ex(
         n, _p(sid), _p(loc), _p(cov), _p(hole), _p(seed), _p(C0), S, _p(center),
         _p(rot), _p(_f64(ev["x_over_x0"])), _p(_f64(ev["bfield"], 3)), float(mass),
-        float(h_max), int(n_iter), _p(out["xp"]), _p(out["Cp"]), _p(out["xf"]),
+        float(h_max), int(n_iter), ctypes.byref(meth) if meth is not None else None,
+        _p(out["xp"]), _p(out["Cp"]), _p(out["xf"]),
         _p(out["Cf"]), _p(out["xs"]), _p(out["Cs"]), _p(out["F"]), _p(out["chi2"]))
     out["status"] = st
     return out
 
 
 def fit_batch(ev, h_max=50.0, n_iter=3, mass=MUON_MASS, t_begin=0, t_end=None,
-              n_threads=None, with_states=False):
+              n_threads=None, with_states=False, method=None):
     """Fit tracks [t_begin, t_end) of a synthetic event (SoA boundary layout).
+    ``method``: None (the baseline) or a dict of variants (see
+    :func:`method_struct`); a field map is taken from ``ev['field_map']``.
 
     Returns the outputs for the full track range (entries outside the range
     are left NaN / zero).
@@ -205,10 +351,12 @@ def fit_batch(ev, h_max=50.0, n_iter=3, mass=MUON_MASS, t_begin=0, t_end=None,
         "status": np.zeros(T, dtype=np.uint8),
     }
     states = np.full((6, M), np.nan) if with_states else None
-    rc = _load().kfo_fit_batch(
+    meth, keep = method_struct(method, ev.get("field_map"))
+    rc = _load().kfo_fit_batch_ex(
         T, _p(offsets), _p(seed), _p(seed_cov), S, _p(center), _p(rot),
         _p(_f64(ev["x_over_x0"])), M, _p(sid), _p(loc), _p(cov), _p(hole),
         _p(_f64(ev["bfield"], 3)), float(mass), float(h_max), int(n_iter),
+        ctypes.byref(meth) if meth is not None else None,
         _p(out["params"]), _p(out["cov"]), _p(out["chi2"]), _p(out["ndf"]),
         _p(out["status"]), _p(states), int(t_begin), int(t_end), int(n_threads))
     if rc != 0:

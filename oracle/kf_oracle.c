@@ -158,30 +158,93 @@ static void free_to_bound(const double c[3], const double R[9],
 /* Runge-Kutta-Nystrom step (Sect. 4.1, Myrheim's Nystrom method)      */
 /* ------------------------------------------------------------------ */
 
-/* Equation of motion in path length s for a constant field:
- *   r'' = qop * kappa * (r' x B),  t' = sqrt(1 + m^2 qop^2) / c.
- * Classic 4-stage Nystrom step:
- *   k1 = a(T), k2 = a(T + h/2 k1), k3 = a(T + h/2 k2), k4 = a(T + h k3)
+/* ------------------------------------------------------------------ */
+/* magnetic field (Sect. 4.3: a constant 3-vector in the paper's      */
+/* studies; position-dependent fields are named as the general case)  */
+/* ------------------------------------------------------------------ */
+
+/* Field at r: the constant B when map is NULL, else trilinear
+ * interpolation of the map's grid values.  Grid point (i, j, l) sits at
+ * origin + (i dx, j dy, l dz) and holds b[((l ny + j) nx + i) 3 + c].
+ * Outside the grid the position is clamped onto its boundary. */
+void kfo_field_at(const double B[3], const kfo_field_map* map,
+                  const double r[3], double out[3]) {
+  if (!map) {
+    out[0] = B[0];
+    out[1] = B[1];
+    out[2] = B[2];
+    return;
+  }
+  const int n[3] = {map->nx, map->ny, map->nz};
+  int i0[3];
+  double w[3];
+  for (int a = 0; a < 3; ++a) {
+    double u = (r[a] - map->origin[a]) / map->spacing[a];
+    if (u < 0.0) u = 0.0;
+    if (u > n[a] - 1) u = n[a] - 1;
+    int i = (int)floor(u);
+    if (i > n[a] - 2) i = n[a] - 2;
+    i0[a] = i;
+    w[a] = u - i;
+  }
+  for (int c = 0; c < 3; ++c) out[c] = 0.0;
+  for (int dl = 0; dl < 2; ++dl)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const double wt = (di ? w[0] : 1.0 - w[0]) * (dj ? w[1] : 1.0 - w[1]) *
+                          (dl ? w[2] : 1.0 - w[2]);
+        const int64_t idx =
+            (((int64_t)(i0[2] + dl) * n[1] + (i0[1] + dj)) * n[0] + (i0[0] + di)) * 3;
+        for (int c = 0; c < 3; ++c) out[c] += wt * map->b[idx + c];
+      }
+}
+
+/* ------------------------------------------------------------------ */
+/* Runge-Kutta-Nystrom step (Sect. 4.1, Myrheim's Nystrom method)      */
+/* ------------------------------------------------------------------ */
+
+/* Equation of motion in path length s:
+ *   r'' = qop * kappa * (r' x B(r)),  t' = sqrt(1 + m^2 qop^2) / c.
+ * 4-stage Nystrom step with the field taken at the stage points:
+ *   k1 = a(r,            T)
+ *   k2 = a(r + h/2 T + h^2/8 k1, T + h/2 k1)
+ *   k3 = a(r + h/2 T + h^2/8 k1, T + h/2 k2)
+ *   k4 = a(r + h T + h^2/2 k3,   T + h k3)
  *   r <- r + h T + h^2/6 (k1 + k2 + k3)
  *   T <- T + h/6 (k1 + 2 k2 + 2 k3 + k4)
- * D_step is the exact derivative of this map at fixed h, obtained by
- * differentiating every stage (chain rule) with respect to the 8 free
- * parameters; D <- D_step * D. */
-void kfo_rkn_step(double f[8], double h, const double B[3], double mass,
-                  double D[64]) {
+ * D_step is the derivative of this map at fixed h with the stage fields
+ * held at their values (exact for a constant field; the field-gradient term
+ * of a map is left out), obtained by differentiating every stage (chain
+ * rule) with respect to the 8 free parameters; D <- D_step * D. */
+void kfo_rkn_step_field(double f[8], double h, const double B[3],
+                        const kfo_field_map* map, double mass, double D[64]) {
   const double lam = f[7];
+  const double r0[3] = {f[0], f[1], f[2]};
   const double T[3] = {f[4], f[5], f[6]};
   const double stage_a[4] = {0.0, 0.5, 0.5, 1.0};
   double k[4][3];
   double dk[4][3][8]; /* d k_i / d free */
   double prev_k[3] = {0, 0, 0};
   double prev_dk[3][8];
+  double Bs[3];
   memset(prev_dk, 0, sizeof(prev_dk));
   for (int s = 0; s < 4; ++s) {
     const double a = stage_a[s] * h;
+    /* field at the stage point (stages 2 and 3 share the midpoint) */
+    if (s == 0) {
+      kfo_field_at(B, map, r0, Bs);
+    } else if (s == 1) {
+      double rm[3];
+      for (int i = 0; i < 3; ++i) rm[i] = r0[i] + 0.5 * h * T[i] + h * h / 8.0 * k[0][i];
+      kfo_field_at(B, map, rm, Bs);
+    } else if (s == 3) {
+      double re[3];
+      for (int i = 0; i < 3; ++i) re[i] = r0[i] + h * T[i] + 0.5 * h * h * k[2][i];
+      kfo_field_at(B, map, re, Bs);
+    }
     double Ts[3], TsxB[3];
     for (int i = 0; i < 3; ++i) Ts[i] = T[i] + a * prev_k[i];
-    cross3(Ts, B, TsxB);
+    cross3(Ts, Bs, TsxB);
     for (int i = 0; i < 3; ++i) k[s][i] = lam * KFO_KAPPA * TsxB[i];
     /* d Ts / d free = E_T + a * d prev_k */
     double dTs[3][8];
@@ -191,7 +254,7 @@ void kfo_rkn_step(double f[8], double h, const double B[3], double mass,
     /* d k = kappa * (Ts x B) d lam + lam * kappa * (d Ts x B) */
     for (int j = 0; j < 8; ++j) {
       double col[3] = {dTs[0][j], dTs[1][j], dTs[2][j]}, cxb[3];
-      cross3(col, B, cxb);
+      cross3(col, Bs, cxb);
       for (int i = 0; i < 3; ++i) {
         dk[s][i][j] = lam * KFO_KAPPA * cxb[i];
         if (j == 7) dk[s][i][j] += KFO_KAPPA * TsxB[i];
@@ -228,6 +291,11 @@ void kfo_rkn_step(double f[8], double h, const double B[3], double mass,
   }
 }
 
+void kfo_rkn_step(double f[8], double h, const double B[3], double mass,
+                  double D[64]) {
+  kfo_rkn_step_field(f, h, B, NULL, mass, D);
+}
+
 /* Straight-line distance along T from r to the plane (c, n). */
 static int plane_distance(const double f[8], const double c[3],
                           const double n[3], double* s) {
@@ -240,9 +308,10 @@ static int plane_distance(const double f[8], const double c[3],
   return KFO_OK;
 }
 
-int kfo_propagate(double f[8], const double c[3], const double R[9],
-                  const double B[3], double mass, double h_max, int n_iter,
-                  double D[64], double* path) {
+int kfo_propagate_field(double f[8], const double c[3], const double R[9],
+                        const double B[3], const kfo_field_map* map,
+                        double mass, double h_max, int n_iter, double D[64],
+                        double* path) {
   double n[3];
   rot_col(R, 2, n);
   mat_identity(D, 8);
@@ -255,27 +324,35 @@ int kfo_propagate(double f[8], const double c[3], const double R[9],
   const double h = s0 / nsub;
   double total = 0.0;
   for (int i = 0; i < nsub; ++i) {
-    kfo_rkn_step(f, h, B, mass, D);
+    kfo_rkn_step_field(f, h, B, map, mass, D);
     total += h;
   }
   for (int it = 0; it < n_iter; ++it) {
     double si;
     st = plane_distance(f, c, n, &si);
     if (st) return st;
-    kfo_rkn_step(f, si, B, mass, D);
+    kfo_rkn_step_field(f, si, B, map, mass, D);
     total += si;
   }
   if (path) *path = total;
   return KFO_OK;
 }
 
-int kfo_transport(const double ca[3], const double Ra[9], const double x[6],
-                  const double cb[3], const double Rb[9], const double B[3],
-                  double mass, double h_max, int n_iter, double x_out[6],
-                  double F[36], double* path) {
+int kfo_propagate(double f[8], const double c[3], const double R[9],
+                  const double B[3], double mass, double h_max, int n_iter,
+                  double D[64], double* path) {
+  return kfo_propagate_field(f, c, R, B, NULL, mass, h_max, n_iter, D, path);
+}
+
+int kfo_transport_field(const double ca[3], const double Ra[9],
+                        const double x[6], const double cb[3],
+                        const double Rb[9], const double B[3],
+                        const kfo_field_map* map, double mass, double h_max,
+                        int n_iter, double x_out[6], double F[36],
+                        double* path) {
   double f[8], Jbf[48], D[64], Jfb[48];
   kfo_bound_to_free(ca, Ra, x, f, Jbf);
-  int st = kfo_propagate(f, cb, Rb, B, mass, h_max, n_iter, D, path);
+  int st = kfo_propagate_field(f, cb, Rb, B, map, mass, h_max, n_iter, D, path);
   if (st) return st;
   /* Path correction at the target plane.  At fixed path length the end
    * point moves by D df; the plane constraint n.(r - c) = 0 then moves the
@@ -286,8 +363,9 @@ int kfo_transport(const double ca[3], const double Ra[9], const double x[6],
   rot_col(Rb, 2, n);
   const double T[3] = {f[4], f[5], f[6]};
   const double nT = dot3(n, T);
-  double TxB[3];
-  cross3(T, B, TxB);
+  double TxB[3], Bend[3];
+  kfo_field_at(B, map, f, Bend); /* field at the end point */
+  cross3(T, Bend, TxB);
   double Fp[8];
   Fp[0] = T[0];
   Fp[1] = T[1];
@@ -309,6 +387,14 @@ int kfo_transport(const double ca[3], const double Ra[9], const double x[6],
   return KFO_OK;
 }
 
+int kfo_transport(const double ca[3], const double Ra[9], const double x[6],
+                  const double cb[3], const double Rb[9], const double B[3],
+                  double mass, double h_max, int n_iter, double x_out[6],
+                  double F[36], double* path) {
+  return kfo_transport_field(ca, Ra, x, cb, Rb, B, NULL, mass, h_max, n_iter,
+                             x_out, F, path);
+}
+
 /* ------------------------------------------------------------------ */
 /* material (Sect. 4.3: surfaces carry material; multiple scattering)  */
 /* ------------------------------------------------------------------ */
@@ -324,6 +410,83 @@ double kfo_highland(double qop, double mass, double xx0, double cosinc) {
   const double eps = xx0 / fabs(cosinc);
   return 0.0136 / (beta * p) * sqrt(eps) *
          (1.0 + 0.038 * log(eps / (beta * beta)));
+}
+
+/* ------------------------------------------------------------------ */
+/* energy loss (Sect. 1: the fit accounts for the energy loss of the  */
+/* particle in the detector material)                                 */
+/* ------------------------------------------------------------------ */
+
+#define KFO_K_BETHE 0.307075e-3     /* 4 pi N_A r_e^2 m_e c^2, GeV cm^2 / mol */
+#define KFO_ME 0.51099895e-3        /* electron mass, GeV */
+
+/* Sternheimer density-effect correction delta(beta gamma) of the PDG
+ * parameterisation with X = log10(beta gamma):
+ *   X >= x1:       2 ln10 X - Cbar
+ *   x0 <= X < x1:  2 ln10 X - Cbar + a (x1 - X)^k
+ *   X < x0:        delta0 10^(2 (X - x0)) */
+double kfo_density_effect(double bg, const kfo_material* m) {
+  const double X = log10(bg);
+  const double two_ln10 = 2.0 * log(10.0);
+  if (X >= m->sh_x1) return two_ln10 * X - m->sh_cbar;
+  if (X >= m->sh_x0)
+    return two_ln10 * X - m->sh_cbar + m->sh_a * pow(m->sh_x1 - X, m->sh_k);
+  return m->sh_delta0 * pow(10.0, 2.0 * (X - m->sh_x0));
+}
+
+/* Mean stopping power (Bethe, unit charge) in GeV cm^2 / g:
+ *   K Z/A / beta^2 [ 1/2 ln(2 me beta^2 gamma^2 Wmax / I^2) - beta^2
+ *                    - delta/2 ],
+ *   Wmax = 2 me beta^2 gamma^2 / (1 + 2 gamma me/M + (me/M)^2). */
+double kfo_bethe(double bg, double mass, const kfo_material* m) {
+  const double b2 = bg * bg / (1.0 + bg * bg);
+  const double gam = sqrt(1.0 + bg * bg);
+  const double r = KFO_ME / mass;
+  const double wmax = 2.0 * KFO_ME * bg * bg / (1.0 + 2.0 * gam * r + r * r);
+  const double arg = 2.0 * KFO_ME * bg * bg * wmax / (m->i_exc * m->i_exc);
+  return KFO_K_BETHE * m->z_over_a / b2 *
+         (0.5 * log(arg) - b2 - 0.5 * kfo_density_effect(bg, m));
+}
+
+/* Landau scale xi = (K/2) (Z/A) (rho x) / beta^2 in GeV for a thickness
+ * rho x in g/cm^2. */
+double kfo_landau_xi(double beta, double thick, const kfo_material* m) {
+  return 0.5 * KFO_K_BETHE * m->z_over_a * thick / (beta * beta);
+}
+
+/* Energy loss in a surface of x/X0 = xx0 crossed at |cos(incidence)| =
+ * cosinc, thickness rho x = xx0 X0rho / cosinc.  The mean loss dE is
+ * evaluated at the current state's momentum.  dir = +1 (forward): the
+ * particle leaves with E' = E - dE; dir = -1 (backward): the upstream energy
+ * E' = E + dE is restored.  On return *qop holds the new q/p, *jac the
+ * derivative d(q/p)'/d(q/p) at fixed dE, which is (p^3 E')/(p'^3 E), and
+ * *var_down the straggling variance of q/p on the downstream side: the
+ * energy spread is a Gaussian with the FWHM 4 xi of the Landau
+ * distribution, sigma_E = 4 xi / (2 sqrt(2 ln 2)), mapped to q/p by
+ * |d(q/p)/dE| = E/p^3 at the downstream energy and momentum.
+ * Returns KFO_NONFINITE when the particle would stop. */
+int kfo_energy_loss(double* qop, double mass, double xx0, double cosinc,
+                    const kfo_material* m, int dir, double* jac,
+                    double* var_down) {
+  *jac = 1.0;
+  *var_down = 0.0;
+  if (!(xx0 > 0.0)) return KFO_OK;
+  if (!(mass > 0.0)) return KFO_BAD_INPUT;
+  const double thick = xx0 * m->x0_rho / fabs(cosinc);
+  const double p = 1.0 / fabs(*qop);
+  const double E = sqrt(p * p + mass * mass);
+  const double beta = p / E;
+  const double dE = kfo_bethe(p / mass, mass, m) * thick;
+  const double E2 = dir > 0 ? E - dE : E + dE;
+  if (!(E2 > mass)) return KFO_NONFINITE;
+  const double p2 = sqrt(E2 * E2 - mass * mass);
+  const double sigE = 4.0 * kfo_landau_xi(beta, thick, m) / (2.0 * sqrt(2.0 * log(2.0)));
+  *jac = (p * p * p * E2) / (p2 * p2 * p2 * E);
+  const double Ed = dir > 0 ? E2 : E, pd = dir > 0 ? p2 : p;
+  const double dqdE = Ed / (pd * pd * pd);
+  *var_down = dqdE * dqdE * sigE * sigE;
+  *qop = (*qop > 0.0 ? 1.0 : -1.0) / p2;
+  return KFO_OK;
 }
 
 /* ------------------------------------------------------------------ */
@@ -430,17 +593,84 @@ int kfo_rts_step(const double xf[6], const double Cf[36], const double xp1[6],
   return KFO_OK;
 }
 
-/* Shared forward/backward skeleton: the caller has filled xp[0], Cp[0]
- * (the prior) and a prediction callback for k >= 1. */
+/* Solve A X = Bm for a general 6x6 A (Gaussian elimination with partial
+ * pivoting), k right-hand sides.  Returns KFO_NON_SPD on a zero pivot. */
+static int gen_solve6(const double A[36], const double* Bm, int k, double* X) {
+  double M[36];
+  memcpy(M, A, sizeof(M));
+  double* R = (double*)malloc(sizeof(double) * 6 * k);
+  memcpy(R, Bm, sizeof(double) * 6 * k);
+  for (int c = 0; c < 6; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 6; ++r)
+      if (fabs(M[r * 6 + c]) > fabs(M[piv * 6 + c])) piv = r;
+    if (!(fabs(M[piv * 6 + c]) > 0.0)) {
+      free(R);
+      return KFO_NON_SPD;
+    }
+    if (piv != c) {
+      for (int j = 0; j < 6; ++j) {
+        const double t = M[c * 6 + j];
+        M[c * 6 + j] = M[piv * 6 + j];
+        M[piv * 6 + j] = t;
+      }
+      for (int j = 0; j < k; ++j) {
+        const double t = R[c * k + j];
+        R[c * k + j] = R[piv * k + j];
+        R[piv * k + j] = t;
+      }
+    }
+    for (int r = c + 1; r < 6; ++r) {
+      const double f = M[r * 6 + c] / M[c * 6 + c];
+      for (int j = c; j < 6; ++j) M[r * 6 + j] -= f * M[c * 6 + j];
+      for (int j = 0; j < k; ++j) R[r * k + j] -= f * R[c * k + j];
+    }
+  }
+  for (int j = 0; j < k; ++j)
+    for (int r = 5; r >= 0; --r) {
+      double t = R[r * k + j];
+      for (int q = r + 1; q < 6; ++q) t -= M[r * 6 + q] * X[q * k + j];
+      X[r * k + j] = t / M[r * 6 + r];
+    }
+  free(R);
+  return KFO_OK;
+}
+
+/* Weighted mean of two estimates of the same state (the smoothed state of
+ * the two-filter smoother, Sect. 2 and Fig. 2):
+ *   K = Cf (Cf + Cb)^-1,  xs = xf + K (xb - xf),  Cs = Cf - K Cf. */
+static int weighted_mean(const double xf[6], const double Cf[36],
+                         const double xb[6], const double Cb[36], double xs[6],
+                         double Cs[36]) {
+  double Sum[36], X[36], K[36], KC[36];
+  for (int i = 0; i < 36; ++i) Sum[i] = Cf[i] + Cb[i];
+  int st = spd_solve6(Sum, Cf, 6, X); /* X = (Cf + Cb)^-1 Cf = K^T */
+  if (st) return st;
+  mat_transpose(X, K, 6, 6);
+  for (int i = 0; i < 6; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 6; ++j) s += K[i * 6 + j] * (xb[j] - xf[j]);
+    xs[i] = xf[i] + s;
+  }
+  mat_mul(K, Cf, KC, 6, 6, 6);
+  for (int i = 0; i < 36; ++i) Cs[i] = Cf[i] - KC[i];
+  return KFO_OK;
+}
+
+/* Prediction callbacks: forward k-1 -> k (fills xp, Cp and the transition
+ * Jacobian F) and backward k -> k-1. */
 typedef int (*predict_fn)(void* ctx, int k, const double* xf_prev,
                           const double* Cf_prev, double* xp, double* Cp,
                           double* F);
+typedef int (*bpredict_fn)(void* ctx, int k, const double* xb,
+                           const double* Cb, double* xo, double* Co);
 
-static int filter_smooth(int n, predict_fn predict, void* ctx,
-                         const double* m, const double* V,
-                         const uint8_t* hole, double* xp, double* Cp,
-                         double* xf, double* Cf, double* xs, double* Cs,
-                         double* F, double* chi2) {
+/* Forward filter over n states; the caller has filled xp[0], Cp[0] (the
+ * prior). */
+static int forward_filter(int n, predict_fn predict, void* ctx,
+                          const double* m, const double* V,
+                          const uint8_t* hole, double* xp, double* Cp,
+                          double* xf, double* Cf, double* F, double* chi2) {
   for (int k = 0; k < n; ++k) {
     if (k > 0) {
       int st = predict(ctx, k, xf + 6 * (k - 1), Cf + 36 * (k - 1), xp + 6 * k,
@@ -459,7 +689,13 @@ static int filter_smooth(int n, predict_fn predict, void* ctx,
       if (st) return st;
     }
   }
-  /* RTS: start from the last filtered state. */
+  return KFO_OK;
+}
+
+/* RTS smoother from the last filtered state back to state 0. */
+static int rts_smooth(int n, const double* xp, const double* Cp,
+                      const double* xf, const double* Cf, const double* F,
+                      double* xs, double* Cs) {
   memcpy(xs + 6 * (n - 1), xf + 6 * (n - 1), sizeof(double) * 6);
   memcpy(Cs + 36 * (n - 1), Cf + 36 * (n - 1), sizeof(double) * 36);
   for (int k = n - 2; k >= 0; --k) {
@@ -470,6 +706,56 @@ static int filter_smooth(int n, predict_fn predict, void* ctx,
     if (st) return st;
   }
   return KFO_OK;
+}
+
+/* Backward-filter smoother (Sect. 2, Fig. 2): a second Kalman filter runs
+ * from the last state to the first, with its own propagation.  It starts at
+ * state n-1 from the forward-filtered parameters with the covariance
+ * scale * Cf_{n-1} (a nearly uninformative start), takes the measurement of
+ * each state it reaches, and its prediction onto state k is combined with
+ * the forward-filtered state k by the weighted mean.  State n-1 keeps the
+ * forward-filtered state (as in the RTS smoother). */
+static int backward_filter_smooth(int n, bpredict_fn bpredict, void* ctx,
+                                  const double* m, const double* V,
+                                  const uint8_t* hole, const double* xf,
+                                  const double* Cf, double scale, double* xs,
+                                  double* Cs) {
+  double xb[6], Cb[36];
+  memcpy(xs + 6 * (n - 1), xf + 6 * (n - 1), sizeof(double) * 6);
+  memcpy(Cs + 36 * (n - 1), Cf + 36 * (n - 1), sizeof(double) * 36);
+  memcpy(xb, xf + 6 * (n - 1), sizeof(xb));
+  for (int i = 0; i < 36; ++i) Cb[i] = scale * Cf[36 * (n - 1) + i];
+  for (int k = n - 1; k >= 1; --k) {
+    if (!hole[k]) {
+      double xu[6], Cu[36], c2;
+      int st = kfo_update(xb, Cb, m + 2 * k, V + 4 * k, xu, Cu, &c2);
+      if (st) return st;
+      memcpy(xb, xu, sizeof(xb));
+      memcpy(Cb, Cu, sizeof(Cb));
+    }
+    double xo[6], Co[36];
+    int st = bpredict(ctx, k, xb, Cb, xo, Co);
+    if (st) return st;
+    memcpy(xb, xo, sizeof(xb));
+    memcpy(Cb, Co, sizeof(Cb));
+    st = weighted_mean(xf + 6 * (k - 1), Cf + 36 * (k - 1), xb, Cb,
+                       xs + 6 * (k - 1), Cs + 36 * (k - 1));
+    if (st) return st;
+  }
+  return KFO_OK;
+}
+
+static int filter_smooth(int n, predict_fn predict, bpredict_fn bpredict,
+                         void* ctx, const double* m, const double* V,
+                         const uint8_t* hole, int smoother, double bf_scale,
+                         double* xp, double* Cp, double* xf, double* Cf,
+                         double* xs, double* Cs, double* F, double* chi2) {
+  int st = forward_filter(n, predict, ctx, m, V, hole, xp, Cp, xf, Cf, F, chi2);
+  if (st) return st;
+  if (smoother == KFO_SMOOTHER_BACKWARD_FILTER)
+    return backward_filter_smooth(n, bpredict, ctx, m, V, hole, xf, Cf,
+                                  bf_scale, xs, Cs);
+  return rts_smooth(n, xp, Cp, xf, Cf, F, xs, Cs);
 }
 
 /* linear model: xp = F xf, Cp = F Cf F^T + Q */
@@ -489,10 +775,33 @@ static int predict_linear(void* vctx, int k, const double* xf_prev,
   return KFO_OK;
 }
 
+/* backward: x_{k-1} = F_k^-1 (x_k - w_k), Cb' = F_k^-1 (Cb + Q_k) F_k^-T */
+static int bpredict_linear(void* vctx, int k, const double* xb,
+                           const double* Cb, double* xo, double* Co) {
+  const linear_ctx* ctx = (const linear_ctx*)vctx;
+  const double* Fk = ctx->F + 36 * k;
+  double M[36], Y[36], YT[36];
+  for (int i = 0; i < 36; ++i) M[i] = Cb[i] + ctx->Q[36 * k + i];
+  int st = gen_solve6(Fk, xb, 1, xo);
+  if (st) return st;
+  st = gen_solve6(Fk, M, 6, Y); /* F^-1 M */
+  if (st) return st;
+  mat_transpose(Y, YT, 6, 6);   /* M F^-T */
+  return gen_solve6(Fk, YT, 6, Co);
+}
+
 int kfo_linear_fit(int n, const double x0[6], const double C0[36],
                    const double* F, const double* Q, const double* m,
                    const double* V, const uint8_t* hole, double* xs,
                    double* Cs, double* chi2) {
+  return kfo_linear_fit_ex(n, x0, C0, F, Q, m, V, hole, KFO_SMOOTHER_RTS, 0.0,
+                           xs, Cs, chi2);
+}
+
+int kfo_linear_fit_ex(int n, const double x0[6], const double C0[36],
+                      const double* F, const double* Q, const double* m,
+                      const double* V, const uint8_t* hole, int smoother,
+                      double bf_scale, double* xs, double* Cs, double* chi2) {
   double* buf = (double*)malloc(sizeof(double) * n * (6 + 36) * 3);
   double* xp = buf;
   double* xf = xp + 6 * n;
@@ -502,15 +811,17 @@ int kfo_linear_fit(int n, const double x0[6], const double C0[36],
   memcpy(xp, x0, sizeof(double) * 6);
   memcpy(Cp, C0, sizeof(double) * 36);
   linear_ctx ctx = {F, Q};
-  int st = filter_smooth(n, predict_linear, &ctx, m, V, hole, xp, Cp, xf, Cf,
-                         xs, Cs, Fs, chi2);
+  int st = filter_smooth(n, predict_linear, bpredict_linear, &ctx, m, V, hole,
+                         smoother, bf_scale, xp, Cp, xf, Cf, xs, Cs, Fs, chi2);
   free(buf);
   return st;
 }
 
 /* track model: RKN transport between the track's surfaces plus the
- * multiple-scattering noise of the surface reached (added before the
- * update, so state k is the direction leaving surface k). */
+ * material effects of the surface reached (added before the update, so
+ * state k is the state leaving surface k): multiple-scattering noise on the
+ * angles and, optionally, the mean energy loss with its straggling noise on
+ * q/p. */
 typedef struct {
   const int32_t* surface_id;
   const double* center;
@@ -519,30 +830,96 @@ typedef struct {
   const double* B;
   double mass, h_max;
   int n_iter;
+  const kfo_method* meth; /* NULL: constant field, no energy loss */
 } track_ctx;
+
+static void unit_dir(const double x[6], double T[3]) {
+  T[0] = cos(x[2]) * sin(x[3]);
+  T[1] = sin(x[2]) * sin(x[3]);
+  T[2] = cos(x[3]);
+}
+
+/* multiple-scattering variances of (phi, theta) for the state x crossing
+ * surface sid (Highland width with the state's momentum and incidence) */
+static void scattering_noise(const track_ctx* ctx, int sid, const double x[6],
+                             double C[36]) {
+  const double xx0 = ctx->x_over_x0[sid];
+  if (!(xx0 > 0.0)) return;
+  double n[3], T[3];
+  rot_col(ctx->rot + 9 * sid, 2, n);
+  unit_dir(x, T);
+  const double th0 = kfo_highland(x[4], ctx->mass, xx0, dot3(n, T));
+  const double st_ = sin(x[3]);
+  C[2 * 6 + 2] += th0 * th0 / (st_ * st_);
+  C[3 * 6 + 3] += th0 * th0;
+}
+
+static double incidence(const track_ctx* ctx, int sid, const double x[6]) {
+  double n[3], T[3];
+  rot_col(ctx->rot + 9 * sid, 2, n);
+  unit_dir(x, T);
+  return dot3(n, T);
+}
+
+/* scale row and column 4 (q/p) of a 6x6 matrix by g */
+static void scale_qop(double C[36], double g) {
+  for (int j = 0; j < 6; ++j) C[4 * 6 + j] *= g;
+  for (int j = 0; j < 6; ++j) C[j * 6 + 4] *= g;
+}
 
 static int predict_track(void* vctx, int k, const double* xf_prev,
                          const double* Cf_prev, double* xp, double* Cp,
                          double* F) {
   const track_ctx* ctx = (const track_ctx*)vctx;
+  const kfo_field_map* map = ctx->meth ? ctx->meth->map : NULL;
   const int sa = ctx->surface_id[k - 1], sb = ctx->surface_id[k];
-  int st = kfo_transport(ctx->center + 3 * sa, ctx->rot + 9 * sa, xf_prev,
-                         ctx->center + 3 * sb, ctx->rot + 9 * sb, ctx->B,
-                         ctx->mass, ctx->h_max, ctx->n_iter, xp, F, NULL);
+  int st = kfo_transport_field(ctx->center + 3 * sa, ctx->rot + 9 * sa, xf_prev,
+                               ctx->center + 3 * sb, ctx->rot + 9 * sb, ctx->B,
+                               map, ctx->mass, ctx->h_max, ctx->n_iter, xp, F,
+                               NULL);
   if (st) return st;
   sandwich6(F, Cf_prev, Cp);
-  const double xx0 = ctx->x_over_x0[sb];
-  if (xx0 > 0.0) {
-    double n[3], T[3];
-    rot_col(ctx->rot + 9 * sb, 2, n);
-    T[0] = cos(xp[2]) * sin(xp[3]);
-    T[1] = sin(xp[2]) * sin(xp[3]);
-    T[2] = cos(xp[3]);
-    const double th0 = kfo_highland(xp[4], ctx->mass, xx0, dot3(n, T));
-    const double st_ = sin(xp[3]);
-    Cp[2 * 6 + 2] += th0 * th0 / (st_ * st_);
-    Cp[3 * 6 + 3] += th0 * th0;
+  scattering_noise(ctx, sb, xp, Cp);
+  if (ctx->meth && ctx->meth->energy_loss && ctx->x_over_x0[sb] > 0.0) {
+    /* q/p' = q/p after the mean loss; F <- G F and Cp <- G Cp G^T with
+     * G = diag(1, 1, 1, 1, jac, 1); then the straggling variance */
+    double jac, var;
+    st = kfo_energy_loss(&xp[4], ctx->mass, ctx->x_over_x0[sb],
+                         incidence(ctx, sb, xp), &ctx->meth->mat, +1, &jac, &var);
+    if (st) return st;
+    for (int j = 0; j < 6; ++j) F[4 * 6 + j] *= jac;
+    scale_qop(Cp, jac);
+    Cp[4 * 6 + 4] += var;
   }
+  return KFO_OK;
+}
+
+/* backward from state k (leaving surface k) to state k-1: the material of
+ * surface k is undone first (its noise added, the mean loss restored), then
+ * the RKN transport runs back to surface k-1 (negative path length). */
+static int bpredict_track(void* vctx, int k, const double* xb,
+                          const double* Cb, double* xo, double* Co) {
+  const track_ctx* ctx = (const track_ctx*)vctx;
+  const kfo_field_map* map = ctx->meth ? ctx->meth->map : NULL;
+  const int sa = ctx->surface_id[k - 1], sb = ctx->surface_id[k];
+  double x[6], C[36], F[36];
+  memcpy(x, xb, sizeof(x));
+  memcpy(C, Cb, sizeof(C));
+  scattering_noise(ctx, sb, x, C);
+  if (ctx->meth && ctx->meth->energy_loss && ctx->x_over_x0[sb] > 0.0) {
+    double jac, var;
+    int st = kfo_energy_loss(&x[4], ctx->mass, ctx->x_over_x0[sb],
+                             incidence(ctx, sb, x), &ctx->meth->mat, -1, &jac, &var);
+    if (st) return st;
+    C[4 * 6 + 4] += var;
+    scale_qop(C, jac);
+  }
+  int st = kfo_transport_field(ctx->center + 3 * sb, ctx->rot + 9 * sb, x,
+                               ctx->center + 3 * sa, ctx->rot + 9 * sa, ctx->B,
+                               map, ctx->mass, ctx->h_max, ctx->n_iter, xo, F,
+                               NULL);
+  if (st) return st;
+  sandwich6(F, C, Co);
   return KFO_OK;
 }
 
@@ -554,6 +931,19 @@ int kfo_fit_track(int n, const int32_t* surface_id, const double* loc,
                   double h_max, int n_iter, double* xp, double* Cp,
                   double* xf, double* Cf, double* xs, double* Cs, double* F,
                   double* chi2) {
+  return kfo_fit_track_ex(n, surface_id, loc, cov, is_hole, seed, seed_cov,
+                          n_surfaces, center, rot, x_over_x0, B, mass, h_max,
+                          n_iter, NULL, xp, Cp, xf, Cf, xs, Cs, F, chi2);
+}
+
+int kfo_fit_track_ex(int n, const int32_t* surface_id, const double* loc,
+                     const double* cov, const uint8_t* is_hole,
+                     const double seed[6], const double seed_cov[36],
+                     int n_surfaces, const double* center, const double* rot,
+                     const double* x_over_x0, const double B[3], double mass,
+                     double h_max, int n_iter, const kfo_method* meth,
+                     double* xp, double* Cp, double* xf, double* Cf,
+                     double* xs, double* Cs, double* F, double* chi2) {
   if (n < 1) return KFO_BAD_INPUT;
   for (int k = 0; k < n; ++k)
     if (surface_id[k] < 0 || surface_id[k] >= n_surfaces) return KFO_BAD_INPUT;
@@ -569,9 +959,11 @@ int kfo_fit_track(int n, const int32_t* surface_id, const double* loc,
   }
   memcpy(xp, seed, sizeof(double) * 6);
   memcpy(Cp, seed_cov, sizeof(double) * 36);
-  track_ctx ctx = {surface_id, center, rot, x_over_x0, B, mass, h_max, n_iter};
-  int st = filter_smooth(n, predict_track, &ctx, m, V, is_hole, xp, Cp, xf, Cf,
-                         xs, Cs, F, chi2);
+  track_ctx ctx = {surface_id, center, rot, x_over_x0, B, mass, h_max, n_iter, meth};
+  const int smoother = meth ? meth->smoother : KFO_SMOOTHER_RTS;
+  const double scale = meth ? meth->bf_scale : 0.0;
+  int st = filter_smooth(n, predict_track, bpredict_track, &ctx, m, V, is_hole,
+                         smoother, scale, xp, Cp, xf, Cf, xs, Cs, F, chi2);
   free(V);
   free(m);
   if (st) return st;
@@ -602,6 +994,7 @@ typedef struct {
   uint8_t* out_status;
   double* out_states;
   int t_begin, t_end;
+  const kfo_method* meth;
 } batch_job;
 
 static void unpack_sym(const double* packed, int64_t stride, int64_t t,
@@ -654,10 +1047,10 @@ static void fit_range(const batch_job* J) {
       double seed[6], C0[36];
       for (int i = 0; i < 6; ++i) seed[i] = J->seed_params[i * T + t];
       unpack_sym(J->seed_cov, T, t, C0);
-      st = kfo_fit_track(n, J->surface_id + o0, loc, cov, J->is_hole + o0, seed,
-                         C0, J->n_surfaces, J->center, J->rot, J->x_over_x0,
-                         J->B, J->mass, J->h_max, J->n_iter, xp, Cp, xf, Cf,
-                         xs, Cs, F, chi2);
+      st = kfo_fit_track_ex(n, J->surface_id + o0, loc, cov, J->is_hole + o0,
+                            seed, C0, J->n_surfaces, J->center, J->rot,
+                            J->x_over_x0, J->B, J->mass, J->h_max, J->n_iter,
+                            J->meth, xp, Cp, xf, Cf, xs, Cs, F, chi2);
       if (st == KFO_OK) {
         for (int k = 0; k < n; ++k)
           if (!J->is_hole[o0 + k]) {
@@ -707,13 +1100,32 @@ int kfo_fit_batch(int n_tracks, const int32_t* offsets,
                   double* out_cov, double* out_chi2, int32_t* out_ndf,
                   uint8_t* out_status, double* out_states, int t_begin,
                   int t_end, int n_threads) {
+  return kfo_fit_batch_ex(n_tracks, offsets, seed_params, seed_cov, n_surfaces,
+                          center, rot, x_over_x0, n_states, surface_id, loc,
+                          cov, is_hole, B, mass, h_max, n_iter, NULL,
+                          out_params, out_cov, out_chi2, out_ndf, out_status,
+                          out_states, t_begin, t_end, n_threads);
+}
+
+int kfo_fit_batch_ex(int n_tracks, const int32_t* offsets,
+                     const double* seed_params, const double* seed_cov,
+                     int n_surfaces, const double* center, const double* rot,
+                     const double* x_over_x0, int64_t n_states,
+                     const int32_t* surface_id, const double* loc,
+                     const double* cov, const uint8_t* is_hole,
+                     const double B[3], double mass, double h_max, int n_iter,
+                     const kfo_method* meth, double* out_params,
+                     double* out_cov, double* out_chi2, int32_t* out_ndf,
+                     uint8_t* out_status, double* out_states, int t_begin,
+                     int t_end, int n_threads) {
   if (n_tracks < 0 || t_begin < 0 || t_end > n_tracks || t_begin > t_end)
     return -1;
   if (n_threads < 1) n_threads = 1;
   batch_job base = {n_tracks, offsets, seed_params, seed_cov, n_surfaces,
                     center, rot, x_over_x0, n_states, surface_id, loc, cov,
                     is_hole, B, mass, h_max, n_iter, out_params, out_cov,
-                    out_chi2, out_ndf, out_status, out_states, t_begin, t_end};
+                    out_chi2, out_ndf, out_status, out_states, t_begin, t_end,
+                    meth};
   const int total = t_end - t_begin;
   if (n_threads == 1 || total < 2 * n_threads) {
     fit_range(&base);

@@ -16,6 +16,10 @@
  *   update with the 2D measurement (gain-matrix form, Joseph covariance);
  *   chi2_k = r^T S^-1 r of the predicted residual;
  *   then the Rauch-Tung-Striebel smoother back to state 0.
+ * Method variants the paper describes (kfo_method): the smoother as a
+ * backward Kalman filter combined with the forward one (Sect. 2, Fig. 2);
+ * the mean energy loss with straggling noise on q/p (Sect. 1); a
+ * position-dependent field given as a grid map (Sect. 4.3).
  *
  * Units: mm, GeV, tesla, ns.  Bound parameters x = (loc0, loc1, phi, theta,
  * q/p, t) (paper Sect. 2, parameter list).  Free parameters
@@ -45,6 +49,56 @@ enum {
 #define KFO_KAPPA 2.99792458e-4   /* GeV / (T mm): curvature = kappa*B*q/p */
 #define KFO_C_LIGHT 299.792458    /* mm / ns */
 
+/* Field map on a regular grid (the general, position-dependent field of
+ * Sect. 4.3): grid point (i, j, l) sits at origin + (i, j, l) * spacing and
+ * holds b[((l * ny + j) * nx + i) * 3 + c] (tesla).  nx, ny, nz >= 2. */
+typedef struct {
+  int nx, ny, nz;
+  double origin[3];
+  double spacing[3];
+  const double* b;
+} kfo_field_map;
+
+/* Material constants for the energy loss (one material for every surface;
+ * a surface's thickness is x/X0 * x0_rho in g/cm^2). */
+typedef struct {
+  double z_over_a;   /* Z/A, mol/g */
+  double i_exc;      /* mean excitation energy, GeV */
+  double x0_rho;     /* radiation length, g/cm^2 */
+  double sh_cbar, sh_x0, sh_x1, sh_a, sh_k, sh_delta0; /* density effect */
+} kfo_material;
+
+enum { KFO_SMOOTHER_RTS = 0, KFO_SMOOTHER_BACKWARD_FILTER = 1 };
+
+/* Method variants (Sect. 2: smoother by a backward filter; Sect. 1: energy
+ * loss in the material; Sect. 4.3: inhomogeneous field). */
+typedef struct {
+  int smoother;        /* KFO_SMOOTHER_* */
+  double bf_scale;     /* backward filter start: bf_scale * Cf of the last state */
+  int energy_loss;     /* 1: mean loss and straggling noise on q/p */
+  kfo_material mat;
+  const kfo_field_map* map; /* NULL: the constant field */
+} kfo_method;
+
+/* Field at r: B when map is NULL, else trilinear interpolation of the map
+ * (positions outside the grid are clamped onto it). */
+void kfo_field_at(const double B[3], const kfo_field_map* map,
+                  const double r[3], double out[3]);
+
+/* Density-effect correction, mean stopping power (GeV cm^2/g, unit charge),
+ * Landau scale xi (GeV) for a thickness in g/cm^2. */
+double kfo_density_effect(double bg, const kfo_material* m);
+double kfo_bethe(double bg, double mass, const kfo_material* m);
+double kfo_landau_xi(double beta, double thick, const kfo_material* m);
+
+/* Mean energy loss through a surface (dir = +1) or its restoration
+ * (dir = -1): updates *qop, returns the q/p Jacobian factor and the
+ * downstream straggling variance of q/p.  KFO_NONFINITE if the particle
+ * stops. */
+int kfo_energy_loss(double* qop, double mass, double xx0, double cosinc,
+                    const kfo_material* m, int dir, double* jac,
+                    double* var_down);
+
 /* Bound -> free on surface (c, R): f[8] and J_bf (8x6, row-major). */
 void kfo_bound_to_free(const double c[3], const double R[9], const double x[6],
                        double f[8], double J[48]);
@@ -54,6 +108,11 @@ void kfo_bound_to_free(const double c[3], const double R[9], const double x[6],
 void kfo_rkn_step(double f[8], double h, const double B[3], double mass,
                   double D[64]);
 
+/* The same step with the field of a map taken at the stage points (the
+ * step Jacobian holds the stage fields fixed). */
+void kfo_rkn_step_field(double f[8], double h, const double B[3],
+                        const kfo_field_map* map, double mass, double D[64]);
+
 /* Propagate free state f to the plane (c, R): ceil(|s0|/h_max) equal RKN
  * steps over the straight-line distance s0, then n_iter Newton corrections.
  * D (8x8) receives the product of the step Jacobians; *path the total length.
@@ -62,12 +121,24 @@ int kfo_propagate(double f[8], const double c[3], const double R[9],
                   const double B[3], double mass, double h_max, int n_iter,
                   double D[64], double* path);
 
+int kfo_propagate_field(double f[8], const double c[3], const double R[9],
+                        const double B[3], const kfo_field_map* map,
+                        double mass, double h_max, int n_iter, double D[64],
+                        double* path);
+
 /* Bound-to-bound transport of x on surface a to surface b: x_out and the
  * 6x6 Jacobian F = J_fb * P * D * J_bf.  Returns a KFO_* status. */
 int kfo_transport(const double ca[3], const double Ra[9], const double x[6],
                   const double cb[3], const double Rb[9], const double B[3],
                   double mass, double h_max, int n_iter, double x_out[6],
                   double F[36], double* path);
+
+int kfo_transport_field(const double ca[3], const double Ra[9],
+                        const double x[6], const double cb[3],
+                        const double Rb[9], const double B[3],
+                        const kfo_field_map* map, double mass, double h_max,
+                        int n_iter, double x_out[6], double F[36],
+                        double* path);
 
 /* Highland width theta0 for x/X0 = xx0 crossed at |cos(incidence)| = cosinc. */
 double kfo_highland(double qop, double mass, double xx0, double cosinc);
@@ -93,6 +164,12 @@ int kfo_linear_fit(int n, const double x0[6], const double C0[36],
                    const double* V, const uint8_t* hole, double* xs,
                    double* Cs, double* chi2);
 
+/* kfo_linear_fit with the smoother chosen (KFO_SMOOTHER_*). */
+int kfo_linear_fit_ex(int n, const double x0[6], const double C0[36],
+                      const double* F, const double* Q, const double* m,
+                      const double* V, const uint8_t* hole, int smoother,
+                      double bf_scale, double* xs, double* Cs, double* chi2);
+
 /* Full fit of one track with every intermediate: arrays of n states.
  * xp/xf/xs [n][6], Cp/Cf/Cs [n][36], F [n][36] (F[0] = identity),
  * chi2 [n].  Returns a KFO_* status. */
@@ -104,6 +181,16 @@ int kfo_fit_track(int n, const int32_t* surface_id, const double* loc,
                   double h_max, int n_iter, double* xp, double* Cp,
                   double* xf, double* Cf, double* xs, double* Cs, double* F,
                   double* chi2);
+
+/* kfo_fit_track with method variants (meth NULL: the baseline method). */
+int kfo_fit_track_ex(int n, const int32_t* surface_id, const double* loc,
+                     const double* cov, const uint8_t* is_hole,
+                     const double seed[6], const double seed_cov[36],
+                     int n_surfaces, const double* center, const double* rot,
+                     const double* x_over_x0, const double B[3], double mass,
+                     double h_max, int n_iter, const kfo_method* meth,
+                     double* xp, double* Cp, double* xf, double* Cf,
+                     double* xs, double* Cs, double* F, double* chi2);
 
 /* Batched fit:
  *   offsets[T+1]; seed_params[6][T]; seed_cov[21][T] (packed);
@@ -122,6 +209,19 @@ int kfo_fit_batch(int n_tracks, const int32_t* offsets,
                   double* out_cov, double* out_chi2, int32_t* out_ndf,
                   uint8_t* out_status, double* out_states, int t_begin,
                   int t_end, int n_threads);
+
+/* kfo_fit_batch with method variants (meth NULL: the baseline method). */
+int kfo_fit_batch_ex(int n_tracks, const int32_t* offsets,
+                     const double* seed_params, const double* seed_cov,
+                     int n_surfaces, const double* center, const double* rot,
+                     const double* x_over_x0, int64_t n_states,
+                     const int32_t* surface_id, const double* loc,
+                     const double* cov, const uint8_t* is_hole,
+                     const double B[3], double mass, double h_max, int n_iter,
+                     const kfo_method* meth, double* out_params,
+                     double* out_cov, double* out_chi2, int32_t* out_ndf,
+                     uint8_t* out_status, double* out_states, int t_begin,
+                     int t_end, int n_threads);
 
 #ifdef __cplusplus
 }

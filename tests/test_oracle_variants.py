@@ -1,0 +1,354 @@
+"""Pins of the oracle's method variants against things other than the
+oracle: the three variants the paper describes besides its baseline fit.
+
+* smoother as a backward Kalman filter combined with the forward filter by a
+  weighted mean (Sect. 2, Fig. 2): converges to batch least squares in the
+  linear-Gaussian case as its start becomes uninformative, agrees with the
+  Gauss-Newton fit of the helix model to the EKF's second order, and gives
+  pulls of unit width;
+* mean energy loss and straggling (Sect. 1): the PDG minimum stopping power
+  of silicon, the plasma-energy limit of the density effect, Landau's FWHM
+  (scipy's Landau distribution) and finite differences of the q/p map;
+* a position-dependent field given as a grid map (Sect. 4.3): exact
+  trilinear interpolation, a uniform map reproducing the constant field, and
+  RKN propagation against scipy's ODE solver on the same field.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_01796_gb300 import synth
+from tests import helix
+from tests.test_oracle_pins import R_TEL, _batch_posterior, plane
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_silicon():
+    vals = {}
+    with open(os.path.join(GOLDEN, "silicon_pdg.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+# ---------------------------------------------------------------- field map
+
+def _map_from(fn, origin, spacing, shape):
+    nx, ny, nz = shape
+    b = np.zeros((nz, ny, nx, 3))
+    for l in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                r = np.array(origin) + np.array([i, j, l]) * np.array(spacing)
+                b[l, j, i] = fn(r)
+    return {"origin": list(origin), "spacing": list(spacing), "b": b}
+
+
+def test_field_map_interpolation_is_exact_for_trilinear_fields():
+    rng = np.random.default_rng(0)
+    coef = rng.normal(size=(8, 3))
+
+    def fn(r):
+        x, y, z = r / 100.0
+        basis = np.array([1, x, y, z, x * y, y * z, x * z, x * y * z])
+        return basis @ coef
+
+    fm = _map_from(fn, (-50.0, -200.0, -300.0), (25.0, 50.0, 75.0), (6, 7, 8))
+    for _ in range(50):
+        r = np.array([-50.0, -200.0, -300.0]) + rng.random(3) * np.array([125.0, 300.0, 525.0])
+        assert np.allclose(oracle.field_at([0, 0, 0], r, fm), fn(r), rtol=0, atol=1e-12)
+    # nodes give the stored values; outside the grid the point is clamped
+    node = np.array([0.0, -100.0, -150.0])
+    assert np.allclose(oracle.field_at([0, 0, 0], node, fm), fn(node), atol=1e-13)
+    far = np.array([1000.0, -1000.0, 0.0])
+    clamped = np.array([75.0, -200.0, 0.0])
+    assert np.allclose(oracle.field_at([0, 0, 0], far, fm), fn(clamped), atol=1e-12)
+    # no map: the constant field
+    assert np.array_equal(oracle.field_at([0.1, 0.2, 2.0], far), [0.1, 0.2, 2.0])
+
+
+def test_uniform_field_map_reproduces_the_constant_field_fit():
+    ev = dict(synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 200)))
+    ref = oracle.fit_batch(ev, with_states=True)
+    B = np.asarray(ev["bfield"], dtype=float)
+    ev["field_map"] = _map_from(lambda r: B, (-100.0, -800.0, -800.0), (300.0, 400.0, 400.0), (4, 5, 5))
+    out = oracle.fit_batch(ev, with_states=True)
+    sd = np.sqrt(np.stack([ref["cov"][i * (i + 1) // 2 + i] for i in range(6)]))
+    assert np.array_equal(out["status"], ref["status"])
+    assert np.max(np.abs(out["params"] - ref["params"]) / sd) < 1e-9
+    assert np.max(np.abs(out["cov"] - ref["cov"]) / np.abs(ref["cov"]).max(axis=0)) < 1e-9
+    assert np.max(np.abs(out["chi2"] - ref["chi2"])) < 1e-9 * ref["chi2"].max()
+
+
+def _gradient_field(r):
+    # linear in position, hence represented exactly by trilinear interpolation
+    return np.array([1e-4 * r[2], 0.0, 2.0 - 1e-3 * r[0]])
+
+
+@pytest.mark.parametrize("qop", [2.0, -2.0])
+def test_rkn_in_a_field_map_matches_the_ode_solution(qop):
+    """A 0.5 GeV track through 10 planes in a field with a gradient, RKN
+    steps of at most 5 mm, against scipy's DOP853 integration of
+    r'' = (q/p) kappa r' x B(r) on the same field (rtol 1e-12), crossing
+    each plane by an event; the RKN error falls as h^4."""
+    from scipy.integrate import solve_ivp
+
+    fm = _map_from(_gradient_field, (-100.0, -1000.0, -1000.0), (100.0, 250.0, 250.0), (11, 9, 9))
+    kappa = 2.99792458e-4
+    x0 = np.array([1.0, -2.0, 0.2, 1.4, qop, 0.0])
+    planes = [30.0 * (i + 1) for i in range(10)]
+
+    def rhs(s, y):
+        T = y[3:]
+        return np.concatenate([T, qop * kappa * np.cross(T, _gradient_field(y[:3]))])
+
+    sp, cp, st, ct = math.sin(x0[2]), math.cos(x0[2]), math.sin(x0[3]), math.cos(x0[3])
+    y = np.array([0.0, x0[0], x0[1], cp * st, sp * st, ct])
+    truth = []
+    for xp in planes:
+        ev = lambda s, yy, xp=xp: yy[0] - xp
+        ev.terminal = True
+        sol = solve_ivp(rhs, (0.0, 500.0), y, method="DOP853", rtol=1e-12, atol=1e-12, events=ev)
+        y = sol.y_events[0][0]
+        truth.append(y[1:3].copy())
+    errs = []
+    for h_max in (10.0, 5.0):
+        ca, Ra = plane(0.0)
+        cur = x0.copy()
+        worst = 0.0
+        for xp, tr in zip(planes, truth):
+            cb, Rb = plane(xp)
+            stt, cur, F, path = oracle.transport_field(ca, Ra, cur, cb, Rb, [0, 0, 0], fm, h_max=h_max)
+            assert stt == oracle.OK
+            worst = max(worst, np.max(np.abs(cur[:2] - tr)))
+            ca, Ra = cb, Rb
+        errs.append(worst)
+    assert errs[1] < 1e-6
+    assert errs[0] / max(errs[1], 1e-15) > 8.0
+
+
+def test_field_map_jacobian_leaves_out_only_the_gradient_term():
+    """The transport Jacobian holds the stage fields fixed: in a uniform map
+    it equals finite differences; in a map with a gradient it differs from
+    them only by the small field-gradient term."""
+    fm_u = _map_from(lambda r: np.array([0.0, 0.0, 2.0]), (-100.0, -1000.0, -1000.0),
+                     (100.0, 250.0, 250.0), (11, 9, 9))
+    fm_g = _map_from(_gradient_field, (-100.0, -1000.0, -1000.0), (100.0, 250.0, 250.0), (11, 9, 9))
+    x0 = np.array([1.0, -2.0, 0.2, 1.4, 1.0, 0.0])
+    ca, Ra = plane(0.0)
+    cb, Rb = plane(60.0)
+    for fm, tol in ((fm_u, 1e-6), (fm_g, 3e-3)):
+        st, xo, F, _ = oracle.transport_field(ca, Ra, x0, cb, Rb, [0, 0, 0], fm)
+        Ffd = np.zeros((6, 6))
+        hs = [1e-4, 1e-4, 1e-6, 1e-6, 1e-6, 1e-4]
+        for j in range(6):
+            xp_, xm_ = x0.copy(), x0.copy()
+            xp_[j] += hs[j]
+            xm_[j] -= hs[j]
+            _, yp, _, _ = oracle.transport_field(ca, Ra, xp_, cb, Rb, [0, 0, 0], fm)
+            _, ym, _, _ = oracle.transport_field(ca, Ra, xm_, cb, Rb, [0, 0, 0], fm)
+            Ffd[:, j] = (yp - ym) / (2 * hs[j])
+        scale = np.maximum(np.abs(Ffd).max(axis=0), 1e-12)
+        assert np.max(np.abs(F - Ffd) / scale) < tol
+
+
+# ---------------------------------------------------------------- energy loss
+
+def test_bethe_minimum_ionization_of_silicon_matches_pdg():
+    g = _golden_silicon()
+    bgs = np.exp(np.linspace(math.log(1.0), math.log(30.0), 4000))
+    d = np.array([oracle.bethe(bg) for bg in bgs]) * 1e3  # MeV cm^2/g
+    i = int(np.argmin(d))
+    assert abs(d[i] - g["dedx_min_MeV_cm2_per_g"]) < 0.005 * g["dedx_min_MeV_cm2_per_g"]
+    assert 2.5 < bgs[i] < 4.5
+    # the loss falls as 1/beta^2 below the minimum and rises slowly above it
+    assert oracle.bethe(0.5) > 3 * oracle.bethe(bgs[i])
+    assert 1.0 < oracle.bethe(1000.0) / oracle.bethe(bgs[i]) < 1.5
+
+
+def test_density_effect_high_energy_limit_from_plasma_energy():
+    g = _golden_silicon()
+    hw = 28.816 * math.sqrt(g["density_g_cm3"] * 0.49848)  # eV
+    assert abs(hw - g["plasma_energy_eV"]) < 0.01
+    for bg in (1e3, 1e4, 1e5):
+        limit = 2.0 * (math.log(hw / 173.0) + math.log(bg) - 0.5)
+        assert abs(oracle.density_effect(bg) - limit) < 2e-3
+    # below the lower bound of the parameterisation the correction is small
+    assert 0.0 < oracle.density_effect(1.0) < 0.15
+
+
+def test_straggling_width_is_the_landau_fwhm():
+    """sigma_E * 2 sqrt(2 ln 2) = 4 xi, Landau's FWHM: scipy's Landau
+    distribution (a stable law with alpha = beta = 1, scale 1) has a FWHM
+    2/pi times that of Landau's lambda variable, whose FWHM is ~4.02 xi."""
+    from scipy import stats
+    from scipy.optimize import brentq
+
+    pdf = stats.landau.pdf
+    xs = np.linspace(-3.0, 5.0, 80001)
+    mode = xs[np.argmax(pdf(xs))]
+    half = pdf(mode) / 2
+    fwhm = brentq(lambda x: pdf(x) - half, mode, 20.0) - brentq(lambda x: pdf(x) - half, -5.0, mode)
+    fwhm_lambda = fwhm * math.pi / 2
+    for p in (0.5, 5.0):
+        qop = 1.0 / p
+        st, q2, jac, var = oracle.energy_loss(qop, 0.01, 1.0)
+        E2 = math.sqrt((1.0 / abs(q2)) ** 2 + oracle.MUON_MASS ** 2)
+        p2 = 1.0 / abs(q2)
+        sigE = math.sqrt(var) * p2 ** 3 / E2
+        beta = p / math.sqrt(p * p + oracle.MUON_MASS ** 2)
+        xi = oracle.landau_xi(beta, 0.01 * 21.82)
+        assert abs(sigE * 2 * math.sqrt(2 * math.log(2)) / xi - fwhm_lambda) < 0.01 * fwhm_lambda
+
+
+@pytest.mark.parametrize("p", [0.3, 1.0, 20.0])
+def test_energy_loss_map_jacobian_and_reversal(p):
+    qop = -1.0 / p
+    xx0, ci = 0.01, 0.8
+    st, q2, jac, var = oracle.energy_loss(qop, xx0, ci)
+    assert st == oracle.OK and q2 < 0 and abs(q2) > abs(qop)
+    # mean loss = stopping power x thickness (x/X0 X0rho / cos)
+    E = math.sqrt(p * p + oracle.MUON_MASS ** 2)
+    E2 = math.sqrt(1.0 / q2 ** 2 + oracle.MUON_MASS ** 2)
+    assert abs((E - E2) - oracle.bethe(p / oracle.MUON_MASS) * xx0 * 21.82 / ci) < 1e-15
+    # jac: central differences of the map; they also carry the slow change
+    # of the loss with energy, which the Jacobian leaves out (a few % of jac-1)
+    h = 1e-6 * abs(qop)
+    qa = oracle.energy_loss(qop + h, xx0, ci)[1]
+    qb = oracle.energy_loss(qop - h, xx0, ci)[1]
+    jfd = (qa - qb) / (2 * h)
+    assert abs((jfd - 1) - (jac - 1)) < 0.05 * abs(jac - 1)
+    # restoring the loss comes back to the start up to the change of the
+    # loss between the two energies
+    st, q3, jac3, var3 = oracle.energy_loss(q2, xx0, ci, direction=-1)
+    assert st == oracle.OK
+    assert abs(q3 - qop) < 1e-3 * abs(q2 - qop)
+    # no material: nothing changes
+    assert oracle.energy_loss(qop, 0.0, 1.0) == (oracle.OK, qop, 1.0, 0.0)
+
+
+def test_particle_that_stops_is_reported():
+    st, *_ = oracle.energy_loss(1.0 / 0.0105, 50.0, 1.0)  # 10 MeV/c muon through 50 X0
+    assert st == oracle.NONFINITE
+
+
+def test_energy_loss_fit_moves_q_over_p_only_on_material():
+    """q/p changes only where a surface has material: on a telescope with
+    material on every other plane the filtered-to-predicted q/p step is zero
+    on the others."""
+    w = synth.scaled(synth.WORKLOADS["tel10_1k"], 5)
+    ev = dict(synth.make_event(w))
+    xx0 = np.array(ev["x_over_x0"], dtype=float)
+    xx0[1::2] = 0.0
+    ev["x_over_x0"] = xx0
+    for t in range(5):
+        r = oracle.fit_track(ev, t, method={"energy_loss": True})
+        assert r["status"] == oracle.OK
+        o0 = ev["offsets"][t]
+        for k in range(1, len(r["xp"])):
+            sid = ev["surface_id"][o0 + k]
+            moved = abs(1 / r["xp"][k][4]) < abs(1 / r["xf"][k - 1][4])
+            assert moved == (xx0[sid] > 0)
+
+
+# ---------------------------------------------------------------- backward filter
+
+def _linear_problem(seed):
+    rng = np.random.default_rng(seed)
+    n = 9
+    Fs = np.zeros((n, 6, 6)); Gs = np.zeros((n, 6, 2)); Qs = np.zeros((n, 6, 6)); qs = np.ones((n, 2))
+    for k in range(1, n):
+        F = np.eye(6)
+        F[0, 2] = 30.0 + rng.normal(); F[1, 3] = -30.0 + rng.normal()
+        F[0, 4] = 0.3 * rng.normal(); F[2, 4] = 0.02 * rng.normal()
+        F[5, 2] = 0.02 * rng.normal(); F[5, 4] = 1e-3
+        Fs[k] = F
+        Gs[k, 2, 0] = 1.0; Gs[k, 3, 1] = 1.0
+        qs[k] = [(2e-4) ** 2 * (1 + rng.random()), (2e-4) ** 2]
+        Qs[k] = Gs[k] @ np.diag(qs[k]) @ Gs[k].T
+    x0 = rng.normal(size=6) * [0.5, 0.5, 5e-3, 5e-3, 0.05, 1.0]
+    C0 = np.diag(np.array([0.5, 0.5, 5e-3, 5e-3, 0.05, 1.0]) ** 2)
+    hole = np.zeros(n, dtype=np.uint8); hole[0] = 1; hole[4] = 1; hole[7] = 1
+    m = rng.normal(size=(n, 2)) * 0.05
+    V = np.array([np.array([[0.0025, 0.0003], [0.0003, 0.0016]]) for _ in range(n)])
+    return x0, C0, Fs, Gs, qs, Qs, m, V, hole
+
+
+def test_backward_filter_smoother_converges_to_least_squares():
+    """Linear-Gaussian model: the weighted mean of the forward filter and a
+    backward filter that starts from scale * Cf equals the batch
+    least-squares posterior up to the start's information, 1/scale of the
+    last state's: errors fall as 1/scale."""
+    x0, C0, Fs, Gs, qs, Qs, m, V, hole = _linear_problem(11)
+    xr, Cr = _batch_posterior(x0, C0, Fs, Gs, qs, m, V, hole)
+    errs = []
+    for scale in (1e3, 1e5):
+        st, xs, Cs, chi2 = oracle.linear_fit(x0, C0, Fs, Qs, m, V, hole, smoother="backward", bf_scale=scale)
+        assert st == oracle.OK
+        e = 0.0
+        for k in range(len(hole)):
+            sd = np.sqrt(np.diag(Cr[k]))
+            e = max(e, np.max(np.abs(xs[k] - xr[k]) / sd), np.max(np.abs(Cs[k] - Cr[k]) / np.outer(sd, sd)))
+        errs.append(e)
+    assert errs[1] < 2e-5
+    assert 50 < errs[0] / errs[1] < 200
+    # the forward chi2 is that of the baseline
+    st, xs0, Cs0, chi2_rts = oracle.linear_fit(x0, C0, Fs, Qs, m, V, hole)
+    assert np.array_equal(chi2, chi2_rts)
+
+
+@pytest.mark.parametrize("bz", [0.0, 2.0])
+def test_backward_filter_smoother_equals_gauss_newton_fit(bz):
+    """No material, seed = truth: the backward-filter smoother's state 0
+    equals the Gauss-Newton fit of the exact trajectory model to the EKF's
+    second order (linearisation about the backward filter's own, initially
+    poorly constrained, states): <= 5e-3 sigma at 5 um, falling in
+    proportion to the hit resolution (a mistake would stay O(sigma))."""
+    worst = []
+    for sig in (0.005, 0.0005):
+        w = synth.scaled(synth.WORKLOADS["tel10_1k"], 30, x_over_x0=0.0, bz=bz, sigma=sig,
+                         p_range=(20.0, 100.0) if bz else (1.0, 10.0))
+        ev = dict(synth.make_event(w))
+        ev["seed_params"] = ev["truth_params"].copy()
+        out = oracle.fit_batch(ev, n_threads=1, method={"smoother": "backward", "bf_scale": 1e6})
+        model = helix.telescope_model(w.plane_x, bz)
+        e = 0.0
+        for t in range(30):
+            o0, o1 = ev["offsets"][t], ev["offsets"][t + 1]
+            m = np.concatenate([ev["loc"][0, o0 + 1:o1], ev["loc"][1, o0 + 1:o1]])
+            C0 = oracle.unpack_sym(ev["seed_cov"][:, t])
+            x, C = helix.lsq_fit(model, m, w.sigma, ev["seed_params"][:, t], C0)
+            sd = np.sqrt(np.diag(C))
+            e = max(e, np.max(np.abs(out["params"][:, t] - x) / sd))
+            Cf = oracle.unpack_sym(out["cov"][:, t])
+            assert np.max(np.abs(Cf - C) / np.outer(sd, sd)) < 1e-3
+        worst.append(e)
+    assert worst[0] < 5e-3
+    assert worst[1] < 0.2 * worst[0]
+
+
+def test_backward_filter_smoother_pulls_and_boundary():
+    """Pulls of unit width and zero mean (Sect. 5.2) over a 30-plane
+    telescope with material and holes; the last state keeps the filtered
+    state, holes pass the prediction, chi2 is the forward filter's."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 6000))
+    out = oracle.fit_batch(ev, method={"smoother": "backward"})
+    ref = oracle.fit_batch(ev)
+    assert np.all(out["status"] == oracle.OK)
+    assert np.array_equal(out["chi2"], ref["chi2"]) and np.array_equal(out["ndf"], ref["ndf"])
+    sd = np.sqrt(np.stack([out["cov"][i * (i + 1) // 2 + i] for i in range(6)]))
+    pull = (out["params"] - ev["truth_params"]) / sd
+    N = pull.shape[1]
+    assert np.all(np.abs(pull.mean(1)) < 4 / math.sqrt(N))
+    assert np.all(np.abs(pull.std(1) - 1) < 4 / math.sqrt(2 * N))
+    for t in range(3):
+        r = oracle.fit_track(ev, t, method={"smoother": "backward"})
+        assert np.array_equal(r["xs"][-1], r["xf"][-1])
+        assert np.array_equal(r["Cs"][-1], r["Cf"][-1])

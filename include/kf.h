@@ -62,7 +62,7 @@
 extern "C" {
 #endif
 
-#define KF_ABI_VERSION 2
+#define KF_ABI_VERSION 3
 
 typedef enum {
   KF_SUCCESS = 0,
@@ -113,9 +113,50 @@ typedef struct {
   const uint8_t* is_hole;      /* [n_states] */
 } kf_measurements;
 
+/* Position-dependent field on a regular grid (paper Sect. 4.3 names
+ * inhomogeneous fields as the general case; its studies use a constant one).
+ * Grid point (i, j, l) sits at origin + (i, j, l) * spacing and holds
+ * b[((l * ny + j) * nx + i) * 3 + c], c = x, y, z, in tesla.  The field at a
+ * point is the trilinear interpolation of the 8 surrounding grid points;
+ * points outside the grid are clamped onto its boundary.  The RKN step takes
+ * the field at its stage points; its Jacobian holds those fields fixed (the
+ * field-gradient term is left out). */
+typedef struct {
+  int32_t nx, ny, nz;          /* grid points per axis, each >= 2 */
+  int32_t reserved;            /* 0 */
+  double origin[3];            /* mm */
+  double spacing[3];           /* mm, each > 0 */
+  const double* b;             /* [nz][ny][nx][3]: device pointer (host
+                                  pointer for kf_fit_host) */
+} kf_field_map;
+
 typedef struct {
   double b[3];                 /* constant field (Bx, By, Bz) in tesla */
+  const kf_field_map* map;     /* NULL: the constant field b; else the map
+                                  (b is then ignored).  A map needs
+                                  KF_PRECISION_FP64. */
 } kf_field;
+
+/* Material of the surfaces for the energy loss (one material for all; a
+ * surface's thickness is x/X0 * x0_rho in g/cm^2).  kf_default_options
+ * fills silicon: the PDG's Z/A, mean excitation energy, radiation length
+ * and Sternheimer density-effect parameters. */
+typedef struct {
+  double z_over_a;             /* mol/g */
+  double i_exc;                /* mean excitation energy, GeV */
+  double x0_rho;               /* radiation length, g/cm^2 */
+  double sh_cbar, sh_x0, sh_x1, sh_a, sh_k, sh_delta0;
+} kf_material;
+
+typedef enum {
+  KF_SMOOTHER_RTS = 0,             /* Rauch-Tung-Striebel with the stored
+                                      Jacobians (Sect. 2) */
+  KF_SMOOTHER_BACKWARD_FILTER = 1  /* a second Kalman filter run from the
+                                      last state to the first with its own
+                                      propagation, combined with the forward
+                                      filter by the weighted mean (Sect. 2,
+                                      Fig. 2) */
+} kf_smoother;
 
 typedef struct {
   double* params;              /* [6][n_tracks], required */
@@ -142,6 +183,16 @@ typedef struct {
                                   CUDA graph held by the handle and replays it
                                   while every argument is unchanged (needs a
                                   non-NULL stream) */
+  int32_t smoother;            /* kf_smoother (default RTS) */
+  int32_t energy_loss;         /* 1: mean energy loss (Bethe, with the
+                                  density effect) applied to q/p at every
+                                  surface with material, with its Jacobian
+                                  factor and a straggling variance on q/p
+                                  (Gaussian of the Landau FWHM 4 xi) */
+  double bf_scale;             /* backward filter: starting covariance is
+                                  bf_scale times the last filtered one
+                                  (default 1e4) */
+  kf_material material;        /* for energy_loss (default silicon) */
   int32_t resident_warps;      /* persistent schedules: warps kept resident on
                                   each SM (0 = as many as fit).  With U
                                   32-track units and W resident warps the
@@ -165,7 +216,12 @@ typedef enum {
 typedef struct kf_handle kf_handle;
 
 /* Fill *opt with the defaults: FP64, muon mass, h_max 50 mm, 3 corrections,
- * 128 threads per CTA, persistent schedule, default register variant. */
+ * 128 threads per CTA, persistent schedule, default register variant, RTS
+ * smoother, no energy loss, silicon material.
+ * Method variants (smoother = KF_SMOOTHER_BACKWARD_FILTER, energy_loss = 1,
+ * or a field map) run in a separate FP64 kernel: they need
+ * KF_PRECISION_FP64 (KF_EUNSUPPORTED otherwise) and are not available in
+ * kf_fit_static and kf_chi2_grad. */
 void kf_default_options(kf_options* opt);
 
 /* Create a handle bound to the current CUDA device.  Returns 0 or kf_error. */

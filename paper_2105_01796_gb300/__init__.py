@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libkfgb.so")
 KF_PRECISION_FP64 = 0
 KF_PRECISION_MIXED = 1
 KF_SCHEDULE_AUTO, KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED = -1, 0, 1, 2
+KF_SMOOTHER_RTS, KF_SMOOTHER_BACKWARD_FILTER = 0, 1
 TRACK_STATUS = {0: "ok", 1: "no_intersection", 2: "non_spd", 3: "nonfinite", 4: "bad_input"}
 MUON_MASS = 0.1056583755
 
@@ -50,8 +51,19 @@ class KfMeasurements(ctypes.Structure):
                 ("is_hole", ctypes.c_void_p)]
 
 
+class KfFieldMap(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("origin", ctypes.c_double * 3),
+                ("spacing", ctypes.c_double * 3), ("b", ctypes.c_void_p)]
+
+
 class KfField(ctypes.Structure):
-    _fields_ = [("b", ctypes.c_double * 3)]
+    _fields_ = [("b", ctypes.c_double * 3), ("map", ctypes.c_void_p)]
+
+
+class KfMaterial(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("z_over_a", "i_exc", "x0_rho", "sh_cbar", "sh_x0",
+                                                 "sh_x1", "sh_a", "sh_k", "sh_delta0")]
 
 
 class KfOutputs(ctypes.Structure):
@@ -65,7 +77,9 @@ class KfOptions(ctypes.Structure):
                 ("h_max", ctypes.c_double), ("n_iter", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("workspace_bytes", ctypes.c_int64),
                 ("schedule", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("resident_warps", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("smoother", ctypes.c_int32),
+                ("energy_loss", ctypes.c_int32), ("bf_scale", ctypes.c_double),
+                ("material", KfMaterial), ("resident_warps", ctypes.c_int32)]
 
 
 _lib = None
@@ -193,7 +207,15 @@ def _structs(ev, max_states):
                     _ptr(ev["x_over_x0"]))
     me = KfMeasurements(int(ev["surface_id"].shape[0]), _ptr(ev["surface_id"]),
                         _ptr(ev["loc"]), _ptr(ev["cov"]), _ptr(ev["is_hole"]))
-    fi = KfField((ctypes.c_double * 3)(*[float(b) for b in ev["bfield"]]))
+    fi = KfField((ctypes.c_double * 3)(*[float(b) for b in ev["bfield"]]), None)
+    fm = ev.get("field_map")
+    if fm is not None:
+        b = fm["b"]
+        nz, ny, nx = (int(v) for v in b.shape[:3])
+        m = KfFieldMap(nx, ny, nz, 0, (ctypes.c_double * 3)(*[float(v) for v in fm["origin"]]),
+                       (ctypes.c_double * 3)(*[float(v) for v in fm["spacing"]]), _ptr(b))
+        fi.map = ctypes.cast(ctypes.pointer(m), ctypes.c_void_p)
+        fi._map = m  # keeps the map struct alive with the field
     return tr, su, me, fi
 
 
@@ -213,6 +235,10 @@ def host_event(ev):
     out = dict(ev)
     for k, dt in _HOST_DTYPES.items():
         out[k] = np.ascontiguousarray(ev[k], dtype=dt)
+    if ev.get("field_map") is not None:
+        fm = dict(ev["field_map"])
+        fm["b"] = np.ascontiguousarray(fm["b"], dtype=np.float64)
+        out["field_map"] = fm
     return out
 
 
@@ -222,6 +248,10 @@ def event_to_device(ev, device="cuda"):
     out = dict(ev)
     for k, dt in _HOST_DTYPES.items():
         out[k] = torch.from_numpy(np.ascontiguousarray(ev[k], dtype=dt)).to(device)
+    if ev.get("field_map") is not None:
+        fm = dict(ev["field_map"])
+        fm["b"] = torch.from_numpy(np.ascontiguousarray(fm["b"], dtype=np.float64)).to(device)
+        out["field_map"] = fm
     out["max_states"] = max_states_of(ev["offsets"])
     return out
 

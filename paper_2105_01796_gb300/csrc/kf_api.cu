@@ -32,7 +32,7 @@ struct kf_handle {
   size_t ckpt_bytes = 0;
   // autotuner cache: best launch options per batch shape
   struct Tuned {
-    int32_t precision, n_tracks, max_states, n_surfaces, bz;
+    int32_t precision, n_tracks, max_states, n_surfaces, bz, variants;
     kf_options best;
     double ms;
   };
@@ -40,7 +40,7 @@ struct kf_handle {
   int n_tuned = 0;
   // cached CUDA graph of the last captured fit and the call it replays
   cudaGraphExec_t graph_exec = nullptr;
-  alignas(8) unsigned char graph_key[512];
+  alignas(8) unsigned char graph_key[1024];
   int32_t graph_launches = 0;
   // device copies for kf_fit_host
   void* dev_io = nullptr;
@@ -118,7 +118,37 @@ int validate(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* 
   if (opt->resident_warps < 0 || opt->resident_warps > 64) return KF_EINVAL;
   for (int i = 0; i < 3; ++i)
     if (!(fi->b[i] == fi->b[i])) return KF_EINVAL;
+  if (opt->smoother != KF_SMOOTHER_RTS && opt->smoother != KF_SMOOTHER_BACKWARD_FILTER) return KF_EUNSUPPORTED;
+  if (opt->energy_loss != 0 && opt->energy_loss != 1) return KF_EINVAL;
+  if (wants_variants(opt->smoother, opt->energy_loss, fi->map) && opt->precision != KF_PRECISION_FP64)
+    return KF_EUNSUPPORTED;
+  if (opt->smoother == KF_SMOOTHER_BACKWARD_FILTER && !(opt->bf_scale > 0.0 && opt->bf_scale < 1e300))
+    return KF_EINVAL;
+  if (opt->energy_loss) {
+    const kf_material& m = opt->material;
+    if (!(opt->mass > 0.0) || !(m.z_over_a > 0.0) || !(m.i_exc > 0.0) || !(m.x0_rho > 0.0)) return KF_EINVAL;
+  }
+  if (fi->map) {
+    const kf_field_map& f = *fi->map;
+    if (f.nx < 2 || f.ny < 2 || f.nz < 2 || !f.b) return KF_EINVAL;
+    for (int i = 0; i < 3; ++i)
+      if (!(f.spacing[i] > 0.0 && f.spacing[i] < 1e300) || !(f.origin[i] == f.origin[i])) return KF_EINVAL;
+  }
   return KF_SUCCESS;
+}
+
+// silicon as tabulated by the PDG (atomic and nuclear properties): Z/A, I,
+// X0 rho and the Sternheimer density-effect parameters
+void silicon(kf_material* m) {
+  m->z_over_a = 0.49848;
+  m->i_exc = 173.0e-9;
+  m->x0_rho = 21.82;
+  m->sh_cbar = 4.4355;
+  m->sh_x0 = 0.2015;
+  m->sh_x1 = 2.8716;
+  m->sh_a = 0.1492;
+  m->sh_k = 3.2546;
+  m->sh_delta0 = 0.14;
 }
 
 }  // namespace
@@ -138,6 +168,10 @@ void kf_default_options(kf_options* opt) {
   opt->min_blocks = 0;
   opt->use_graph = 0;
   opt->resident_warps = 0;
+  opt->smoother = KF_SMOOTHER_RTS;
+  opt->energy_loss = 0;
+  opt->bf_scale = 1e4;
+  silicon(&opt->material);
 }
 
 int kf_abi_version(void) { return KF_ABI_VERSION; }
@@ -273,6 +307,27 @@ int prepare_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   return KF_SUCCESS;
 }
 
+// method-variant fields of the launch parameters
+void fill_variants(FitParams* p, const kf_field* fi, const kf_options& opt) {
+  p->smoother = opt.smoother;
+  p->energy_loss = opt.energy_loss;
+  p->bf_scale = opt.bf_scale;
+  const kf_material& m = opt.material;
+  const double mat[9] = {m.z_over_a, m.i_exc, m.x0_rho, m.sh_cbar, m.sh_x0, m.sh_x1, m.sh_a, m.sh_k, m.sh_delta0};
+  for (int i = 0; i < 9; ++i) p->mat[i] = mat[i];
+  if (fi->map) {
+    const kf_field_map& f = *fi->map;
+    p->map_n[0] = f.nx;
+    p->map_n[1] = f.ny;
+    p->map_n[2] = f.nz;
+    for (int i = 0; i < 3; ++i) {
+      p->map_origin[i] = f.origin[i];
+      p->map_inv_spacing[i] = 1.0 / f.spacing[i];
+    }
+    p->map_b = f.b;
+  }
+}
+
 // Queue the fit on `stream` (no allocation, no synchronisation).
 int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
                 const kf_field* fi, const kf_options& opt, const kf_outputs* out, cudaStream_t stream,
@@ -319,12 +374,15 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   p.error_flag = h->error_flag;
   p.order = opt.schedule == KF_SCHEDULE_SORTED ? h->order : nullptr;
   p.resident_warps = opt.resident_warps;
+  const bool variants = wants_variants(opt.smoother, opt.energy_loss, fi->map);
+  if (variants) fill_variants(&p, fi, opt);
   int c = 0;
   for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk, ++c) {
     p.track0 = (int32_t)t0;
     p.n_tracks = (int32_t)((tr->n_tracks - t0) < chunk ? (tr->n_tracks - t0) : chunk);
     p.work_counter = opt.schedule == KF_SCHEDULE_GRID ? nullptr : h->counters + c;
-    e = launch_fit(p, opt.precision, opt.block, opt.min_blocks, stream);
+    e = variants ? launch_fit_variants(p, opt.block, stream)
+                 : launch_fit(p, opt.precision, opt.block, opt.min_blocks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "fit launch");
     ++launches;
   }
@@ -340,11 +398,12 @@ struct GraphKey {
   kf_field fi;
   kf_options opt;
   kf_outputs out;
+  kf_field_map map;  // the map the field points to (zero when none)
   void* stream;
   // the handle's buffers the graph's kernels point into
   const void* bufs[5];
 };
-static_assert(sizeof(GraphKey) <= 512, "graph key storage");
+static_assert(sizeof(GraphKey) <= 1024, "graph key storage");
 
 // Resident warps per SM (at least 4, at most 16) for which the
 // ceil(n_tracks / 32) units of a persistent launch fill every round but the
@@ -391,6 +450,7 @@ GraphKey make_key(const kf_handle* h, const kf_tracks* tr, const kf_surfaces* su
   k.fi = *fi;
   k.opt = opt;
   k.out = *out;
+  if (fi->map) k.map = *fi->map;
   k.stream = stream;
   k.bufs[0] = h->ws;
   k.bufs[1] = h->surf;
@@ -467,10 +527,11 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   int rc = validate(tr, su, me, fi, &base, out);
   if (rc) return rc;
   const int bz = fi->b[0] == 0.0 && fi->b[1] == 0.0;
+  const int variants = wants_variants(base.smoother, base.energy_loss, fi->map);
   for (int k = 0; k < h->n_tuned; ++k) {
     const kf_handle::Tuned& c = h->tuned[k];
     if (c.precision == base.precision && c.n_tracks == tr->n_tracks && c.max_states == tr->max_states &&
-        c.n_surfaces == su->n_surfaces && c.bz == bz) {
+        c.n_surfaces == su->n_surfaces && c.bz == bz && c.variants == variants) {
       *best_out = base;
       best_out->schedule = c.best.schedule;
       best_out->block = c.best.block;
@@ -564,6 +625,7 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   slot.max_states = tr->max_states;
   slot.n_surfaces = su->n_surfaces;
   slot.bz = bz;
+  slot.variants = variants;
   slot.best = best;
   slot.ms = best_t;
   *best_out = best;
@@ -585,6 +647,8 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   dummy.params = dummy.cov = dummy.chi2 = &one;
   int rc = validate(tr, su, me, fi, &opt, &dummy);
   if (rc) return rc;
+  // the adjoint differentiates the baseline method only
+  if (wants_variants(opt.smoother, opt.energy_loss, fi->map)) return KF_EUNSUPPORTED;
   cudaStream_t stream = (cudaStream_t)stream_v;
   if (grad_align) {
     cudaError_t e = cudaMemsetAsync(grad_align, 0, sizeof(double) * 6 * (size_t)su->n_surfaces, stream);
@@ -669,6 +733,13 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   const size_t o_sid = take(M * 4), o_loc = take(2 * M * 8), o_cov = take(3 * M * 8), o_h = take(M);
   const size_t o_p = take(6 * T * 8), o_pc = take(21 * T * 8), o_chi = take(T * 8), o_ndf = take(T * 4),
                o_st = take(T), o_states = take(out->states ? 6 * M * 8 : 0);
+  size_t map_bytes = 0;
+  if (fi->map) {
+    const kf_field_map& f = *fi->map;
+    if (f.nx < 2 || f.ny < 2 || f.nz < 2 || !f.b) return KF_EINVAL;
+    map_bytes = (size_t)f.nx * (size_t)f.ny * (size_t)f.nz * 3 * sizeof(double);
+  }
+  const size_t o_map = take(map_bytes);
   if (h->dev_io_bytes < off) {
     if (h->dev_io) cudaFree(h->dev_io);
     h->dev_io = nullptr;
@@ -683,7 +754,8 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
                    {o_sc, tr->seed_cov, 21 * T * 8},   {o_c, su->center, 3 * S * 8},
                    {o_r, su->rot, 9 * S * 8},          {o_x, su->x_over_x0, S * 8},
                    {o_sid, me->surface_id, M * 4},     {o_loc, me->loc, 2 * M * 8},
-                   {o_cov, me->cov, 3 * M * 8},        {o_h, me->is_hole, M}};
+                   {o_cov, me->cov, 3 * M * 8},        {o_h, me->is_hole, M},
+                   {o_map, fi->map ? fi->map->b : nullptr, map_bytes}};
   for (const Cp& c : in) {
     if (c.bytes == 0) continue;
     if (!c.src) return KF_EINVAL;
@@ -710,7 +782,14 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   dout.ndf = (int32_t*)(b + o_ndf);
   dout.status = (uint8_t*)(b + o_st);
   dout.states = out->states ? (double*)(b + o_states) : nullptr;
-  int rc = kf_fit_ex(h, &dtr, &dsu, &dme, fi, opt, &dout, stream_v);
+  kf_field dfi = *fi;
+  kf_field_map dmap;
+  if (fi->map) {
+    dmap = *fi->map;
+    dmap.b = (const double*)(b + o_map);
+    dfi.map = &dmap;
+  }
+  int rc = kf_fit_ex(h, &dtr, &dsu, &dme, &dfi, opt, &dout, stream_v);
   if (rc) return rc;
   const Cp outs[] = {{o_p, out->params, 6 * T * 8}, {o_pc, out->cov, 21 * T * 8}, {o_chi, out->chi2, T * 8},
                      {o_ndf, out->ndf, T * 4},      {o_st, out->status, T},     {o_states, out->states, 6 * M * 8}};

@@ -60,7 +60,22 @@ struct FitParams {
                            // units from this counter (zeroed before launch)
   const int32_t* order;    // non-null: slot s fits track order[s]
   int32_t resident_warps;  // persistent launch: warps per SM (0 = occupancy)
+  // method variants (the FP64 variant kernel)
+  int32_t smoother;        // 0 RTS, 1 backward filter + weighted mean
+  int32_t energy_loss;     // 1: mean loss and straggling on q/p
+  double bf_scale;         // backward filter start: bf_scale * Cf_{n-1}
+  double mat[9];           // z_over_a, i_exc, x0_rho, Sternheimer cbar, x0,
+                           // x1, a, k, delta0
+  int32_t map_n[3];        // field-map grid points per axis
+  double map_origin[3];
+  double map_inv_spacing[3];
+  const double* map_b;     // null: the constant field bfield
 };
+
+// True when the options or the field ask for a method variant.
+inline bool wants_variants(int smoother, int energy_loss, const void* map) {
+  return smoother != 0 || energy_loss != 0 || map != nullptr;
+}
 
 // Pack the SoA surface table into [S][kSurfStride] doubles.
 cudaError_t launch_pack_surfaces(int n_surfaces, const double* center,
@@ -76,6 +91,10 @@ cudaError_t launch_selftest(long long n, unsigned long long* counters, cudaStrea
 // 0 = the default variant).
 cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks,
                        cudaStream_t stream);
+
+// The FP64 kernel of the method variants (kf_variants.cu): backward-filter
+// smoother, energy loss, field map; same records as the FP64 path.
+cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stream);
 
 // Gradients of sum_t w_t chi2_t with respect to the seeds and the
 // per-surface alignment (kf_adjoint.cu).  ckpt holds n_ckpt checkpoints of 27

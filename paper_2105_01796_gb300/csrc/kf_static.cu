@@ -88,6 +88,8 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   if (opt.schedule < KF_SCHEDULE_GRID || opt.schedule > KF_SCHEDULE_PERSISTENT) return KF_EUNSUPPORTED;
   if (opt.min_blocks < 0 || opt.min_blocks > 4) return KF_EUNSUPPORTED;
   if (opt.resident_warps < 0 || opt.resident_warps > 64) return KF_EINVAL;
+  // the static block serves the baseline method only
+  if (wants_variants(opt.smoother, opt.energy_loss, fi->map)) return KF_EUNSUPPORTED;
   // size limits of the static block
   if (su->n_surfaces > kMaxSurfaces) return KF_ESIZE;
   // one track's records (both precisions' parts, each 256-byte aligned) must fit

@@ -3,9 +3,14 @@
 This module only *simulates* inputs.  It holds none of the fit's arithmetic:
 no Runge-Kutta-Nystrom stepping, no Jacobians, no Kalman update or smoother.
 Truth trajectories are the closed-form helix of a unit charge in a constant
-field along z; multiple scattering is drawn with the Highland width at every
-crossed plane; hits are Gaussian-smeared local positions.  Both the CUDA path
-and the CPU oracle fit exactly these arrays.
+field along z, or, for a workload with a position-dependent field, a classical
+fourth-order Runge-Kutta integration of the equations of motion written with
+x as the independent variable (slopes dy/dx, dz/dx; 0.5 mm steps, every plane
+reached exactly); multiple scattering is drawn with the Highland width at
+every crossed plane; hits are Gaussian-smeared local positions.  Both the
+CUDA path and the CPU oracle fit exactly these arrays.  A field-map workload
+also returns the map (the analytic field sampled on a grid) that the fit
+interpolates.
 
 Stands in for the paper's Fatras single-muon samples (paper Sect. 5: a
 telescope of planes perpendicular to x, constant 2 T field along z, single
@@ -62,6 +67,13 @@ class Workload:
     misalign: tuple | None = None  # (shift sigma mm, rotation sigma rad) of the
                                    # true planes; the event keeps the nominal
                                    # geometry and records align_true
+    fringe: float = 0.0       # > 0: the field falls along x as
+                              # Bz = bz (1 - fringe (x/1000)^2) with the
+                              # matching Bx = -2 fringe bz x z / 1000^2
+                              # (curl-free in the x-z plane); the fit gets it
+                              # as a grid map
+    map_step: float = 25.0    # grid spacing of that map along x (mm); twice
+                              # that along y and z
 
 
 def _planes(n, step):
@@ -82,6 +94,8 @@ WORKLOADS = {
                          (1.0, 100.0), seed=4),
     "align20_100k": Workload("align20_100k", 100_000, _planes(20, 30.0), 0.005, 2.0, 0.050,
                              (1.0, 10.0), seed=3, misalign=(0.100, 0.001)),
+    "fringe30_100k": Workload("fringe30_100k", 100_000, _planes(30, 25.0), 0.01, 2.0, 0.030,
+                              (0.5, 100.0), seed=5, fringe=0.3),
 }
 
 
@@ -178,8 +192,122 @@ def _helix_at(x0, y0, z0, phi, st, ct, omega, s):
     return x, y, z, phi - omega * s
 
 
+def fringe_field(w: Workload, x, y, z):
+    """The analytic field of a fringe workload at (x, y, z) (arrays)."""
+    L2 = 1000.0 ** 2
+    bx = -2.0 * w.fringe * w.bz * x * z / L2
+    by = np.zeros_like(x)
+    bz = w.bz * (1.0 - w.fringe * x * x / L2)
+    return bx, by, bz
+
+
+def field_map_of(w: Workload) -> dict:
+    """Grid map of the fringe field covering the telescope: x from -50 mm
+    past the last plane, y and z over the plane size."""
+    hx = w.map_step
+    hy = 2.0 * w.map_step
+    x0 = -50.0
+    nx = int(math.ceil((max(w.plane_x) + 50.0 - x0) / hx)) + 1
+    y0 = -w.half_width - hy
+    ny = int(math.ceil(2 * (w.half_width + hy) / hy)) + 1
+    gx = x0 + hx * np.arange(nx)
+    gy = y0 + hy * np.arange(ny)
+    gz = y0 + hy * np.arange(ny)
+    Z, Y, X = np.meshgrid(gz, gy, gx, indexing="ij")
+    bx, by, bz = fringe_field(w, X, Y, Z)
+    return {"origin": [x0, y0, y0], "spacing": [hx, hy, hy],
+            "b": np.ascontiguousarray(np.stack([bx, by, bz], axis=-1))}
+
+
+def _advance_in_x(w, y, z, ty, tz, t, qop, gam, x_from, x_to):
+    """Classical RK4 in x of (y, z, ty, tz, t) with ty = dy/dx, tz = dz/dx:
+    d(ty)/dx = (q/p) k N [tz Bx + ty tz By - (1 + ty^2) Bz],
+    d(tz)/dx = (q/p) k N [(1 + tz^2) By - ty Bx - ty tz Bz],
+    dt/dx = N gam, N = sqrt(1 + ty^2 + tz^2) (gam = dt/ds)."""
+    nstep = max(1, int(math.ceil((x_to - x_from) / 0.5)))
+    dx = (x_to - x_from) / nstep
+
+    def deriv(x, s):
+        yy, zz, a, b, _ = s
+        bx, by, bz = fringe_field(w, np.full_like(yy, x), yy, zz)
+        N = np.sqrt(1.0 + a * a + b * b)
+        k = qop * _KAPPA * N
+        return (a, b, k * (b * bx + a * b * by - (1.0 + a * a) * bz),
+                k * ((1.0 + b * b) * by - a * bx - a * b * bz), N * gam)
+
+    s = (y, z, ty, tz, t)
+    x = x_from
+    for _ in range(nstep):
+        k1 = deriv(x, s)
+        k2 = deriv(x + dx / 2, tuple(v + dx / 2 * d for v, d in zip(s, k1)))
+        k3 = deriv(x + dx / 2, tuple(v + dx / 2 * d for v, d in zip(s, k2)))
+        k4 = deriv(x + dx, tuple(v + dx * d for v, d in zip(s, k3)))
+        s = tuple(v + dx / 6 * (a + 2 * b + 2 * c + d) for v, a, b, c, d in zip(s, k1, k2, k3, k4))
+        x += dx
+    return s
+
+
+def _simulate_fringe(w: Workload, ids, attempt, mass):
+    """_simulate for the fringe field: trajectories integrated in x."""
+    n = len(ids)
+    npl = len(w.plane_x)
+    s = w.seed
+    phi0 = -w.phi_half + 2 * w.phi_half * _uniform(s, ids, attempt, _P_PHI, 0)
+    th0 = (math.pi / 2 - w.theta_half) + 2 * w.theta_half * _uniform(s, ids, attempt, _P_THETA, 0)
+    q = np.where(_uniform(s, ids, attempt, _P_CHARGE, 0) < 0.5, -1.0, 1.0)
+    lo, hi = math.log(w.p_range[0]), math.log(w.p_range[1])
+    p = np.exp(lo + (hi - lo) * _uniform(s, ids, attempt, _P_MOM, 0))
+    qop = q / p
+    if w.nhit_range is None:
+        nhit = np.full(n, npl, dtype=np.int64)
+    else:
+        a, b = w.nhit_range
+        nhit = a + np.minimum((_uniform(s, ids, attempt, _P_NHIT, 0) * (b - a + 1)).astype(np.int64), b - a)
+    gam = np.sqrt(1.0 + mass * mass * qop * qop) / _C
+    ok = np.ones(n, dtype=bool)
+    loc = np.zeros((2, npl, n)); meas = np.zeros((2, npl, n))
+    leave = np.zeros((4, npl, n))
+    hole = np.zeros((npl, n), dtype=bool)
+    phi = phi0.copy(); th = th0.copy()
+    y = np.zeros(n); z = np.zeros(n); t = np.zeros(n)
+    x_prev = 0.0
+    for j, xp in enumerate(w.plane_x):
+        crossed = j < nhit
+        ok &= np.abs(phi) < 1.2
+        cphi = np.cos(np.clip(phi, -1.2, 1.2))
+        ty = np.tan(np.clip(phi, -1.2, 1.2))
+        tz = np.cos(th) / (np.sin(th) * cphi)
+        y, z, ty, tz, t = _advance_in_x(w, y, z, ty, tz, t, qop, gam, x_prev, xp)
+        N = np.sqrt(1.0 + ty * ty + tz * tz)
+        phi1 = np.arctan2(ty, 1.0)
+        th1 = np.arctan2(np.sqrt(1.0 + ty * ty), tz)
+        cos_inc = 1.0 / N
+        ok &= ~crossed | ((cos_inc > w.min_cos_incidence) & (np.abs(y) <= w.half_width)
+                          & (np.abs(z) <= w.half_width))
+        loc[0, j] = y; loc[1, j] = z
+        meas[0, j] = y + w.sigma * _normal(s, ids, attempt, _P_HIT, 2 * j)
+        meas[1, j] = z + w.sigma * _normal(s, ids, attempt, _P_HIT, 2 * j + 1)
+        hole[j] = _uniform(s, ids, attempt, _P_HOLE, j) < w.hole_prob
+        if w.x_over_x0 > 0:
+            th0w = _highland_width(qop, w.x_over_x0, np.maximum(np.abs(cos_inc), 1e-3), mass)
+            dphi = th0w / np.sin(th1) * _normal(s, ids, attempt, _P_MS, 2 * j)
+            dth = th0w * _normal(s, ids, attempt, _P_MS, 2 * j + 1)
+        else:
+            dphi = dth = 0.0
+        phi = phi1 + dphi
+        th = th1 + dth
+        leave[0, j] = phi; leave[1, j] = th; leave[2, j] = t
+        x_prev = xp
+    nmeas = np.sum(~hole & (np.arange(npl)[:, None] < nhit[None, :]), axis=0)
+    ok &= nmeas >= w.min_meas
+    return dict(phi0=phi0, th0=th0, qop=qop, nhit=nhit, loc=loc, meas=meas,
+                leave=leave, hole=hole, ok=ok)
+
+
 def _simulate(w: Workload, ids, attempt, mass):
     """Simulate tracks `ids` (attempt per track); return arrays + ok mask."""
+    if w.fringe > 0:
+        return _simulate_fringe(w, ids, attempt, mass)
     n = len(ids)
     npl = len(w.plane_x)
     s = w.seed
@@ -357,6 +485,7 @@ def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200) ->
         bfield=np.array([0.0, 0.0, w.bz]), surface_id=surface_id, loc=loc,
         cov=cov, is_hole=is_hole, truth_states=truth_states,
         sigma=w.sigma, rejected=rejected, align_true=alignment_draw(w),
+        **({"field_map": field_map_of(w)} if w.fringe > 0 else {}),
     )
 
 

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_host_only_entry_points(lib):
-    assert lib.kf_abi_version() == 2
+    assert lib.kf_abi_version() == 3
     o = kf.kf_default_options()
     assert o.precision == 0 and abs(o.mass - 0.1056583755) < 1e-15
     assert o.h_max == 50.0 and o.n_iter == 3 and o.block == 128
@@ -62,3 +62,30 @@ def test_kernels_compiled_for_sm103a():
     # the build compiles every kernel for sm_103a only
     assert os.path.exists(_build.LIB)
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors have the C structs' sizes and field offsets (the
+    header compiled with gcc on this host)."""
+    import subprocess
+    inc = os.path.join(os.path.dirname(__file__), "..", "include")
+    checks = {
+        "kf_tracks": kf.KfTracks, "kf_surfaces": kf.KfSurfaces, "kf_measurements": kf.KfMeasurements,
+        "kf_field_map": kf.KfFieldMap, "kf_field": kf.KfField, "kf_material": kf.KfMaterial,
+        "kf_outputs": kf.KfOutputs, "kf_options": kf.KfOptions,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kf.h"', "int main(void) {"]
+    for cname, py in checks.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, "-o", str(exe), str(src)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for cname, py in checks.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)

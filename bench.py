@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of graph replay")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the method-variant kernel (backward filter + energy loss + field map)")
     return ap.parse_args()
 
 
@@ -113,15 +115,58 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_tracks_per_s(ev, n_sample, cores):
+def oracle_tracks_per_s(ev, n_sample, cores, method=None):
     """Oracle (plain FP64 C, POSIX threads) over the first n_sample tracks."""
     import oracle
     from paper_2105_01796_gb300 import synth
     sub = synth.subset(ev, np.arange(min(n_sample, ev["n_tracks"])))
     t0 = time.perf_counter()
-    oracle.fit_batch(sub, n_threads=cores)
+    oracle.fit_batch(sub, n_threads=cores, method=method)
     dt = time.perf_counter() - t0
     return sub["n_tracks"] / dt, dt, sub["n_tracks"]
+
+
+VARIANT_WORKLOAD = "fringe30_100k"
+VARIANT_DISTINCT = 10_000
+
+
+def time_variants(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks):
+    """The method-variant kernel (FP64) with all three variants at once:
+    backward-filter smoother, energy loss and the fringe field map.  The
+    workload's first 10k tracks are simulated and tiled to the full count
+    (the simulation integrates every track numerically)."""
+    w = synth.WORKLOADS[VARIANT_WORKLOAD]
+    base = synth.make_event(synth.scaled(w, min(VARIANT_DISTINCT, n_tracks)))
+    ev = synth.subset(base, np.arange(n_tracks) % base["n_tracks"])
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(n_tracks)
+    kw = dict(smoother=kf.KF_SMOOTHER_BACKWARD_FILTER, energy_loss=1)
+    best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(kf.KF_PRECISION_FP64, **kw), stream)
+    opt = kf.kf_default_options(kf.KF_PRECISION_FP64, schedule=best.schedule, block=best.block,
+                                resident_warps=best.resident_warps, use_graph=1, **kw)
+    for _ in range(warmup):
+        kf.kf_fit_ex(h, dev, out, opt, stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        l2_flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kf.kf_fit_ex(h, dev, out, opt, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    st = out["status"].cpu().numpy()
+    step = float(np.mean(ms))
+    return base, {"workload": VARIANT_WORKLOAD, "tracks": n_tracks,
+                  "distinct_tracks": int(base["n_tracks"]),
+                  "method": "backward-filter smoother + energy loss + field map (FP64)",
+                  "value": n_tracks / (step / 1e3), "unit": "tracks/s", "ms_per_step": step,
+                  "ok_tracks": int((st == 0).sum()),
+                  "launch_shape": {"schedule": ["grid", "persistent", "sorted"][best.schedule],
+                                   "block": best.block, "resident_warps": best.resident_warps,
+                                   "cuda_graph": True}}
 
 
 def run_reference(args, rank, world):
@@ -230,6 +275,12 @@ def run_ours(args, rank, world, local):
     step_ms = kdist.max_over_ranks(float(np.mean(ms)), device="cuda")
     value = world * T / (step_ms / 1e3)
 
+    variants = None
+    variant_event = None
+    if not args.no_variants:
+        variant_event, variants = time_variants(h, kf, synth, torch, stream, l2_flush,
+                                                max(3, args.steps // 2), args.warmup, T)
+
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None
     if not args.no_e2e:
@@ -286,6 +337,11 @@ def run_ours(args, rank, world, local):
         v, dt, n = oracle_tracks_per_s(ev, T, cores)
         cpu = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle",
                "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt)}
+        if variants is not None:
+            vv, vdt, vn = oracle_tracks_per_s(variant_event, VARIANT_DISTINCT, cores,
+                                              method={"smoother": "backward", "energy_loss": True})
+            variants["cpu_oracle"] = {"value": vv, "unit": "tracks/s", "cores": cores,
+                                      "sample": "%d distinct tracks, one pass (%.1f s)" % (vn, vdt)}
     other_ms = float(np.mean(ms_other))
     line = {
         "metric": "tracks_fitted_per_s", "value": value, "unit": "tracks/s",
@@ -311,6 +367,7 @@ def run_ours(args, rank, world, local):
                      "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
                      "algorithmic_bytes_per_launch": nbytes},
         "cpu_baseline": cpu,
+        "variants": variants,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,

@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="plain launches instead of graph replay")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the method-variant kernel (backward filter + energy loss + field map)")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (chi2 gradient) kernel")
     return ap.parse_args()
 
 
@@ -140,6 +141,51 @@ def oracle_tracks_per_s(ev, n_sample, cores, method=None):
     sub = synth.subset(ev, np.arange(min(n_sample, ev["n_tracks"])))
     t0 = time.perf_counter()
     oracle.fit_batch(sub, n_threads=cores, method=method)
+    dt = time.perf_counter() - t0
+    return sub["n_tracks"] / dt, dt, sub["n_tracks"]
+
+
+ADJOINT_WORKLOAD = "align20_100k"
+
+
+def time_adjoint(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks):
+    """The adjoint kernel: chi2 per track and its gradient with respect to
+    the seeds and the 6 x 21 alignment parameters (at zero alignment) on the
+    misaligned 20-plane telescope."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS[ADJOINT_WORKLOAD], n_tracks))
+    dev = kf.event_to_device(ev)
+    T, S = int(ev["n_tracks"]), int(ev["center"].shape[1])
+    chi2 = torch.empty(T, dtype=torch.float64, device="cuda")
+    gs = torch.empty((6, T), dtype=torch.float64, device="cuda")
+    ga = torch.empty((6, S), dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        kf.kf_chi2_grad(h, dev, out_chi2=chi2, grad_seed=gs, grad_align=ga, stream=stream)
+    torch.cuda.synchronize()
+    ms = []
+    torch.cuda.nvtx.range_push("timed_adjoint")
+    for _ in range(steps):
+        l2_flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kf.kf_chi2_grad(h, dev, out_chi2=chi2, grad_seed=gs, grad_align=ga, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    torch.cuda.nvtx.range_pop()
+    step = float(np.mean(ms))
+    return ev, {"workload": ADJOINT_WORKLOAD, "tracks": T, "states_per_track": 21,
+                "gradient": "d(sum chi2)/d(seeds [6][T], alignment [6][21]) at zero alignment (FP64)",
+                "value": T / (step / 1e3), "unit": "tracks/s", "ms_per_step": step}
+
+
+def oracle_gradient_rate(ev, n_sample, cores):
+    """The oracle's gradient by central finite differences over a sample."""
+    import oracle
+    from paper_2105_01796_gb300 import synth
+    sub = synth.subset(ev, np.arange(min(n_sample, ev["n_tracks"])))
+    t0 = time.perf_counter()
+    oracle.chi2_gradient_fd(sub, n_threads=cores)
     dt = time.perf_counter() - t0
     return sub["n_tracks"] / dt, dt, sub["n_tracks"]
 
@@ -297,6 +343,11 @@ def run_ours(args, rank, world, local):
     step_ms = kdist.max_over_ranks(float(np.mean(ms)), device="cuda")
     value = world * T / (step_ms / 1e3)
 
+    adjoint = None
+    adjoint_event = None
+    if not args.no_adjoint:
+        adjoint_event, adjoint = time_adjoint(h, kf, synth, torch, stream, l2_flush,
+                                              max(3, args.steps // 2), args.warmup, T)
     variants = None
     variant_event = None
     if not args.no_variants:
@@ -361,6 +412,12 @@ def run_ours(args, rank, world, local):
         v, dt, n = oracle_tracks_per_s(ev, T, cores)
         cpu = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle",
                "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt)}
+        if adjoint is not None:
+            av, adt, an = oracle_gradient_rate(adjoint_event, 200, cores)
+            adjoint["cpu_oracle"] = {"value": av, "unit": "tracks/s", "cores": cores,
+                                     "kind": "oracle central finite differences",
+                                     "sample": "%d tracks, %d + 12 x %d batch fits (%.1f s)"
+                                               % (an, 12, adjoint_event["center"].shape[1], adt)}
         if variants is not None:
             vv, vdt, vn = oracle_tracks_per_s(variant_event, VARIANT_DISTINCT, cores,
                                               method={"smoother": "backward", "energy_loss": True})
@@ -395,6 +452,7 @@ def run_ours(args, rank, world, local):
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,
         "variants": variants,
+        "adjoint": adjoint,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,

@@ -132,3 +132,26 @@ def test_field_map_host_entry_and_graph_replay(handle):
         kf.kf_fit_ex(handle, dev, out, opt, s)
         s.synchronize()
         assert np.array_equal(out["params"].cpu().numpy(), ref["params"])
+
+
+def test_full_size_variants_sampled(handle):
+    """The bench's variant configuration: 100k fringe-field tracks (10k
+    distinct, tiled) with all three variants, in the autotuned launch shape;
+    300 sampled tracks against the oracle."""
+    import torch
+    base = synth.make_event(synth.scaled(synth.WORKLOADS["fringe30_100k"], 10_000))
+    T = 100_000
+    ev = synth.subset(base, np.arange(T) % base["n_tracks"])
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(T)
+    method = dict(BACKWARD, **ELOSS)
+    best, _ = kf.kf_autotune(handle, dev, out, kf.kf_default_options(FP64, **kopts(method)))
+    opt = kf.kf_default_options(FP64, schedule=best.schedule, block=best.block,
+                                resident_warps=best.resident_warps, **kopts(method))
+    kf.kf_fit_ex(handle, dev, out, opt)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+    pick = np.random.default_rng(5).choice(T, 300, replace=False)
+    r = oracle.fit_batch(synth.subset(ev, pick), method=method)
+    gs = {k: (v[..., pick] if v.ndim == 2 else v[pick]) for k, v in g.items()}
+    compare(gs, r, FP64)

@@ -118,20 +118,6 @@ __device__ __forceinline__ void value_step(float h, const float bs[3], const flo
   }
 }
 
-// asin(s) - s for |s| <= 0.1 (series to s^9; truncation < 2e-13)
-__device__ __forceinline__ float asin_tail(float s) {
-  const float s2 = s * s;
-  return s * s2 * (1.0f / 6.0f + s2 * (3.0f / 40.0f + s2 * (5.0f / 112.0f + s2 * (35.0f / 1152.0f))));
-}
-
-// new angle = old + asin(sin_delta), the delta being the small rotation from
-// the old to the new direction; a large rotation falls back to atan2.
-__device__ __forceinline__ double angle_step(double old, double sin_delta, float cos_delta, double y, double x) {
-  const float sf = d2f(sin_delta);
-  if (fabsf(sf) <= 0.1f && cos_delta > 0.0f) return (old + sin_delta) + f2d(asin_tail(sf));
-  return atan2(y, x);
-}
-
 // rotate (c, s) of an angle by a small float increment delta
 __device__ __forceinline__ void rotate(double& c, double& s, float delta) {
   float sh, ch;
@@ -148,12 +134,13 @@ template <bool BZ>
 __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, const double r0[3], const double x[6],
                                const Dir& d, const float Bf[3], float m2, float h_max, int n_iter, double xp[6],
                                double rp[3], Dir& dp, JacF& J, float& sin_th, float& cos_inc) {
-  // start point (FP64 accumulators): the filtered point on surface a
-  double r[3] = {r0[0], r0[1], r0[2]}, T[3];
-  T[0] = d.cp * d.st;
-  T[1] = d.sp * d.st;
-  T[2] = d.ct;
-  double t = x[5];
+  // start point (FP64 accumulator): the filtered point on surface a; start
+  // direction from the carried cosines and sines.  The direction change over
+  // the transition is accumulated in FP32 (accT): the RKN increments carry
+  // full relative precision, and the end angles follow from it below.
+  double r[3] = {r0[0], r0[1], r0[2]};
+  const double Td[3] = {d.cp * d.st, d.sp * d.st, d.ct};
+  const float T0f[3] = {d2f(Td[0]), d2f(Td[1]), d2f(Td[2])};
   const float lam = d2f(x[4]);
   const float lk = lam * (float)kKappa;
   const float bs[3] = {lk * Bf[0], lk * Bf[1], lk * Bf[2]};
@@ -174,11 +161,12 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     g.gtl = 0.0f;
   }
   const float nb[3] = {sb.nf(0), sb.nf(1), sb.nf(2)};
+  float accT[3] = {0.0f, 0.0f, 0.0f};  // T_end - T_start
+  float tinc = 0.0f;                    // t_end - t_start
   // main steps over the straight-line distance
-  float Tf[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
   {
     const double dist = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
-    const float nT = nb[0] * Tf[0] + nb[1] * Tf[1] + nb[2] * Tf[2];
+    const float nT = nb[0] * T0f[0] + nb[1] * T0f[1] + nb[2] * T0f[2];
     if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
     const float s0 = d2f(dist) / nT;
     const float nsub_f = ceilf(fabsf(s0) / h_max);
@@ -187,28 +175,31 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     const float h = s0 / (float)nsub;
     const double hd = f2d(h);
     for (int k = 0; k < nsub; ++k) {
+      const float Tf[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
+      double Tk[3] = {Td[0], Td[1], Td[2]};
       if (k > 0) {
-        Tf[0] = d2f(T[0]); Tf[1] = d2f(T[1]); Tf[2] = d2f(T[2]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) Tk[i] += f2d(accT[i]);
       }
       cols_step<BZ>(g, h, bs, kB, Tf, dtl);
       float dr[3], dT[3];
       value_step<BZ>(h, bs, Tf, dr, dT);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        r[i] = fma(hd, T[i], r[i]) + f2d(dr[i]);
-        T[i] += f2d(dT[i]);
+        r[i] = fma(hd, Tk[i], r[i]) + f2d(dr[i]);
+        accT[i] += dT[i];
       }
-      t += f2d(h * dtds);
+      tinc += h * dtds;
     }
   }
   // Newton corrections onto the plane, as float offsets from the main end
   {
     const double dm = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
     const float dmf = d2f(dm);
-    const float T0[3] = {d2f(T[0]), d2f(T[1]), d2f(T[2])};
+    const float Tm[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
     float orr[3] = {0.0f, 0.0f, 0.0f}, oT[3] = {0.0f, 0.0f, 0.0f}, ot = 0.0f;
     for (int it = 0; it < n_iter; ++it) {
-      const float Tc[3] = {T0[0] + oT[0], T0[1] + oT[1], T0[2] + oT[2]};
+      const float Tc[3] = {Tm[0] + oT[0], Tm[1] + oT[1], Tm[2] + oT[2]};
       const float dist = dmf - (nb[0] * orr[0] + nb[1] * orr[1] + nb[2] * orr[2]);
       const float nT = nb[0] * Tc[0] + nb[1] * Tc[1] + nb[2] * Tc[2];
       if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
@@ -226,23 +217,29 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       r[i] += f2d(orr[i]);
-      T[i] += f2d(oT[i]);
+      accT[i] += oT[i];
     }
-    t += f2d(ot);
+    tinc += ot;
   }
-  // end frame: unit direction, angles by small rotations, local position
-  const double rho2 = fma(T[1], T[1], T[0] * T[0]);
-  const double irho = rsqrt_nr<1>(rho2);
-  dp.cp = T[0] * irho;
-  dp.sp = T[1] * irho;
-  const double rho = rho2 * irho;
-  const double inn = rsqrt_nr<1>(fma(T[2], T[2], rho2));
-  dp.st = rho * inn;
-  dp.ct = T[2] * inn;
+  const double t = x[5] + f2d(tinc);
+  // end angles: the rotation from the start to the end direction, computed in
+  // FP32 from the start direction c and its change a = accT (no cancellation
+  // of large terms):
+  //   tan dphi = (c0 a1 - c1 a0) / (rho^2 + c0 a0 + c1 a1),
+  //   tan dtheta = (c2 drho - rho a2) / (c2 (c2 + a2) + rho (rho + drho)),
+  // with rho = |(c0, c1)| and drho the change of rho; the FP64 angles and
+  // their cosines / sines then turn by these increments.
   {
-    const double sdp = fma(d.cp, dp.sp, -d.sp * dp.cp);
-    const float cdp = d2f(d.cp) * d2f(dp.cp) + d2f(d.sp) * d2f(dp.sp);
-    double phi = angle_step(d.phi, sdp, cdp, dp.sp, dp.cp);
+    const float c0 = T0f[0], c1 = T0f[1], c2 = T0f[2];
+    const float a0 = accT[0], a1 = accT[1], a2 = accT[2];
+    const float rho_sq = c0 * c0 + c1 * c1;
+    const float dphi = atan2f(c0 * a1 - c1 * a0, rho_sq + c0 * a0 + c1 * a1);
+    const float drho_sq = 2.0f * (c0 * a0 + c1 * a1) + a0 * a0 + a1 * a1;
+    const float rho = sqrtf(rho_sq), rho_end = sqrtf(rho_sq + drho_sq);
+    const float drho = drho_sq / (rho + rho_end);
+    const float dth = atan2f(c2 * drho - rho * a2, c2 * (c2 + a2) + rho * (rho + drho));
+    dp = d;
+    double phi = d.phi + f2d(dphi);
     // keep phi in (-pi, pi]; compared on the integer pipe (doubles of one
     // sign order like their magnitudes' bit patterns)
     const double pi = 3.141592653589793;
@@ -250,9 +247,9 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     if (bp > bpi) phi -= 2.0 * pi;
     else if (bp < 0 && (bp & 0x7fffffffffffffffLL) >= bpi) phi += 2.0 * pi;
     dp.phi = phi;
-    const double sdt = fma(dp.st, d.ct, -dp.ct * d.st);
-    const float cdt = d2f(dp.st) * d2f(d.st) + d2f(dp.ct) * d2f(d.ct);
-    dp.theta = angle_step(d.theta, sdt, cdt, dp.st, dp.ct);
+    dp.theta = d.theta + f2d(dth);
+    rotate(dp.cp, dp.sp, dphi);
+    rotate(dp.ct, dp.st, dth);
   }
   rp[0] = r[0];
   rp[1] = r[1];

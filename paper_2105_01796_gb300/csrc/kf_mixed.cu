@@ -48,10 +48,22 @@ struct WSM {
   __device__ float& f(int k, int e) const { return w32[((size_t)k * kRec32Mixed + e) * nt + i]; }
 };
 
-// direction: angles and their cosines / sines, all FP64
+// direction: the angles and the unit direction vector, all FP64
 struct Dir {
-  double phi, theta, cp, sp, ct, st;
+  double phi, theta;
+  double T[3];  // (cos phi sin theta, sin phi sin theta, cos theta), unit up to rounding
 };
+
+// float cosines and sines of the direction's angles, from T
+__device__ __forceinline__ void dir_cs(const double T[3], float& cp, float& sp, float& ct, float& st) {
+  const float t0 = d2f(T[0]), t1 = d2f(T[1]), t2 = d2f(T[2]);
+  const float rho = sqrtf(t0 * t0 + t1 * t1);
+  const float irho = 1.0f / rho, itn = rsqrtf(rho * rho + t2 * t2);
+  cp = t0 * irho;
+  sp = t1 * irho;
+  st = rho * itn;
+  ct = t2 * itn;
+}
 
 // FP32 Jacobian columns along the path (G = D J_bf): phi, theta, q/p
 struct Cols {
@@ -118,15 +130,22 @@ __device__ __forceinline__ void value_step(float h, const float bs[3], const flo
   }
 }
 
-// rotate (c, s) of an angle by a small float increment delta
-__device__ __forceinline__ void rotate(double& c, double& s, float delta) {
+// turn the unit direction T by small angle increments (a, b) of (phi, theta):
+// every term of the change is proportional to the increments, so it is
+// formed in FP32 with full relative precision and added to the FP64 vector
+__device__ __forceinline__ void turn(double T[3], float a, float b) {
+  float cp, sp, ct, st;
+  dir_cs(T, cp, sp, ct, st);
   float sh, ch;
-  sincosf(0.5f * delta, &sh, &ch);
-  const float sd = 2.0f * sh * ch, cm1 = -2.0f * sh * sh;
-  const float cf = d2f(c), sf = d2f(s);
-  const float dc = cf * cm1 - sf * sd, ds = sf * cm1 + cf * sd;
-  c += f2d(dc);
-  s += f2d(ds);
+  sincosf(0.5f * a, &sh, &ch);
+  const float sa = 2.0f * sh * ch, ca1 = -2.0f * sh * sh;  // sin a, cos a - 1
+  sincosf(0.5f * b, &sh, &ch);
+  const float sb = 2.0f * sh * ch, cb1 = -2.0f * sh * sh;
+  const float dcp = cp * ca1 - sp * sa, dsp = sp * ca1 + cp * sa;
+  const float dct = ct * cb1 - st * sb, dst = st * cb1 + ct * sb;
+  T[0] += f2d(cp * dst + dcp * st + dcp * dst);
+  T[1] += f2d(sp * dst + dsp * st + dsp * dst);
+  T[2] += f2d(dct);
 }
 
 // Transport the filtered state (x, d) on surface a to surface b.
@@ -139,7 +158,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   // the transition is accumulated in FP32 (accT): the RKN increments carry
   // full relative precision, and the end angles follow from it below.
   double r[3] = {r0[0], r0[1], r0[2]};
-  const double Td[3] = {d.cp * d.st, d.sp * d.st, d.ct};
+  const double* Td = d.T;
   const float T0f[3] = {d2f(Td[0]), d2f(Td[1]), d2f(Td[2])};
   const float lam = d2f(x[4]);
   const float lk = lam * (float)kKappa;
@@ -150,7 +169,8 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   const float dtl = m2 * lam * (float)kInvC / gam;  // d(dt/ds)/dlam
   Cols g;
   {
-    const float cpf = d2f(d.cp), spf = d2f(d.sp), ctf = d2f(d.ct), stf = d2f(d.st);
+    float cpf, spf, ctf, stf;
+    dir_cs(d.T, cpf, spf, ctf, stf);
     g.gT[0][0] = -spf * stf; g.gT[1][0] = cpf * stf; g.gT[2][0] = 0.0f;
     g.gT[0][1] = cpf * ctf;  g.gT[1][1] = spf * ctf; g.gT[2][1] = -stf;
 #pragma unroll
@@ -162,10 +182,14 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   }
   const float nb[3] = {sb.nf(0), sb.nf(1), sb.nf(2)};
   float accT[3] = {0.0f, 0.0f, 0.0f};  // T_end - T_start
+  float accR[3] = {0.0f, 0.0f, 0.0f};  // r_end - r_start - s0 T_start
   float tinc = 0.0f;                    // t_end - t_start
-  // main steps over the straight-line distance
+  // main steps over the straight-line distance s0: the position moves by
+  // s0 T_start (FP64) plus the FP32 offsets of the curvature and of the
+  // direction change
+  double s0d, dist;
   {
-    const double dist = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
+    dist = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
     const float nT = nb[0] * T0f[0] + nb[1] * T0f[1] + nb[2] * T0f[2];
     if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
     const float s0 = d2f(dist) / nT;
@@ -173,29 +197,25 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     if (!(nsub_f <= 64.0f)) return ST_NO_INTERSECTION;
     const int nsub = nsub_f < 1.0f ? 1 : (int)nsub_f;
     const float h = s0 / (float)nsub;
-    const double hd = f2d(h);
+    s0d = f2d(h) * (double)nsub;
     for (int k = 0; k < nsub; ++k) {
       const float Tf[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
-      double Tk[3] = {Td[0], Td[1], Td[2]};
-      if (k > 0) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) Tk[i] += f2d(accT[i]);
-      }
       cols_step<BZ>(g, h, bs, kB, Tf, dtl);
       float dr[3], dT[3];
       value_step<BZ>(h, bs, Tf, dr, dT);
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        r[i] = fma(hd, Tk[i], r[i]) + f2d(dr[i]);
+        accR[i] += h * accT[i] + dr[i];
         accT[i] += dT[i];
       }
       tinc += h * dtds;
     }
   }
-  // Newton corrections onto the plane, as float offsets from the main end
+  // Newton corrections onto the plane, as float offsets from the main end;
+  // the remaining distance n.(c - r_main) = dist - s0 (n.T_start) - n.accR
   {
-    const double dm = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
-    const float dmf = d2f(dm);
+    const double nTd = sb.n(0) * Td[0] + sb.n(1) * Td[1] + sb.n(2) * Td[2];
+    const float dmf = d2f(fma(-s0d, nTd, dist)) - (nb[0] * accR[0] + nb[1] * accR[1] + nb[2] * accR[2]);
     const float Tm[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
     float orr[3] = {0.0f, 0.0f, 0.0f}, oT[3] = {0.0f, 0.0f, 0.0f}, ot = 0.0f;
     for (int it = 0; it < n_iter; ++it) {
@@ -216,7 +236,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      r[i] += f2d(orr[i]);
+      r[i] = fma(s0d, Td[i], r[i]) + f2d(accR[i] + orr[i]);
       accT[i] += oT[i];
     }
     tinc += ot;
@@ -248,8 +268,8 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     else if (bp < 0 && (bp & 0x7fffffffffffffffLL) >= bpi) phi += 2.0 * pi;
     dp.phi = phi;
     dp.theta = d.theta + f2d(dth);
-    rotate(dp.cp, dp.sp, dphi);
-    rotate(dp.ct, dp.st, dth);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dp.T[i] = Td[i] + f2d(accT[i]);
   }
   rp[0] = r[0];
   rp[1] = r[1];
@@ -262,7 +282,8 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   xp[5] = t;
 
   // path correction and free -> bound Jacobian (FP32)
-  const float cph = d2f(dp.cp), sph = d2f(dp.sp), cth = d2f(dp.ct), sth = d2f(dp.st);
+  float cph, sph, cth, sth;
+  dir_cs(dp.T, cph, sph, cth, sth);
   const float Tu[3] = {cph * sth, sph * sth, cth};
   const float nT = nb[0] * Tu[0] + nb[1] * Tu[1] + nb[2] * Tu[2];
   float AT[3];
@@ -517,8 +538,14 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
     Dir d;
     d.phi = x[2];
     d.theta = x[3];
-    sincos(x[2], &d.sp, &d.cp);  // the only FP64 trigonometry of the track
-    sincos(x[3], &d.st, &d.ct);
+    {
+      double sp, cp, st, ct;
+      sincos(x[2], &sp, &cp);  // the only FP64 trigonometry of the track
+      sincos(x[3], &st, &ct);
+      d.T[0] = cp * st;
+      d.T[1] = sp * st;
+      d.T[2] = ct;
+    }
     int sid_prev = p.surface_id[o0];
     {
       const Surf s0{s_surf + sid_prev * kSurfStride};
@@ -657,8 +684,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         d = dp;
         d.phi = x[2];
         d.theta = x[3];
-        rotate(d.cp, d.sp, dx[2]);
-        rotate(d.ct, d.st, dx[3]);
+        turn(d.T, dx[2], dx[3]);
       } else {
 #pragma unroll
         for (int e = 0; e < 6; ++e) {

@@ -13,6 +13,10 @@ LIB = os.path.join(HERE, "libkfgb.so")
 SOURCES = ["kf_kernels.cu", "kf_mixed.cu", "kf_adjoint.cu", "kf_variants.cu", "kf_api.cu", "kf_static.cu"]
 HEADERS = ["kf_internal.h", "kf_device.cuh", "kf_fp64.cuh", os.path.join("..", "..", "include", "kf.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# per-file flags: the mixed kernel's FP32 divisions and square roots (step
+# lengths, Jacobian normalisations, angle increments) need no IEEE rounding;
+# its FP64 helpers use explicit intrinsics and are unaffected
+FILE_FLAGS = {"kf_mixed.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def nvcc() -> str:
@@ -41,7 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc] + flags + FILE_FLAGS.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s" % (src, r.stderr))

@@ -130,10 +130,17 @@ __device__ __forceinline__ void value_step(float h, const float bs[3], const flo
   }
 }
 
-// turn the unit direction T by small angle increments (a, b) of (phi, theta):
-// every term of the change is proportional to the increments, so it is
-// formed in FP32 with full relative precision and added to the FP64 vector
-__device__ __forceinline__ void turn(double T[3], float a, float b) {
+// The filter's increments of the state that the next transport applies
+// (zero after a hole): in-plane move of the point, change of the unit
+// direction, and the increments of phi, theta and t.
+struct Pend {
+  float r[3], T[3], phi, theta, t;
+};
+
+// change of the unit direction T when (phi, theta) turn by small increments
+// (a, b): every term is proportional to the increments, so FP32 carries it
+// with full relative precision
+__device__ __forceinline__ void turn_inc(const double T[3], float a, float b, float out[3]) {
   float cp, sp, ct, st;
   dir_cs(T, cp, sp, ct, st);
   float sh, ch;
@@ -143,23 +150,35 @@ __device__ __forceinline__ void turn(double T[3], float a, float b) {
   const float sb = 2.0f * sh * ch, cb1 = -2.0f * sh * sh;
   const float dcp = cp * ca1 - sp * sa, dsp = sp * ca1 + cp * sa;
   const float dct = ct * cb1 - st * sb, dst = st * cb1 + ct * sb;
-  T[0] += f2d(cp * dst + dcp * st + dcp * dst);
-  T[1] += f2d(sp * dst + dsp * st + dsp * dst);
-  T[2] += f2d(dct);
+  out[0] = cp * dst + dcp * st + dcp * dst;
+  out[1] = sp * dst + dsp * st + dsp * dst;
+  out[2] = dct;
 }
 
-// Transport the filtered state (x, d) on surface a to surface b.
+// float cosines and sines of a float direction
+__device__ __forceinline__ void dir_csf(const float t[3], float& cp, float& sp, float& ct, float& st) {
+  const float rho = sqrtf(t[0] * t[0] + t[1] * t[1]);
+  const float irho = 1.0f / rho, itn = rsqrtf(rho * rho + t[2] * t[2]);
+  cp = t[0] * irho;
+  sp = t[1] * irho;
+  st = rho * itn;
+  ct = t[2] * itn;
+}
+
+// Transport the filtered state on surface a to surface b.  The filtered
+// state is the predicted one (point r0, direction d, time x[5]) plus the
+// filter's pending FP32 increments pd; x[4] is the filtered q/p.
 template <bool BZ>
 __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, const double r0[3], const double x[6],
-                               const Dir& d, const float Bf[3], float m2, float h_max, int n_iter, double xp[6],
-                               double rp[3], Dir& dp, JacF& J, float& sin_th, float& cos_inc) {
-  // start point (FP64 accumulator): the filtered point on surface a; start
-  // direction from the carried cosines and sines.  The direction change over
-  // the transition is accumulated in FP32 (accT): the RKN increments carry
-  // full relative precision, and the end angles follow from it below.
+                               const Dir& d, const Pend& pd, const float Bf[3], float m2, float h_max, int n_iter,
+                               double xp[6], double rp[3], Dir& dp, JacF& J, float& sin_th, float& cos_inc) {
+  // The point and the direction stay FP64 (predicted values of surface a);
+  // everything that moves them here (the pending filter increments, the RKN
+  // curvature terms, the direction change accT, the plane corrections) is
+  // summed in FP32 and added once at the end.
   double r[3] = {r0[0], r0[1], r0[2]};
   const double* Td = d.T;
-  const float T0f[3] = {d2f(Td[0]), d2f(Td[1]), d2f(Td[2])};
+  const float T0f[3] = {d2f(Td[0]) + pd.T[0], d2f(Td[1]) + pd.T[1], d2f(Td[2]) + pd.T[2]};
   const float lam = d2f(x[4]);
   const float lk = lam * (float)kKappa;
   const float bs[3] = {lk * Bf[0], lk * Bf[1], lk * Bf[2]};
@@ -170,7 +189,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   Cols g;
   {
     float cpf, spf, ctf, stf;
-    dir_cs(d.T, cpf, spf, ctf, stf);
+    dir_csf(T0f, cpf, spf, ctf, stf);
     g.gT[0][0] = -spf * stf; g.gT[1][0] = cpf * stf; g.gT[2][0] = 0.0f;
     g.gT[0][1] = cpf * ctf;  g.gT[1][1] = spf * ctf; g.gT[2][1] = -stf;
 #pragma unroll
@@ -192,7 +211,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     dist = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
     const float nT = nb[0] * T0f[0] + nb[1] * T0f[1] + nb[2] * T0f[2];
     if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
-    const float s0 = d2f(dist) / nT;
+    const float s0 = (d2f(dist) - (nb[0] * pd.r[0] + nb[1] * pd.r[1] + nb[2] * pd.r[2])) / nT;
     const float nsub_f = ceilf(fabsf(s0) / h_max);
     if (!(nsub_f <= 64.0f)) return ST_NO_INTERSECTION;
     const int nsub = nsub_f < 1.0f ? 1 : (int)nsub_f;
@@ -211,11 +230,17 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
       tinc += h * dtds;
     }
   }
-  // Newton corrections onto the plane, as float offsets from the main end;
-  // the remaining distance n.(c - r_main) = dist - s0 (n.T_start) - n.accR
+  // Newton corrections onto the plane, as float offsets from the main end.
+  // The main end is r_main = r0 + s0 Td + off with the FP32 offset
+  // off = pd.r + s0 pd.T + accR; the remaining distance is
+  // n.(c - r_main) = dist - s0 (n.Td) - n.off.
+  const float s0f = d2f(s0d);
+  float off[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) off[i] = pd.r[i] + s0f * pd.T[i] + accR[i];
   {
     const double nTd = sb.n(0) * Td[0] + sb.n(1) * Td[1] + sb.n(2) * Td[2];
-    const float dmf = d2f(fma(-s0d, nTd, dist)) - (nb[0] * accR[0] + nb[1] * accR[1] + nb[2] * accR[2]);
+    const float dmf = d2f(fma(-s0d, nTd, dist)) - (nb[0] * off[0] + nb[1] * off[1] + nb[2] * off[2]);
     const float Tm[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
     float orr[3] = {0.0f, 0.0f, 0.0f}, oT[3] = {0.0f, 0.0f, 0.0f}, ot = 0.0f;
     for (int it = 0; it < n_iter; ++it) {
@@ -236,12 +261,12 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      r[i] = fma(s0d, Td[i], r[i]) + f2d(accR[i] + orr[i]);
+      r[i] = fma(s0d, Td[i], r[i]) + f2d(off[i] + orr[i]);
       accT[i] += oT[i];
     }
     tinc += ot;
   }
-  const double t = x[5] + f2d(tinc);
+  const double t = x[5] + f2d(pd.t + tinc);
   // end angles: the rotation from the start to the end direction, computed in
   // FP32 from the start direction c and its change a = accT (no cancellation
   // of large terms):
@@ -259,7 +284,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     const float drho = drho_sq / (rho + rho_end);
     const float dth = atan2f(c2 * drho - rho * a2, c2 * (c2 + a2) + rho * (rho + drho));
     dp = d;
-    double phi = d.phi + f2d(dphi);
+    double phi = d.phi + f2d(pd.phi + dphi);
     // keep phi in (-pi, pi]; compared on the integer pipe (doubles of one
     // sign order like their magnitudes' bit patterns)
     const double pi = 3.141592653589793;
@@ -267,9 +292,9 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     if (bp > bpi) phi -= 2.0 * pi;
     else if (bp < 0 && (bp & 0x7fffffffffffffffLL) >= bpi) phi += 2.0 * pi;
     dp.phi = phi;
-    dp.theta = d.theta + f2d(dth);
+    dp.theta = d.theta + f2d(pd.theta + dth);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dp.T[i] = Td[i] + f2d(accT[i]);
+    for (int i = 0; i < 3; ++i) dp.T[i] = Td[i] + f2d(pd.T[i] + accT[i]);
   }
   rp[0] = r[0];
   rp[1] = r[1];
@@ -525,12 +550,13 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
   int nmeas = 0;
   if (status == ST_OK) {
     // ------------------------------------------------ forward filter
-    // x[2..5] (phi, theta, q/p, t) are FP64 accumulators; the position is
-    // carried as the FP64 point r on the current surface (loc0/loc1 of the
-    // filtered state are r's local coordinates).
-    // the filtered covariance is kept in FP32 between states: it only feeds
-    // the FP32 transport F Cf F^T (the Joseph update produces it in FP64)
+    // Between states the FP64 state is the prediction of the last surface
+    // (point r, direction d, time x[5]) plus the filter's FP32 increments
+    // in pd, which the next transport applies; the filtered q/p is x[4].
+    // The filtered covariance is kept in FP32 between states: it only feeds
+    // the FP32 transport F Cf F^T (the Joseph update produces it in FP64).
     double x[6], r[3];
+    Pend pd = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, 0.0f, 0.0f, 0.0f};
     float Cf[21];
     float dx[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // x_f - x_p of the last state
 #pragma unroll
@@ -572,7 +598,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
         JacF J;
         float sin_th, cos_inc;
-        status = transport_mixed<BZ>(sa, sb, r, x, d, Bf, m2, h_max, p.n_iter, xp, rp, dp, J, sin_th, cos_inc);
+        status = transport_mixed<BZ>(sa, sb, r, x, d, pd, Bf, m2, h_max, p.n_iter, xp, rp, dp, J, sin_th, cos_inc);
         if (status != ST_OK) break;
         const float* Cr = Cf;
         // Cp = F Cf F^T, rows of Bm = F Cf formed on the fly
@@ -675,28 +701,29 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
               v = fma(-Cp[sym(1, a)], K[b][1], v);
               Cf[sy(a, b)] = d2f(v);
             }
-        // the filtered point: the predicted point moved in the plane by
-        // (dx0, dx1); angles, q/p and t receive their increments
+        // the filtered state: the prediction plus the increments, which stay
+        // pending in FP32 (the point moves in the plane by (dx0, dx1)); only
+        // q/p is updated here
 #pragma unroll
-        for (int c = 0; c < 3; ++c) r[c] = rp[c] + f2d(dx[0] * sk.uf(c) + dx[1] * sk.vf(c));
-#pragma unroll
-        for (int e = 2; e < 6; ++e) x[e] = xp[e] + f2d(dx[e]);
-        d = dp;
-        d.phi = x[2];
-        d.theta = x[3];
-        turn(d.T, dx[2], dx[3]);
+        for (int c = 0; c < 3; ++c) pd.r[c] = dx[0] * sk.uf(c) + dx[1] * sk.vf(c);
+        turn_inc(dp.T, dx[2], dx[3], pd.T);
+        pd.phi = dx[2];
+        pd.theta = dx[3];
+        pd.t = dx[5];
+        x[4] = xp[4] + f2d(dx[4]);
       } else {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) {
-          x[e] = xp[e];
-          dx[e] = 0.0f;
-        }
+        for (int e = 0; e < 6; ++e) dx[e] = 0.0f;
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cf[e] = Cpf[e];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r[c] = rp[c];
-        d = dp;
+        pd = Pend{{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, 0.0f, 0.0f, 0.0f};
+        x[4] = xp[4];
       }
+      // the FP64 state moves to the prediction of surface k
+#pragma unroll
+      for (int c = 0; c < 3; ++c) r[c] = rp[c];
+      d = dp;
+      x[5] = xp[5];
 #pragma unroll
       for (int e = 0; e < 6; ++e) ws.f(k, DXF + e) = dx[e];
       sid_prev = sid;
@@ -795,14 +822,9 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         }
       }
       if (n == 1) {
+        // the filtered state 0: the seed plus the filter increment
 #pragma unroll
-        for (int e = 0; e < 6; ++e) xs[e] = x[e];
-        xs[0] = p.seed_params[0 * TT + t];
-        xs[1] = p.seed_params[1 * TT + t];
-        if (!p.is_hole[o0]) {
-          xs[0] += f2d(dx[0]);
-          xs[1] += f2d(dx[1]);
-        }
+        for (int e = 0; e < 6; ++e) xs[e] = p.seed_params[e * TT + t] + f2d(dx[e]);
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cs_out[e] = f2d(Cf[e]);
       } else {

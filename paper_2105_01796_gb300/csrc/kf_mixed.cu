@@ -130,6 +130,36 @@ __device__ __forceinline__ void value_step(float h, const float bs[3], const flo
   }
 }
 
+// float cosines and sines of the direction's angles, carried with it
+struct CS {
+  float cp, sp, ct, st;
+};
+
+// sin(a) and cos(a) - 1 for a small float angle: series for |a| <= 0.1
+// (truncation below 3e-12 relative), sincosf otherwise
+__device__ __forceinline__ void sin_cosm1(float a, float& s, float& cm1) {
+  if (fabsf(a) <= 0.1f) {
+    const float a2 = a * a;
+    s = a * (1.0f - a2 * (1.0f / 6.0f) * (1.0f - a2 * (1.0f / 20.0f) * (1.0f - a2 * (1.0f / 42.0f))));
+    cm1 = -0.5f * a2 * (1.0f - a2 * (1.0f / 12.0f) * (1.0f - a2 * (1.0f / 30.0f) * (1.0f - a2 * (1.0f / 56.0f))));
+  } else {
+    float sh, ch;
+    sincosf(0.5f * a, &sh, &ch);
+    s = 2.0f * sh * ch;
+    cm1 = -2.0f * sh * sh;
+  }
+}
+
+// atan2(y, x) for a small angle (x > 0, |y| <= 0.1 x): series of atan(y/x)
+// (truncation below 1e-10 relative); atan2f otherwise
+__device__ __forceinline__ float small_atan2(float y, float x) {
+  if (x > 0.0f && fabsf(y) <= 0.1f * x) {
+    const float q = y / x, q2 = q * q;
+    return q * (1.0f - q2 * (1.0f / 3.0f - q2 * (1.0f / 5.0f - q2 * (1.0f / 7.0f - q2 * (1.0f / 9.0f)))));
+  }
+  return atan2f(y, x);
+}
+
 // The filter's increments of the state that the next transport applies
 // (zero after a hole): in-plane move of the point, change of the unit
 // direction, and the increments of phi, theta and t.
@@ -137,41 +167,35 @@ struct Pend {
   float r[3], T[3], phi, theta, t;
 };
 
-// change of the unit direction T when (phi, theta) turn by small increments
+// change of the unit direction when (phi, theta) turn by small increments
 // (a, b): every term is proportional to the increments, so FP32 carries it
-// with full relative precision
-__device__ __forceinline__ void turn_inc(const double T[3], float a, float b, float out[3]) {
-  float cp, sp, ct, st;
-  dir_cs(T, cp, sp, ct, st);
-  float sh, ch;
-  sincosf(0.5f * a, &sh, &ch);
-  const float sa = 2.0f * sh * ch, ca1 = -2.0f * sh * sh;  // sin a, cos a - 1
-  sincosf(0.5f * b, &sh, &ch);
-  const float sb = 2.0f * sh * ch, cb1 = -2.0f * sh * sh;
+// with full relative precision.  cs enters as the cosines / sines of the
+// old angles and leaves as those of the new ones.
+__device__ __forceinline__ void turn_inc(CS& cs, float a, float b, float out[3]) {
+  float sa, ca1, sb, cb1;  // sin, cos - 1
+  sin_cosm1(a, sa, ca1);
+  sin_cosm1(b, sb, cb1);
+  const float cp = cs.cp, sp = cs.sp, ct = cs.ct, st = cs.st;
   const float dcp = cp * ca1 - sp * sa, dsp = sp * ca1 + cp * sa;
   const float dct = ct * cb1 - st * sb, dst = st * cb1 + ct * sb;
   out[0] = cp * dst + dcp * st + dcp * dst;
   out[1] = sp * dst + dsp * st + dsp * dst;
   out[2] = dct;
+  cs.cp = cp + dcp;
+  cs.sp = sp + dsp;
+  cs.ct = ct + dct;
+  cs.st = st + dst;
 }
 
-// float cosines and sines of a float direction
-__device__ __forceinline__ void dir_csf(const float t[3], float& cp, float& sp, float& ct, float& st) {
-  const float rho = sqrtf(t[0] * t[0] + t[1] * t[1]);
-  const float irho = 1.0f / rho, itn = rsqrtf(rho * rho + t[2] * t[2]);
-  cp = t[0] * irho;
-  sp = t[1] * irho;
-  st = rho * itn;
-  ct = t[2] * itn;
-}
 
 // Transport the filtered state on surface a to surface b.  The filtered
 // state is the predicted one (point r0, direction d, time x[5]) plus the
 // filter's pending FP32 increments pd; x[4] is the filtered q/p.
 template <bool BZ>
 __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, const double r0[3], const double x[6],
-                               const Dir& d, const Pend& pd, const float Bf[3], float m2, float h_max, int n_iter,
-                               double xp[6], double rp[3], Dir& dp, JacF& J, float& sin_th, float& cos_inc) {
+                               const Dir& d, const Pend& pd, CS& cs, const float Bf[3], float m2, float h_max,
+                               int n_iter, double xp[6], double rp[3], Dir& dp, JacF& J, float& sin_th,
+                               float& cos_inc) {
   // The point and the direction stay FP64 (predicted values of surface a);
   // everything that moves them here (the pending filter increments, the RKN
   // curvature terms, the direction change accT, the plane corrections) is
@@ -188,8 +212,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   const float dtl = m2 * lam * (float)kInvC / gam;  // d(dt/ds)/dlam
   Cols g;
   {
-    float cpf, spf, ctf, stf;
-    dir_csf(T0f, cpf, spf, ctf, stf);
+    const float cpf = cs.cp, spf = cs.sp, ctf = cs.ct, stf = cs.st;
     g.gT[0][0] = -spf * stf; g.gT[1][0] = cpf * stf; g.gT[2][0] = 0.0f;
     g.gT[0][1] = cpf * ctf;  g.gT[1][1] = spf * ctf; g.gT[2][1] = -stf;
 #pragma unroll
@@ -278,11 +301,11 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     const float c0 = T0f[0], c1 = T0f[1], c2 = T0f[2];
     const float a0 = accT[0], a1 = accT[1], a2 = accT[2];
     const float rho_sq = c0 * c0 + c1 * c1;
-    const float dphi = atan2f(c0 * a1 - c1 * a0, rho_sq + c0 * a0 + c1 * a1);
+    const float dphi = small_atan2(c0 * a1 - c1 * a0, rho_sq + c0 * a0 + c1 * a1);
     const float drho_sq = 2.0f * (c0 * a0 + c1 * a1) + a0 * a0 + a1 * a1;
     const float rho = sqrtf(rho_sq), rho_end = sqrtf(rho_sq + drho_sq);
     const float drho = drho_sq / (rho + rho_end);
-    const float dth = atan2f(c2 * drho - rho * a2, c2 * (c2 + a2) + rho * (rho + drho));
+    const float dth = small_atan2(c2 * drho - rho * a2, c2 * (c2 + a2) + rho * (rho + drho));
     dp = d;
     double phi = d.phi + f2d(pd.phi + dphi);
     // keep phi in (-pi, pi]; compared on the integer pipe (doubles of one
@@ -309,6 +332,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   // path correction and free -> bound Jacobian (FP32)
   float cph, sph, cth, sth;
   dir_cs(dp.T, cph, sph, cth, sth);
+  cs = CS{cph, sph, cth, sth};
   const float Tu[3] = {cph * sth, sph * sth, cth};
   const float nT = nb[0] * Tu[0] + nb[1] * Tu[1] + nb[2] * Tu[2];
   float AT[3];
@@ -557,6 +581,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
     // the FP32 transport F Cf F^T (the Joseph update produces it in FP64).
     double x[6], r[3];
     Pend pd = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, 0.0f, 0.0f, 0.0f};
+    CS cs;  // float cosines / sines of the filtered direction
     float Cf[21];
     float dx[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // x_f - x_p of the last state
 #pragma unroll
@@ -571,6 +596,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
       d.T[0] = cp * st;
       d.T[1] = sp * st;
       d.T[2] = ct;
+      cs = CS{d2f(cp), d2f(sp), d2f(ct), d2f(st)};
     }
     int sid_prev = p.surface_id[o0];
     {
@@ -598,7 +624,8 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
         JacF J;
         float sin_th, cos_inc;
-        status = transport_mixed<BZ>(sa, sb, r, x, d, pd, Bf, m2, h_max, p.n_iter, xp, rp, dp, J, sin_th, cos_inc);
+        status = transport_mixed<BZ>(sa, sb, r, x, d, pd, cs, Bf, m2, h_max, p.n_iter, xp, rp, dp, J, sin_th,
+                                     cos_inc);
         if (status != ST_OK) break;
         const float* Cr = Cf;
         // Cp = F Cf F^T, rows of Bm = F Cf formed on the fly
@@ -706,7 +733,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         // q/p is updated here
 #pragma unroll
         for (int c = 0; c < 3; ++c) pd.r[c] = dx[0] * sk.uf(c) + dx[1] * sk.vf(c);
-        turn_inc(dp.T, dx[2], dx[3], pd.T);
+        turn_inc(cs, dx[2], dx[3], pd.T);
         pd.phi = dx[2];
         pd.theta = dx[3];
         pd.t = dx[5];

@@ -50,8 +50,8 @@ MIXED_TRAFFIC_SOURCES_SHA256 = "e2815b4302e1ceef505eb71e1be40d809cb95611644cda6d
 def mixed_kernel_sources_sha256():
     import hashlib
     h = hashlib.sha256()
-    for f in ("kf_mixed.cu", "kf_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2105_01796_gb300", "csrc", f), "rb") as fh:
+    for f in ("csrc/kf_mixed.cu", "csrc/kf_device.cuh", "_build.py"):
+        with open(os.path.join(ROOT, "paper_2105_01796_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 

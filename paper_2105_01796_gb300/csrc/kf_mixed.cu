@@ -7,7 +7,7 @@
 //   * FP32: RKN stages, the step Jacobians, path correction, the 6x6
 //     transport F C F^T, the Highland noise, the gain K, the smoother gain
 //     algebra and the smoothed covariance.
-//   * FP64: the Joseph covariance update, chi2, the Cholesky factorisation
+//   * FP64: the Joseph covariance update, chi2, the LDL^T factorisation
 //     of the predicted covariance and its solves (the smoother's inverse),
 //     and the accumulators of position, direction, time and the parameter
 //     vector, which receive FP32 increments.
@@ -23,8 +23,8 @@
 // and the smoothed covariance Cs = Cf + A (Cs' - Cp') A^T equals
 //   Cs = F^-1 (Q - Q Cp'^-1 Q) F^-T + A Cs' A^T,
 // a sum of two positive semi-definite terms (no cancellation against Cf).
-// Only the (phi, theta) columns of Cp'^-1 are needed: one FP64 Cholesky
-// factorisation and two FP64 triangular-solve pairs per state.
+// Only the (phi, theta) columns of Cp'^-1 are needed: one FP64 LDL^T
+// factorisation of a 4x4 block and two FP64 triangular-solve pairs per state.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -231,7 +231,7 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   // direction change
   double s0d, dist;
   {
-    dist = sb.nc() - (sb.n(0) * r[0] + sb.n(1) * r[1] + sb.n(2) * r[2]);
+    dist = fma(-sb.n(2), r[2], fma(-sb.n(1), r[1], fma(-sb.n(0), r[0], sb.nc())));
     const float nT = nb[0] * T0f[0] + nb[1] * T0f[1] + nb[2] * T0f[2];
     if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
     const float s0 = (d2f(dist) - (nb[0] * pd.r[0] + nb[1] * pd.r[1] + nb[2] * pd.r[2])) / nT;
@@ -239,7 +239,8 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     if (!(nsub_f <= 64.0f)) return ST_NO_INTERSECTION;
     const int nsub = nsub_f < 1.0f ? 1 : (int)nsub_f;
     const float h = s0 / (float)nsub;
-    s0d = f2d(h) * (double)nsub;
+    s0d = f2d(h);
+    if (nsub > 1) s0d *= (double)nsub;  // exact: nsub is a small integer
     for (int k = 0; k < nsub; ++k) {
       const float Tf[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
       cols_step<BZ>(g, h, bs, kB, Tf, dtl);
@@ -467,40 +468,40 @@ __device__ __forceinline__ void invert_F(const float F[25], float Fi[6][6]) {
 
 // Columns phi and theta of Cp^-1 in FP64, by block elimination with the
 // angle block last: a = (loc0, loc1, q/p, t), b = (phi, theta).
-//   X = Caa^-1 Cab (4x4 Cholesky, two solves), Sig = Cbb - Cab^T X (the 2x2
+//   X = Caa^-1 Cab (4x4 LDL^T, two solves), Sig = Cbb - Cab^T X (the 2x2
 //   Schur complement), then (Cp^-1)[b][b] = Sig^-1, (Cp^-1)[a][b] = -X Sig^-1.
 // Cp is SPD iff the four pivots of Caa and Sig are positive.  Returns false
 // otherwise.  w[0] = Cp^-1 e_phi, w[1] = Cp^-1 e_theta (6 each).
 __device__ __forceinline__ bool angle_columns_of_inverse(const double Cp[21], double w[2][6]) {
   constexpr int ia[4] = {0, 1, 4, 5};
-  double L[4][4], idg[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) L[r][c] = Cp[sym(ia[r], ia[c])];
+  // LDL^T of the 4x4 block (no square roots): U = L D below the diagonal
+  double L[4][4], U[4][4], iD[4];
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    double dj = L[j][j];
+    double dj = Cp[sym(ia[j], ia[j])];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (q < j) dj = fma(-L[j][q], L[j][q], dj);
+      if (q < j) dj = fma(-U[j][q], L[j][q], dj);
     if (!dpos(dj)) {
       ok = false;
       dj = 1.0;
     }
-    idg[j] = rsqrt_nr<1>(dj);
+    iD[j] = rcp_nr<1>(dj);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       if (r > j) {
-        double v = L[r][j];
+        double u = Cp[sym(ia[r], ia[j])];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (q < j) v = fma(-L[r][q], L[j][q], v);
-        L[r][j] = v * idg[j];
+          if (q < j) u = fma(-U[r][q], L[j][q], u);
+        U[r][j] = u;
+        L[r][j] = u * iD[j];
       }
     }
   }
+  // X = Caa^-1 Cab: unit-lower forward solve, scaling by D^-1, unit-upper
+  // backward solve
   double X[4][2];
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
@@ -511,15 +512,15 @@ __device__ __forceinline__ bool angle_columns_of_inverse(const double Cp[21], do
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (q < r) v = fma(-L[r][q], y[q], v);
-      y[r] = v * idg[r];
+      y[r] = v;
     }
 #pragma unroll
     for (int r = 3; r >= 0; --r) {
-      double v = y[r];
+      double v = y[r] * iD[r];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (q > r) v = fma(-L[q][r], X[q][m], v);
-      X[r][m] = v * idg[r];
+      X[r][m] = v;
     }
   }
   double s00 = Cp[sy(2, 2)], s01 = Cp[sy(3, 2)], s11 = Cp[sy(3, 3)];

@@ -28,7 +28,7 @@ FP64 path (everything in double precision):
 Mixed path: the double-precision part the method requires is
     per measured state   JOSEPH + CHI2
     per smoother step    INV_COLS + NRANK   (the (phi, theta) columns of
-                         Cp^-1 by a 4x4 Cholesky of the loc/q/p/t block, two
+                         Cp^-1 by a 4x4 LDL^T of the loc/q/p/t block, two
                          solves and the 2x2 Schur complement of the angle
                          block; N = Q - Q Cp^-1 Q)
 and everything else runs in FP32 (counted as fp32 work).
@@ -44,10 +44,11 @@ CHI2 = 16
 CHOL = 2 * 35 + 15 + 6
 SOLVE6 = 6 * 2 * 36
 SOLVE2 = 48 + 42
-# 4x4 Cholesky (6 FMA, 4 rsqrt, 4 FMA + 6 mul), two solve pairs (2 x 32),
-# Schur complement (12 FMA), its inverse (det 3, 1/det 1, 3 mul), off-block
-# columns (8 x (FMA + mul) + 8 negations folded) -> flops
-INV_COLS = (2 * 6 + 4 + 2 * 4 + 6) + 2 * 32 + 2 * 12 + 7 + 8 * 3
+# 4x4 LDL^T (pivots 6 FMA, U 4 FMA, L 6 mul, 4 reciprocals), two solves
+# (unit-lower 6 FMA, D^-1 4 mul, unit-upper 6 FMA each), Schur complement
+# (12 FMA), its inverse (det 3, 1/det 1, 3 mul), off-block columns
+# (8 x (FMA + mul)) -> flops
+INV_COLS = (2 * 6 + 2 * 4 + 6 + 4) + 2 * (2 * 6 + 4 + 2 * 6) + 2 * 12 + 7 + 8 * 3
 NRANK = 7
 RTS_UPD = 84 + 21 + 2 * 216 + 2 * 126 + 21
 # FP32 side of the mixed smoother: F^-1 (block form), gain A, xs, Cs

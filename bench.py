@@ -39,12 +39,12 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 
 # DRAM traffic of the mixed kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of a 80k-track, 2.48M-state launch of the same
-# workload (profiles/fit_kernel_MixedBody_tel30_80k.md): 821.709 + 867.981 MB.
+# workload (profiles/fit_kernel_MixedBody_tel30_80k.md): 822.223 + 869.466 MB.
 # Traffic grows in proportion to the states, so a launch's traffic is this
-# per-state figure times its states.  It holds only for the kernel sources
-# that were captured: any change to them makes the figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = 1.689690624e9 / 2.48e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "e2815b4302e1ceef505eb71e1be40d809cb95611644cda6dfa32a9fb7331eb99"
+# per-state figure times its states.  It holds only for the kernel sources and
+# build flags that were captured: any change to them makes the figure null.
+MIXED_TRAFFIC_BYTES_PER_STATE = 1.69168896e9 / 2.48e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "51c1661bdceaa98042bf09afcb9a4af21e950d75700dafd99b571ac7689a5805"
 
 
 def mixed_kernel_sources_sha256():

@@ -6,7 +6,7 @@
 // metric of the smoother paragraph).  chi2 depends only on the forward
 // filter, so the smoother contributes nothing to this gradient.
 //
-// Method (reverse mode over the states, forward mode inside one transport):
+// Method (reverse mode throughout):
 //   forward:  FP64 filter; (x_f, C_f) checkpointed every kSeg states.
 //   backward: for each segment, last first, recompute its filtered states
 //     from the checkpoint; then for k = last .. 1 of the segment
@@ -15,11 +15,11 @@
 //          adjoints of (x_f,k, C_f,k) -> adjoints of (x_p,k, C_p,k)
 //       3. reverse through C_p = F C_f F^T + Q: Lambda_Cf = F^T Lambda_Cp F,
 //          lambda_F = 2 Lambda_Cp F C_f, lambda_Q = Lambda_Cp
-//       4. the transport's sensitivities to the 18 inputs it depends on
-//          (x_f,k-1; the alignment of surfaces k-1 and k) by dual numbers
-//          carrying two tangent directions per pass (9 passes), contracted at
-//          once with (lambda_xp, lambda_F, lambda_Q): this includes the
-//          derivative of F itself.
+//       4. one reverse sweep through the transport (its RKN steps recorded
+//          on a small tape) gives the adjoints of its 18 inputs (x_f,k-1; the
+//          alignment of surfaces k-1 and k) for the contraction with
+//          (lambda_xp, lambda_F, lambda_Q): this includes the derivative of
+//          F itself, since the sweep runs through the code that forms F.
 //     state 0: reverse through its update; x_p,0 is the seed.
 // Alignment of a surface (shifts along its local axes, then rotations about
 // them):  c' = c + R (du, dv, dn),  R' = R Ru(alpha) Rv(beta) Rn(gamma).
@@ -36,98 +36,7 @@ using namespace dev;
 
 constexpr int kSeg = 8;  // states per checkpoint segment (about sqrt(n) for n ~ 30-60)
 
-// ---------------------------------------------------------------------------
-// dual numbers: value + N directional derivatives (forward-mode AD)
-// ---------------------------------------------------------------------------
-template <int N>
-struct Dual {
-  double v;
-  double d[N];
-  __device__ Dual() {}
-  __device__ Dual(double x) : v(x) {
-#pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = 0.0;
-  }
-};
-
-template <int N> __device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r; r.v = a.v + b.v;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
-  return r;
-}
-template <int N> __device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r; r.v = a.v - b.v;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
-  return r;
-}
-template <int N> __device__ __forceinline__ Dual<N> operator-(const Dual<N>& a) {
-  Dual<N> r; r.v = -a.v;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
-  return r;
-}
-template <int N> __device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r; r.v = a.v * b.v;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = fma(a.d[i], b.v, a.v * b.d[i]);
-  return r;
-}
-template <int N> __device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r; r.v = a.v / b.v;
-  const double ib = 1.0 / b.v;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
-  return r;
-}
-template <int N> __device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, double b) { Dual<N> r = a; r.v += b; return r; }
-template <int N> __device__ __forceinline__ Dual<N> operator+(double b, const Dual<N>& a) { return a + b; }
-template <int N> __device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, double b) { Dual<N> r = a; r.v -= b; return r; }
-template <int N> __device__ __forceinline__ Dual<N> operator-(double b, const Dual<N>& a) { return (-a) + b; }
-template <int N> __device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, double b) {
-  Dual<N> r; r.v = a.v * b;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
-  return r;
-}
-template <int N> __device__ __forceinline__ Dual<N> operator*(double b, const Dual<N>& a) { return a * b; }
-template <int N> __device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, double b) { return a * (1.0 / b); }
-template <int N> __device__ __forceinline__ Dual<N> operator/(double a, const Dual<N>& b) { return Dual<N>(a) / b; }
-template <int N> __device__ __forceinline__ Dual<N>& operator+=(Dual<N>& a, const Dual<N>& b) { a = a + b; return a; }
-template <int N> __device__ __forceinline__ Dual<N>& operator-=(Dual<N>& a, const Dual<N>& b) { a = a - b; return a; }
-
-template <int N> __device__ __forceinline__ Dual<N> chain(const Dual<N>& a, double f, double df) {
-  Dual<N> r; r.v = f;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = df * a.d[i];
-  return r;
-}
-template <int N> __device__ __forceinline__ Dual<N> sqrt(const Dual<N>& a) {
-  const double s = ::sqrt(a.v);
-  return chain(a, s, 0.5 / s);
-}
-template <int N> __device__ __forceinline__ Dual<N> sin(const Dual<N>& a) { return chain(a, ::sin(a.v), ::cos(a.v)); }
-template <int N> __device__ __forceinline__ Dual<N> cos(const Dual<N>& a) { return chain(a, ::cos(a.v), -::sin(a.v)); }
-template <int N> __device__ __forceinline__ Dual<N> log(const Dual<N>& a) { return chain(a, ::log(a.v), 1.0 / a.v); }
-template <int N> __device__ __forceinline__ Dual<N> fabs(const Dual<N>& a) { return a.v < 0.0 ? -a : a; }
-template <int N> __device__ __forceinline__ Dual<N> atan2(const Dual<N>& y, const Dual<N>& x) {
-  Dual<N> r; r.v = ::atan2(y.v, x.v);
-  const double id = 1.0 / (x.v * x.v + y.v * y.v);
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = (x.v * y.d[i] - y.v * x.d[i]) * id;
-  return r;
-}
-// the double overloads stay visible next to the Dual templates
-using ::atan2;
-using ::cos;
-using ::fabs;
-using ::log;
-using ::sin;
-using ::sqrt;
-
 __device__ __forceinline__ double val(double x) { return x; }
-template <int N> __device__ __forceinline__ double val(const Dual<N>& x) { return x.v; }
 
 // ---------------------------------------------------------------------------
 // geometry with alignment
@@ -168,7 +77,7 @@ __device__ __forceinline__ Plane<S> aligned_plane(const Surf& s, const S a[6]) {
 }
 
 // ---------------------------------------------------------------------------
-// the transport, generic in the scalar type (double or Dual<N>); same
+// the transport (generic in the scalar type; used with double); same
 // arithmetic as the FP64 fit kernel
 // ---------------------------------------------------------------------------
 template <class S>
@@ -487,6 +396,602 @@ __device__ void update_adj(const double xp[6], const double Cp[21], const double
   for (int i = 0; i < 6; ++i) lp[i] = lf[i] - (i < 2 ? lr[i] : 0.0);
 }
 
+// ---------------------------------------------------------------------------
+// reverse mode through one transport
+//
+// The gradient of a scalar of the transport's outputs,
+//   phi = lxp . xp + sum lJ . F + lq_phi q_phi + lq_theta q_theta,
+// with respect to the transport's inputs (x and the two aligned planes) is
+// taken by one reverse sweep over the same arithmetic as transport_s<double>
+// (RKN steps with their Jacobian columns, plane intersections, end frame,
+// path correction, free -> bound, Highland noise).  The second derivatives
+// that the F term brings in are exact: the reverse sweep runs through the
+// code that forms F.
+// ---------------------------------------------------------------------------
+constexpr int kTape = 16;  // RKN steps recorded per transport (more are recomputed)
+
+struct StepIn {  // state entering one RKN step
+  double r[3], T[3], gT[3][3], h;
+};
+
+struct Tape {
+  StepIn st[kTape];
+  int n_steps, nsub;
+  double s0;
+};
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// A(v) = lk (v x B)
+__device__ __forceinline__ void Aop(const double v[3], const double B[3], double lk, double o[3]) {
+  o[0] = (v[1] * B[2] - v[2] * B[1]) * lk;
+  o[1] = (v[2] * B[0] - v[0] * B[2]) * lk;
+  o[2] = (v[0] * B[1] - v[1] * B[0]) * lk;
+}
+
+// reverse of o = A(v): vbar += lk (B x obar), lkbar += (v x B) . obar
+__device__ __forceinline__ void Aop_rev(const double v[3], const double B[3], double lk, const double ob[3],
+                                        double vb[3], double& lkb) {
+  double bx[3], vx[3];
+  cross3(B, ob, bx);
+  cross3(v, B, vx);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) vb[i] += lk * bx[i];
+  lkb += vx[0] * ob[0] + vx[1] * ob[1] + vx[2] * ob[2];
+}
+
+// Reverse of one RKN step.  In: the step's input state (T, gT, lam, h) and
+// the adjoints of its outputs (Tb = adjoint of T', gTb = of gT'; the
+// additive parts r, t, gr, gtl pass their adjoints rb, tb, grb, gtlb through
+// unchanged).  Out: Tb, gTb replaced by the adjoints of the inputs; lamb and
+// hb accumulated.
+__device__ void rkn_rev(const StepIn& in, double lam, const double B[3], double mass, const double rb[3],
+                        double tb, const double grb[3][3], double gtlb, double Tb[3], double gTb[3][3],
+                        double& lamb, double& hb) {
+  const double h = in.h;
+  const double h2 = h * h * 0.5, h3 = h * h * h * (1.0 / 6.0), h4 = h * h * h * h * (1.0 / 24.0);
+  const double lk = lam * kKappa;
+  const double* T = in.T;
+  double a1[3], a2[3], a3[3], a4[3], u0[3], u1[3], u2[3], u3[3];
+  Aop(T, B, lk, a1);
+  Aop(a1, B, lk, a2);
+  Aop(a2, B, lk, a3);
+  Aop(a3, B, lk, a4);
+  Aop(T, B, kKappa, u0);
+  Aop(u0, B, lk, u1);
+  Aop(u1, B, lk, u2);
+  Aop(u2, B, lk, u3);
+  double lkb = 0.0;
+  double Tin_b[3], a1b[3], a2b[3], a3b[3], a4b[3], u0b[3] = {0, 0, 0}, u1b[3] = {0, 0, 0}, u2b[3] = {0, 0, 0},
+                                                   u3b[3] = {0, 0, 0};
+  // t' = t + h gam / c;  gtl' = gtl + h lam m^2 / (c gam)
+  const double m2 = mass * mass;
+  const double gam = sqrt(1.0 + lam * lam * m2);
+  double gamb = tb * h * kInvC - gtlb * h * lam * m2 * kInvC / (gam * gam);
+  hb += tb * gam * kInvC + gtlb * lam * m2 * kInvC / gam;
+  lamb += gtlb * h * m2 * kInvC / gam;
+  lamb += gamb * lam * m2 / gam;
+  // r' = r + h T + h2 a1 + h3 a2 + h4 a3;  T' = T + h a1 + h2 a2 + h3 a3 + h4 a4
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Tin_b[i] = Tb[i] + h * rb[i];
+    a1b[i] = h2 * rb[i] + h * Tb[i];
+    a2b[i] = h3 * rb[i] + h2 * Tb[i];
+    a3b[i] = h4 * rb[i] + h3 * Tb[i];
+    a4b[i] = h4 * Tb[i];
+    hb += rb[i] * (T[i] + h * a1[i] + 0.5 * h * h * a2[i] + h * h * h * (1.0 / 6.0) * a3[i]);
+    hb += Tb[i] * (a1[i] + h * a2[i] + 0.5 * h * h * a3[i] + h * h * h * (1.0 / 6.0) * a4[i]);
+  }
+  // Jacobian columns
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double v[3] = {in.gT[0][c], in.gT[1][c], in.gT[2][c]};
+    double b1[3], b2[3], b3[3], b4[3];
+    Aop(v, B, lk, b1);
+    Aop(b1, B, lk, b2);
+    Aop(b2, B, lk, b3);
+    Aop(b3, B, lk, b4);
+    double vb[3], b1b[3], b2b[3], b3b[3], b4b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double rho = grb[i][c], nu = gTb[i][c];
+      vb[i] = h * rho + nu;
+      b1b[i] = h2 * rho + h * nu;
+      b2b[i] = h3 * rho + h2 * nu;
+      b3b[i] = h4 * rho + h3 * nu;
+      b4b[i] = h4 * nu;
+      hb += rho * (v[i] + h * b1[i] + 0.5 * h * h * b2[i] + h * h * h * (1.0 / 6.0) * b3[i]);
+      hb += nu * (b1[i] + h * b2[i] + 0.5 * h * h * b3[i] + h * h * h * (1.0 / 6.0) * b4[i]);
+      if (c == 2) {
+        u0b[i] += h2 * rho + h * nu;
+        u1b[i] += h * h * h * (1.0 / 3.0) * rho + h * h * nu;
+        u2b[i] += h * h * h * h * 0.125 * rho + h * h * h * 0.5 * nu;
+        u3b[i] += h * h * h * h * (1.0 / 6.0) * nu;
+        hb += rho * (h * u0[i] + h * h * u1[i] + 0.5 * h * h * h * u2[i]);
+        hb += nu * (u0[i] + 2.0 * h * u1[i] + 1.5 * h * h * u2[i] + (2.0 / 3.0) * h * h * h * u3[i]);
+      }
+    }
+    Aop_rev(b3, B, lk, b4b, b3b, lkb);
+    Aop_rev(b2, B, lk, b3b, b2b, lkb);
+    Aop_rev(b1, B, lk, b2b, b1b, lkb);
+    Aop_rev(v, B, lk, b1b, vb, lkb);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gTb[i][c] = vb[i];
+  }
+  Aop_rev(u2, B, lk, u3b, u2b, lkb);
+  Aop_rev(u1, B, lk, u2b, u1b, lkb);
+  Aop_rev(u0, B, lk, u1b, u0b, lkb);
+  {
+    double dummy = 0.0;
+    Aop_rev(T, B, kKappa, u0b, Tin_b, dummy);  // u0 = kappa (T x B)
+  }
+  Aop_rev(a3, B, lk, a4b, a3b, lkb);
+  Aop_rev(a2, B, lk, a3b, a2b, lkb);
+  Aop_rev(a1, B, lk, a2b, a1b, lkb);
+  Aop_rev(T, B, lk, a1b, Tin_b, lkb);
+  lamb += kKappa * lkb;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Tb[i] = Tin_b[i];
+}
+
+__device__ __forceinline__ void save_step(const PropS<double>& s, double h, StepIn& o) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    o.r[i] = s.r[i];
+    o.T[i] = s.T[i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o.gT[i][c] = s.gT[i][c];
+  }
+  o.h = h;
+}
+
+// The transport with its tape: values exactly as transport_s<double>, the
+// state entering each RKN step recorded (the first kTape).
+__device__ int transport_tape(const Plane<double>& pa, const Plane<double>& pb, const double x[6],
+                              const double B[3], double mass, double h_max, int n_iter, double xx0, double xp[6],
+                              JacS<double>& J, double& qphi, double& qth, Tape& tp, PropS<double>& s_end) {
+  PropS<double> s;
+  const double sp = sin(x[2]), cp = cos(x[2]), st = sin(x[3]), ct = cos(x[3]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.r[i] = pa.c[i] + x[0] * pa.u(i) + x[1] * pa.v(i);
+  s.T[0] = cp * st;
+  s.T[1] = sp * st;
+  s.T[2] = ct;
+  s.t = x[5];
+  s.lam = x[4];
+  s.gT[0][0] = -(sp * st); s.gT[1][0] = cp * st; s.gT[2][0] = 0.0;
+  s.gT[0][1] = cp * ct;    s.gT[1][1] = sp * ct; s.gT[2][1] = -st;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    s.gT[i][2] = 0.0;
+    s.gr[i][0] = s.gr[i][1] = s.gr[i][2] = 0.0;
+  }
+  s.gtl = 0.0;
+  auto dist = [&](double& out) -> bool {
+    const double d = pb.n(0) * (pb.c[0] - s.r[0]) + pb.n(1) * (pb.c[1] - s.r[1]) + pb.n(2) * (pb.c[2] - s.r[2]);
+    const double nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
+    if (!(::fabs(nT) > 1e-9)) return false;
+    out = d / nT;
+    return true;
+  };
+  double s0;
+  if (!dist(s0)) return ST_NO_INTERSECTION;
+  const double nsub_d = ::ceil(::fabs(s0) / h_max);
+  if (!(nsub_d <= 64.0)) return ST_NO_INTERSECTION;
+  const int nsub = nsub_d < 1.0 ? 1 : (int)nsub_d;
+  const double h = s0 / (double)nsub;
+  tp.nsub = nsub;
+  tp.s0 = s0;
+  int ns = 0;
+  for (int k = 0; k < nsub; ++k, ++ns) {
+    if (ns < kTape) save_step(s, h, tp.st[ns]);
+    rkn_step_s<double>(s, h, B, mass);
+  }
+  for (int it = 0; it < n_iter; ++it, ++ns) {
+    double si;
+    if (!dist(si)) return ST_NO_INTERSECTION;
+    if (ns < kTape) save_step(s, si, tp.st[ns]);
+    rkn_step_s<double>(s, si, B, mass);
+  }
+  tp.n_steps = ns;
+  s_end = s;
+  // the end frame and the outputs, as in transport_s
+  const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
+  const double phi = atan2(s.T[1], s.T[0]);
+  const double rho = sqrt(rho2);
+  const double theta = atan2(rho, s.T[2]);
+  const double tn = sqrt(rho2 + s.T[2] * s.T[2]);
+  const double cph = s.T[0] / rho, sph = s.T[1] / rho, sth = rho / tn, cth = s.T[2] / tn;
+  const double nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
+  const double lk = s.lam * kKappa;
+  double AT[3];
+  crossB(s.T, B, lk, AT);
+  const double dtds = sqrt(1.0 + s.lam * s.lam * (mass * mass)) * kInvC;
+  double Gr[3][5], GT[3][5], Gt[5];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Gr[i][0] = pa.u(i);
+    Gr[i][1] = pa.v(i);
+    Gr[i][2] = s.gr[i][0];
+    Gr[i][3] = s.gr[i][1];
+    Gr[i][4] = s.gr[i][2];
+    GT[i][0] = 0.0;
+    GT[i][1] = 0.0;
+    GT[i][2] = s.gT[i][0];
+    GT[i][3] = s.gT[i][1];
+    GT[i][4] = s.gT[i][2];
+  }
+  Gt[0] = Gt[1] = Gt[2] = Gt[3] = 0.0;
+  Gt[4] = s.gtl;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const double w = -(pb.n(0) * Gr[0][c] + pb.n(1) * Gr[1][c] + pb.n(2) * Gr[2][c]) / nT;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Gr[i][c] += s.T[i] * w;
+      GT[i][c] += AT[i] * w;
+    }
+    Gt[c] += dtds * w;
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    J.f[0][c] = pb.u(0) * Gr[0][c] + pb.u(1) * Gr[1][c] + pb.u(2) * Gr[2][c];
+    J.f[1][c] = pb.v(0) * Gr[0][c] + pb.v(1) * Gr[1][c] + pb.v(2) * Gr[2][c];
+    J.f[2][c] = (cph * GT[1][c] - sph * GT[0][c]) / sth;
+    J.f[3][c] = cph * cth * GT[0][c] + sph * cth * GT[1][c] - sth * GT[2][c];
+    J.ft[c] = Gt[c];
+  }
+  const double d0 = s.r[0] - pb.c[0], d1 = s.r[1] - pb.c[1], d2 = s.r[2] - pb.c[2];
+  xp[0] = d0 * pb.u(0) + d1 * pb.u(1) + d2 * pb.u(2);
+  xp[1] = d0 * pb.v(0) + d1 * pb.v(1) + d2 * pb.v(2);
+  xp[2] = phi;
+  xp[3] = theta;
+  xp[4] = s.lam;
+  xp[5] = s.t;
+  if (xx0 > 0.0) {
+    const double l = ::fabs(s.lam);
+    const double g2 = 1.0 + l * l * (mass * mass);
+    const double eps = xx0 / ::fabs(nT / tn);
+    const double th0 = 0.0136 * l * sqrt(g2) * sqrt(eps) * (1.0 + 0.038 * log(eps * g2));
+    qth = th0 * th0;
+    qphi = qth / (sth * sth);
+  } else {
+    qth = 0.0;
+    qphi = 0.0;
+  }
+  return ST_OK;
+}
+
+// Adjoints of the transport's inputs for the output adjoints (lxp, lJ, lJt,
+// lqp, lqt), from the tape and end state of transport_tape on the same
+// inputs.  Outputs: lx[6] and the adjoints of the planes' centres and
+// rotations (row-major 3x3 whose columns are u, v, n).
+__device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, const double x[6], const double B[3],
+                              double mass, double xx0, const Tape& tp, const PropS<double>& s,
+                              const double lxp[6], const double lJ[4][5], const double lJt[5], double lqp,
+                              double lqt, double lx[6], double lca[3], double lRa[9], double lcb[3],
+                              double lRb[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) lca[i] = lcb[i] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) lRa[i] = lRb[i] = 0.0;
+  // adjoints of the end state
+  double rb[3] = {0, 0, 0}, Tb[3] = {0, 0, 0}, tb = lxp[5], lamb = lxp[4], grb[3][3], gTb[3][3], gtlb = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) grb[i][c] = gTb[i][c] = 0.0;
+  double nbb[3] = {0, 0, 0}, ubb[3] = {0, 0, 0}, vbb[3] = {0, 0, 0};  // plane b axes
+  double uab[3] = {0, 0, 0}, vab[3] = {0, 0, 0};                       // plane a axes
+  const double m2 = mass * mass;
+  // ---- end frame values (recomputed)
+  const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
+  const double rho = sqrt(rho2);
+  const double tn2 = rho2 + s.T[2] * s.T[2];
+  const double tn = sqrt(tn2);
+  const double cph = s.T[0] / rho, sph = s.T[1] / rho, sth = rho / tn, cth = s.T[2] / tn;
+  const double nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
+  const double lk = s.lam * kKappa;
+  double AT[3];
+  crossB(s.T, B, lk, AT);
+  const double gam_e = sqrt(1.0 + s.lam * s.lam * m2);
+  const double dtds = gam_e * kInvC;
+  double Gr0[3][5], GT0[3][5], w[5], Gr[3][5], GT[3][5];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Gr0[i][0] = pa.u(i);
+    Gr0[i][1] = pa.v(i);
+    Gr0[i][2] = s.gr[i][0];
+    Gr0[i][3] = s.gr[i][1];
+    Gr0[i][4] = s.gr[i][2];
+    GT0[i][0] = 0.0;
+    GT0[i][1] = 0.0;
+    GT0[i][2] = s.gT[i][0];
+    GT0[i][3] = s.gT[i][1];
+    GT0[i][4] = s.gT[i][2];
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    w[c] = -(pb.n(0) * Gr0[0][c] + pb.n(1) * Gr0[1][c] + pb.n(2) * Gr0[2][c]) / nT;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Gr[i][c] = Gr0[i][c] + s.T[i] * w[c];
+      GT[i][c] = GT0[i][c] + AT[i] * w[c];
+    }
+  }
+  double nTb = 0.0, cphb = 0.0, sphb = 0.0, cthb = 0.0, sthb = 0.0, phib = lxp[2], thetab = lxp[3], tnb = 0.0;
+  // ---- Highland noise
+  if (xx0 > 0.0) {
+    const double l = ::fabs(s.lam);
+    const double g2 = 1.0 + l * l * m2;
+    const double cinc = nT / tn;
+    const double eps = xx0 / ::fabs(cinc);
+    const double Lg = 1.0 + 0.038 * log(eps * g2);
+    const double th0 = 0.0136 * l * sqrt(g2) * sqrt(eps) * Lg;
+    const double qthb = lqt + lqp / (sth * sth);
+    sthb += lqp * (-2.0 * th0 * th0 / (sth * sth * sth));
+    const double th0b = 2.0 * th0 * qthb;
+    const double dl = th0 * (1.0 / l + l * m2 / g2 + 0.038 * (2.0 * l * m2 / g2) / Lg);
+    const double deps = th0 * (0.5 / eps + 0.038 / (eps * Lg));
+    lamb += th0b * dl * (s.lam >= 0.0 ? 1.0 : -1.0);
+    const double cb = th0b * deps * (-eps / cinc);
+    nTb += cb / tn;
+    tnb -= cb * nT / (tn * tn);
+  }
+  // ---- outputs xp
+  {
+    const double d[3] = {s.r[0] - pb.c[0], s.r[1] - pb.c[1], s.r[2] - pb.c[2]};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double db = lxp[0] * pb.u(i) + lxp[1] * pb.v(i);
+      ubb[i] += lxp[0] * d[i];
+      vbb[i] += lxp[1] * d[i];
+      rb[i] += db;
+      lcb[i] -= db;
+    }
+  }
+  // ---- J = projections of the corrected G columns
+  double Grb[3][5], GTb[3][5], Gtb[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const double l0 = lJ[0][c], l1 = lJ[1][c], l2 = lJ[2][c], l3 = lJ[3][c];
+    const double q = l2 / sth;
+    const double f2 = (cph * GT[1][c] - sph * GT[0][c]) / sth;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Grb[i][c] = l0 * pb.u(i) + l1 * pb.v(i);
+      ubb[i] += l0 * Gr[i][c];
+      vbb[i] += l1 * Gr[i][c];
+    }
+    GTb[0][c] = -q * sph + l3 * cph * cth;
+    GTb[1][c] = q * cph + l3 * sph * cth;
+    GTb[2][c] = -l3 * sth;
+    cphb += q * GT[1][c] + l3 * cth * GT[0][c];
+    sphb += -q * GT[0][c] + l3 * cth * GT[1][c];
+    sthb += -l2 * f2 / sth - l3 * GT[2][c];
+    cthb += l3 * (cph * GT[0][c] + sph * GT[1][c]);
+    Gtb[c] = lJt[c];
+  }
+  // ---- path correction: G = G0 + (T, AT, dtds) w, w = -(n.Gr0)/nT
+  double ATb[3] = {0, 0, 0}, dtdsb = 0.0;
+  double Gr0b[3][5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const double wb = Grb[0][c] * s.T[0] + Grb[1][c] * s.T[1] + Grb[2][c] * s.T[2] + GTb[0][c] * AT[0] +
+                      GTb[1][c] * AT[1] + GTb[2][c] * AT[2] + Gtb[c] * dtds;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      Tb[i] += w[c] * Grb[i][c];
+      ATb[i] += w[c] * GTb[i][c];
+      Gr0b[i][c] = Grb[i][c] - wb * pb.n(i) / nT;
+      nbb[i] += -wb * Gr0[i][c] / nT;
+    }
+    dtdsb += w[c] * Gtb[c];
+    nTb += -wb * w[c] / nT;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    uab[i] += Gr0b[i][0];
+    vab[i] += Gr0b[i][1];
+    grb[i][0] = Gr0b[i][2];
+    grb[i][1] = Gr0b[i][3];
+    grb[i][2] = Gr0b[i][4];
+    gTb[i][0] = GTb[i][2];
+    gTb[i][1] = GTb[i][3];
+    gTb[i][2] = GTb[i][4];
+  }
+  gtlb = Gtb[4];
+  // AT = lk (T x B); dtds = sqrt(1 + lam^2 m^2) / c
+  {
+    double lkb = 0.0;
+    Aop_rev(s.T, B, lk, ATb, Tb, lkb);
+    lamb += kKappa * lkb;
+    lamb += dtdsb * s.lam * m2 * kInvC / gam_e;
+  }
+  // nT = n . T
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    nbb[i] += nTb * s.T[i];
+    Tb[i] += nTb * pb.n(i);
+  }
+  // end angles and direction cosines
+  {
+    double rhob = 0.0, rho2b = 0.0;
+    Tb[0] += cphb / rho;
+    rhob -= cphb * s.T[0] / rho2;
+    Tb[1] += sphb / rho;
+    rhob -= sphb * s.T[1] / rho2;
+    rhob += sthb / tn;
+    tnb -= sthb * rho / tn2;
+    Tb[2] += cthb / tn;
+    tnb -= cthb * s.T[2] / tn2;
+    // theta = atan2(rho, T2)
+    rhob += thetab * s.T[2] / tn2;
+    Tb[2] -= thetab * rho / tn2;
+    // tn = sqrt(rho2 + T2^2)
+    rho2b += tnb / (2.0 * tn);
+    Tb[2] += tnb * s.T[2] / tn;
+    rho2b += rhob / (2.0 * rho);
+    // phi = atan2(T1, T0)
+    Tb[1] += phib * s.T[0] / rho2;
+    Tb[0] -= phib * s.T[1] / rho2;
+    Tb[0] += 2.0 * s.T[0] * rho2b;
+    Tb[1] += 2.0 * s.T[1] * rho2b;
+  }
+  // ---- reverse over the RKN steps, last first
+  const int nsteps = tp.n_steps;
+  double hb_main = 0.0;  // adjoint of the main steps' common length h = s0 / nsub
+  for (int j = nsteps - 1; j >= 0; --j) {
+    StepIn in;
+    if (j < kTape) {
+      in = tp.st[j];
+    } else {
+      // beyond the tape: recompute the forward from the last recorded step
+      PropS<double> q;
+      const StepIn& base = tp.st[kTape - 1];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        q.r[i] = base.r[i];
+        q.T[i] = base.T[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          q.gT[i][c] = base.gT[i][c];
+          q.gr[i][c] = 0.0;
+        }
+      }
+      q.t = 0.0;
+      q.gtl = 0.0;
+      q.lam = x[4];
+      double hj = base.h;
+      for (int k = kTape - 1; k < j; ++k) {
+        rkn_step_s<double>(q, hj, B, mass);
+        if (k + 1 < tp.nsub) {
+          hj = tp.s0 / (double)tp.nsub;
+        } else {
+          hj = (pb.n(0) * (pb.c[0] - q.r[0]) + pb.n(1) * (pb.c[1] - q.r[1]) + pb.n(2) * (pb.c[2] - q.r[2])) /
+               (pb.n(0) * q.T[0] + pb.n(1) * q.T[1] + pb.n(2) * q.T[2]);
+        }
+      }
+      save_step(q, hj, in);
+    }
+    double hb = 0.0;
+    rkn_rev(in, x[4], B, mass, rb, tb, grb, gtlb, Tb, gTb, lamb, hb);
+    if (j >= tp.nsub) {
+      // correction step: si = (n.(c - r))/(n.T) of the state entering it
+      const double nTi = pb.n(0) * in.T[0] + pb.n(1) * in.T[1] + pb.n(2) * in.T[2];
+      const double db = hb / nTi, nTib = -hb * in.h / nTi;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        nbb[i] += db * (pb.c[i] - in.r[i]) + nTib * in.T[i];
+        lcb[i] += db * pb.n(i);
+        rb[i] -= db * pb.n(i);
+        Tb[i] += nTib * pb.n(i);
+      }
+    } else {
+      hb_main += hb;
+    }
+  }
+  // ---- the main steps' length: h = s0 / nsub, s0 = (n.(c - r0))/(n.T0) of
+  // the start state (whose adjoints rb, Tb now are)
+  {
+    const StepIn& st0 = tp.st[0];
+    const double s0b = hb_main / (double)tp.nsub;
+    const double nT0 = pb.n(0) * st0.T[0] + pb.n(1) * st0.T[1] + pb.n(2) * st0.T[2];
+    const double db = s0b / nT0, nT0b = -s0b * tp.s0 / nT0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      nbb[i] += db * (pb.c[i] - st0.r[i]) + nT0b * st0.T[i];
+      lcb[i] += db * pb.n(i);
+      rb[i] -= db * pb.n(i);
+      Tb[i] += nT0b * pb.n(i);
+    }
+  }
+  // ---- the start: r = ca + x0 ua + x1 va; T and the G columns from the
+  // angles; t = x5; q/p = x4
+  {
+    const double sp = sin(x[2]), cp = cos(x[2]), st = sin(x[3]), ct = cos(x[3]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      lca[i] += rb[i];
+      uab[i] += x[0] * rb[i];
+      vab[i] += x[1] * rb[i];
+    }
+    lx[0] = rb[0] * pa.u(0) + rb[1] * pa.u(1) + rb[2] * pa.u(2);
+    lx[1] = rb[0] * pa.v(0) + rb[1] * pa.v(1) + rb[2] * pa.v(2);
+    // dT/dphi = (-sp st, cp st, 0), dT/dtheta = (cp ct, sp ct, -st);
+    // gT[:,0] = dT/dphi, gT[:,1] = dT/dtheta
+    lx[2] = Tb[0] * (-sp * st) + Tb[1] * (cp * st) + gTb[0][0] * (-cp * st) + gTb[1][0] * (-sp * st) +
+            gTb[0][1] * (-sp * ct) + gTb[1][1] * (cp * ct);
+    lx[3] = Tb[0] * (cp * ct) + Tb[1] * (sp * ct) - Tb[2] * st + gTb[0][0] * (-sp * ct) + gTb[1][0] * (cp * ct) +
+            gTb[0][1] * (-cp * st) + gTb[1][1] * (-sp * st) + gTb[2][1] * (-ct);
+    lx[4] = lamb;
+    lx[5] = tb;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    lRa[3 * i + 0] += uab[i];
+    lRa[3 * i + 1] += vab[i];
+    lRb[3 * i + 0] += ubb[i];
+    lRb[3 * i + 1] += vbb[i];
+    lRb[3 * i + 2] += nbb[i];
+  }
+}
+
+// Reverse of aligned_plane: adjoints of the plane's centre lc and rotation lR
+// (row-major) -> adjoints of its 6 alignment parameters (accumulated in ga).
+//   c' = c + R (du, dv, dn):        d(du, dv, dn) = R^T lc
+//   R' = R M, M = Ru(al) Rv(be) Rn(ga):  lM = R^T lR, d(angle) = <lM, dM/d(angle)>
+__device__ __forceinline__ void aligned_plane_rev(const Surf& s, const double a[6], const double lc[3],
+                                                  const double lR[9], double ga[6]) {
+#pragma unroll
+  for (int e = 0; e < 3; ++e) ga[e] += s.R(0, e) * lc[0] + s.R(1, e) * lc[1] + s.R(2, e) * lc[2];
+  double lM[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) lM[i][j] = s.R(0, i) * lR[0 * 3 + j] + s.R(1, i) * lR[1 * 3 + j] + s.R(2, i) * lR[2 * 3 + j];
+  const double ca = cos(a[3]), sa = sin(a[3]), cb = cos(a[4]), sb = sin(a[4]), cg = cos(a[5]), sg = sin(a[5]);
+  const double Ru[3][3] = {{1, 0, 0}, {0, ca, -sa}, {0, sa, ca}};
+  const double Rv[3][3] = {{cb, 0, sb}, {0, 1, 0}, {-sb, 0, cb}};
+  const double Rn[3][3] = {{cg, -sg, 0}, {sg, cg, 0}, {0, 0, 1}};
+  const double dRu[3][3] = {{0, 0, 0}, {0, -sa, -ca}, {0, ca, -sa}};
+  const double dRv[3][3] = {{-sb, 0, cb}, {0, 0, 0}, {-cb, 0, -sb}};
+  const double dRn[3][3] = {{-sg, -cg, 0}, {cg, -sg, 0}, {0, 0, 0}};
+  auto mul3 = [](const double X[3][3], const double Y[3][3], double Z[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Z[i][j] = X[i][0] * Y[0][j] + X[i][1] * Y[1][j] + X[i][2] * Y[2][j];
+  };
+  double VN[3][3], dVN[3][3], VdN[3][3], D[3][3];
+  mul3(Rv, Rn, VN);
+  mul3(dRv, Rn, dVN);
+  mul3(Rv, dRn, VdN);
+  double acc[3] = {0.0, 0.0, 0.0};
+  mul3(dRu, VN, D);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[0] += lM[i][j] * D[i][j];
+  mul3(Ru, dVN, D);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[1] += lM[i][j] * D[i][j];
+  mul3(Ru, VdN, D);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[2] += lM[i][j] * D[i][j];
+  ga[3] += acc[0];
+  ga[4] += acc[1];
+  ga[5] += acc[2];
+}
+
 struct GradParams {
   FitParams f;          // geometry, inputs, options (outputs unused)
   const double* align;  // [6][S] or null (zero alignment)
@@ -698,10 +1203,20 @@ __global__ void __launch_bounds__(128) kf_grad_kernel(const GradParams g) {
 #pragma unroll
       for (int e = 0; e < 21; ++e) Cprev[e] = act ? bC[i][e] : 0.0;
       double F[6][6];
+      // the transport k-1 -> k with its tape (values as in the forward pass)
+      double aa[6], ab[6];
+      load_align(g, sa, aa);
+      load_align(g, sbi, ab);
+      const Plane<double> pa = aligned_plane<double>(Surf{s_surf + sa * kSurfStride}, aa);
+      const Plane<double> pb = aligned_plane<double>(Surf{s_surf + sbi * kSurfStride}, ab);
+      const double B[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
+      const double xxb = Surf{s_surf + sbi * kSurfStride}.xx0();
+      Tape tp;
+      PropS<double> s_end;
       if (act) {
         double xp[6], Cp[21], qp, qt;
         JacS<double> J;
-        transport_values(g, s_surf, sa, sbi, xprev, xp, J, qp, qt);
+        transport_tape(pa, pb, xprev, B, p.mass, p.h_max, p.n_iter, xxb, xp, J, qp, qt, tp, s_end);
         dense_F(J, F);
         cov_transport(F, Cprev, qp, qt, Cp);
         if (!p.is_hole[o0 + k]) {
@@ -710,96 +1225,67 @@ __global__ void __launch_bounds__(128) kf_grad_kernel(const GradParams g) {
           update_adj(xp, Cp, m, V, w, lf, Lf, lp, Lp);
         } else {
 #pragma unroll
-          for (int a = 0; a < 6; ++a) {
-            lp[a] = lf[a];
+          for (int a2 = 0; a2 < 6; ++a2) {
+            lp[a2] = lf[a2];
 #pragma unroll
-            for (int b = 0; b < 6; ++b) Lp[a][b] = Lf[a][b];
+            for (int b2 = 0; b2 < 6; ++b2) Lp[a2][b2] = Lf[a2][b2];
           }
         }
       } else {
 #pragma unroll
-        for (int a = 0; a < 6; ++a) {
-          lp[a] = 0.0;
+        for (int a2 = 0; a2 < 6; ++a2) {
+          lp[a2] = 0.0;
 #pragma unroll
-          for (int b = 0; b < 6; ++b) {
-            Lp[a][b] = 0.0;
-            F[a][b] = (a == b) ? 1.0 : 0.0;
+          for (int b2 = 0; b2 < 6; ++b2) {
+            Lp[a2][b2] = 0.0;
+            F[a2][b2] = (a2 == b2) ? 1.0 : 0.0;
           }
         }
       }
       // lambda_F = 2 Lp F Cf (only rows 0-3, 5 and columns 0-4 of F vary)
       double lF[6][6];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
+      for (int a2 = 0; a2 < 6; ++a2) {
         double LF[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
           double v = 0.0;
 #pragma unroll
-          for (int q = 0; q < 6; ++q) v += Lp[a][q] * F[q][c];
+          for (int q = 0; q < 6; ++q) v += Lp[a2][q] * F[q][c];
           LF[c] = v;
         }
 #pragma unroll
-        for (int b = 0; b < 6; ++b) {
+        for (int b2 = 0; b2 < 6; ++b2) {
           double v = 0.0;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) v += LF[c] * Cprev[sym(c, b)];
-          lF[a][b] = 2.0 * v;
+          for (int c = 0; c < 6; ++c) v += LF[c] * Cprev[sym(c, b2)];
+          lF[a2][b2] = 2.0 * v;
         }
       }
-      // sensitivities of the transport to its 18 inputs, two per pass
-      double lx[6];
+      // reverse sweep through the transport: adjoints of x_f,k-1 and of
+      // both planes' alignment, contracted with (lambda_xp, lambda_F, Lambda_Q)
+      double lx[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      double galign[12];
+#pragma unroll
+      for (int e = 0; e < 12; ++e) galign[e] = 0.0;
+      if (act) {
+        double lJ[4][5], lJt[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) lJ[r][c] = lF[r][c];
+          lJt[c] = lF[5][c];
+        }
+        double lca[3], lRa[9], lcb[3], lRb[9];
+        transport_rev(pa, pb, xprev, B, p.mass, xxb, tp, s_end, lp, lJ, lJt, Lp[2][2], Lp[3][3], lx, lca, lRa,
+                      lcb, lRb);
+        aligned_plane_rev(Surf{s_surf + sa * kSurfStride}, aa, lca, lRa, galign);
+        aligned_plane_rev(Surf{s_surf + sbi * kSurfStride}, ab, lcb, lRb, galign + 6);
+      }
+      if (g.grad_align) {
 #pragma unroll 1
-      for (int pass = 0; pass < 9; ++pass) {
-        double gdir[2] = {0.0, 0.0};
-        if (act) {
-          Dual<2> xd[6], aa[6], ab[6];
-#pragma unroll
-          for (int e = 0; e < 6; ++e) {
-            xd[e] = Dual<2>(xprev[e]);
-            const double va = g.align ? g.align[(size_t)e * p.n_surfaces + sa] : 0.0;
-            const double vb = g.align ? g.align[(size_t)e * p.n_surfaces + sbi] : 0.0;
-            aa[e] = Dual<2>(va);
-            ab[e] = Dual<2>(vb);
-          }
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            const int dir = 2 * pass + q;
-            if (dir < 6) xd[dir].d[q] = 1.0;
-            else if (dir < 12) aa[dir - 6].d[q] = 1.0;
-            else ab[dir - 12].d[q] = 1.0;
-          }
-          const Plane<Dual<2>> pa = aligned_plane<Dual<2>>(Surf{s_surf + sa * kSurfStride}, aa);
-          const Plane<Dual<2>> pb = aligned_plane<Dual<2>>(Surf{s_surf + sbi * kSurfStride}, ab);
-          const double B[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
-          Dual<2> xpd[6], qpd, qtd;
-          JacS<Dual<2>> Jd;
-          transport_s<Dual<2>>(pa, pb, xd, B, p.mass, p.h_max, p.n_iter, Surf{s_surf + sbi * kSurfStride}.xx0(),
-                               xpd, Jd, qpd, qtd);
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            double v = Lp[2][2] * qpd.d[q] + Lp[3][3] * qtd.d[q];
-#pragma unroll
-            for (int e = 0; e < 6; ++e) v += lp[e] * xpd[e].d[q];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-              for (int c = 0; c < 5; ++c) v += lF[r][c] * Jd.f[r][c].d[q];
-#pragma unroll
-            for (int c = 0; c < 5; ++c) v += lF[5][c] * Jd.ft[c].d[q];
-            gdir[q] = v;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int dir = 2 * pass + q;
-          if (dir < 6) {
-            lx[dir] = gdir[q];
-          } else if (g.grad_align) {
-            const int sid = dir < 12 ? sa : sbi;
-            add_align_grad(g.grad_align, p.n_surfaces, sid, (dir - 6) % 6, gdir[q], act);
-          }
-        }
+        for (int e = 0; e < 12; ++e)
+          add_align_grad(g.grad_align, p.n_surfaces, e < 6 ? sa : sbi, e % 6, galign[e], act);
       }
       if (act) {
         // Lambda_Cf = F^T Lp F

@@ -148,10 +148,12 @@ def oracle_tracks_per_s(ev, n_sample, cores, method=None):
 ADJOINT_WORKLOAD = "align20_100k"
 
 
-def time_adjoint(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks):
+def time_adjoint(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks, reduce=None):
     """The adjoint kernel: chi2 per track and its gradient with respect to
     the seeds and the 6 x 21 alignment parameters (at zero alignment) on the
-    misaligned 20-plane telescope."""
+    misaligned 20-plane telescope.  With several ranks, each fits its own
+    batch and the alignment gradient is summed over ranks (one all-reduce of
+    126 doubles) inside the timed region."""
     ev = synth.make_event(synth.scaled(synth.WORKLOADS[ADJOINT_WORKLOAD], n_tracks))
     dev = kf.event_to_device(ev)
     T, S = int(ev["n_tracks"]), int(ev["center"].shape[1])
@@ -169,6 +171,8 @@ def time_adjoint(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         kf.kf_chi2_grad(h, dev, out_chi2=chi2, grad_seed=gs, grad_align=ga, stream=stream)
+        if reduce is not None:
+            reduce(ga)
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
@@ -347,7 +351,8 @@ def run_ours(args, rank, world, local):
     adjoint_event = None
     if not args.no_adjoint:
         adjoint_event, adjoint = time_adjoint(h, kf, synth, torch, stream, l2_flush,
-                                              max(3, args.steps // 2), args.warmup, T)
+                                              max(3, args.steps // 2), args.warmup, T,
+                                              reduce=kdist.sum_over_ranks if world > 1 else None)
     variants = None
     variant_event = None
     if not args.no_variants:

@@ -68,3 +68,46 @@ def test_two_rank_gloo_collectives():
     assert b0 == 0 and e0 == b1 and e1 == 1000
     assert t0 == t1 == 11.0                     # max over ranks
     assert g0 == g1 == h0 == h1 == 1000.0       # sum of the shards' track counts
+
+
+def _grad_worker(rank, world, port, results):
+    import torch
+    import torch.distributed as dist
+    import oracle
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ev = synth.make_event(synth.scaled(synth.WORKLOADS["align20_100k"], 60))
+        b, e = kdist.shard_range(60, rank, world, ev["offsets"])
+        shard = synth.subset(ev, np.arange(b, e))
+        _, ga = oracle.chi2_gradient_fd(shard, n_threads=1)
+        g = torch.from_numpy(np.ascontiguousarray(ga.ravel()))
+        kdist.sum_over_ranks(g)
+        results[rank] = g.numpy().copy()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_alignment_gradient_sums_to_the_full_gradient():
+    """The alignment gradient of the summed chi2 over a batch equals the sum of
+    the shards' gradients: each rank takes the oracle's gradient of its track
+    range and one all-reduce (120 + 6 values here) adds them."""
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    import oracle
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    results = mgr.dict()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, 2, port, results)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["align20_100k"], 60))
+    _, full = oracle.chi2_gradient_fd(ev, n_threads=1)
+    for r in range(2):
+        got = results[r].reshape(full.shape)
+        assert np.max(np.abs(got - full)) <= 1e-6 * np.max(np.abs(full))

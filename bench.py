@@ -353,6 +353,8 @@ def run_ours(args, rank, world, local):
         adjoint_event, adjoint = time_adjoint(h, kf, synth, torch, stream, l2_flush,
                                               max(3, args.steps // 2), args.warmup, T,
                                               reduce=kdist.sum_over_ranks if world > 1 else None)
+        a_ms = kdist.max_over_ranks(adjoint["ms_per_step"], device="cuda")
+        adjoint.update(ms_per_step=a_ms, value=world * adjoint["tracks"] / (a_ms / 1e3))
     variants = None
     variant_event = None
     if not args.no_variants:

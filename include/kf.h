@@ -328,10 +328,11 @@ const char* kf_last_cuda_error(void);
 /* Diagnostic: run the device self-check of the library's numeric helpers
  * (float<->double conversions on the integer pipe, and the Newton-refined
  * double 1/sqrt and 1/x) over n_patterns inputs on the current device.
- * counts[5] (host memory) receives the mismatch counts: [0] float->double,
+ * counts[6] (host memory) receives the mismatch counts: [0] float->double,
  * [1] double->float (round to nearest even), [2] 1/sqrt one step beyond 1e-13
- * relative, [3] 1/x one step beyond 1e-13, [4] two-step forms beyond 4 ulp.
- * All zero means the helpers behave as documented.  Synchronous. */
+ * relative, [3] 1/x one step beyond 1e-13, [4] two-step forms beyond 4 ulp,
+ * [5] the full-range forms of the FP64 path (any normal double) beyond
+ * 4 ulp.  All zero means the helpers behave as documented.  Synchronous. */
 int kf_selftest(int64_t n_patterns, uint64_t* counts);
 
 /* ABI version of the loaded library (KF_ABI_VERSION). */

@@ -287,8 +287,8 @@ def kf_fit_ex(handle: Handle, dev_ev, out, opt: KfOptions | None = None, stream=
 
 
 def kf_selftest(n_patterns=1 << 22):
-    """Device self-check of the numeric helpers; returns the 5 mismatch counts."""
-    counts = np.zeros(5, dtype=np.uint64)
+    """Device self-check of the numeric helpers; returns the 6 mismatch counts."""
+    counts = np.zeros(6, dtype=np.uint64)
     _check(load().kf_selftest(int(n_patterns), counts.ctypes.data_as(ctypes.c_void_p)))
     return [int(c) for c in counts]
 

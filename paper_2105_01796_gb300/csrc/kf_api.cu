@@ -179,11 +179,12 @@ int kf_abi_version(void) { return KF_ABI_VERSION; }
 int kf_selftest(int64_t n_patterns, uint64_t* counts) {
   if (!counts || n_patterns < 0) return KF_EINVAL;
   unsigned long long* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, 5 * sizeof(unsigned long long));
+  cudaError_t e = cudaMalloc(&d, 6 * sizeof(unsigned long long));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(selftest)");
-  e = cudaMemset(d, 0, 5 * sizeof(unsigned long long));
+  e = cudaMemset(d, 0, 6 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = launch_selftest(n_patterns, d, nullptr);
-  if (e == cudaSuccess) e = cudaMemcpy(counts, d, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = launch_selftest_any(n_patterns, d + 5, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(counts, d, 6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(e, "selftest");
   return KF_SUCCESS;

@@ -13,6 +13,28 @@
 namespace kfgb {
 namespace dev {
 
+// 1/sqrt(x) (x > 0) and 1/x (x != 0) for the whole double range: the
+// argument is scaled by a power of two into [1, 4) (resp. [1, 2)) on the
+// integer pipe, the two-step Newton form runs there, and the result is
+// scaled back.  Arguments with extreme exponents (zero, subnormal, Inf, NaN)
+// take CUDA's double operations, so NaN and Inf propagate as usual.
+__device__ __forceinline__ double rsqrt_any(double x) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023;
+  if (e < -1000 || e > 1000) return 1.0 / sqrt(x);
+  const int k = e >> 1;
+  const double r = rsqrt_nr<2>(__hiloint2double(hi - (k << 21), __double2loint(x)));
+  return __hiloint2double(__double2hiint(r) - (k << 20), __double2loint(r));
+}
+
+__device__ __forceinline__ double rcp_any(double x) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - 1023;
+  if (e < -1000 || e > 1000) return 1.0 / x;
+  const double r = rcp_nr<2>(__hiloint2double(hi - (e << 20), __double2loint(x)));
+  return __hiloint2double(__double2hiint(r) - (e << 20), __double2loint(r));
+}
+
 // ---------------------------------------------------------------------------
 // transport Jacobian F of one transition: rows 0..3 and 5 over columns 0..4
 // are stored; row 4 (q/p) is e4 times the energy-loss factor, column 5 is e5.
@@ -65,7 +87,7 @@ __device__ __forceinline__ int kalman_update(const double xp[6], const double Cp
   const double S00 = V[0] + Cp[sy(0, 0)], S01 = V[1] + Cp[sy(1, 0)], S11 = V[2] + Cp[sy(1, 1)];
   const double det = S00 * S11 - S01 * S01;
   if (!(det > 0.0) || !(S00 > 0.0)) return ST_NON_SPD;
-  const double idet = 1.0 / det;
+  const double idet = rcp_any(det);
   const double r0 = m[0] - xp[0], r1 = m[1] - xp[1];
   chi2 = (S11 * r0 * r0 - 2.0 * S01 * r0 * r1 + S00 * r1 * r1) * idet;
   // gain in R
@@ -131,8 +153,8 @@ __device__ __forceinline__ int rts_smooth_fp64(const WS& ws, int n, double xs[6]
 #pragma unroll
       for (int q = 0; q < 6; ++q) if (q < j) dj -= L[sy(j, q)] * L[sy(j, q)];
       if (!(dj > 0.0)) status = ST_NON_SPD;
-      const double ljj = sqrt(dj);
-      idg[j] = 1.0 / ljj;
+      idg[j] = rsqrt_any(dj);  // Newton-refined, double rounding level
+      const double ljj = dj * idg[j];
       L[sy(j, j)] = ljj;
 #pragma unroll
       for (int r = 0; r < 6; ++r) if (r > j) {

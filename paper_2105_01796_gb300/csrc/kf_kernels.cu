@@ -96,9 +96,11 @@ __device__ __forceinline__ void rkn_step(Prop<R>& s, double h, const double B[3]
       s.gT[i][c] = nt;
     }
   }
+  // sqrt(1 + m^2 lam^2) and its reciprocal from one Newton-refined 1/sqrt
   const double g2 = 1.0 + mass * mass * s.lam * s.lam;
-  const R gam = (R)sqrt(g2);
-  s.gtl += hr * (R)(mass * mass * s.lam * kInvC) / gam;
+  const double igam = rsqrt_any(g2);
+  const R gam = (R)(g2 * igam);
+  s.gtl += hr * (R)(mass * mass * s.lam * kInvC * igam);
   // advance the double accumulators with float (mixed) increments
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -116,7 +118,7 @@ __device__ __forceinline__ bool plane_step(const Prop<R>& s, const Surf& sb, dou
   const double d = sb.n(0) * (sb.c(0) - s.r[0]) + sb.n(1) * (sb.c(1) - s.r[1]) + sb.n(2) * (sb.c(2) - s.r[2]);
   const double nT = sb.n(0) * s.T[0] + sb.n(1) * s.T[1] + sb.n(2) * s.T[2];
   if (!(fabs(nT) > 1e-9)) return false;
-  out = d / nT;
+  out = d * rcp_any(nT);
   return true;
 }
 
@@ -164,14 +166,19 @@ __device__ __forceinline__ int transport(const Surf& sa, const Surf& sb, const d
   }
 
   // end point: unit direction and bound angles
+  // square roots and quotients of the end frame from Newton-refined
+  // reciprocal square roots (two steps: double rounding level)
   const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
+  const double irho_d = rsqrt_any(rho2);
+  const double rho_d = rho2 * irho_d;
   const double phi = atan2(s.T[1], s.T[0]);
-  const double theta = atan2(sqrt(rho2), s.T[2]);
+  const double theta = atan2(rho_d, s.T[2]);
   const R Tr[3] = {(R)s.T[0], (R)s.T[1], (R)s.T[2]};
-  const R rho = (R)sqrt(rho2);
-  const R tn = (R)sqrt(rho2 + s.T[2] * s.T[2]);
-  const R cph = Tr[0] / rho, sph = Tr[1] / rho;
-  const R sth = rho / tn, cth = Tr[2] / tn;
+  const double itn_d = rsqrt_any(rho2 + s.T[2] * s.T[2]);
+  const R rho = (R)rho_d;
+  const R tn = (R)((rho2 + s.T[2] * s.T[2]) * itn_d);
+  const R cph = Tr[0] * (R)irho_d, sph = Tr[1] * (R)irho_d;
+  const R sth = rho * (R)itn_d, cth = Tr[2] * (R)itn_d;
   const R nb[3] = {(R)sb.n(0), (R)sb.n(1), (R)sb.n(2)};
   const R nT = nb[0] * Tr[0] + nb[1] * Tr[1] + nb[2] * Tr[2];
 
@@ -182,7 +189,7 @@ __device__ __forceinline__ int transport(const Surf& sa, const Surf& sb, const d
   R AT[3];
   applyA<R, BZ>(bs, Tr, AT);
   const R dtds = (R)(sqrt(1.0 + mass * mass * s.lam * s.lam) * kInvC);
-  const R inv_nT = R(1) / nT;
+  const R inv_nT = (R)rcp_any((double)nT);
   // columns 0..4: loc0, loc1, phi, theta, q/p; full G columns after correction
   R Gr[3][5], GT[3][5], Gt[5];
 #pragma unroll
@@ -213,7 +220,7 @@ __device__ __forceinline__ int transport(const Surf& sa, const Surf& sb, const d
   // free -> bound at b
   const R ub[3] = {(R)sb.u(0), (R)sb.u(1), (R)sb.u(2)};
   const R vb[3] = {(R)sb.v(0), (R)sb.v(1), (R)sb.v(2)};
-  const R inv_sth = R(1) / sth;
+  const R inv_sth = (R)rcp_any((double)sth);
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     J.f[0][c] = ub[0] * Gr[0][c] + ub[1] * Gr[1][c] + ub[2] * Gr[2][c];
@@ -396,6 +403,26 @@ __device__ __forceinline__ void fit_one_fp64(const FitParams& p, const double* s
   if (p.out_status) p.out_status[t] = (uint8_t)status;
 }
 
+// self-check of the full-range Newton helpers against CUDA's double 1/sqrt
+// and 1/x over positive and negative values across 1e-300 .. 1e300;
+// counter: cases beyond 4 ulp
+__global__ void selftest_any_kernel(long long n, unsigned long long* counter) {
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long c = 0;
+  for (long long i = i0; i < n; i += stride) {
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 31)) * 0xBF58476D1CE4E5B9ULL;
+    z ^= z >> 29;
+    const double y = exp2((double)((int)(z % 1990) - 995)) * (1.0 + (double)((z >> 20) & 0xfffff) / 1048576.0);
+    const double rs_ref = 1.0 / sqrt(y), rc_ref = 1.0 / y;
+    if (fabs(rsqrt_any(y) - rs_ref) > 8.9e-16 * rs_ref) ++c;
+    if (fabs(rcp_any(y) - rc_ref) > 8.9e-16 * rc_ref) ++c;
+    if (fabs(rcp_any(-y) + rc_ref) > 8.9e-16 * rc_ref) ++c;
+  }
+  if (c) atomicAdd(counter, c);
+}
+
 __global__ void pack_surfaces_kernel(int n, const double* __restrict__ center, const double* __restrict__ rot,
                                      const double* __restrict__ xx0, double* __restrict__ out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -462,6 +489,11 @@ __global__ void length_scatter_kernel(int n, int max_states, const int32_t* __re
 }
 
 }  // namespace
+
+cudaError_t launch_selftest_any(long long n, unsigned long long* counter, cudaStream_t stream) {
+  selftest_any_kernel<<<152 * 4, 256, 0, stream>>>(n, counter);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pack_surfaces(int n_surfaces, const double* center, const double* rot,
                                  const double* x_over_x0, double* packed, cudaStream_t stream) {

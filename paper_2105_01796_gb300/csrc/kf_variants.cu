@@ -143,8 +143,10 @@ __device__ __forceinline__ void rkn_step_field(const FitParams& p, GProp& s, dou
       s.gT[i][c] = g[i] + h / 6.0 * (d1[i] + 2.0 * d2[i] + 2.0 * d3[i] + d4[i]);
     }
   }
-  const double gam = sqrt(1.0 + mass * mass * s.lam * s.lam);
-  s.gtl += h * mass * mass * s.lam * kInvC / gam;
+  const double g2 = 1.0 + mass * mass * s.lam * s.lam;
+  const double igam = rsqrt_any(g2);
+  const double gam = g2 * igam;
+  s.gtl += h * mass * mass * s.lam * kInvC * igam;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     s.r[i] += h * s.T[i] + h * h / 6.0 * lk * (TB1[i] + TB2[i] + TB3[i]);
@@ -157,7 +159,7 @@ __device__ __forceinline__ bool plane_distance(const GProp& s, const Surf& sb, d
   const double d = sb.n(0) * (sb.c(0) - s.r[0]) + sb.n(1) * (sb.c(1) - s.r[1]) + sb.n(2) * (sb.c(2) - s.r[2]);
   const double nT = sb.n(0) * s.T[0] + sb.n(1) * s.T[1] + sb.n(2) * s.T[2];
   if (!(fabs(nT) > 1e-9)) return false;
-  out = d / nT;
+  out = d * rcp_any(nT);
   return true;
 }
 
@@ -201,12 +203,15 @@ __device__ __forceinline__ int transport_field(const FitParams& p, const Surf& s
   }
   // end point: bound angles and the unit direction
   const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
+  const double irho = rsqrt_any(rho2);
+  const double rho = rho2 * irho;
   const double phi = atan2(s.T[1], s.T[0]);
-  const double theta = atan2(sqrt(rho2), s.T[2]);
-  const double rho = sqrt(rho2);
-  const double tn = sqrt(rho2 + s.T[2] * s.T[2]);
-  const double cph = s.T[0] / rho, sph = s.T[1] / rho;
-  const double sth = rho / tn, cth = s.T[2] / tn;
+  const double theta = atan2(rho, s.T[2]);
+  const double tn2 = rho2 + s.T[2] * s.T[2];
+  const double itn = rsqrt_any(tn2);
+  const double tn = tn2 * itn;
+  const double cph = s.T[0] * irho, sph = s.T[1] * irho;
+  const double sth = rho * itn, cth = s.T[2] * itn;
   const double nT = sb.n(0) * s.T[0] + sb.n(1) * s.T[1] + sb.n(2) * s.T[2];
   // path correction with F' = (T, dt/ds, (q/p) kappa T x B(end), 0)
   double Be[3], TB[3];
@@ -214,7 +219,7 @@ __device__ __forceinline__ int transport_field(const FitParams& p, const Surf& s
   cross3(s.T, Be, TB);
   const double lk = s.lam * kKappa;
   const double dtds = sqrt(1.0 + mass * mass * s.lam * s.lam) * kInvC;
-  const double inv_nT = 1.0 / nT;
+  const double inv_nT = rcp_any(nT);
   double Gr[3][5], GT[3][5], Gt[5];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -241,7 +246,7 @@ __device__ __forceinline__ int transport_field(const FitParams& p, const Surf& s
     }
     Gt[c] += dtds * w;
   }
-  const double inv_sth = 1.0 / sth;
+  const double inv_sth = rcp_any(sth);
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     J.f[0][c] = sb.u(0) * Gr[0][c] + sb.u(1) * Gr[1][c] + sb.u(2) * Gr[2][c];
@@ -372,17 +377,18 @@ __device__ __forceinline__ void add_scattering(const FitParams& p, double la, do
 // X = S^-1 B for SPD S (packed) and a symmetric right-hand side B (packed),
 // through the Cholesky factor of the Jacobi-scaled D^-1/2 S D^-1/2; K = X^T.
 __device__ __forceinline__ int spd_solve_sym(const double S[21], const double B[21], double X[6][6]) {
-  double d[6], L[21];
+  double L[21];
+  double id[6];  // 1 / sqrt(S_ii), the Jacobi scaling
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     if (!(S[sy(i, i)] > 0.0)) return ST_NON_SPD;
-    d[i] = sqrt(S[sy(i, i)]);
+    id[i] = rsqrt_any(S[sy(i, i)]);
   }
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < 6; ++j)
-      if (j <= i) L[sy(i, j)] = S[sy(i, j)] / (d[i] * d[j]);
+      if (j <= i) L[sy(i, j)] = S[sy(i, j)] * (id[i] * id[j]);
   double idg[6];
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -391,9 +397,8 @@ __device__ __forceinline__ int spd_solve_sym(const double S[21], const double B[
     for (int q = 0; q < 6; ++q)
       if (q < j) dj -= L[sy(j, q)] * L[sy(j, q)];
     if (!(dj > 0.0)) return ST_NON_SPD;
-    const double ljj = sqrt(dj);
-    idg[j] = 1.0 / ljj;
-    L[sy(j, j)] = ljj;
+    idg[j] = rsqrt_any(dj);
+    L[sy(j, j)] = dj * idg[j];
 #pragma unroll
     for (int r = 0; r < 6; ++r)
       if (r > j) {
@@ -409,7 +414,7 @@ __device__ __forceinline__ int spd_solve_sym(const double S[21], const double B[
     double y[6];
 #pragma unroll
     for (int r = 0; r < 6; ++r) {
-      double v = B[sym(r, c)] / d[r];
+      double v = B[sym(r, c)] * id[r];
 #pragma unroll
       for (int q = 0; q < 6; ++q)
         if (q < r) v -= L[sy(r, q)] * y[q];
@@ -425,7 +430,7 @@ __device__ __forceinline__ int spd_solve_sym(const double S[21], const double B[
       z[r] = v * idg[r];
     }
 #pragma unroll
-    for (int r = 0; r < 6; ++r) X[r][c] = z[r] / d[r];
+    for (int r = 0; r < 6; ++r) X[r][c] = z[r] * id[r];
   }
   return ST_OK;
 }

@@ -216,7 +216,7 @@ def test_full_size_tel30_100k_sampled(handle, prec):
 def test_numeric_helpers_selftest(handle):
     """Integer-pipe float<->double conversions match the hardware ones bit for
     bit; the Newton-refined 1/sqrt and 1/x meet their stated error bounds."""
-    assert kf.kf_selftest(1 << 22) == [0, 0, 0, 0, 0]
+    assert kf.kf_selftest(1 << 22) == [0, 0, 0, 0, 0, 0]
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
@@ -307,3 +307,31 @@ def test_full_size_uneven_1m_sampled(handle):
     r = oracle.fit_batch(synth.subset(ev, sample))
     compare({k: (v[..., sample] if v is not None else None) for k, v in g.items()}, r, MIXED)
     assert np.all(g["status"] == 0)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_fault_inputs_and_extreme_tracks(handle, prec):
+    """Host-made faults give a per-track status and NaN outputs for that
+    track only, never a trap: NaN and Inf inputs, a non-SPD seed covariance,
+    a track nearly parallel to the planes; and a straight track (q/p ~ 0)
+    fits normally.  Statuses and the other tracks agree with the oracle."""
+    ev = dict(synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 16)))
+    sp = ev["seed_params"].copy()
+    sc = ev["seed_cov"].copy()
+    loc = ev["loc"].copy()
+    o = ev["offsets"]
+    sp[2, 1] = np.nan                        # NaN seed angle
+    loc[0, o[2] + 3] = np.inf                # Inf measurement
+    sc[0, 3] = -sc[0, 3]                     # negative seed variance of loc0
+    sp[2, 4] = 0.5 * np.pi - 1e-12           # direction parallel to the planes
+    sp[4, 5] = 1e-9                          # (nearly) infinite momentum
+    ev["seed_params"], ev["seed_cov"], ev["loc"] = sp, sc, loc
+    g = gpu_fit(handle, ev, prec)
+    r = oracle.fit_batch(ev)
+    bad = [1, 2, 3, 4]
+    for t in bad:
+        assert g["status"][t] != 0 and r["status"][t] != 0, (t, g["status"][t], r["status"][t])
+        assert np.all(np.isnan(g["params"][:, t])) and np.isnan(g["chi2"][t])
+    assert g["status"][5] == 0 and r["status"][5] == 0
+    good = np.setdiff1d(np.arange(16), bad)
+    compare(g, r, prec, tracks=good)

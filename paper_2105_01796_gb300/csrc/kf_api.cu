@@ -42,9 +42,13 @@ struct kf_handle {
   cudaGraphExec_t graph_exec = nullptr;
   alignas(8) unsigned char graph_key[1024];
   int32_t graph_launches = 0;
-  // device copies for kf_fit_host
+  // device copies for kf_fit_host, and its copy streams and events (the
+  // pipelined host path overlaps the copies of one chunk of tracks with the
+  // fit of another)
   void* dev_io = nullptr;
   size_t dev_io_bytes = 0;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_fit[2] = {nullptr, nullptr};
   int32_t last_launches = 0;
 };
 
@@ -241,6 +245,12 @@ void kf_destroy(kf_handle* h) {
   if (h->hist) cudaFree(h->hist);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->ckpt) cudaFree(h->ckpt);
+  if (h->s_in) cudaStreamDestroy(h->s_in);
+  if (h->s_out) cudaStreamDestroy(h->s_out);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
+    if (h->ev_fit[i]) cudaEventDestroy(h->ev_fit[i]);
+  }
   delete h;
 }
 
@@ -329,14 +339,26 @@ void fill_variants(FitParams* p, const kf_field* fi, const kf_options& opt) {
   }
 }
 
-// Queue the fit on `stream` (no allocation, no synchronisation).
+// Queue the fit of tracks [t_begin, t_end) on `stream` (no allocation, no
+// synchronisation).  pack: also pack the surface table first.  A partial
+// range (the host entry's pipelined chunks) cannot use the length-sorted
+// order, which spans the whole batch: it runs the persistent schedule.
 int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
-                const kf_field* fi, const kf_options& opt, const kf_outputs* out, cudaStream_t stream,
-                const FitPlan& plan, int* launches_out) {
+                const kf_field* fi, const kf_options& opt_in, const kf_outputs* out, cudaStream_t stream,
+                const FitPlan& plan, int* launches_out, int64_t t_begin = 0, int64_t t_end = -1,
+                bool pack = true) {
+  if (t_end < 0) t_end = tr->n_tracks;
+  kf_options opt = opt_in;
+  const bool whole = t_begin == 0 && t_end == tr->n_tracks;
+  if (!whole && opt.schedule == KF_SCHEDULE_SORTED) opt.schedule = KF_SCHEDULE_PERSISTENT;
   const int64_t chunk = plan.chunk;
-  cudaError_t e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
-  int launches = 1;
+  cudaError_t e = cudaSuccess;
+  int launches = 0;
+  if (pack) {
+    e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
+    launches = 1;
+  }
   if (opt.schedule != KF_SCHEDULE_GRID) {
     e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * plan.n_chunks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
@@ -378,9 +400,9 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   const bool variants = wants_variants(opt.smoother, opt.energy_loss, fi->map);
   if (variants) fill_variants(&p, fi, opt);
   int c = 0;
-  for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk, ++c) {
+  for (int64_t t0 = t_begin; t0 < t_end; t0 += chunk, ++c) {
     p.track0 = (int32_t)t0;
-    p.n_tracks = (int32_t)((tr->n_tracks - t0) < chunk ? (tr->n_tracks - t0) : chunk);
+    p.n_tracks = (int32_t)((t_end - t0) < chunk ? (t_end - t0) : chunk);
     p.work_counter = opt.schedule == KF_SCHEDULE_GRID ? nullptr : h->counters + c;
     e = variants ? launch_fit_variants(p, opt.block, stream)
                  : launch_fit(p, opt.precision, opt.block, opt.min_blocks, stream);
@@ -720,6 +742,27 @@ int kf_fit(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me
   return KF_SUCCESS;
 }
 
+// streams and events of the pipelined host path, created on first use
+static int ensure_host_streams(kf_handle* h) {
+  if (h->s_in) return KF_SUCCESS;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fit[i], cudaEventDisableTiming);
+  }
+  return e == cudaSuccess ? KF_SUCCESS : cuda_fail(e, "host-path streams");
+}
+
+// copy columns [c0, c1) of a row-major [rows][ncol] array of `elem`-byte
+// elements between host and device (same layout on both sides)
+static cudaError_t copy_cols(void* dst, const void* src, size_t ncol, size_t elem, size_t rows, size_t c0,
+                             size_t c1, cudaMemcpyKind kind, cudaStream_t s) {
+  if (c1 <= c0 || rows == 0) return cudaSuccess;
+  const size_t pitch = ncol * elem, off = c0 * elem;
+  return cudaMemcpy2DAsync((char*)dst + off, pitch, (const char*)src + off, pitch, (c1 - c0) * elem, rows, kind, s);
+}
+
 int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
                 const kf_field* fi, const kf_options* opt, const kf_outputs* out, void* stream_v) {
   if (!h || !tr || !su || !me || !fi || !out) return KF_EINVAL;
@@ -750,19 +793,6 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     h->dev_io_bytes = off;
   }
   char* b = (char*)h->dev_io;
-  struct Cp { size_t o; const void* src; size_t bytes; };
-  const Cp in[] = {{o_off, tr->offsets, (T + 1) * 4}, {o_sp, tr->seed_params, 6 * T * 8},
-                   {o_sc, tr->seed_cov, 21 * T * 8},   {o_c, su->center, 3 * S * 8},
-                   {o_r, su->rot, 9 * S * 8},          {o_x, su->x_over_x0, S * 8},
-                   {o_sid, me->surface_id, M * 4},     {o_loc, me->loc, 2 * M * 8},
-                   {o_cov, me->cov, 3 * M * 8},        {o_h, me->is_hole, M},
-                   {o_map, fi->map ? fi->map->b : nullptr, map_bytes}};
-  for (const Cp& c : in) {
-    if (c.bytes == 0) continue;
-    if (!c.src) return KF_EINVAL;
-    cudaError_t e = cudaMemcpyAsync(b + c.o, c.src, c.bytes, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
-  }
   kf_tracks dtr = *tr;
   dtr.offsets = (const int32_t*)(b + o_off);
   dtr.seed_params = (const double*)(b + o_sp);
@@ -790,19 +820,108 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     dmap.b = (const double*)(b + o_map);
     dfi.map = &dmap;
   }
-  int rc = kf_fit_ex(h, &dtr, &dsu, &dme, &dfi, opt, &dout, stream_v);
-  if (rc) return rc;
-  const Cp outs[] = {{o_p, out->params, 6 * T * 8}, {o_pc, out->cov, 21 * T * 8}, {o_chi, out->chi2, T * 8},
-                     {o_ndf, out->ndf, T * 4},      {o_st, out->status, T},     {o_states, out->states, 6 * M * 8}};
-  for (const Cp& c : outs) {
-    if (!c.src || c.bytes == 0) continue;
-    cudaError_t e = cudaMemcpyAsync((void*)c.src, b + c.o, c.bytes, cudaMemcpyDeviceToHost, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+  kf_options o;
+  if (opt) o = *opt; else kf_default_options(&o);
+  struct Cp { size_t o; const void* src; size_t bytes; };
+  // Two chunks of tracks when the batch is large: the inputs of chunk 1
+  // travel while chunk 0 is fitted, the outputs of chunk 0 while chunk 1 is.
+  // (Not for a schedule still to be tuned, a graph, or a small batch.)
+  const bool pipelined = T >= 20000 && o.schedule != KF_SCHEDULE_AUTO && !o.use_graph && tr->offsets && out->params;
+  if (!pipelined) {
+    const Cp in[] = {{o_off, tr->offsets, (T + 1) * 4}, {o_sp, tr->seed_params, 6 * T * 8},
+                     {o_sc, tr->seed_cov, 21 * T * 8},   {o_c, su->center, 3 * S * 8},
+                     {o_r, su->rot, 9 * S * 8},          {o_x, su->x_over_x0, S * 8},
+                     {o_sid, me->surface_id, M * 4},     {o_loc, me->loc, 2 * M * 8},
+                     {o_cov, me->cov, 3 * M * 8},        {o_h, me->is_hole, M},
+                     {o_map, fi->map ? fi->map->b : nullptr, map_bytes}};
+    for (const Cp& c : in) {
+      if (c.bytes == 0) continue;
+      if (!c.src) return KF_EINVAL;
+      cudaError_t e = cudaMemcpyAsync(b + c.o, c.src, c.bytes, cudaMemcpyHostToDevice, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+    }
+    int rc = kf_fit_ex(h, &dtr, &dsu, &dme, &dfi, opt, &dout, stream_v);
+    if (rc) return rc;
+    const Cp outs[] = {{o_p, out->params, 6 * T * 8}, {o_pc, out->cov, 21 * T * 8}, {o_chi, out->chi2, T * 8},
+                       {o_ndf, out->ndf, T * 4},      {o_st, out->status, T},     {o_states, out->states, 6 * M * 8}};
+    for (const Cp& c : outs) {
+      if (!c.src || c.bytes == 0) continue;
+      cudaError_t e = cudaMemcpyAsync((void*)c.src, b + c.o, c.bytes, cudaMemcpyDeviceToHost, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+    }
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  } else {
+    if (!tr->seed_params || !tr->seed_cov || !su->center || !su->rot || !su->x_over_x0 || !out->cov || !out->chi2)
+      return KF_EINVAL;
+    if (M > 0 && (!me->surface_id || !me->loc || !me->cov || !me->is_hole)) return KF_EINVAL;
+    int rc = validate(&dtr, &dsu, &dme, &dfi, &o, &dout);
+    if (rc) return rc;
+    if ((rc = ensure_host_streams(h))) return rc;
+    FitPlan plan;
+    if ((rc = prepare_fit(h, &dtr, &dsu, o, &plan))) return rc;
+    const size_t tcut[3] = {0, T / 2, T};
+    size_t scut[3];
+    for (int c = 0; c < 3; ++c) {
+      const int32_t v = tr->offsets[tcut[c]];
+      if (v < 0 || (size_t)v > M) return KF_EINVAL;
+      scut[c] = (size_t)v;
+    }
+    cudaError_t e = cudaSuccess;
+    auto H2D = cudaMemcpyHostToDevice;
+    // inputs: the shared pieces with chunk 0, then chunk by chunk
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+      cudaStream_t s = h->s_in;
+      if (c == 0) {
+        e = cudaMemcpyAsync(b + o_off, tr->offsets, (T + 1) * 4, H2D, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_c, su->center, 3 * S * 8, H2D, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_r, su->rot, 9 * S * 8, H2D, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_x, su->x_over_x0, S * 8, H2D, s);
+        if (e == cudaSuccess && map_bytes) e = cudaMemcpyAsync(b + o_map, fi->map->b, map_bytes, H2D, s);
+      }
+      const size_t t0 = tcut[c], t1 = tcut[c + 1], s0 = scut[c], s1 = scut[c + 1];
+      if (e == cudaSuccess) e = copy_cols(b + o_sp, tr->seed_params, T, 8, 6, t0, t1, H2D, s);
+      if (e == cudaSuccess) e = copy_cols(b + o_sc, tr->seed_cov, T, 8, 21, t0, t1, H2D, s);
+      if (e == cudaSuccess) e = copy_cols(b + o_sid, me->surface_id, M, 4, 1, s0, s1, H2D, s);
+      if (e == cudaSuccess) e = copy_cols(b + o_loc, me->loc, M, 8, 2, s0, s1, H2D, s);
+      if (e == cudaSuccess) e = copy_cols(b + o_cov, me->cov, M, 8, 3, s0, s1, H2D, s);
+      if (e == cudaSuccess) e = copy_cols(b + o_h, me->is_hole, M, 1, 1, s0, s1, H2D, s);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "host-path H2D");
+    // the fits, chunk by chunk on the caller's stream
+    int launches = 0;
+    for (int c = 0; c < 2; ++c) {
+      e = cudaStreamWaitEvent(stream, h->ev_in[c], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+      int l = 0;
+      rc = enqueue_fit(h, &dtr, &dsu, &dme, &dfi, o, &dout, stream, plan, &l, (int64_t)tcut[c],
+                       (int64_t)tcut[c + 1], c == 0);
+      if (rc) return rc;
+      launches += l;
+      e = cudaEventRecord(h->ev_fit[c], stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
+    h->last_launches = launches;
+    // outputs, chunk by chunk once its fit is done
+    auto D2H = cudaMemcpyDeviceToHost;
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+      cudaStream_t s = h->s_out;
+      e = cudaStreamWaitEvent(s, h->ev_fit[c], 0);
+      const size_t t0 = tcut[c], t1 = tcut[c + 1], s0 = scut[c], s1 = scut[c + 1];
+      if (e == cudaSuccess) e = copy_cols(out->params, b + o_p, T, 8, 6, t0, t1, D2H, s);
+      if (e == cudaSuccess) e = copy_cols(out->cov, b + o_pc, T, 8, 21, t0, t1, D2H, s);
+      if (e == cudaSuccess) e = copy_cols(out->chi2, b + o_chi, T, 8, 1, t0, t1, D2H, s);
+      if (e == cudaSuccess && out->ndf) e = copy_cols(out->ndf, b + o_ndf, T, 4, 1, t0, t1, D2H, s);
+      if (e == cudaSuccess && out->status) e = copy_cols(out->status, b + o_st, T, 1, 1, t0, t1, D2H, s);
+      if (e == cudaSuccess && out->states) e = copy_cols(out->states, b + o_states, M, 8, 6, s0, s1, D2H, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "host-path D2H");
+    e = cudaStreamSynchronize(h->s_out);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   }
-  cudaError_t e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   int32_t flag = 0;
-  e = cudaMemcpy(&flag, h->error_flag, sizeof(flag), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(&flag, h->error_flag, sizeof(flag), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(error flag)");
   if (flag) return KF_EDEVICE;
   return KF_SUCCESS;

@@ -335,3 +335,17 @@ def test_fault_inputs_and_extreme_tracks(handle, prec):
     assert g["status"][5] == 0 and r["status"][5] == 0
     good = np.setdiff1d(np.arange(16), bad)
     compare(g, r, prec, tracks=good)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_pipelined_host_entry_equals_device_entry(handle, prec):
+    """A large host batch runs in two chunks whose copies overlap the other
+    chunk's fit; the results equal the device entry's bit for bit (uneven
+    tracks, smoothed states requested, the sorted schedule asked for)."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 30001))
+    ref = gpu_fit(handle, ev, prec, with_states=True, schedule=kf.KF_SCHEDULE_PERSISTENT)
+    for sched in (kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED, kf.KF_SCHEDULE_GRID):
+        host = kf.kf_fit_host(handle, ev, kf.kf_default_options(prec, schedule=sched), with_states=True)
+        for k in ("params", "cov", "chi2", "ndf", "status", "states"):
+            assert np.array_equal(host[k], ref[k], equal_nan=True), (sched, k)
+        assert handle.last_launch_count() >= 3

@@ -28,6 +28,7 @@
 #include <stdint.h>
 
 #include "kf_device.cuh"
+#include "kf_fp64.cuh"
 #include "kf_internal.h"
 
 namespace kfgb {
@@ -36,7 +37,6 @@ using namespace dev;
 
 constexpr int kSeg = 8;  // states per checkpoint segment (about sqrt(n) for n ~ 30-60)
 
-__device__ __forceinline__ double val(double x) { return x; }
 
 // ---------------------------------------------------------------------------
 // geometry with alignment
@@ -128,8 +128,10 @@ __device__ __forceinline__ void rkn_step_s(PropS<S>& s, const S& h, const double
       s.gT[i][c] = nt;
     }
   }
-  const S gam = sqrt(one + s.lam * s.lam * (mass * mass));
-  s.gtl += h * (s.lam * (mass * mass * kInvC)) / gam;
+  const S g2 = one + s.lam * s.lam * (mass * mass);
+  const S igam = rsqrt_any(g2);
+  const S gam = g2 * igam;
+  s.gtl += h * (s.lam * (mass * mass * kInvC)) * igam;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     s.r[i] = s.r[i] + h * s.T[i] + (h2 * a1[i] + h3 * a2[i] + h4 * a3[i]);
@@ -143,116 +145,6 @@ struct JacS {
   S f[4][5];  // rows loc0, loc1, phi, theta over columns loc0..q/p
   S ft[5];    // time row
 };
-
-// transport x on plane a to plane b; also the Highland variances of b
-template <class S>
-__device__ int transport_s(const Plane<S>& pa, const Plane<S>& pb, const S x[6], const double B[3], double mass,
-                           double h_max, int n_iter, double xx0, S xp[6], JacS<S>& J, S& qphi, S& qth) {
-  PropS<S> s;
-  const S sp = sin(x[2]), cp = cos(x[2]), st = sin(x[3]), ct = cos(x[3]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) s.r[i] = pa.c[i] + x[0] * pa.u(i) + x[1] * pa.v(i);
-  s.T[0] = cp * st;
-  s.T[1] = sp * st;
-  s.T[2] = ct;
-  s.t = x[5];
-  s.lam = x[4];
-  s.gT[0][0] = -(sp * st); s.gT[1][0] = cp * st; s.gT[2][0] = S(0.0);
-  s.gT[0][1] = cp * ct;    s.gT[1][1] = sp * ct; s.gT[2][1] = -st;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    s.gT[i][2] = S(0.0);
-    s.gr[i][0] = S(0.0);
-    s.gr[i][1] = S(0.0);
-    s.gr[i][2] = S(0.0);
-  }
-  s.gtl = S(0.0);
-  auto dist = [&](S& out) -> bool {
-    const S d = pb.n(0) * (pb.c[0] - s.r[0]) + pb.n(1) * (pb.c[1] - s.r[1]) + pb.n(2) * (pb.c[2] - s.r[2]);
-    const S nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
-    if (!(::fabs(val(nT)) > 1e-9)) return false;
-    out = d / nT;
-    return true;
-  };
-  S s0;
-  if (!dist(s0)) return ST_NO_INTERSECTION;
-  const double nsub_d = ::ceil(::fabs(val(s0)) / h_max);
-  if (!(nsub_d <= 64.0)) return ST_NO_INTERSECTION;
-  const int nsub = nsub_d < 1.0 ? 1 : (int)nsub_d;
-  const S h = s0 / (double)nsub;
-  for (int k = 0; k < nsub; ++k) rkn_step_s(s, h, B, mass);
-  for (int it = 0; it < n_iter; ++it) {
-    S si;
-    if (!dist(si)) return ST_NO_INTERSECTION;
-    rkn_step_s(s, si, B, mass);
-  }
-  const S rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
-  const S phi = atan2(s.T[1], s.T[0]);
-  const S rho = sqrt(rho2);
-  const S theta = atan2(rho, s.T[2]);
-  const S tn = sqrt(rho2 + s.T[2] * s.T[2]);
-  const S cph = s.T[0] / rho, sph = s.T[1] / rho, sth = rho / tn, cth = s.T[2] / tn;
-  const S nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
-  // path correction
-  const S lk = s.lam * kKappa;
-  S AT[3];
-  crossB(s.T, B, lk, AT);
-  const S dtds = sqrt(S(1.0) + s.lam * s.lam * (mass * mass)) * kInvC;
-  S Gr[3][5], GT[3][5], Gt[5];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    Gr[i][0] = pa.u(i);
-    Gr[i][1] = pa.v(i);
-    Gr[i][2] = s.gr[i][0];
-    Gr[i][3] = s.gr[i][1];
-    Gr[i][4] = s.gr[i][2];
-    GT[i][0] = S(0.0);
-    GT[i][1] = S(0.0);
-    GT[i][2] = s.gT[i][0];
-    GT[i][3] = s.gT[i][1];
-    GT[i][4] = s.gT[i][2];
-  }
-  Gt[0] = S(0.0); Gt[1] = S(0.0); Gt[2] = S(0.0); Gt[3] = S(0.0);
-  Gt[4] = s.gtl;
-#pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    const S w = -(pb.n(0) * Gr[0][c] + pb.n(1) * Gr[1][c] + pb.n(2) * Gr[2][c]) / nT;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      Gr[i][c] += s.T[i] * w;
-      GT[i][c] += AT[i] * w;
-    }
-    Gt[c] += dtds * w;
-  }
-#pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    J.f[0][c] = pb.u(0) * Gr[0][c] + pb.u(1) * Gr[1][c] + pb.u(2) * Gr[2][c];
-    J.f[1][c] = pb.v(0) * Gr[0][c] + pb.v(1) * Gr[1][c] + pb.v(2) * Gr[2][c];
-    J.f[2][c] = (cph * GT[1][c] - sph * GT[0][c]) / sth;
-    J.f[3][c] = cph * cth * GT[0][c] + sph * cth * GT[1][c] - sth * GT[2][c];
-    J.ft[c] = Gt[c];
-  }
-  const S d0 = s.r[0] - pb.c[0], d1 = s.r[1] - pb.c[1], d2 = s.r[2] - pb.c[2];
-  xp[0] = d0 * pb.u(0) + d1 * pb.u(1) + d2 * pb.u(2);
-  xp[1] = d0 * pb.v(0) + d1 * pb.v(1) + d2 * pb.v(2);
-  xp[2] = phi;
-  xp[3] = theta;
-  xp[4] = s.lam;
-  xp[5] = s.t;
-  // multiple scattering at b (Highland, unit direction of the prediction)
-  if (xx0 > 0.0) {
-    const S l = fabs(s.lam);
-    const S g2 = S(1.0) + l * l * (mass * mass);
-    const S eps = xx0 / fabs(nT / tn);
-    const S th0 = 0.0136 * l * sqrt(g2) * sqrt(eps) * (1.0 + 0.038 * log(eps * g2));
-    qth = th0 * th0;
-    qphi = qth / (sth * sth);
-  } else {
-    qth = S(0.0);
-    qphi = S(0.0);
-  }
-  return ST_OK;
-}
 
 // F as a dense 6x6 (row 4 = e4, column 5 = e5)
 __device__ __forceinline__ void dense_F(const JacS<double>& J, double F[6][6]) {
@@ -402,7 +294,7 @@ __device__ void update_adj(const double xp[6], const double Cp[21], const double
 // The gradient of a scalar of the transport's outputs,
 //   phi = lxp . xp + sum lJ . F + lq_phi q_phi + lq_theta q_theta,
 // with respect to the transport's inputs (x and the two aligned planes) is
-// taken by one reverse sweep over the same arithmetic as transport_s<double>
+// taken by one reverse sweep over the arithmetic of transport_tape
 // (RKN steps with their Jacobian columns, plane intersections, end frame,
 // path correction, free -> bound, Highland noise).  The second derivatives
 // that the F term brings in are exact: the reverse sweep runs through the
@@ -470,11 +362,12 @@ __device__ void rkn_rev(const StepIn& in, double lam, const double B[3], double 
                                                    u3b[3] = {0, 0, 0};
   // t' = t + h gam / c;  gtl' = gtl + h lam m^2 / (c gam)
   const double m2 = mass * mass;
-  const double gam = sqrt(1.0 + lam * lam * m2);
-  double gamb = tb * h * kInvC - gtlb * h * lam * m2 * kInvC / (gam * gam);
-  hb += tb * gam * kInvC + gtlb * lam * m2 * kInvC / gam;
-  lamb += gtlb * h * m2 * kInvC / gam;
-  lamb += gamb * lam * m2 / gam;
+  const double g2 = 1.0 + lam * lam * m2;
+  const double igam = rsqrt_any(g2), gam = g2 * igam;
+  double gamb = tb * h * kInvC - gtlb * h * lam * m2 * kInvC * igam * igam;
+  hb += tb * gam * kInvC + gtlb * lam * m2 * kInvC * igam;
+  lamb += gtlb * h * m2 * kInvC * igam;
+  lamb += gamb * lam * m2 * igam;
   // r' = r + h T + h2 a1 + h3 a2 + h4 a3;  T' = T + h a1 + h2 a2 + h3 a3 + h4 a4
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -549,11 +442,13 @@ __device__ __forceinline__ void save_step(const PropS<double>& s, double h, Step
   o.h = h;
 }
 
-// The transport with its tape: values exactly as transport_s<double>, the
-// state entering each RKN step recorded (the first kTape).
+// The transport x on plane a -> plane b (the same arithmetic as the FP64
+// fit kernel) with the Highland variances of b; with TAPE, the state
+// entering each RKN step is recorded (the first kTape) for the reverse sweep.
+template <bool TAPE>
 __device__ int transport_tape(const Plane<double>& pa, const Plane<double>& pb, const double x[6],
                               const double B[3], double mass, double h_max, int n_iter, double xx0, double xp[6],
-                              JacS<double>& J, double& qphi, double& qth, Tape& tp, PropS<double>& s_end) {
+                              JacS<double>& J, double& qphi, double& qth, Tape* tp, PropS<double>& s_end) {
   PropS<double> s;
   const double sp = sin(x[2]), cp = cos(x[2]), st = sin(x[3]), ct = cos(x[3]);
 #pragma unroll
@@ -575,7 +470,7 @@ __device__ int transport_tape(const Plane<double>& pa, const Plane<double>& pb, 
     const double d = pb.n(0) * (pb.c[0] - s.r[0]) + pb.n(1) * (pb.c[1] - s.r[1]) + pb.n(2) * (pb.c[2] - s.r[2]);
     const double nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
     if (!(::fabs(nT) > 1e-9)) return false;
-    out = d / nT;
+    out = d * rcp_any(nT);
     return true;
   };
   double s0;
@@ -584,29 +479,37 @@ __device__ int transport_tape(const Plane<double>& pa, const Plane<double>& pb, 
   if (!(nsub_d <= 64.0)) return ST_NO_INTERSECTION;
   const int nsub = nsub_d < 1.0 ? 1 : (int)nsub_d;
   const double h = s0 / (double)nsub;
-  tp.nsub = nsub;
-  tp.s0 = s0;
+  if (TAPE) {
+    tp->nsub = nsub;
+    tp->s0 = s0;
+  }
   int ns = 0;
   for (int k = 0; k < nsub; ++k, ++ns) {
-    if (ns < kTape) save_step(s, h, tp.st[ns]);
+    if (TAPE && ns < kTape) save_step(s, h, tp->st[ns]);
     rkn_step_s<double>(s, h, B, mass);
   }
   for (int it = 0; it < n_iter; ++it, ++ns) {
     double si;
     if (!dist(si)) return ST_NO_INTERSECTION;
-    if (ns < kTape) save_step(s, si, tp.st[ns]);
+    if (TAPE && ns < kTape) save_step(s, si, tp->st[ns]);
     rkn_step_s<double>(s, si, B, mass);
   }
-  tp.n_steps = ns;
-  s_end = s;
-  // the end frame and the outputs, as in transport_s
+  if (TAPE) {
+    tp->n_steps = ns;
+    s_end = s;
+  }
+  // the end frame and the outputs
   const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
+  const double irho = rsqrt_any(rho2);
+  const double rho = rho2 * irho;
   const double phi = atan2(s.T[1], s.T[0]);
-  const double rho = sqrt(rho2);
   const double theta = atan2(rho, s.T[2]);
-  const double tn = sqrt(rho2 + s.T[2] * s.T[2]);
-  const double cph = s.T[0] / rho, sph = s.T[1] / rho, sth = rho / tn, cth = s.T[2] / tn;
+  const double tn2 = rho2 + s.T[2] * s.T[2];
+  const double itn = rsqrt_any(tn2);
+  const double tn = tn2 * itn;
+  const double cph = s.T[0] * irho, sph = s.T[1] * irho, sth = rho * itn, cth = s.T[2] * itn;
   const double nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
+  const double inv_nT = rcp_any(nT), inv_sth = rcp_any(sth);
   const double lk = s.lam * kKappa;
   double AT[3];
   crossB(s.T, B, lk, AT);
@@ -629,7 +532,7 @@ __device__ int transport_tape(const Plane<double>& pa, const Plane<double>& pb, 
   Gt[4] = s.gtl;
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    const double w = -(pb.n(0) * Gr[0][c] + pb.n(1) * Gr[1][c] + pb.n(2) * Gr[2][c]) / nT;
+    const double w = -(pb.n(0) * Gr[0][c] + pb.n(1) * Gr[1][c] + pb.n(2) * Gr[2][c]) * inv_nT;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       Gr[i][c] += s.T[i] * w;
@@ -641,7 +544,7 @@ __device__ int transport_tape(const Plane<double>& pa, const Plane<double>& pb, 
   for (int c = 0; c < 5; ++c) {
     J.f[0][c] = pb.u(0) * Gr[0][c] + pb.u(1) * Gr[1][c] + pb.u(2) * Gr[2][c];
     J.f[1][c] = pb.v(0) * Gr[0][c] + pb.v(1) * Gr[1][c] + pb.v(2) * Gr[2][c];
-    J.f[2][c] = (cph * GT[1][c] - sph * GT[0][c]) / sth;
+    J.f[2][c] = (cph * GT[1][c] - sph * GT[0][c]) * inv_sth;
     J.f[3][c] = cph * cth * GT[0][c] + sph * cth * GT[1][c] - sth * GT[2][c];
     J.ft[c] = Gt[c];
   }
@@ -655,10 +558,11 @@ __device__ int transport_tape(const Plane<double>& pa, const Plane<double>& pb, 
   if (xx0 > 0.0) {
     const double l = ::fabs(s.lam);
     const double g2 = 1.0 + l * l * (mass * mass);
-    const double eps = xx0 / ::fabs(nT / tn);
-    const double th0 = 0.0136 * l * sqrt(g2) * sqrt(eps) * (1.0 + 0.038 * log(eps * g2));
+    const double eps = xx0 * ::fabs(tn * inv_nT);
+    const double ge = g2 * eps;
+    const double th0 = 0.0136 * l * (ge * rsqrt_any(ge)) * (1.0 + 0.038 * log(ge));
     qth = th0 * th0;
-    qphi = qth / (sth * sth);
+    qphi = qth * (inv_sth * inv_sth);
   } else {
     qth = 0.0;
     qphi = 0.0;
@@ -690,16 +594,18 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
   const double m2 = mass * mass;
   // ---- end frame values (recomputed)
   const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
-  const double rho = sqrt(rho2);
+  const double irho = rsqrt_any(rho2), rho = rho2 * irho, irho2 = irho * irho;
   const double tn2 = rho2 + s.T[2] * s.T[2];
-  const double tn = sqrt(tn2);
-  const double cph = s.T[0] / rho, sph = s.T[1] / rho, sth = rho / tn, cth = s.T[2] / tn;
+  const double itn = rsqrt_any(tn2), tn = tn2 * itn, itn2 = itn * itn;
+  const double cph = s.T[0] * irho, sph = s.T[1] * irho, sth = rho * itn, cth = s.T[2] * itn;
   const double nT = pb.n(0) * s.T[0] + pb.n(1) * s.T[1] + pb.n(2) * s.T[2];
+  const double inv_nT = rcp_any(nT), inv_sth = rcp_any(sth);
   const double lk = s.lam * kKappa;
   double AT[3];
   crossB(s.T, B, lk, AT);
-  const double gam_e = sqrt(1.0 + s.lam * s.lam * m2);
-  const double dtds = gam_e * kInvC;
+  const double g2_e = 1.0 + s.lam * s.lam * m2;
+  const double igam_e = rsqrt_any(g2_e);
+  const double dtds = g2_e * igam_e * kInvC;
   double Gr0[3][5], GT0[3][5], w[5], Gr[3][5], GT[3][5];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -716,7 +622,7 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    w[c] = -(pb.n(0) * Gr0[0][c] + pb.n(1) * Gr0[1][c] + pb.n(2) * Gr0[2][c]) / nT;
+    w[c] = -(pb.n(0) * Gr0[0][c] + pb.n(1) * Gr0[1][c] + pb.n(2) * Gr0[2][c]) * inv_nT;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       Gr[i][c] = Gr0[i][c] + s.T[i] * w[c];
@@ -728,19 +634,22 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
   if (xx0 > 0.0) {
     const double l = ::fabs(s.lam);
     const double g2 = 1.0 + l * l * m2;
-    const double cinc = nT / tn;
-    const double eps = xx0 / ::fabs(cinc);
-    const double Lg = 1.0 + 0.038 * log(eps * g2);
-    const double th0 = 0.0136 * l * sqrt(g2) * sqrt(eps) * Lg;
-    const double qthb = lqt + lqp / (sth * sth);
-    sthb += lqp * (-2.0 * th0 * th0 / (sth * sth * sth));
+    const double icinc = tn * inv_nT;  // 1 / cos(incidence)
+    const double eps = xx0 * ::fabs(icinc);
+    const double ge = g2 * eps;
+    const double Lg = 1.0 + 0.038 * log(ge);
+    const double iLg = rcp_any(Lg), ig2 = rcp_any(g2), ieps = rcp_any(eps);
+    const double th0 = 0.0136 * l * (ge * rsqrt_any(ge)) * Lg;
+    const double is2 = inv_sth * inv_sth;
+    const double qthb = lqt + lqp * is2;
+    sthb += lqp * (-2.0 * th0 * th0 * is2 * inv_sth);
     const double th0b = 2.0 * th0 * qthb;
-    const double dl = th0 * (1.0 / l + l * m2 / g2 + 0.038 * (2.0 * l * m2 / g2) / Lg);
-    const double deps = th0 * (0.5 / eps + 0.038 / (eps * Lg));
+    const double dl = th0 * (rcp_any(l) + l * m2 * ig2 + 0.038 * (2.0 * l * m2 * ig2) * iLg);
+    const double deps = th0 * ieps * (0.5 + 0.038 * iLg);
     lamb += th0b * dl * (s.lam >= 0.0 ? 1.0 : -1.0);
-    const double cb = th0b * deps * (-eps / cinc);
-    nTb += cb / tn;
-    tnb -= cb * nT / (tn * tn);
+    const double cb = th0b * deps * (-eps * icinc);
+    nTb += cb * itn;
+    tnb -= cb * nT * itn2;
   }
   // ---- outputs xp
   {
@@ -759,8 +668,8 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     const double l0 = lJ[0][c], l1 = lJ[1][c], l2 = lJ[2][c], l3 = lJ[3][c];
-    const double q = l2 / sth;
-    const double f2 = (cph * GT[1][c] - sph * GT[0][c]) / sth;
+    const double q = l2 * inv_sth;
+    const double f2 = (cph * GT[1][c] - sph * GT[0][c]) * inv_sth;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       Grb[i][c] = l0 * pb.u(i) + l1 * pb.v(i);
@@ -772,7 +681,7 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
     GTb[2][c] = -l3 * sth;
     cphb += q * GT[1][c] + l3 * cth * GT[0][c];
     sphb += -q * GT[0][c] + l3 * cth * GT[1][c];
-    sthb += -l2 * f2 / sth - l3 * GT[2][c];
+    sthb += -l2 * f2 * inv_sth - l3 * GT[2][c];
     cthb += l3 * (cph * GT[0][c] + sph * GT[1][c]);
     Gtb[c] = lJt[c];
   }
@@ -787,11 +696,11 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
     for (int i = 0; i < 3; ++i) {
       Tb[i] += w[c] * Grb[i][c];
       ATb[i] += w[c] * GTb[i][c];
-      Gr0b[i][c] = Grb[i][c] - wb * pb.n(i) / nT;
-      nbb[i] += -wb * Gr0[i][c] / nT;
+      Gr0b[i][c] = Grb[i][c] - wb * pb.n(i) * inv_nT;
+      nbb[i] += -wb * Gr0[i][c] * inv_nT;
     }
     dtdsb += w[c] * Gtb[c];
-    nTb += -wb * w[c] / nT;
+    nTb += -wb * w[c] * inv_nT;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -810,7 +719,7 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
     double lkb = 0.0;
     Aop_rev(s.T, B, lk, ATb, Tb, lkb);
     lamb += kKappa * lkb;
-    lamb += dtdsb * s.lam * m2 * kInvC / gam_e;
+    lamb += dtdsb * s.lam * m2 * kInvC * igam_e;
   }
   // nT = n . T
 #pragma unroll
@@ -821,24 +730,24 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
   // end angles and direction cosines
   {
     double rhob = 0.0, rho2b = 0.0;
-    Tb[0] += cphb / rho;
-    rhob -= cphb * s.T[0] / rho2;
-    Tb[1] += sphb / rho;
-    rhob -= sphb * s.T[1] / rho2;
-    rhob += sthb / tn;
-    tnb -= sthb * rho / tn2;
-    Tb[2] += cthb / tn;
-    tnb -= cthb * s.T[2] / tn2;
+    Tb[0] += cphb * irho;
+    rhob -= cphb * s.T[0] * irho2;
+    Tb[1] += sphb * irho;
+    rhob -= sphb * s.T[1] * irho2;
+    rhob += sthb * itn;
+    tnb -= sthb * rho * itn2;
+    Tb[2] += cthb * itn;
+    tnb -= cthb * s.T[2] * itn2;
     // theta = atan2(rho, T2)
-    rhob += thetab * s.T[2] / tn2;
-    Tb[2] -= thetab * rho / tn2;
+    rhob += thetab * s.T[2] * itn2;
+    Tb[2] -= thetab * rho * itn2;
     // tn = sqrt(rho2 + T2^2)
-    rho2b += tnb / (2.0 * tn);
-    Tb[2] += tnb * s.T[2] / tn;
-    rho2b += rhob / (2.0 * rho);
+    rho2b += tnb * 0.5 * itn;
+    Tb[2] += tnb * s.T[2] * itn;
+    rho2b += rhob * 0.5 * irho;
     // phi = atan2(T1, T0)
-    Tb[1] += phib * s.T[0] / rho2;
-    Tb[0] -= phib * s.T[1] / rho2;
+    Tb[1] += phib * s.T[0] * irho2;
+    Tb[0] -= phib * s.T[1] * irho2;
     Tb[0] += 2.0 * s.T[0] * rho2b;
     Tb[1] += 2.0 * s.T[1] * rho2b;
   }
@@ -883,7 +792,8 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
     if (j >= tp.nsub) {
       // correction step: si = (n.(c - r))/(n.T) of the state entering it
       const double nTi = pb.n(0) * in.T[0] + pb.n(1) * in.T[1] + pb.n(2) * in.T[2];
-      const double db = hb / nTi, nTib = -hb * in.h / nTi;
+      const double inTi = rcp_any(nTi);
+      const double db = hb * inTi, nTib = -hb * in.h * inTi;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         nbb[i] += db * (pb.c[i] - in.r[i]) + nTib * in.T[i];
@@ -901,7 +811,8 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
     const StepIn& st0 = tp.st[0];
     const double s0b = hb_main / (double)tp.nsub;
     const double nT0 = pb.n(0) * st0.T[0] + pb.n(1) * st0.T[1] + pb.n(2) * st0.T[2];
-    const double db = s0b / nT0, nT0b = -s0b * tp.s0 / nT0;
+    const double inT0 = rcp_any(nT0);
+    const double db = s0b * inT0, nT0b = -s0b * tp.s0 * inT0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       nbb[i] += db * (pb.c[i] - st0.r[i]) + nT0b * st0.T[i];
@@ -1019,8 +930,9 @@ __device__ __forceinline__ int transport_values(const GradParams& g, const doubl
   const Plane<double> pa = aligned_plane<double>(Surf{s_surf + sa * kSurfStride}, aa);
   const Plane<double> pb = aligned_plane<double>(Surf{s_surf + sb * kSurfStride}, ab);
   const double B[3] = {g.f.bfield[0], g.f.bfield[1], g.f.bfield[2]};
-  return transport_s<double>(pa, pb, x, B, g.f.mass, g.f.h_max, g.f.n_iter,
-                             Surf{s_surf + sb * kSurfStride}.xx0(), xp, J, qp, qt);
+  PropS<double> s_end;
+  return transport_tape<false>(pa, pb, x, B, g.f.mass, g.f.h_max, g.f.n_iter, Surf{s_surf + sb * kSurfStride}.xx0(),
+                               xp, J, qp, qt, nullptr, s_end);
 }
 
 __device__ __forceinline__ void cov_transport(const double F[6][6], const double Cf[21], double qp, double qt,
@@ -1216,7 +1128,7 @@ __global__ void __launch_bounds__(128) kf_grad_kernel(const GradParams g) {
       if (act) {
         double xp[6], Cp[21], qp, qt;
         JacS<double> J;
-        transport_tape(pa, pb, xprev, B, p.mass, p.h_max, p.n_iter, xxb, xp, J, qp, qt, tp, s_end);
+        transport_tape<true>(pa, pb, xprev, B, p.mass, p.h_max, p.n_iter, xxb, xp, J, qp, qt, &tp, s_end);
         dense_F(J, F);
         cov_transport(F, Cprev, qp, qt, Cp);
         if (!p.is_hole[o0 + k]) {

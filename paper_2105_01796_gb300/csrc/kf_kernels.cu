@@ -1,15 +1,11 @@
-// kf_kernels.cu -- sm_103a kernels of the Kalman-filter track fit
-// (arXiv 2105.01796): forward filter (Runge-Kutta-Nystrom propagation in a
-// constant field, Jacobian transport, multiple-scattering noise, gain-matrix
+// kf_kernels.cu -- the FP64 fit kernel (sm_103a) of the Kalman-filter track
+// fit (arXiv 2105.01796): forward filter (Runge-Kutta-Nystrom propagation in
+// a constant field, Jacobian transport, multiple-scattering noise, gain-matrix
 // update with the Joseph covariance form, chi2) and the Rauch-Tung-Striebel
-// smoother, fused into one launch with one track per thread.
-//
-// Precision modes (template PREC):
-//   0 = FP64: every step in double precision.
-//   1 = mixed: propagation, Jacobian and covariance transport and the gain in
-//       float; the Joseph covariance update, the smoother's Cholesky solve and
-//       chi2 in double.  Positions, directions, time and the parameter vector
-//       are double-precision accumulators that receive float increments.
+// smoother, fused into one launch with one track per thread, every step in
+// double precision; plus the small helper kernels (surface packing, the
+// length sort of the sorted schedule, a self-check).  The mixed-precision
+// kernel is in kf_mixed.cu, the method variants in kf_variants.cu.
 // Paper references: Sect. 2 (filter step list, RTS smoother with the stored
 // Jacobians), Sect. 4.1 (RKN transport; local<->global Jacobians at both
 // surfaces), Sect. 4.2 (double-precision inverter), Sect. 4.3 (surfaces in
@@ -26,9 +22,6 @@ namespace kfgb {
 namespace {
 using namespace dev;
 
-// this file holds the FP64 path; the mixed path is in kf_mixed.cu
-template <int PREC> struct Prec;
-template <> struct Prec<0> { using R = double; };
 
 // ---------------------------------------------------------------------------
 // propagation state: free parameters (double accumulators) plus the columns
@@ -247,13 +240,11 @@ __device__ __forceinline__ int transport(const Surf& sa, const Surf& sb, const d
 // ---------------------------------------------------------------------------
 template <bool BZ>
 __device__ __forceinline__ void fit_one_fp64(const FitParams& p, const double* s_surf, int i) {
-  constexpr int PREC = 0;
-  using R = typename Prec<PREC>::R;
-  using RC = Rec<PREC>;
+  using R = double;
+  using RC = Rec<0>;
   const int t = track_of(p, i);
   const size_t TT = (size_t)p.n_tracks_total;
-  const WS ws{p.ws64, p.ws32, (size_t)p.n_tracks, PREC == 0 ? kRec64Fp64 : kRec64Mixed,
-              PREC == 0 ? 0 : kRec32Mixed, i};
+  const WS ws{p.ws64, p.ws32, (size_t)p.n_tracks, kRec64Fp64, 0, i};
   const int64_t o0 = p.offsets[t], o1 = p.offsets[t + 1];
   const int n = (int)(o1 - o0);
   int status = ST_OK;

@@ -43,14 +43,14 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # Traffic grows in proportion to the states, so a launch's traffic is this
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = 1.69168896e9 / 2.48e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "51c1661bdceaa98042bf09afcb9a4af21e950d75700dafd99b571ac7689a5805"
+MIXED_TRAFFIC_BYTES_PER_STATE = (598.226432e6 + 539.438592e6) / 2.48e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "c1a88950f8d75af0b216f656c3c613b9e94fc4a894a4ef7d6d3014775aa8c71c"
 
 
 def mixed_kernel_sources_sha256():
     import hashlib
     h = hashlib.sha256()
-    for f in ("csrc/kf_mixed.cu", "csrc/kf_device.cuh", "_build.py"):
+    for f in ("csrc/kf_mixed.cu", "csrc/kf_device.cuh", "csrc/kf_internal.h", "_build.py"):
         with open(os.path.join(ROOT, "paper_2105_01796_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -455,7 +455,7 @@ def run_ours(args, rank, world, local):
                      "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
                      "algorithmic_bytes_per_launch": nbytes,
                      "traffic_note": ("ncu capture of an 80k-track launch scaled by states; the "
-                                      "smoother's per-state record round trip (348 B each way)")
+                                      "smoother's per-state record round trip (216 B each way)")
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,
         "variants": variants,

@@ -36,8 +36,12 @@ namespace kfgb {
 namespace {
 using namespace dev;
 
-constexpr int XP = 0, CP = 6;  // ws64 record fields
-constexpr int FJ = 0, QPHI = 25, QTH = 26, DXF = 27;  // ws32 record fields
+// per-state record: x_p in FP64 (written for state 0, and for every state
+// when the smoothed states are output); the transport Jacobian, the
+// scattering variances, the filter increment and the predicted covariance
+// (FP32-exact values) in FP32
+constexpr int XP = 0;                                                    // ws64 fields
+constexpr int FJ = 0, QPHI = 25, QTH = 26, DXF = 27, CPF = 33;          // ws32 fields
 
 struct WSM {
   double* w64;
@@ -678,10 +682,14 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cp[e] = f2d(Cpf[e]);
       }
+      if (k == 0 || p.out_states) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) ws.d(k, XP + e) = xp[e];
+        for (int e = 0; e < 6; ++e) ws.d(k, XP + e) = xp[e];
+      }
+      if (k > 0) {
 #pragma unroll
-      for (int e = 0; e < 21; ++e) ws.d(k, CP + e) = Cp[e];
+        for (int e = 0; e < 21; ++e) ws.f(k, CPF + e) = Cpf[e];
+      }
       const Surf sk{s_surf + sid * kSurfStride};
       if (!p.is_hole[o0 + k]) {
         // gain-matrix update: gain in FP32, Joseph covariance and chi2 in FP64
@@ -774,7 +782,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         // FP64: the (phi, theta) columns of Cp_{k+1}^-1
         double Cp1[21];
 #pragma unroll
-        for (int e = 0; e < 21; ++e) Cp1[e] = ws.d(k + 1, CP + e);
+        for (int e = 0; e < 21; ++e) Cp1[e] = f2d(ws.f(k + 1, CPF + e));
         double w[2][6];
         if (!angle_columns_of_inverse(Cp1, w)) {
           status = ST_NON_SPD;

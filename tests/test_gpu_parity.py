@@ -163,7 +163,7 @@ def test_empty_batch(handle):
 def test_chunked_equals_single_launch(handle, prec):
     ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel30_100k"], 1500))
     a = gpu_fit(handle, ev, prec)
-    per_track = 31 * (720 if prec == FP64 else 27 * 8 + 33 * 4)
+    per_track = 31 * (720 if prec == FP64 else 6 * 8 + 54 * 4)
     b = gpu_fit(handle, ev, prec, workspace_bytes=per_track * 400)  # 4 chunks
     assert handle.last_launch_count() == 1 + 4
     for k in ("params", "cov", "chi2", "ndf", "status"):

@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the method-variant kernel (backward filter + energy loss + field map)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (chi2 gradient) kernel")
+    ap.add_argument("--no-scale", action="store_true",
+                    help="skip the 4M-track throughput-scale workload (mixed and FP64)")
     return ap.parse_args()
 
 
@@ -239,6 +241,69 @@ def time_variants(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks
                                    "cuda_graph": True}}
 
 
+SCALE_WORKLOAD = "tel30_4m"
+
+
+def step_stats(ms):
+    """Per-step device times: mean and RMS spread over the timed steps
+    (the paper's protocol), plus the median, minimum and maximum."""
+    a = np.asarray(ms, dtype=np.float64)
+    return {"mean": float(a.mean()), "rms": float(a.std()), "median": float(np.median(a)),
+            "min": float(a.min()), "max": float(a.max()), "n": int(a.size)}
+
+
+def time_scale(kf, synth, torch, stream, l2_flush, steps, warmup, rank, no_cpu):
+    """The throughput-scale workload: 4,000,000 tracks x 30 planes in one
+    batch, mixed and FP64, each in its autotuned launch shape replayed from a
+    CUDA graph.  Its own handle, freed afterwards (the FP64 record alone
+    takes 89 GB)."""
+    w = synth.WORKLOADS[SCALE_WORKLOAD]
+    w = synth.scaled(w, w.n_tracks, seed=w.seed + 1000 * rank)
+    t0 = time.perf_counter()
+    ev = synth.make_event(w, with_truth_states=False)
+    gen_s = time.perf_counter() - t0
+    T = int(ev["n_tracks"])
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(T)
+    h = kf.Handle()
+    res = {"workload": SCALE_WORKLOAD, "tracks": T, "planes": 30, "x_over_x0": 0.01, "sigma_um": 50,
+           "p_GeV": [1, 100], "generation_s": gen_s}
+    for name, prec in (("mixed", kf.KF_PRECISION_MIXED), ("fp64", kf.KF_PRECISION_FP64)):
+        best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(prec), stream)
+        opt = kf.kf_default_options(prec, schedule=best.schedule, block=best.block, min_blocks=best.min_blocks,
+                                    resident_warps=best.resident_warps, use_graph=1)
+        for _ in range(warmup):
+            kf.kf_fit_ex(h, dev, out, opt, stream)
+        torch.cuda.synchronize()
+        ms = []
+        torch.cuda.nvtx.range_push("timed_scale_" + name)
+        for _ in range(steps):
+            l2_flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kf.kf_fit_ex(h, dev, out, opt, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        torch.cuda.nvtx.range_pop()
+        st = step_stats(ms)
+        res[name] = {"value": T / (st["mean"] / 1e3), "unit": "tracks/s", "ms_per_step": st["mean"],
+                     "step_ms": st, "ok_tracks": int((out["status"] == 0).sum().item()),
+                     "launch_shape": {"schedule": ["grid", "persistent", "sorted"][best.schedule],
+                                      "block": best.block, "min_blocks": best.min_blocks,
+                                      "resident_warps": best.resident_warps, "cuda_graph": True}}
+    res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
+    del h, out, dev
+    torch.cuda.empty_cache()
+    if not no_cpu and rank == 0:
+        cores = os.cpu_count() or 1
+        v, dt, n = oracle_tracks_per_s(ev, 20_000, cores)
+        res["cpu_oracle"] = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                             "sample": "first %d tracks, one pass (%.1f s)" % (n, dt)}
+    return res
+
+
 def run_reference(args, rank, world):
     """CPU oracle arm: each step fits a bounded sample on the host cores."""
     if rank != 0:
@@ -355,6 +420,13 @@ def run_ours(args, rank, world, local):
                                               reduce=kdist.sum_over_ranks if world > 1 else None)
         a_ms = kdist.max_over_ranks(adjoint["ms_per_step"], device="cuda")
         adjoint.update(ms_per_step=a_ms, value=world * adjoint["tracks"] / (a_ms / 1e3))
+    scale = None
+    if not args.no_scale:
+        scale = time_scale(kf, synth, torch, stream, l2_flush, max(3, args.steps // 2), args.warmup,
+                           rank, args.no_cpu)
+        for name in ("mixed", "fp64"):
+            s_ms = kdist.max_over_ranks(scale[name]["ms_per_step"], device="cuda")
+            scale[name].update(ms_per_step=s_ms, value=world * scale["tracks"] / (s_ms / 1e3))
     variants = None
     variant_event = None
     if not args.no_variants:
@@ -417,8 +489,11 @@ def run_ours(args, rank, world, local):
         # warm the oracle build, then time a bounded sample
         oracle_tracks_per_s(ev, 500, cores)
         v, dt, n = oracle_tracks_per_s(ev, T, cores)
+        v1, dt1, n1 = oracle_tracks_per_s(ev, 5000, 1)
         cpu = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle",
-               "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt)}
+               "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt),
+               "single_core": {"value": v1, "unit": "tracks/s",
+                               "sample": "first %d tracks, one thread (%.1f s)" % (n1, dt1)}}
         if adjoint is not None:
             av, adt, an = oracle_gradient_rate(adjoint_event, 200, cores)
             adjoint["cpu_oracle"] = {"value": av, "unit": "tracks/s", "cores": cores,
@@ -434,6 +509,7 @@ def run_ours(args, rank, world, local):
     line = {
         "metric": "tracks_fitted_per_s", "value": value, "unit": "tracks/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "step_ms": step_stats(ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "tracks_per_gpu": T, "planes": 30, "states": M,
@@ -442,7 +518,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between timed steps (256 MiB write); inputs 165 MB > L2",
                    "parallelism": "one independent batch per GPU" if world > 1 else "single GPU"},
         "fp64_path" if args.precision == "mixed" else "mixed_path": {
-            "value": world * T / (other_ms / 1e3), "ms_per_step": other_ms,
+            "value": world * T / (other_ms / 1e3), "ms_per_step": other_ms, "step_ms": step_stats(ms_other),
             "ok_tracks": int((st_other == 0).sum())},
         "ok_tracks": int((st == 0).sum()),
         "launch_shape": tuned,
@@ -458,12 +534,17 @@ def run_ours(args, rank, world, local):
                                       "smoother's per-state record round trip (216 B each way)")
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,
+        "scale": scale,
         "variants": variants,
         "adjoint": adjoint,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if clocks and clocks.get("sm_mhz"):
+        # the same derived peak at the median SM clock sampled under load
+        pk = FP64_PEAK_TFLOPS * clocks["sm_mhz"] / 2070.0
+        line["roofline"].update(peak_at_sampled_clock=pk, frac_at_sampled_clock=achieved / pk)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

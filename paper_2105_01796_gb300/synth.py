@@ -25,7 +25,8 @@ Layout of the returned event (the library's structure-of-arrays boundary):
   offsets[T+1] int32, seed_params[6][T], seed_cov[21][T] (packed lower
   triangle), truth_params[6][T]; center[3][S], rot[9][S] (row-major R whose
   columns are u, v, n), x_over_x0[S]; surface_id[M] int32, loc[2][M],
-  cov[3][M] (V00, V01, V11), is_hole[M] uint8, truth_states[6][M]; bfield[3].
+  cov[3][M] (V00, V01, V11), is_hole[M] uint8, truth_states[6][M] (or None);
+  bfield[3].
 State 0 of every track is the reference plane x = 0 (surface 0), which has no
 measurement and no material; the seed lives there.
 """
@@ -33,6 +34,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -401,13 +403,11 @@ def _simulate(w: Workload, ids, attempt, mass):
                 leave=leave, hole=hole, ok=ok)
 
 
-def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200) -> dict:
-    """Simulate workload `w` and return the event dict (see module doc)."""
-    T = w.n_tracks
-    npl = len(w.plane_x)
-    ids_all = np.arange(T, dtype=np.uint64)
-    attempt = np.zeros(T, dtype=np.uint64)
-    sim = _simulate(w, ids_all, attempt, mass)
+def _simulate_with_retries(w: Workload, ids, mass: float, max_attempts: int):
+    """Simulate tracks `ids`, redrawing each rejected track with the next
+    attempt number until it is accepted. Returns (sim, attempt, rejected)."""
+    attempt = np.zeros(len(ids), dtype=np.uint64)
+    sim = _simulate(w, ids, attempt, mass)
     rejected = 0
     for _ in range(max_attempts):
         bad = np.nonzero(~sim["ok"])[0]
@@ -415,12 +415,76 @@ def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200) ->
             break
         rejected += bad.size
         attempt[bad] += 1
-        sub = _simulate(w, ids_all[bad], attempt[bad], mass)
+        sub = _simulate(w, ids[bad], attempt[bad], mass)
         for k, v in sub.items():
             if isinstance(v, np.ndarray):
                 sim[k][..., bad] = v
     else:
         raise RuntimeError("track simulation did not converge")
+    return sim, attempt, rejected
+
+
+def _simulate_tracks(w: Workload, ids, mass: float, max_attempts: int, with_truth_states: bool):
+    """Simulate tracks `ids` and return per-track arrays plus the per-plane
+    arrays of the crossed planes in state order (track by track, planes in
+    order): a contiguous range of tracks maps to a contiguous range of
+    states, so ranges simulated apart concatenate to the whole batch."""
+    sim, attempt, rejected = _simulate_with_retries(w, ids, mass, max_attempts)
+    npl = len(w.plane_x)
+    nhit = sim["nhit"]
+    crossed = np.arange(npl)[None, :] < nhit[:, None]       # [tracks, npl]
+
+    def per_state(a):                                      # [npl, tracks] -> crossed states
+        return np.ascontiguousarray(a.T)[crossed]
+
+    hole = per_state(sim["hole"])
+    out = dict(phi0=sim["phi0"], th0=sim["th0"], qop=sim["qop"], nhit=nhit, attempt=attempt,
+               hole=hole, plane=np.broadcast_to(np.arange(npl, dtype=np.int32), crossed.shape)[crossed],
+               m0=np.where(hole, 0.0, per_state(sim["meas"][0])),
+               m1=np.where(hole, 0.0, per_state(sim["meas"][1])))
+    if with_truth_states:
+        out.update(l0=per_state(sim["loc"][0]), l1=per_state(sim["loc"][1]),
+                   a0=per_state(sim["leave"][0]), a1=per_state(sim["leave"][1]),
+                   a2=per_state(sim["leave"][2]))
+    return out, rejected
+
+
+def _simulate_range(args):
+    w, lo, hi, mass, max_attempts, with_truth_states = args
+    return _simulate_tracks(w, np.arange(lo, hi, dtype=np.uint64), mass, max_attempts, with_truth_states)
+
+
+def default_workers(n_tracks: int) -> int:
+    """Processes make_event uses: one per 250k tracks, at most one per core."""
+    return max(1, min(os.cpu_count() or 1, n_tracks // 250_000))
+
+
+def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200,
+               workers: int | None = None, with_truth_states: bool = True) -> dict:
+    """Simulate workload `w` and return the event dict (see module doc).
+
+    Every draw is keyed by (seed, track, attempt, purpose), so the tracks can
+    be simulated in contiguous ranges by `workers` processes (spawned, so it
+    is safe after CUDA is initialised) with the same result as one process.
+    `with_truth_states=False` leaves out the per-state truth (truth_states is
+    then None), which large batches that are only fitted do not need.
+    """
+    T = w.n_tracks
+    npl = len(w.plane_x)
+    ids_all = np.arange(T, dtype=np.uint64)
+    workers = default_workers(T) if workers is None else max(1, int(workers))
+    if workers == 1 or T < 2 * workers:
+        sim, rejected = _simulate_tracks(w, ids_all, mass, max_attempts, with_truth_states)
+    else:
+        import multiprocessing as mp
+        cuts = [T * i // workers for i in range(workers + 1)]
+        jobs = [(w, cuts[i], cuts[i + 1], mass, max_attempts, with_truth_states) for i in range(workers)]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_simulate_range, jobs)
+        sim = {k: np.concatenate([pt[0][k] for pt in parts]) for k in parts[0][0]}
+        rejected = sum(pt[1] for pt in parts)
+        del parts
+    attempt = sim["attempt"]
 
     nhit = sim["nhit"]
     nstates = nhit + 1
@@ -429,28 +493,26 @@ def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200) ->
     M = int(offsets[-1])
     if M >= 2 ** 31:
         raise ValueError("too many states for int32 offsets")
-    # scatter per-plane arrays into the ragged state list
-    k_idx = np.arange(npl)
-    valid = k_idx[:, None] < nhit[None, :]               # [npl, T]
-    pos = offsets[:-1][None, :] + 1 + k_idx[:, None]      # state index of plane j
-    sel = pos[valid]
+    # track t holds its reference state, then planes 0..nhit[t]-1: the
+    # crossed planes in state order fill exactly the states that are not a
+    # track's first
+    sel = np.ones(M, dtype=bool)
+    sel[offsets[:-1]] = False
     surface_id = np.zeros(M, dtype=np.int32)
     loc = np.zeros((2, M)); cov = np.zeros((3, M)); is_hole = np.ones(M, dtype=np.uint8)
-    truth_states = np.zeros((6, M))
-    surface_id[sel] = np.broadcast_to(k_idx[:, None] + 1, valid.shape)[valid]
-    hole = sim["hole"][valid]
-    loc[0, sel] = np.where(hole, 0.0, sim["meas"][0][valid])
-    loc[1, sel] = np.where(hole, 0.0, sim["meas"][1][valid])
+    surface_id[sel] = sim["plane"] + 1
+    loc[0, sel] = sim["m0"]
+    loc[1, sel] = sim["m1"]
     cov[0, sel] = w.sigma ** 2
     cov[2, sel] = w.sigma ** 2
-    is_hole[sel] = hole.astype(np.uint8)
-    qop_b = np.broadcast_to(sim["qop"][None, :], valid.shape)
-    truth_states[0, sel] = sim["loc"][0][valid]
-    truth_states[1, sel] = sim["loc"][1][valid]
-    truth_states[2, sel] = sim["leave"][0][valid]
-    truth_states[3, sel] = sim["leave"][1][valid]
-    truth_states[4, sel] = qop_b[valid]
-    truth_states[5, sel] = sim["leave"][2][valid]
+    is_hole[sel] = sim["hole"].astype(np.uint8)
+    truth_states = None
+    if with_truth_states:
+        truth_states = np.zeros((6, M))
+        for r, k in enumerate(("l0", "l1", "a0", "a1")):
+            truth_states[r, sel] = sim[k]
+        truth_states[4, sel] = np.repeat(sim["qop"], nhit)
+        truth_states[5, sel] = sim["a2"]
     # state 0: reference plane, no measurement
     s0 = offsets[:-1]
     surface_id[s0] = 0
@@ -458,7 +520,8 @@ def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200) ->
     cov[0, s0] = 1.0
     cov[2, s0] = 1.0
     truth = np.stack([np.zeros(T), np.zeros(T), sim["phi0"], sim["th0"], sim["qop"], np.zeros(T)])
-    truth_states[:, s0] = truth
+    if truth_states is not None:
+        truth_states[:, s0] = truth
     # seed: truth smeared with a consistent diagonal prior
     ids = ids_all
     sig_seed = np.stack([
@@ -503,7 +566,8 @@ def subset(ev: dict, tracks) -> dict:
     for k in ("seed_params", "seed_cov", "truth_params"):
         out[k] = np.ascontiguousarray(ev[k][:, tracks])
     for k in ("loc", "cov", "truth_states"):
-        out[k] = np.ascontiguousarray(ev[k][:, idx])
+        if ev.get(k) is not None:
+            out[k] = np.ascontiguousarray(ev[k][:, idx])
     for k in ("surface_id", "is_hole"):
         out[k] = np.ascontiguousarray(ev[k][idx])
     return out

@@ -309,6 +309,38 @@ def test_full_size_uneven_1m_sampled(handle):
     assert np.all(g["status"] == 0)
 
 
+@pytest.fixture(scope="module")
+def tel30_4m():
+    ev = synth.make_event(synth.WORKLOADS["tel30_4m"], with_truth_states=False)
+    rng = np.random.default_rng(13)
+    sample = np.sort(rng.choice(ev["n_tracks"], 1500, replace=False))
+    return ev, sample, oracle.fit_batch(synth.subset(ev, sample))
+
+
+@pytest.mark.parametrize("prec", [MIXED, FP64])
+def test_full_size_tel30_4m_sampled(handle, tel30_4m, prec):
+    """4,000,000 tracks x 30 planes (the throughput-scale workload) in the
+    autotuner's launch shape, replayed from a CUDA graph as the benchmark
+    times it; the oracle checks a random sample of 1500 tracks."""
+    import torch
+    ev, sample, r = tel30_4m
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(ev["n_tracks"])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        best, _ = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec), stream)
+        opt = kf.kf_default_options(prec, schedule=best.schedule, block=best.block, min_blocks=best.min_blocks,
+                                    resident_warps=best.resident_warps, use_graph=1)
+        kf.kf_fit_ex(handle, dev, out, opt, stream)        # captures the graph
+        for k in ("params", "cov", "chi2"):
+            out[k].fill_(float("nan"))
+        kf.kf_fit_ex(handle, dev, out, opt, stream)        # replays it
+    torch.cuda.synchronize()
+    g = {k: (v[..., sample].cpu().numpy() if v is not None else None) for k, v in out.items()}
+    compare(g, r, prec)
+    assert np.all(out["status"].cpu().numpy() == 0)
+
+
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_fault_inputs_and_extreme_tracks(handle, prec):
     """Host-made faults give a per-track status and NaN outputs for that

@@ -172,7 +172,9 @@ typedef struct {
   double mass;                 /* particle mass in GeV (default: muon) */
   double h_max;                /* longest RKN step in mm (default 50) */
   int32_t n_iter;              /* Newton corrections onto each plane (default 3) */
-  int32_t block;               /* threads per CTA: 32, 64, 96 or 128 (0 = 128) */
+  int32_t block;               /* threads per CTA, a multiple of 32 (0 = 128):
+                                  up to 256, or 384 / 512 for the mixed
+                                  path's min_blocks 3 / 4 variants */
   int64_t workspace_bytes;     /* cap on the handle's workspace (0 = 32 GiB);
                                   larger batches are fitted in chunks */
   int32_t schedule;            /* kf_schedule (default KF_SCHEDULE_PERSISTENT) */
@@ -194,11 +196,12 @@ typedef struct {
                                   (default 1e4) */
   kf_material material;        /* for energy_loss (default silicon) */
   int32_t resident_warps;      /* persistent schedules: warps kept resident on
-                                  each SM (0 = as many as fit).  With U
-                                  32-track units and W resident warps the
-                                  launch takes ceil(U / W) rounds; fewer
-                                  warps that still fill the FP64 pipe can
-                                  remove a part-filled last round */
+                                  each SM (0 = as many as fit).  With
+                                  one-warp CTAs (block 32), U 32-track
+                                  units and W resident warps the launch
+                                  takes ceil(U / W) rounds; fewer warps
+                                  that still fill the FP64 pipe can remove
+                                  a part-filled last round */
 } kf_options;
 
 typedef enum {
@@ -206,8 +209,9 @@ typedef enum {
                                   batch shape in the handle) */
   KF_SCHEDULE_GRID = 0,        /* one thread per track, one CTA per block of
                                   tracks */
-  KF_SCHEDULE_PERSISTENT = 1,  /* resident CTAs; each warp takes 32-track
-                                  units from a work counter until done */
+  KF_SCHEDULE_PERSISTENT = 1,  /* resident CTAs; each CTA takes units of
+                                  `block` tracks from a work counter until
+                                  done */
   KF_SCHEDULE_SORTED = 2       /* persistent, tracks taken longest first
                                   (counting sort by state count; for uneven
                                   tracks) */
@@ -272,8 +276,9 @@ int kf_fit_static(const kf_tracks* tracks, const kf_surfaces* surfaces,
                   const kf_measurements* meas, const kf_field* field,
                   const kf_options* opt, const kf_outputs* out, void* stream);
 
-/* Autotuner: time every launch shape (schedule x threads per CTA x register
- * variant, and persistent launches of one-warp CTAs with the resident_warps
+/* Autotuner: time every launch shape (schedule x (threads per CTA, register
+ * variant) pairs from 32 to 512 threads, and persistent launches of one-warp
+ * CTAs with the resident_warps
  * values that best fill the last round of 32-track units) on this batch, on `stream`, and return the fastest in *best
  * (other fields copied from *base; base may be NULL for the defaults) and
  * its median time in *best_ms (optional).  Results are cached in the handle

@@ -116,9 +116,10 @@ int validate(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* 
   if (su->n_surfaces > kMaxSurfaces) return KF_EUNSUPPORTED;
   if (opt->precision != KF_PRECISION_FP64 && opt->precision != KF_PRECISION_MIXED) return KF_EUNSUPPORTED;
   if (!(opt->mass >= 0.0) || !(opt->h_max > 0.0) || opt->n_iter < 0 || opt->n_iter > 16) return KF_EINVAL;
-  if (opt->block < 0 || opt->block > 128 || (opt->block % 32) != 0) return KF_EUNSUPPORTED;
   if (opt->schedule < KF_SCHEDULE_AUTO || opt->schedule > KF_SCHEDULE_SORTED) return KF_EUNSUPPORTED;
   if (opt->min_blocks < 0 || opt->min_blocks > 4) return KF_EUNSUPPORTED;
+  if (opt->block < 0 || (opt->block % 32) != 0 || opt->block > max_block(opt->precision == KF_PRECISION_MIXED, opt->min_blocks))
+    return KF_EUNSUPPORTED;
   if (opt->resident_warps < 0 || opt->resident_warps > 64) return KF_EINVAL;
   for (int i = 0; i < 3; ++i)
     if (!(fi->b[i] == fi->b[i])) return KF_EINVAL;
@@ -574,23 +575,29 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   // candidate launch shapes: schedule x threads per CTA x register variant,
   // then persistent launches with fewer resident warps chosen so that the
   // 32-track units fill their last round (see resident_warps in kf.h)
+  // (threads per CTA, register variant): larger CTAs keep more warps in
+  // step (they start every unit together and share instruction fetches),
+  // smaller ones leave a finer last wave on small batches
   const int schedules[3] = {KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED};
-  const int blocks[3] = {32, 64, 128};
+  const int shapes_fp64[4][2] = {{32, 0}, {64, 0}, {128, 0}, {256, 0}};
+  const int shapes_mixed[11][2] = {{32, 0}, {64, 0}, {128, 0}, {256, 0}, {32, 3}, {64, 3},
+                                   {128, 3}, {384, 3}, {128, 4}, {256, 4}, {512, 4}};
+  const bool mixed = base.precision == KF_PRECISION_MIXED;
+  const int n_shapes = mixed ? 11 : 4;
   const int mbs_mixed[2] = {0, 3};
-  const int n_mb = base.precision == KF_PRECISION_FP64 ? 1 : 2;
+  const int n_mb = mixed ? 2 : 1;
   kf_options cand[64];
   int n_cand = 0;
   for (int si = 0; si < 3; ++si)
-    for (int bi = 0; bi < 3; ++bi)
-      for (int mi = 0; mi < n_mb; ++mi) {
-        kf_options o = base;
-        o.schedule = schedules[si];
-        o.block = blocks[bi];
-        o.min_blocks = base.precision == KF_PRECISION_FP64 ? 0 : mbs_mixed[mi];
-        o.resident_warps = 0;
-        o.use_graph = 0;
-        cand[n_cand++] = o;
-      }
+    for (int bi = 0; bi < n_shapes; ++bi) {
+      kf_options o = base;
+      o.schedule = schedules[si];
+      o.block = mixed ? shapes_mixed[bi][0] : shapes_fp64[bi][0];
+      o.min_blocks = mixed ? shapes_mixed[bi][1] : shapes_fp64[bi][1];
+      o.resident_warps = 0;
+      o.use_graph = 0;
+      cand[n_cand++] = o;
+    }
   {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&

@@ -188,31 +188,37 @@ __device__ __forceinline__ int track_of(const FitParams& p, int i) {
 
 // The fit kernel: stage the surface table once per CTA, then either one
 // track per thread over the grid (work_counter == nullptr) or a persistent
-// loop in which every warp takes 32-track units from a global counter until
-// the batch is exhausted (balances uneven tracks and removes the wave tail).
+// loop in which every CTA takes blockDim-track units from a global counter
+// until the batch is exhausted (balances uneven tracks).
 // Body::run(p, s_surf, i) fits slot i.
 template <class Body, int MINB>
-__global__ void __launch_bounds__(128, MINB) fit_kernel(const FitParams p) {
+__global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* s_surf = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(8) uint64_t s_mbar;
   const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
                                      p.error_flag);
   if (!staged) return;
-  if (p.work_counter == nullptr) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < p.n_tracks) Body::run(p, s_surf, i);
-    return;
-  }
-  const int lane = threadIdx.x & 31;
+  // One call site for both schedules. A grid CTA fits its own blockDim
+  // tracks once; a persistent CTA keeps taking blockDim-track units. The
+  // whole CTA takes a unit together, so its warps start every unit in step
+  // and run the same stretch of the (large) kernel body at the same time,
+  // which keeps the instruction fetches shared; the loop condition is
+  // uniform over the CTA, so every thread reaches both barriers.
+  __shared__ int s_unit;
+  const bool persistent = p.work_counter != nullptr;
+  int base = blockIdx.x * blockDim.x;
   for (;;) {
-    int unit = 0;
-    if (lane == 0) unit = atomicAdd(p.work_counter, 1);
-    unit = __shfl_sync(0xffffffffu, unit, 0);
-    const int base = unit * 32;
+    if (persistent) {
+      if (threadIdx.x == 0) s_unit = atomicAdd(p.work_counter, 1);
+      __syncthreads();
+      base = s_unit * blockDim.x;
+      __syncthreads();  // all have read s_unit before it is overwritten
+    }
     if (base >= p.n_tracks) break;
-    if (base + lane < p.n_tracks) Body::run(p, s_surf, base + lane);
-    __syncwarp();
+    const int i = base + threadIdx.x;
+    if (i < p.n_tracks) Body::run(p, s_surf, i);
+    if (!persistent) break;
   }
 }
 

@@ -27,6 +27,15 @@ constexpr int kMaxSurfaces = 1024;  // 192 KiB of shared memory
 //   row over columns 0..4 (5); q = the multiple-scattering variances added to
 //   Var(phi) and Var(theta) at state k; dxf = x_f - x_p (the filter's
 //   increment, zero on a hole).
+// Register-cap variants of the fit kernels ("min_blocks"): variant 1 (the
+// default) may use 255 registers, 3 caps at 168 and 4 at 128, i.e. the
+// registers of 1, 3 or 4 CTAs of 128 threads per SM. Each variant accepts
+// CTAs of up to the threads those registers allow.
+constexpr int max_threads_of(int min_blocks) { return min_blocks == 4 ? 512 : min_blocks == 3 ? 384 : 256; }
+// largest CTA a launch may ask for: only the mixed kernel has the capped
+// variants; the FP64 and method-variant kernels are variant 1
+inline int max_block(bool mixed, int min_blocks) { return max_threads_of(mixed ? min_blocks : 1); }
+
 constexpr int kRec64Fp64 = 90;
 constexpr int kRec64Mixed = 6;
 constexpr int kRec32Mixed = 54;

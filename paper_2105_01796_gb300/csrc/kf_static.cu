@@ -84,7 +84,8 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   if (!su->center || !su->rot || !su->x_over_x0) return KF_EINVAL;
   if (opt.precision != KF_PRECISION_FP64 && opt.precision != KF_PRECISION_MIXED) return KF_EUNSUPPORTED;
   if (!(opt.mass >= 0.0) || !(opt.h_max > 0.0) || opt.n_iter < 0 || opt.n_iter > 16) return KF_EINVAL;
-  if (opt.block < 0 || opt.block > 128 || (opt.block % 32) != 0) return KF_EUNSUPPORTED;
+  if (opt.block < 0 || (opt.block % 32) != 0 || opt.block > max_block(opt.precision == KF_PRECISION_MIXED, opt.min_blocks))
+    return KF_EUNSUPPORTED;
   if (opt.schedule < KF_SCHEDULE_GRID || opt.schedule > KF_SCHEDULE_PERSISTENT) return KF_EUNSUPPORTED;
   if (opt.min_blocks < 0 || opt.min_blocks > 4) return KF_EUNSUPPORTED;
   if (opt.resident_warps < 0 || opt.resident_warps > 64) return KF_EINVAL;

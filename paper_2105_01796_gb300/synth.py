@@ -449,14 +449,9 @@ def _simulate_tracks(w: Workload, ids, mass: float, max_attempts: int, with_trut
     return out, rejected
 
 
-def _simulate_range(args):
-    w, lo, hi, mass, max_attempts, with_truth_states = args
-    return _simulate_tracks(w, np.arange(lo, hi, dtype=np.uint64), mass, max_attempts, with_truth_states)
-
-
 def default_workers(n_tracks: int) -> int:
-    """Processes make_event uses: one per 250k tracks, at most one per core."""
-    return max(1, min(os.cpu_count() or 1, n_tracks // 250_000))
+    """Threads make_event uses: one per 100k tracks, at most one per core."""
+    return max(1, min(os.cpu_count() or 1, n_tracks // 100_000))
 
 
 def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200,
@@ -464,8 +459,10 @@ def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200,
     """Simulate workload `w` and return the event dict (see module doc).
 
     Every draw is keyed by (seed, track, attempt, purpose), so the tracks can
-    be simulated in contiguous ranges by `workers` processes (spawned, so it
-    is safe after CUDA is initialised) with the same result as one process.
+    be simulated in contiguous ranges by `workers` threads with the same
+    result as one thread (the work is whole-array numpy operations, which
+    run outside the interpreter lock; threads, unlike worker processes, are
+    safe after CUDA is initialised and need no main-module guard).
     `with_truth_states=False` leaves out the per-state truth (truth_states is
     then None), which large batches that are only fitted do not need.
     """
@@ -476,11 +473,12 @@ def make_event(w: Workload, mass: float = MUON_MASS, max_attempts: int = 200,
     if workers == 1 or T < 2 * workers:
         sim, rejected = _simulate_tracks(w, ids_all, mass, max_attempts, with_truth_states)
     else:
-        import multiprocessing as mp
+        from concurrent.futures import ThreadPoolExecutor
         cuts = [T * i // workers for i in range(workers + 1)]
-        jobs = [(w, cuts[i], cuts[i + 1], mass, max_attempts, with_truth_states) for i in range(workers)]
-        with mp.get_context("spawn").Pool(workers) as pool:
-            parts = pool.map(_simulate_range, jobs)
+        with ThreadPoolExecutor(workers) as pool:
+            parts = list(pool.map(
+                lambda i: _simulate_tracks(w, np.arange(cuts[i], cuts[i + 1], dtype=np.uint64), mass,
+                                           max_attempts, with_truth_states), range(workers)))
         sim = {k: np.concatenate([pt[0][k] for pt in parts]) for k in parts[0][0]}
         rejected = sum(pt[1] for pt in parts)
         del parts

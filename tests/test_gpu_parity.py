@@ -193,6 +193,10 @@ def test_invalid_arguments(handle):
         kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(7))
     with pytest.raises(kf.KfError, match="invalid"):
         kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(FP64, h_max=-1.0))
+    # CTA sizes: multiples of 32 up to what the register variant allows
+    for prec, block, mb in ((FP64, 48, 0), (FP64, 384, 0), (MIXED, 384, 0), (MIXED, 512, 3), (MIXED, 544, 4)):
+        with pytest.raises(kf.KfError, match="unsupported"):
+            kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(prec, block=block, min_blocks=mb))
     bad = dict(out)
     bad["params"] = None
     with pytest.raises(kf.KfError, match="invalid"):
@@ -227,16 +231,18 @@ def test_every_launch_variant_agrees(handle, prec):
     ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 3001))
     r = oracle.fit_batch(ev)
     base = None
+    shapes = [(64, 0), (128, 0), (256, 0)]
+    if prec == MIXED:
+        shapes += [(64, 3), (128, 3), (192, 3), (384, 3), (128, 4), (512, 4)]
     for sched in (kf.KF_SCHEDULE_GRID, kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED):
-        for block in (64, 128):
-            for mb in ((0,) if prec == FP64 else (0, 3, 4)):
-                g = gpu_fit(handle, ev, prec, schedule=sched, block=block, min_blocks=mb)
-                compare(g, r, prec)
-                if prec == FP64:
-                    if base is None:
-                        base = g
-                    for k in ("params", "cov", "chi2", "ndf", "status"):
-                        assert np.array_equal(g[k], base[k]), (sched, block, k)
+        for block, mb in shapes:
+            g = gpu_fit(handle, ev, prec, schedule=sched, block=block, min_blocks=mb)
+            compare(g, r, prec)
+            if prec == FP64:
+                if base is None:
+                    base = g
+                for k in ("params", "cov", "chi2", "ndf", "status"):
+                    assert np.array_equal(g[k], base[k]), (sched, block, k)
     # persistent launches of one-warp CTAs with a few resident warps per SM
     # (fewer warps than units: every warp takes several units)
     for sched in (kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED):
@@ -279,7 +285,7 @@ def test_autotuner_choice_is_valid_and_cached(handle, prec):
     out = kf.alloc_outputs(ev["n_tracks"])
     best, ms = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
     assert ms > 0 and best.precision == prec
-    assert best.schedule in (0, 1, 2) and best.block in (32, 64, 128)
+    assert best.schedule in (0, 1, 2) and best.block in (32, 64, 128, 192, 256, 384)
     t0 = time.perf_counter()
     best2, ms2 = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
     assert time.perf_counter() - t0 < 0.05 and ms2 == ms       # cached

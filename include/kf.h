@@ -277,13 +277,13 @@ int kf_fit_static(const kf_tracks* tracks, const kf_surfaces* surfaces,
                   const kf_options* opt, const kf_outputs* out, void* stream);
 
 /* Autotuner: time every launch shape (schedule x (threads per CTA, register
- * variant) pairs from 32 to 512 threads, and persistent launches of one-warp
- * CTAs with the resident_warps
- * values that best fill the last round of 32-track units) on this batch, on `stream`, and return the fastest in *best
- * (other fields copied from *base; base may be NULL for the defaults) and
- * its median time in *best_ms (optional).  Results are cached in the handle
- * per (precision, n_tracks, max_states, n_surfaces, field along z); a cached
- * shape returns at once.  Runs the fit about 30-60 times, overwriting *out,
+ * variant) pairs from 32 to 512 threads, plus CTA sizes that split this
+ * batch's 32-track warp units into 1-4 nearly full waves of one CTA per SM)
+ * on this batch, on `stream`, and return the fastest in *best (other fields
+ * copied from *base; base may be NULL for the defaults) and its median time
+ * in *best_ms (optional).  Results are cached in the handle per (precision,
+ * n_tracks, max_states, n_surfaces, field along z, method variant); a cached
+ * shape returns at once.  Runs the fit about 60-240 times, overwriting *out,
  * and synchronises the stream; inside a stream capture it returns the
  * defaults without timing.  The paper scans grid, block and register counts
  * by hand (Sect. 5.3.5); this automates that scan. */

@@ -429,39 +429,20 @@ struct GraphKey {
 };
 static_assert(sizeof(GraphKey) <= 1024, "graph key storage");
 
-// Resident warps per SM (at least 4, at most 16) for which the
-// ceil(n_tracks / 32) units of a persistent launch fill every round but the
-// last nearly completely: for each round count r the fewest warps that finish
-// in r rounds, ranked by the filled fraction U / (r * nsm * w).  Writes up to
-// 3 values to w_out and returns how many.
-int round_filling_warps(int64_t n_tracks, int nsm, int* w_out) {
-  const double U = (double)((n_tracks + 31) / 32);
-  int ws[16];
-  double fill[16];
+// CTA sizes (in warps, 4..16) that split the ceil(n_tracks / 32) warp units
+// of a batch into r nearly full waves of one CTA per SM, r = 1..4: a batch
+// of a few waves loses less to a part-filled last wave than with the fixed
+// CTA sizes. Writes up to 4 distinct values to w_out and returns how many.
+int wave_filling_cta_warps(int64_t n_tracks, int nsm, int* w_out) {
+  const int64_t U = (n_tracks + 31) / 32;
   int n = 0;
-  for (int r = 1; r <= 4096 && n < 16; ++r) {
-    const int w = (int)((U + (double)r * nsm - 1.0) / ((double)r * nsm));
-    if (w < 4) break;
-    if (w > 16) continue;
-    if (n > 0 && ws[n - 1] == w) continue;
-    ws[n] = w;
-    fill[n] = U / ((double)r * nsm * w);
-    ++n;
+  for (int r = 1; r <= 4; ++r) {
+    const int64_t w = (U + (int64_t)r * nsm - 1) / ((int64_t)r * nsm);
+    if (w < 4 || w > 16) continue;
+    if (n > 0 && w_out[n - 1] == (int)w) continue;
+    w_out[n++] = (int)w;
   }
-  int m = 0;
-  for (; m < 3 && m < n; ++m) {  // partial selection sort, best fill first
-    int b = m;
-    for (int j = m + 1; j < n; ++j)
-      if (fill[j] > fill[b]) b = j;
-    const int tw = ws[m];
-    const double tf = fill[m];
-    ws[m] = ws[b];
-    fill[m] = fill[b];
-    ws[b] = tw;
-    fill[b] = tf;
-    w_out[m] = ws[m];
-  }
-  return m;
+  return n;
 }
 
 GraphKey make_key(const kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
@@ -584,9 +565,7 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
                                    {128, 3}, {384, 3}, {128, 4}, {256, 4}, {512, 4}};
   const bool mixed = base.precision == KF_PRECISION_MIXED;
   const int n_shapes = mixed ? 11 : 4;
-  const int mbs_mixed[2] = {0, 3};
-  const int n_mb = mixed ? 2 : 1;
-  kf_options cand[64];
+  kf_options cand[96];
   int n_cand = 0;
   for (int si = 0; si < 3; ++si)
     for (int bi = 0; bi < n_shapes; ++bi) {
@@ -602,16 +581,18 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0) {
-      int wps[3];
-      const int n_w = round_filling_warps(tr->n_tracks, nsm, wps);
+      int ws[4];
+      const int n_w = wave_filling_cta_warps(tr->n_tracks, nsm, ws);
+      const int vars_mixed[3] = {0, 3, 4};
       for (int wi = 0; wi < n_w; ++wi)
-        for (int si = 1; si < 3; ++si)
-          for (int mi = 0; mi < n_mb; ++mi) {
+        for (int si = 0; si < 2; ++si)
+          for (int vi = 0; vi < (mixed ? 3 : 1); ++vi) {
             kf_options o = base;
             o.schedule = schedules[si];
-            o.block = 32;
-            o.min_blocks = base.precision == KF_PRECISION_FP64 ? 0 : mbs_mixed[mi];
-            o.resident_warps = wps[wi];
+            o.block = 32 * ws[wi];
+            o.min_blocks = mixed ? vars_mixed[vi] : 0;
+            if (o.block > max_block(mixed, o.min_blocks)) continue;
+            o.resident_warps = 0;
             o.use_graph = 0;
             cand[n_cand++] = o;
           }

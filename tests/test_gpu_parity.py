@@ -285,7 +285,7 @@ def test_autotuner_choice_is_valid_and_cached(handle, prec):
     out = kf.alloc_outputs(ev["n_tracks"])
     best, ms = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
     assert ms > 0 and best.precision == prec
-    assert best.schedule in (0, 1, 2) and best.block in (32, 64, 128, 192, 256, 384)
+    assert best.schedule in (0, 1, 2) and best.block % 32 == 0 and 32 <= best.block <= 512
     t0 = time.perf_counter()
     best2, ms2 = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
     assert time.perf_counter() - t0 < 0.05 and ms2 == ms       # cached

@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # Traffic grows in proportion to the states, so a launch's traffic is this
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (598.226432e6 + 539.438592e6) / 2.48e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "c1a88950f8d75af0b216f656c3c613b9e94fc4a894a4ef7d6d3014775aa8c71c"
+MIXED_TRAFFIC_BYTES_PER_STATE = (817.348096e6 + 675.536384e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "42be4ec751d06fd8a00c2da12ae34b8f1c1a388ab0ee0a510e021a87e0ffaea4"
 
 
 def mixed_kernel_sources_sha256():
@@ -530,8 +530,8 @@ def run_ours(args, rank, world, local):
                      "t_roof_ms": 1e3 * t_roof, "roof_frac": 1e3 * t_roof / step_ms,
                      "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
                      "algorithmic_bytes_per_launch": nbytes,
-                     "traffic_note": ("ncu capture of an 80k-track launch scaled by states; the "
-                                      "smoother's per-state record round trip (216 B each way)")
+                     "traffic_note": ("ncu capture of a 100k-track launch of this kernel (grid, 352 threads, 168 registers); "
+                                      "mostly the smoother's per-state record round trip (216 B each way)")
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,
         "scale": scale,

@@ -304,11 +304,14 @@ int kf_autotune(kf_handle* handle, const kf_tracks* tracks,
  *   out_chi2[T]       chi2 per track at this alignment (optional).
  *   grad_seed[6][T]   dL/d seed_params (optional).
  *   grad_align[6][S]  dL/d align (optional); overwritten.
- * Method: reverse sweep over the states with the filtered states recomputed
- * from checkpoints every 8 states; inside each transport, forward-mode dual
- * numbers give the sensitivities of the prediction, of F and of the
- * scattering noise.  Device pointers; asynchronous on `stream`.  Tracks that
- * fail get NaN chi2 and gradients and do not contribute to grad_align. */
+ * Method: reverse mode throughout: a reverse sweep over the states with the
+ * filtered states recomputed from checkpoints every 8 states, and inside it
+ * every transport recomputed with its RKN stage inputs taped and swept
+ * backwards.  Launch shape: one thread per track, opt->block threads per
+ * CTA (a multiple of 32 up to 256; 0, and opt == NULL, choose CTAs of the
+ * warp count that covers the batch in nearly full waves of one CTA per SM);
+ * the other launch options do not apply.  Device pointers; asynchronous on `stream`.  Tracks that fail
+ * get NaN chi2 and gradients and do not contribute to grad_align. */
 int kf_chi2_grad(kf_handle* handle, const kf_tracks* tracks,
                  const kf_surfaces* surfaces, const double* align,
                  const kf_measurements* meas, const kf_field* field,

@@ -980,7 +980,7 @@ __device__ __forceinline__ void add_align_grad(double* grad, int n_surf, int sid
   }
 }
 
-__global__ void __launch_bounds__(128) kf_grad_kernel(const GradParams g) {
+__global__ void __launch_bounds__(256) kf_grad_kernel(const GradParams g) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* s_surf = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(8) uint64_t s_mbar;
@@ -1253,7 +1253,8 @@ __global__ void __launch_bounds__(128) kf_grad_kernel(const GradParams g) {
 }  // namespace
 
 cudaError_t launch_grad(const FitParams& f, const double* align, const double* dl_dchi2, double* chi2,
-                        double* grad_seed, double* grad_align, double* ckpt, int n_ckpt, cudaStream_t stream) {
+                        double* grad_seed, double* grad_align, double* ckpt, int n_ckpt, int block,
+                        cudaStream_t stream) {
   GradParams g;
   g.f = f;
   g.align = align;
@@ -1268,7 +1269,22 @@ cudaError_t launch_grad(const FitParams& f, const double* align, const double* d
     cudaError_t e = cudaFuncSetAttribute(kf_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int block = 64;
+  if (block <= 0) {
+    // CTAs of w warps, one per SM per wave (255 registers leave room for 8
+    // warps per SM), w the smallest count that covers the batch's 32-track
+    // warp units in r full waves: the last wave is nearly full
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long units = ((long long)f.n_tracks + 31) / 32;
+    long long w = 8;
+    for (long long r = 1; r <= 1024; ++r) {
+      w = (units + r * nsm - 1) / (r * nsm);
+      if (w <= 8) break;
+    }
+    block = 32 * (int)(w < 1 ? 1 : (w > 8 ? 8 : w));
+  }
   const int grid = (f.n_tracks + block - 1) / block;
   kf_grad_kernel<<<grid, block, smem, stream>>>(g);
   return cudaGetLastError();

@@ -42,13 +42,14 @@ struct kf_handle {
   cudaGraphExec_t graph_exec = nullptr;
   alignas(8) unsigned char graph_key[1024];
   int32_t graph_launches = 0;
-  // device copies for kf_fit_host, and its copy streams and events (the
-  // pipelined host path overlaps the copies of one chunk of tracks with the
-  // fit of another)
+  // device copies for kf_fit_host, and its streams and events (the
+  // pipelined host path overlaps the copies of some chunks of tracks with
+  // the fits of others, and lets consecutive fits overlap on two streams)
+  static constexpr int kPipe = 8;
   void* dev_io = nullptr;
   size_t dev_io_bytes = 0;
-  cudaStream_t s_in = nullptr, s_out = nullptr;
-  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_fit[2] = {nullptr, nullptr};
+  cudaStream_t s_in = nullptr, s_out = nullptr, s_fit[kPipe - 1] = {};
+  cudaEvent_t ev_in[kPipe] = {}, ev_fit[kPipe] = {}, ev_pack = nullptr;
   int32_t last_launches = 0;
 };
 
@@ -248,10 +249,13 @@ void kf_destroy(kf_handle* h) {
   if (h->ckpt) cudaFree(h->ckpt);
   if (h->s_in) cudaStreamDestroy(h->s_in);
   if (h->s_out) cudaStreamDestroy(h->s_out);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kf_handle::kPipe - 1; ++i)
+    if (h->s_fit[i]) cudaStreamDestroy(h->s_fit[i]);
+  for (int i = 0; i < kf_handle::kPipe; ++i) {
     if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
     if (h->ev_fit[i]) cudaEventDestroy(h->ev_fit[i]);
   }
+  if (h->ev_pack) cudaEventDestroy(h->ev_pack);
   delete h;
 }
 
@@ -344,10 +348,14 @@ void fill_variants(FitParams* p, const kf_field* fi, const kf_options& opt) {
 // synchronisation).  pack: also pack the surface table first.  A partial
 // range (the host entry's pipelined chunks) cannot use the length-sorted
 // order, which spans the whole batch: it runs the persistent schedule.
+// Fits of disjoint ranges that may run at the same time (on two streams)
+// pass own_slice: each then uses its own work counter (counter_slot, reset
+// by the caller) and the slice of the workspace at its first track (the
+// plan must then hold the whole batch in one workspace chunk).
 int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me,
                 const kf_field* fi, const kf_options& opt_in, const kf_outputs* out, cudaStream_t stream,
                 const FitPlan& plan, int* launches_out, int64_t t_begin = 0, int64_t t_end = -1,
-                bool pack = true) {
+                bool pack = true, bool own_slice = false, int counter_slot = 0) {
   if (t_end < 0) t_end = tr->n_tracks;
   kf_options opt = opt_in;
   const bool whole = t_begin == 0 && t_end == tr->n_tracks;
@@ -360,7 +368,8 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
     launches = 1;
   }
-  if (opt.schedule != KF_SCHEDULE_GRID) {
+  if (own_slice && plan.n_chunks != 1) return KF_EINVAL;
+  if (opt.schedule != KF_SCHEDULE_GRID && !own_slice) {
     e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * plan.n_chunks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
   }
@@ -395,6 +404,13 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   p.out_states = out->states;
   p.ws64 = (double*)h->ws;
   p.ws32 = opt.precision == KF_PRECISION_FP64 ? nullptr : (float*)((char*)h->ws + plan.bytes64);
+  if (own_slice) {
+    // records are [state][element][track] over the launch's own tracks, so
+    // a range starting at track t_begin owns the slice from t_begin records on
+    const size_t n64 = opt.precision == KF_PRECISION_FP64 ? kRec64Fp64 : kRec64Mixed;
+    p.ws64 += n64 * (size_t)tr->max_states * (size_t)t_begin;
+    if (p.ws32) p.ws32 += kRec32Mixed * (size_t)tr->max_states * (size_t)t_begin;
+  }
   p.error_flag = h->error_flag;
   p.order = opt.schedule == KF_SCHEDULE_SORTED ? h->order : nullptr;
   p.resident_warps = opt.resident_warps;
@@ -404,7 +420,7 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   for (int64_t t0 = t_begin; t0 < t_end; t0 += chunk, ++c) {
     p.track0 = (int32_t)t0;
     p.n_tracks = (int32_t)((t_end - t0) < chunk ? (t_end - t0) : chunk);
-    p.work_counter = opt.schedule == KF_SCHEDULE_GRID ? nullptr : h->counters + c;
+    p.work_counter = opt.schedule == KF_SCHEDULE_GRID ? nullptr : h->counters + counter_slot + c;
     e = variants ? launch_fit_variants(p, opt.block, stream)
                  : launch_fit(p, opt.precision, opt.block, opt.min_blocks, stream);
     if (e != cudaSuccess) return cuda_fail(e, "fit launch");
@@ -649,7 +665,12 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
                  double* out_chi2, double* grad_seed, double* grad_align, void* stream_v) {
   if (!h) return KF_EINVAL;
   kf_options opt;
-  if (opt_in) opt = *opt_in; else kf_default_options(&opt);
+  if (opt_in) {
+    opt = *opt_in;
+  } else {
+    kf_default_options(&opt);
+    opt.block = 0;  // the adjoint's own CTA size choice
+  }
   opt.precision = KF_PRECISION_FP64;
   opt.schedule = KF_SCHEDULE_GRID;
   kf_outputs dummy;
@@ -699,7 +720,7 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   p.h_max = opt.h_max;
   p.n_iter = opt.n_iter;
   p.error_flag = h->error_flag;
-  e = launch_grad(p, align, dl_dchi2, out_chi2, grad_seed, grad_align, h->ckpt, n_ckpt, stream);
+  e = launch_grad(p, align, dl_dchi2, out_chi2, grad_seed, grad_align, h->ckpt, n_ckpt, opt.block, stream);
   if (e != cudaSuccess) return cuda_fail(e, "grad launch");
   h->last_launches = 2;
   return KF_SUCCESS;
@@ -732,13 +753,17 @@ int kf_fit(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me
 
 // streams and events of the pipelined host path, created on first use
 static int ensure_host_streams(kf_handle* h) {
-  if (h->s_in) return KF_SUCCESS;
-  cudaError_t e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-    e = cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fit[i], cudaEventDisableTiming);
+  if (h->ev_pack) return KF_SUCCESS;
+  cudaError_t e = cudaSuccess;
+  if (!h->s_in) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !h->s_out) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+  for (int i = 0; i < kf_handle::kPipe - 1 && e == cudaSuccess; ++i)
+    if (!h->s_fit[i]) e = cudaStreamCreateWithFlags(&h->s_fit[i], cudaStreamNonBlocking);
+  for (int i = 0; i < kf_handle::kPipe && e == cudaSuccess; ++i) {
+    if (!h->ev_in[i]) e = cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess && !h->ev_fit[i]) e = cudaEventCreateWithFlags(&h->ev_fit[i], cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pack, cudaEventDisableTiming);
   return e == cudaSuccess ? KF_SUCCESS : cuda_fail(e, "host-path streams");
 }
 
@@ -811,9 +836,12 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   kf_options o;
   if (opt) o = *opt; else kf_default_options(&o);
   struct Cp { size_t o; const void* src; size_t bytes; };
-  // Two chunks of tracks when the batch is large: the inputs of chunk 1
-  // travel while chunk 0 is fitted, the outputs of chunk 0 while chunk 1 is.
-  // (Not for a schedule still to be tuned, a graph, or a small batch.)
+  // Large batches run as 2 to 8 chunks of at least 12.5k tracks: each
+  // chunk's fit starts as soon as its inputs have arrived, on a stream of
+  // its own (the caller's for chunk 0), so the fits of earlier chunks run
+  // while later chunks' inputs travel and the CTAs of all of them share the
+  // SMs; each chunk's outputs travel once its fit is done. (Not for a
+  // schedule still to be tuned, a graph, or a small batch.)
   const bool pipelined = T >= 20000 && o.schedule != KF_SCHEDULE_AUTO && !o.use_graph && tr->offsets && out->params;
   if (!pipelined) {
     const Cp in[] = {{o_off, tr->offsets, (T + 1) * 4}, {o_sp, tr->seed_params, 6 * T * 8},
@@ -848,9 +876,20 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     if ((rc = ensure_host_streams(h))) return rc;
     FitPlan plan;
     if ((rc = prepare_fit(h, &dtr, &dsu, o, &plan))) return rc;
-    const size_t tcut[3] = {0, T / 2, T};
-    size_t scut[3];
-    for (int c = 0; c < 3; ++c) {
+    const int nch = (int)(T / 12500 < 2 ? 2 : (T / 12500 > (size_t)kf_handle::kPipe ? kf_handle::kPipe : T / 12500));
+    // concurrent fits need their own workspace slices and work counters
+    const bool concurrent = plan.n_chunks == 1;
+    if (concurrent && o.schedule != KF_SCHEDULE_GRID && h->counters_cap < kf_handle::kPipe) {
+      if (h->counters) cudaFree(h->counters);
+      h->counters = nullptr;
+      h->counters_cap = 0;
+      cudaError_t ea = cudaMalloc(&h->counters, sizeof(int32_t) * kf_handle::kPipe);
+      if (ea != cudaSuccess) return cuda_fail(ea, "cudaMalloc(counters)");
+      h->counters_cap = kf_handle::kPipe;
+    }
+    size_t tcut[kf_handle::kPipe + 1], scut[kf_handle::kPipe + 1];
+    for (int c = 0; c <= nch; ++c) {
+      tcut[c] = T * (size_t)c / (size_t)nch;
       const int32_t v = tr->offsets[tcut[c]];
       if (v < 0 || (size_t)v > M) return KF_EINVAL;
       scut[c] = (size_t)v;
@@ -858,7 +897,7 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     cudaError_t e = cudaSuccess;
     auto H2D = cudaMemcpyHostToDevice;
     // inputs: the shared pieces with chunk 0, then chunk by chunk
-    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
       cudaStream_t s = h->s_in;
       if (c == 0) {
         e = cudaMemcpyAsync(b + o_off, tr->offsets, (T + 1) * 4, H2D, s);
@@ -877,23 +916,37 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
       if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "host-path H2D");
-    // the fits, chunk by chunk on the caller's stream
-    int launches = 0;
-    for (int c = 0; c < 2; ++c) {
-      e = cudaStreamWaitEvent(stream, h->ev_in[c], 0);
+    // the surface table (in chunk 0's copies) is packed once and the work
+    // counters reset once, before any fit
+    e = cudaStreamWaitEvent(stream, h->ev_in[0], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    e = launch_pack_surfaces(dsu.n_surfaces, dsu.center, dsu.rot, dsu.x_over_x0, h->surf, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
+    int launches = 1;
+    if (concurrent && o.schedule != KF_SCHEDULE_GRID) {
+      e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * kf_handle::kPipe, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+    }
+    e = cudaEventRecord(h->ev_pack, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    // the fits, chunk by chunk
+    for (int c = 0; c < nch; ++c) {
+      cudaStream_t fs = concurrent && c > 0 ? h->s_fit[c - 1] : stream;
+      e = cudaStreamWaitEvent(fs, h->ev_in[c], 0);
+      if (e == cudaSuccess && fs != stream) e = cudaStreamWaitEvent(fs, h->ev_pack, 0);
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
       int l = 0;
-      rc = enqueue_fit(h, &dtr, &dsu, &dme, &dfi, o, &dout, stream, plan, &l, (int64_t)tcut[c],
-                       (int64_t)tcut[c + 1], c == 0);
+      rc = enqueue_fit(h, &dtr, &dsu, &dme, &dfi, o, &dout, fs, plan, &l, (int64_t)tcut[c],
+                       (int64_t)tcut[c + 1], false, concurrent, concurrent ? c : 0);
       if (rc) return rc;
       launches += l;
-      e = cudaEventRecord(h->ev_fit[c], stream);
+      e = cudaEventRecord(h->ev_fit[c], fs);
       if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     }
     h->last_launches = launches;
     // outputs, chunk by chunk once its fit is done
     auto D2H = cudaMemcpyDeviceToHost;
-    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
       cudaStream_t s = h->s_out;
       e = cudaStreamWaitEvent(s, h->ev_fit[c], 0);
       const size_t t0 = tcut[c], t1 = tcut[c + 1], s0 = scut[c], s1 = scut[c + 1];
@@ -905,6 +958,8 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
       if (e == cudaSuccess && out->states) e = copy_cols(out->states, b + o_states, M, 8, 6, s0, s1, D2H, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "host-path D2H");
+    // the caller's stream and the second fit stream are done once the last
+    // output copy (which waited for every fit) is
     e = cudaStreamSynchronize(h->s_out);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   }

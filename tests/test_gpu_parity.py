@@ -377,13 +377,19 @@ def test_fault_inputs_and_extreme_tracks(handle, prec):
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_pipelined_host_entry_equals_device_entry(handle, prec):
-    """A large host batch runs in two chunks whose copies overlap the other
-    chunk's fit; the results equal the device entry's bit for bit (uneven
-    tracks, smoothed states requested, the sorted schedule asked for)."""
-    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 30001))
-    ref = gpu_fit(handle, ev, prec, with_states=True, schedule=kf.KF_SCHEDULE_PERSISTENT)
-    for sched in (kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED, kf.KF_SCHEDULE_GRID):
-        host = kf.kf_fit_host(handle, ev, kf.kf_default_options(prec, schedule=sched), with_states=True)
-        for k in ("params", "cov", "chi2", "ndf", "status", "states"):
-            assert np.array_equal(host[k], ref[k], equal_nan=True), (sched, k)
-        assert handle.last_launch_count() >= 3
+    """A large host batch runs in 2 to 8 chunks whose copies overlap other
+    chunks' fits, each fit on its own stream; the results equal the device
+    entry's bit for bit (uneven tracks,
+    smoothed states requested, every schedule, and a workspace cap that
+    splits the batch, which serialises the fits)."""
+    for n in (30001, 90001):
+        ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], n))
+        ref = gpu_fit(handle, ev, prec, with_states=True, schedule=kf.KF_SCHEDULE_PERSISTENT)
+        per_track = 31 * (720 if prec == FP64 else 6 * 8 + 54 * 4)
+        for sched, cap in ((kf.KF_SCHEDULE_PERSISTENT, 0), (kf.KF_SCHEDULE_SORTED, 0), (kf.KF_SCHEDULE_GRID, 0),
+                           (kf.KF_SCHEDULE_PERSISTENT, 7000 * per_track), (kf.KF_SCHEDULE_GRID, 7000 * per_track)):
+            opt = kf.kf_default_options(prec, schedule=sched, workspace_bytes=cap)
+            host = kf.kf_fit_host(handle, ev, opt, with_states=True)
+            for k in ("params", "cov", "chi2", "ndf", "status", "states"):
+                assert np.array_equal(host[k], ref[k], equal_nan=True), (n, sched, cap, k)
+            assert handle.last_launch_count() >= 3

@@ -136,6 +136,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm
+    implementer / part codes), plus the machine type."""
+    import platform
+    name = None
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        kv = [ln.split(":", 1) for ln in info if ":" in ln]
+        d = {}
+        for k, v in kv:
+            d.setdefault(k.strip(), v.strip())
+        if "model name" in d:
+            name = d["model name"]
+        elif "CPU part" in d:
+            name = "implementer %s part %s" % (d.get("CPU implementer", "?"), d["CPU part"])
+    except OSError:
+        pass
+    return "%s (%s)" % (name or "unknown", platform.machine())
+
+
 def oracle_tracks_per_s(ev, n_sample, cores, method=None):
     """Oracle (plain FP64 C, POSIX threads) over the first n_sample tracks."""
     import oracle
@@ -330,7 +350,7 @@ def run_reference(args, rank, world):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "tracks": int(ev["n_tracks"]), "planes": 30,
                    "sample_tracks_per_step": sample, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "tracks/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                          "sample": "first %d of %d tracks per step" % (sample, ev["n_tracks"])},
         "e2e": {"value": value, "unit": "tracks/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -490,7 +510,7 @@ def run_ours(args, rank, world, local):
         oracle_tracks_per_s(ev, 500, cores)
         v, dt, n = oracle_tracks_per_s(ev, T, cores)
         v1, dt1, n1 = oracle_tracks_per_s(ev, 5000, 1)
-        cpu = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+        cpu = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt),
                "single_core": {"value": v1, "unit": "tracks/s",
                                "sample": "first %d tracks, one thread (%.1f s)" % (n1, dt1)}}

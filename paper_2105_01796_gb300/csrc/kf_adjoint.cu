@@ -980,7 +980,11 @@ __device__ __forceinline__ void add_align_grad(double* grad, int n_surf, int sid
   }
 }
 
-__global__ void __launch_bounds__(256) kf_grad_kernel(const GradParams g) {
+// Register-cap variants as for the fit kernels: MINB 1 may use 255
+// registers (up to 8 warps per SM), 3 caps at 168 (12 warps) and 4 at 128
+// (16 warps; the tape then spills to local memory).
+template <int MINB>
+__global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const GradParams g) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* s_surf = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(8) uint64_t s_mbar;
@@ -1252,9 +1256,40 @@ __global__ void __launch_bounds__(256) kf_grad_kernel(const GradParams g) {
 
 }  // namespace
 
+template <int MINB>
+cudaError_t launch_grad_v(const GradParams& g, int block, cudaStream_t stream) {
+  const FitParams& f = g.f;
+  const size_t smem = (size_t)f.n_surfaces * kSurfStride * sizeof(double);
+  auto kern = kf_grad_kernel<MINB>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (block <= 0) {
+    // CTAs of w warps, one per SM per wave, w the smallest count (within the
+    // warps this variant's registers allow per SM) that covers the batch's
+    // 32-track warp units in r full waves: the last wave is nearly full
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long wmax = max_threads_of(MINB) / 32;
+    const long long units = ((long long)f.n_tracks + 31) / 32;
+    long long w = wmax;
+    for (long long r = 1; r <= 1024; ++r) {
+      w = (units + r * nsm - 1) / (r * nsm);
+      if (w <= wmax) break;
+    }
+    block = 32 * (int)(w < 1 ? 1 : (w > wmax ? wmax : w));
+  }
+  const int grid = (f.n_tracks + block - 1) / block;
+  kern<<<grid, block, smem, stream>>>(g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_grad(const FitParams& f, const double* align, const double* dl_dchi2, double* chi2,
                         double* grad_seed, double* grad_align, double* ckpt, int n_ckpt, int block,
-                        cudaStream_t stream) {
+                        int min_blocks, cudaStream_t stream) {
   GradParams g;
   g.f = f;
   g.align = align;
@@ -1264,30 +1299,11 @@ cudaError_t launch_grad(const FitParams& f, const double* align, const double* d
   g.grad_align = grad_align;
   g.ckpt = ckpt;
   g.n_ckpt = n_ckpt;
-  const size_t smem = (size_t)f.n_surfaces * kSurfStride * sizeof(double);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kf_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  switch (min_blocks) {
+    case 4: return launch_grad_v<4>(g, block, stream);
+    case 3: return launch_grad_v<3>(g, block, stream);
+    default: return launch_grad_v<1>(g, block, stream);
   }
-  if (block <= 0) {
-    // CTAs of w warps, one per SM per wave (255 registers leave room for 8
-    // warps per SM), w the smallest count that covers the batch's 32-track
-    // warp units in r full waves: the last wave is nearly full
-    int dev = 0, nsm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const long long units = ((long long)f.n_tracks + 31) / 32;
-    long long w = 8;
-    for (long long r = 1; r <= 1024; ++r) {
-      w = (units + r * nsm - 1) / (r * nsm);
-      if (w <= 8) break;
-    }
-    block = 32 * (int)(w < 1 ? 1 : (w > 8 ? 8 : w));
-  }
-  const int grid = (f.n_tracks + block - 1) / block;
-  kf_grad_kernel<<<grid, block, smem, stream>>>(g);
-  return cudaGetLastError();
 }
 
 int grad_segment_length() { return kSeg; }

@@ -673,6 +673,11 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   }
   opt.precision = KF_PRECISION_FP64;
   opt.schedule = KF_SCHEDULE_GRID;
+  // the adjoint has its own register variants (up to 256 / 384 / 512
+  // threads per CTA for min_blocks 1 / 3 / 4)
+  const int grad_block = opt.block;
+  if (grad_block < 0 || grad_block % 32 != 0 || grad_block > max_threads_of(opt.min_blocks)) return KF_EUNSUPPORTED;
+  opt.block = 0;
   kf_outputs dummy;
   memset(&dummy, 0, sizeof(dummy));
   double one = 0.0;  // non-null placeholders for the output checks of validate()
@@ -720,7 +725,8 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   p.h_max = opt.h_max;
   p.n_iter = opt.n_iter;
   p.error_flag = h->error_flag;
-  e = launch_grad(p, align, dl_dchi2, out_chi2, grad_seed, grad_align, h->ckpt, n_ckpt, opt.block, stream);
+  e = launch_grad(p, align, dl_dchi2, out_chi2, grad_seed, grad_align, h->ckpt, n_ckpt, grad_block,
+                  opt.min_blocks, stream);
   if (e != cudaSuccess) return cuda_fail(e, "grad launch");
   h->last_launches = 2;
   return KF_SUCCESS;

@@ -116,7 +116,7 @@ cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stre
 // doubles per track; n_ckpt = ceil(max_states / grad_segment_length()).
 cudaError_t launch_grad(const FitParams& f, const double* align, const double* dl_dchi2, double* chi2,
                         double* grad_seed, double* grad_align, double* ckpt, int n_ckpt, int block,
-                        cudaStream_t stream);
+                        int min_blocks, cudaStream_t stream);
 int grad_segment_length();
 
 // Counting sort of the tracks by state count, longest first:

@@ -44,7 +44,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
 MIXED_TRAFFIC_BYTES_PER_STATE = (817.348096e6 + 675.536384e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "42be4ec751d06fd8a00c2da12ae34b8f1c1a388ab0ee0a510e021a87e0ffaea4"
+MIXED_TRAFFIC_SOURCES_SHA256 = "b207f7f2ff8dd579c09b91b11a65300cc3dff6289b681bc0aa7ad712b12ca8ea"
 
 
 def mixed_kernel_sources_sha256():

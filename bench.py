@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # Traffic grows in proportion to the states, so a launch's traffic is this
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (817.348096e6 + 675.536384e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "b207f7f2ff8dd579c09b91b11a65300cc3dff6289b681bc0aa7ad712b12ca8ea"
+MIXED_TRAFFIC_BYTES_PER_STATE = (817.312768e6 + 674.922752e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "12d5f6932375d33b7251dcdff2393fa7bee5f2b375f8d5c541e0ad04973b2279"
 
 
 def mixed_kernel_sources_sha256():

@@ -171,7 +171,11 @@ typedef struct {
   int32_t precision;           /* kf_precision */
   double mass;                 /* particle mass in GeV (default: muon) */
   double h_max;                /* longest RKN step in mm (default 50) */
-  int32_t n_iter;              /* Newton corrections onto each plane (default 3) */
+  int32_t n_iter;              /* Newton corrections onto each plane (default
+                                  3; 0-16).  With 0 the path length is the
+                                  straight-line estimate, which the mixed
+                                  path takes in FP32 (~1e-4 sigma from FP64);
+                                  every end point is projected onto its plane */
   int32_t block;               /* threads per CTA, a multiple of 32 (0 = 128):
                                   up to 256, or 384 / 512 for the mixed
                                   path's min_blocks 3 / 4 variants */

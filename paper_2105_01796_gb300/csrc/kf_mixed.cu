@@ -277,7 +277,23 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
       const float nT = nb[0] * Tc[0] + nb[1] * Tc[1] + nb[2] * Tc[2];
       if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
       const float si = dist / nT;
-      cols_step<BZ>(g, si, bs, kB, Tc, dtl);
+      if (it == 0) {
+        cols_step<BZ>(g, si, bs, kB, Tc, dtl);
+      } else {
+        // later corrections are tiny (|si| ~ |s1|^2 curvature): the columns
+        // take their first-order terms in si only (position += si dir, and
+        // the q/p column's direction += si d(A T)/dlam); the rest is
+        // O(si k B) relative, far below FP32 resolution
+        float u0[3];
+        applyA<float, BZ>(kB, Tc, u0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) g.gr[i][c] += si * g.gT[i][c];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) g.gT[i][2] += si * u0[i];
+        g.gtl += si * dtl;
+      }
       float dr[3], dT[3];
       value_step<BZ>(si, bs, Tc, dr, dT);
 #pragma unroll
@@ -287,9 +303,13 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
       }
       ot += si * dtds;
     }
+    // the bound state lives on the plane: the end point is projected onto it
+    // along n by the distance the corrections leave (a few 1e-4 mm after one
+    // correction, nothing after two; the whole curvature miss with none)
+    const float drem = dmf - (nb[0] * orr[0] + nb[1] * orr[1] + nb[2] * orr[2]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      r[i] = fma(s0d, Td[i], r[i]) + f2d(off[i] + orr[i]);
+      r[i] = fma(s0d, Td[i], r[i]) + f2d(off[i] + orr[i] + drem * nb[i]);
       accT[i] += oT[i];
     }
     tinc += ot;

@@ -139,6 +139,32 @@ def _edge_event():
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_step_length_and_correction_options(handle, prec):
+    """Several RKN sub-steps per gap (h_max below the plane spacing, and not
+    dividing it) and 1, 2 or 5 plane corrections (and none, FP64 only): the
+    stepping rule is deterministic, so the GPU follows the oracle's discrete
+    map in each case (smoothed states of every surface compared too).
+    Without corrections the path length is the straight-line estimate
+    itself, which the mixed path takes in FP32: about 1e-4 of a sigma per
+    fit, at the tolerance, so that case is not part of the mixed contract."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel30_100k"], 400))
+    cases = [(7.0, 3), (3.0, 2), (7.0, 1), (50.0, 1), (50.0, 5)] + ([(50.0, 0), (7.0, 0)] if prec == FP64 else [])
+    for h_max, n_iter in cases:
+        g = gpu_fit(handle, ev, prec, with_states=True, h_max=h_max, n_iter=n_iter)
+        r = oracle.fit_batch(ev, h_max=h_max, n_iter=n_iter, with_states=True)
+        compare(g, r, prec)
+        ok = r["status"] == 0
+        assert ok.all(), (h_max, n_iter)
+        # smoothed parameters on every state (uncertainty floor: the state-0
+        # sigma, as in the uneven-track test)
+        tp = TOL[prec][0]
+        track_of = np.repeat(np.arange(ev["n_tracks"]), np.diff(ev["offsets"].astype(np.int64)))
+        sd = np.sqrt(np.stack([r["cov"][i * (i + 1) // 2 + i] for i in range(6)]))[:, track_of]
+        err = np.abs(g["states"] - r["states"]) / np.maximum(np.abs(r["states"]), sd)
+        assert err.max() < 10 * tp, (h_max, n_iter, err.max())
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_edge_cases(handle, prec):
     ev = _edge_event()
     g = gpu_fit(handle, ev, prec, with_states=True)

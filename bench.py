@@ -256,12 +256,13 @@ def time_variants(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks
                   "method": "backward-filter smoother + energy loss + field map (FP64)",
                   "value": n_tracks / (step / 1e3), "unit": "tracks/s", "ms_per_step": step,
                   "ok_tracks": int((st == 0).sum()),
-                  "launch_shape": {"schedule": ["grid", "persistent", "sorted"][best.schedule],
+                  "launch_shape": {"schedule": SCHEDULE_NAMES[best.schedule],
                                    "block": best.block, "resident_warps": best.resident_warps,
                                    "cuda_graph": True}}
 
 
 SCALE_WORKLOAD = "tel30_4m"
+SCHEDULE_NAMES = ["grid", "persistent", "sorted", "waves"]
 
 
 def step_stats(ms):
@@ -310,7 +311,7 @@ def time_scale(kf, synth, torch, stream, l2_flush, steps, warmup, rank, no_cpu):
         st = step_stats(ms)
         res[name] = {"value": T / (st["mean"] / 1e3), "unit": "tracks/s", "ms_per_step": st["mean"],
                      "step_ms": st, "ok_tracks": int((out["status"] == 0).sum().item()),
-                     "launch_shape": {"schedule": ["grid", "persistent", "sorted"][best.schedule],
+                     "launch_shape": {"schedule": SCHEDULE_NAMES[best.schedule],
                                       "block": best.block, "min_blocks": best.min_blocks,
                                       "resident_warps": best.resident_warps, "cuda_graph": True}}
     res["mixed_over_fp64"] = res["mixed"]["value"] / res["fp64"]["value"]
@@ -392,7 +393,7 @@ def run_ours(args, rank, world, local):
         opt = kf.kf_default_options(prec_id[prec], schedule=best.schedule, block=best.block,
                                     min_blocks=best.min_blocks, resident_warps=best.resident_warps,
                                     use_graph=0 if args.no_graph else 1)
-        tuned[prec] = {"schedule": ["grid", "persistent", "sorted"][best.schedule], "block": best.block,
+        tuned[prec] = {"schedule": SCHEDULE_NAMES[best.schedule], "block": best.block,
                        "min_blocks": best.min_blocks, "resident_warps": best.resident_warps,
                        "cuda_graph": not args.no_graph}
         for _ in range(warmup):
@@ -473,7 +474,7 @@ def run_ours(args, rank, world, local):
         sh = tuned[args.precision]
         opt = kf.kf_default_options(prec_id[args.precision], block=sh["block"], min_blocks=sh["min_blocks"],
                                     resident_warps=sh["resident_warps"],
-                                    schedule=["grid", "persistent", "sorted"].index(sh["schedule"]))
+                                    schedule=SCHEDULE_NAMES.index(sh["schedule"]))
         for _ in range(args.warmup):
             kf.kf_fit_host(h, hev, opt, out=outs, stream=stream)
         torch.cuda.synchronize()

@@ -216,9 +216,13 @@ typedef enum {
   KF_SCHEDULE_PERSISTENT = 1,  /* resident CTAs; each CTA takes units of
                                   `block` tracks from a work counter until
                                   done */
-  KF_SCHEDULE_SORTED = 2       /* persistent, tracks taken longest first
+  KF_SCHEDULE_SORTED = 2,      /* persistent, tracks taken longest first
                                   (counting sort by state count; for uneven
                                   tracks) */
+  KF_SCHEDULE_WAVES = 3        /* grid launches: full waves of `block`-thread
+                                  CTAs (every SM's resident CTAs), then one
+                                  launch that spreads the remaining tracks
+                                  over all SMs in smaller CTAs */
 } kf_schedule;
 
 typedef struct kf_handle kf_handle;

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libkfgb.so")
 
 KF_PRECISION_FP64 = 0
 KF_PRECISION_MIXED = 1
-KF_SCHEDULE_AUTO, KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED = -1, 0, 1, 2
+KF_SCHEDULE_AUTO, KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED, KF_SCHEDULE_WAVES = -1, 0, 1, 2, 3
 KF_SMOOTHER_RTS, KF_SMOOTHER_BACKWARD_FILTER = 0, 1
 TRACK_STATUS = {0: "ok", 1: "no_intersection", 2: "non_spd", 3: "nonfinite", 4: "bad_input"}
 MUON_MASS = 0.1056583755

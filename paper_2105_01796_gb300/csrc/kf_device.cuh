@@ -225,26 +225,53 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitP
 // launch with the persistent grid (resident CTAs on every SM) or one thread
 // per track
 template <class Body, int MINB>
-cudaError_t launch_body(const FitParams& p, int block, cudaStream_t stream) {
+cudaError_t launch_body(const FitParams& p, int block, cudaStream_t stream, int* launched = nullptr) {
   const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);
   auto kern = fit_kernel<Body, MINB>;
+  if (launched) *launched = 1;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   int grid = (p.n_tracks + block - 1) / block;
-  if (p.work_counter) {
+  if (p.work_counter || p.waves) {
     int dev = 0, nsm = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, block, smem);
     if (e != cudaSuccess) return e;
-    long long resident = (long long)nsm * (occ > 0 ? occ : 1);
-    if (p.resident_warps > 0) {
-      const long long want = ((long long)nsm * p.resident_warps * 32 + block - 1) / block;
-      if (want < resident) resident = want;
+    if (occ < 1) occ = 1;
+    if (p.work_counter) {
+      long long resident = (long long)nsm * occ;
+      if (p.resident_warps > 0) {
+        const long long want = ((long long)nsm * p.resident_warps * 32 + block - 1) / block;
+        if (want < resident) resident = want;
+      }
+      if (grid > resident) grid = (int)resident;
+    } else {
+      // full waves of `block`-thread CTAs (every SM's resident CTAs), then
+      // the remainder spread over all SMs in one wave of smaller CTAs, so
+      // that the last wave leaves no SM idle
+      const long long per_wave = (long long)nsm * occ * block;
+      const long long full = ((long long)p.n_tracks / per_wave) * per_wave;
+      const long long rest = (long long)p.n_tracks - full;
+      if (full > 0 && rest > 0) {
+        const long long rest_warps = (rest + 31) / 32;
+        long long b2 = 32 * ((rest_warps + (long long)nsm * occ - 1) / ((long long)nsm * occ));
+        if (b2 > block) b2 = block;
+        FitParams a = p;
+        a.n_tracks = (int32_t)full;
+        kern<<<(int)(full / block), block, smem, stream>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        FitParams b = p;
+        b.track0 = p.track0 + (int32_t)full;
+        b.n_tracks = (int32_t)rest;
+        kern<<<(int)((rest + b2 - 1) / b2), (int)b2, smem, stream>>>(b);
+        if (launched) *launched = 2;
+        return cudaGetLastError();
+      }
     }
-    if (grid > resident) grid = (int)resident;
   }
   kern<<<grid, block, smem, stream>>>(p);
   return cudaGetLastError();

@@ -72,6 +72,7 @@ struct FitParams {
                            // units from this counter (zeroed before launch)
   const int32_t* order;    // non-null: slot s fits track order[s]
   int32_t resident_warps;  // persistent launch: warps per SM (0 = occupancy)
+  int32_t waves;           // grid launch split into full waves + one spread wave (host side)
   // method variants (the FP64 variant kernel)
   int32_t smoother;        // 0 RTS, 1 backward filter + weighted mean
   int32_t energy_loss;     // 1: mean loss and straggling on q/p
@@ -104,12 +105,13 @@ cudaError_t launch_selftest_any(long long n, unsigned long long* counter, cudaSt
 // One fused filter + smoother launch over p.n_tracks tracks.  min_blocks
 // selects the register-cap variant (__launch_bounds__ minimum CTAs per SM;
 // 0 = the default variant).
+// *launched (optional) gets the number of kernel launches queued.
 cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int* launched = nullptr);
 
 // The FP64 kernel of the method variants (kf_variants.cu): backward-filter
 // smoother, energy loss, field map; same records as the FP64 path.
-cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stream);
+cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stream, int* launched = nullptr);
 
 // Gradients of sum_t w_t chi2_t with respect to the seeds and the
 // per-surface alignment (kf_adjoint.cu).  ckpt holds n_ckpt checkpoints of 27

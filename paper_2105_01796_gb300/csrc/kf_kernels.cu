@@ -443,9 +443,9 @@ struct Fp64Body {
 };
 
 template <bool BZ>
-cudaError_t launch_fp64(const FitParams& p, int block, int min_blocks, cudaStream_t stream) {
+cudaError_t launch_fp64(const FitParams& p, int block, int min_blocks, cudaStream_t stream, int* launched) {
   (void)min_blocks;  // a register cap below 255 spills this kernel heavily
-  return launch_body<Fp64Body<BZ>, 1>(p, block, stream);
+  return launch_body<Fp64Body<BZ>, 1>(p, block, stream, launched);
 }
 
 // counting sort of tracks by state count (longest first)
@@ -494,15 +494,17 @@ cudaError_t launch_pack_surfaces(int n_surfaces, const double* center, const dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_fit_mixed(const FitParams& p, int block, int min_blocks, cudaStream_t stream);
+cudaError_t launch_fit_mixed(const FitParams& p, int block, int min_blocks, cudaStream_t stream, int* launched);
 
-cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks, cudaStream_t stream) {
+cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks, cudaStream_t stream,
+                       int* launched) {
+  if (launched) *launched = 0;
   if (p.n_tracks <= 0) return cudaSuccess;
   if (block <= 0) block = 128;
   const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
-  if (precision == 0) return bz ? launch_fp64<true>(p, block, min_blocks, stream)
-                                : launch_fp64<false>(p, block, min_blocks, stream);
-  return launch_fit_mixed(p, block, min_blocks, stream);
+  if (precision == 0) return bz ? launch_fp64<true>(p, block, min_blocks, stream, launched)
+                                : launch_fp64<false>(p, block, min_blocks, stream, launched);
+  return launch_fit_mixed(p, block, min_blocks, stream, launched);
 }
 
 cudaError_t launch_length_order(int n_tracks, int max_states, const int32_t* offsets, int32_t* hist,

@@ -926,19 +926,20 @@ struct MixedBody {
 };
 
 template <bool BZ>
-cudaError_t launch_m(const FitParams& p, int block, int min_blocks, cudaStream_t stream) {
+cudaError_t launch_m(const FitParams& p, int block, int min_blocks, cudaStream_t stream, int* launched) {
   switch (min_blocks) {
-    case 4: return launch_body<MixedBody<BZ>, 4>(p, block, stream);
-    case 3: return launch_body<MixedBody<BZ>, 3>(p, block, stream);
-    default: return launch_body<MixedBody<BZ>, 1>(p, block, stream);
+    case 4: return launch_body<MixedBody<BZ>, 4>(p, block, stream, launched);
+    case 3: return launch_body<MixedBody<BZ>, 3>(p, block, stream, launched);
+    default: return launch_body<MixedBody<BZ>, 1>(p, block, stream, launched);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_fit_mixed(const FitParams& p, int block, int min_blocks, cudaStream_t stream) {
+cudaError_t launch_fit_mixed(const FitParams& p, int block, int min_blocks, cudaStream_t stream, int* launched) {
   const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
-  return bz ? launch_m<true>(p, block, min_blocks, stream) : launch_m<false>(p, block, min_blocks, stream);
+  return bz ? launch_m<true>(p, block, min_blocks, stream, launched)
+            : launch_m<false>(p, block, min_blocks, stream, launched);
 }
 
 }  // namespace kfgb

@@ -647,9 +647,10 @@ struct VariantBody {
 
 }  // namespace
 
-cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stream) {
+cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stream, int* launched) {
+  if (launched) *launched = 0;
   if (p.n_tracks <= 0) return cudaSuccess;
-  return dev::launch_body<VariantBody, 1>(p, block ? block : 128, stream);
+  return dev::launch_body<VariantBody, 1>(p, block ? block : 128, stream, launched);
 }
 
 }  // namespace kfgb

@@ -260,7 +260,7 @@ def test_every_launch_variant_agrees(handle, prec):
     shapes = [(64, 0), (128, 0), (256, 0)]
     if prec == MIXED:
         shapes += [(64, 3), (128, 3), (192, 3), (384, 3), (128, 4), (512, 4)]
-    for sched in (kf.KF_SCHEDULE_GRID, kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED):
+    for sched in (kf.KF_SCHEDULE_GRID, kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED, kf.KF_SCHEDULE_WAVES):
         for block, mb in shapes:
             g = gpu_fit(handle, ev, prec, schedule=sched, block=block, min_blocks=mb)
             compare(g, r, prec)
@@ -311,7 +311,7 @@ def test_autotuner_choice_is_valid_and_cached(handle, prec):
     out = kf.alloc_outputs(ev["n_tracks"])
     best, ms = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
     assert ms > 0 and best.precision == prec
-    assert best.schedule in (0, 1, 2) and best.block % 32 == 0 and 32 <= best.block <= 512
+    assert best.schedule in (0, 1, 2, 3) and best.block % 32 == 0 and 32 <= best.block <= 512
     t0 = time.perf_counter()
     best2, ms2 = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec))
     assert time.perf_counter() - t0 < 0.05 and ms2 == ms       # cached
@@ -371,6 +371,24 @@ def test_full_size_tel30_4m_sampled(handle, tel30_4m, prec):
     g = {k: (v[..., sample].cpu().numpy() if v is not None else None) for k, v in out.items()}
     compare(g, r, prec)
     assert np.all(out["status"].cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_wave_split_launch_equals_grid(handle, prec):
+    """The wave-split schedule: 50k uneven tracks in 64-thread CTAs are one
+    full wave (every SM's resident CTAs) plus a second launch that spreads
+    the rest over all SMs in smaller CTAs. Per-track results do not depend
+    on the launch shape, so they equal the plain grid launch bit for bit."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 50000))
+    a = gpu_fit(handle, ev, prec, schedule=kf.KF_SCHEDULE_GRID, block=64)
+    b = gpu_fit(handle, ev, prec, schedule=kf.KF_SCHEDULE_WAVES, block=64)
+    assert handle.last_launch_count() == 1 + 2          # pack + two fit launches
+    for k in ("params", "cov", "chi2", "ndf", "status"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(ev["n_tracks"], 1000, replace=False))
+    r = oracle.fit_batch(synth.subset(ev, sample))
+    compare({k: (v[..., sample] if v is not None else None) for k, v in b.items()}, r, prec)
 
 
 @pytest.mark.parametrize("prec", [FP64, MIXED])

@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # Traffic grows in proportion to the states, so a launch's traffic is this
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (817.312768e6 + 674.922752e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "12d5f6932375d33b7251dcdff2393fa7bee5f2b375f8d5c541e0ad04973b2279"
+MIXED_TRAFFIC_BYTES_PER_STATE = (482.757376e6 + 387.44064e6 + 318.986496e6 + 277.01248e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "9235835839c9d10a253bb9bdadba60d66e1aa9cca47c0d3b640f4a4c72ece05d"
 
 
 def mixed_kernel_sources_sha256():
@@ -551,7 +551,7 @@ def run_ours(args, rank, world, local):
                      "t_roof_ms": 1e3 * t_roof, "roof_frac": 1e3 * t_roof / step_ms,
                      "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
                      "algorithmic_bytes_per_launch": nbytes,
-                     "traffic_note": ("ncu capture of a 100k-track launch of this kernel (grid, 352 threads, 168 registers); "
+                     "traffic_note": ("ncu capture of both launches of a 100k-track step of this kernel (wave split, 168 registers); "
                                       "mostly the smoother's per-state record round trip (216 B each way)")
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,

@@ -47,6 +47,37 @@ MIXED_TRAFFIC_BYTES_PER_STATE = (482.757376e6 + 387.44064e6 + 318.986496e6 + 277
 MIXED_TRAFFIC_SOURCES_SHA256 = "9235835839c9d10a253bb9bdadba60d66e1aa9cca47c0d3b640f4a4c72ece05d"
 
 
+# FP64 flops the hardware counted (ncu: 2 x fused + unfused FP64 warp
+# instructions x 32) per track in one 100k-track launch of the variant kernel
+# (fringe30, 31 states, all three variants) and of the adjoint kernel
+# (align20, 21 states); reported while those kernels' sources match
+EXT_FLOPS_PER_TRACK = {"variants": (396304830 * 2 + 268752510) * 32 / 1e5,
+                       "adjoint": (475581250 * 2 + 309928125) * 32 / 1e5}
+EXT_SOURCES_SHA256 = "fa420e8504a63c69b6055d2df60e0f1874c979e582d7d7fea208f6e6b2e2a818"
+
+
+def ext_kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("csrc/kf_variants.cu", "csrc/kf_adjoint.cu", "csrc/kf_fp64.cuh", "csrc/kf_device.cuh",
+              "csrc/kf_internal.h", "_build.py"):
+        with open(os.path.join(ROOT, "paper_2105_01796_gb300", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def ext_roofline(kind, tracks, ms):
+    """Roofline entry of the variant or adjoint kernel from its hardware-
+    counted FP64 flops per track (None once the kernel has changed)."""
+    if ext_kernel_sources_sha256() != EXT_SOURCES_SHA256:
+        return None
+    flops = EXT_FLOPS_PER_TRACK[kind] * tracks
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_launch": flops,
+            "flops_source": "hardware-counted FP64 flops (ncu) of a 100k-track launch, per track"}
+
+
 def mixed_kernel_sources_sha256():
     import hashlib
     h = hashlib.sha256()
@@ -441,6 +472,8 @@ def run_ours(args, rank, world, local):
                                               reduce=kdist.sum_over_ranks if world > 1 else None)
         a_ms = kdist.max_over_ranks(adjoint["ms_per_step"], device="cuda")
         adjoint.update(ms_per_step=a_ms, value=world * adjoint["tracks"] / (a_ms / 1e3))
+    if adjoint is not None:
+        adjoint["roofline"] = ext_roofline("adjoint", adjoint["tracks"], adjoint["ms_per_step"])
     scale = None
     if not args.no_scale:
         scale = time_scale(kf, synth, torch, stream, l2_flush, max(3, args.steps // 2), args.warmup,
@@ -453,6 +486,7 @@ def run_ours(args, rank, world, local):
     if not args.no_variants:
         variant_event, variants = time_variants(h, kf, synth, torch, stream, l2_flush,
                                                 max(3, args.steps // 2), args.warmup, T)
+        variants["roofline"] = ext_roofline("variants", variants["tracks"], variants["ms_per_step"])
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None

@@ -259,7 +259,10 @@ int kf_fit_ex(kf_handle* handle, const kf_tracks* tracks,
 
 /* Same as kf_fit_ex but every pointer in tracks, surfaces, meas and out is a
  * HOST pointer: the handle copies the inputs to its device buffers, fits, and
- * copies the outputs back before returning (synchronous). */
+ * copies the outputs back before returning (synchronous).  Batches of at
+ * least 20 000 tracks run as 2-8 chunks whose copies overlap the other
+ * chunks' fits (each chunk's fit on a stream of the handle); pinned host
+ * memory makes the copies asynchronous.  Results equal kf_fit_ex's. */
 int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
                 const kf_surfaces* surfaces, const kf_measurements* meas,
                 const kf_field* field, const kf_options* opt,
@@ -274,8 +277,10 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
  * the packed surface table (up to 1024 surfaces) and the per-state records;
  * larger batches run as several launches on `stream`.  Returns KF_ESIZE when
  * n_surfaces > 1024 or when one track's records (max_states x 720 B in FP64,
- * max_states x 264 B in mixed precision) do not fit the block.  Device
- * pointers, asynchronous on `stream`, same outputs as kf_fit_ex.
+ * max_states x 264 B in mixed precision) do not fit the block, and
+ * KF_EUNSUPPORTED for schedules other than GRID and PERSISTENT and for the
+ * method variants.  Device pointers, asynchronous on `stream`, same outputs
+ * as kf_fit_ex.
  * The first call on a device looks up the block's device address; make it
  * before capturing a stream.  Every call reuses the same block, which keeps
  * the previous call's contents: calls whose GPU work overlaps (other streams

@@ -35,7 +35,7 @@ namespace kfgb {
 namespace {
 using namespace dev;
 
-constexpr int kSeg = 8;  // states per checkpoint segment (about sqrt(n) for n ~ 30-60)
+constexpr int kSeg = 5;  // states per checkpoint segment (about sqrt(n) for n ~ 20-40)
 
 
 // ---------------------------------------------------------------------------

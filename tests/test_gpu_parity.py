@@ -232,9 +232,27 @@ def test_invalid_arguments(handle):
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_full_size_tel30_100k_sampled(handle, prec):
     """The benchmark workload at full size, in the benchmark's launch
-    configuration; the oracle checks a random sample of 1500 tracks."""
+    configuration (the autotuner's shape, replayed from a CUDA graph into
+    NaN-filled outputs); the oracle checks a random sample of 1500 tracks,
+    and the whole batch equals the default launch bit for bit."""
+    import torch
     ev = synth.make_event(synth.WORKLOADS["tel30_100k"])
-    g = gpu_fit(handle, ev, prec)
+    ref = gpu_fit(handle, ev, prec)
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(ev["n_tracks"])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        best, _ = kf.kf_autotune(handle, dev, out, kf.kf_default_options(prec), stream)
+        opt = kf.kf_default_options(prec, schedule=best.schedule, block=best.block, min_blocks=best.min_blocks,
+                                    resident_warps=best.resident_warps, use_graph=1)
+        kf.kf_fit_ex(handle, dev, out, opt, stream)        # captures the graph
+        for k in ("params", "cov", "chi2"):
+            out[k].fill_(float("nan"))
+        kf.kf_fit_ex(handle, dev, out, opt, stream)        # replays it
+    torch.cuda.synchronize()
+    g = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+    for k in ("params", "cov", "chi2", "ndf", "status"):
+        assert np.array_equal(g[k], ref[k]), k
     rng = np.random.default_rng(5)
     sample = np.sort(rng.choice(ev["n_tracks"], 1500, replace=False))
     r = oracle.fit_batch(synth.subset(ev, sample))

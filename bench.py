@@ -52,8 +52,8 @@ MIXED_TRAFFIC_SOURCES_SHA256 = "9235835839c9d10a253bb9bdadba60d66e1aa9cca47c0d3b
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
 # (align20, 21 states); reported while those kernels' sources match
 EXT_FLOPS_PER_TRACK = {"variants": (396343307 * 2 + 268774064) * 32 / 1e5,
-                       "adjoint": (475581250 * 2 + 309928125) * 32 / 1e5}
-EXT_SOURCES_SHA256 = "fa420e8504a63c69b6055d2df60e0f1874c979e582d7d7fea208f6e6b2e2a818"
+                       "adjoint": (464212500 * 2 + 305600000) * 32 / 1e5}
+EXT_SOURCES_SHA256 = "9beb858b6c94ff9eb0c1e79eaa3dd49d2590e3a77cc6a6bd00ff019452f2d379"
 
 
 def ext_kernel_sources_sha256():

@@ -99,3 +99,25 @@ def test_gradient_points_towards_the_true_misalignment(handle):
         step[0] = 0.0
         align[1] += step
     assert total < c0
+
+
+def test_full_size_gradients_sampled_and_additive(handle):
+    """The bench's adjoint workload at full size (100k tracks x 21 states):
+    seed gradients of 40 sampled tracks against the oracle's central
+    differences on those tracks, chi2 against the oracle, and the alignment
+    gradient of the batch equal to the sum of its two halves' (one sum over
+    tracks, so it holds at any size)."""
+    ev = synth.make_event(synth.WORKLOADS["align20_100k"], with_truth_states=False)
+    T, S = int(ev["n_tracks"]), ev["center"].shape[1]
+    align = np.zeros((6, S))
+    chi2, gs, ga = _grad(handle, ev, align)
+    pick = np.sort(np.random.default_rng(21).choice(T, 40, replace=False))
+    sub = synth.subset(ev, pick)
+    ref_chi2 = oracle.chi2_per_track(sub, align)
+    assert np.max(np.abs(chi2[pick] - ref_chi2) / ref_chi2) < 1e-9
+    fs, _ = oracle.chi2_gradient_fd(sub, align)
+    assert _rel(gs[:, pick], fs) < 1e-5, _rel(gs[:, pick], fs)
+    half = T // 2
+    _, _, ga0 = _grad(handle, synth.subset(ev, np.arange(half)), align)
+    _, _, ga1 = _grad(handle, synth.subset(ev, np.arange(half, T)), align)
+    assert np.max(np.abs(ga - (ga0 + ga1))) <= 1e-10 * np.max(np.abs(ga))

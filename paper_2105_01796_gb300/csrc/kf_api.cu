@@ -929,70 +929,71 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     }
     cudaError_t e = cudaSuccess;
     auto H2D = cudaMemcpyHostToDevice;
-    // inputs: the shared pieces with chunk 0, then chunk by chunk
-    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
-      cudaStream_t s = h->s_in;
-      if (c == 0) {
-        e = cudaMemcpyAsync(b + o_off, tr->offsets, (T + 1) * 4, H2D, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_c, su->center, 3 * S * 8, H2D, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_r, su->rot, 9 * S * 8, H2D, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_x, su->x_over_x0, S * 8, H2D, s);
-        if (e == cudaSuccess && map_bytes) e = cudaMemcpyAsync(b + o_map, fi->map->b, map_bytes, H2D, s);
-      }
-      const size_t t0 = tcut[c], t1 = tcut[c + 1], s0 = scut[c], s1 = scut[c + 1];
-      if (e == cudaSuccess) e = copy_cols(b + o_sp, tr->seed_params, T, 8, 6, t0, t1, H2D, s);
-      if (e == cudaSuccess) e = copy_cols(b + o_sc, tr->seed_cov, T, 8, 21, t0, t1, H2D, s);
-      if (e == cudaSuccess) e = copy_cols(b + o_sid, me->surface_id, M, 4, 1, s0, s1, H2D, s);
-      if (e == cudaSuccess) e = copy_cols(b + o_loc, me->loc, M, 8, 2, s0, s1, H2D, s);
-      if (e == cudaSuccess) e = copy_cols(b + o_cov, me->cov, M, 8, 3, s0, s1, H2D, s);
-      if (e == cudaSuccess) e = copy_cols(b + o_h, me->is_hole, M, 1, 1, s0, s1, H2D, s);
-      if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "host-path H2D");
-    // the surface table (in chunk 0's copies) is packed once and the work
-    // counters reset once, before any fit
-    e = cudaStreamWaitEvent(stream, h->ev_in[0], 0);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-    e = launch_pack_surfaces(dsu.n_surfaces, dsu.center, dsu.rot, dsu.x_over_x0, h->surf, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
-    int launches = 1;
-    if (concurrent && uses_counter(o.schedule)) {
-      e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * kf_handle::kPipe, stream);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
-    }
-    e = cudaEventRecord(h->ev_pack, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-    // the fits, chunk by chunk
+    auto D2H = cudaMemcpyDeviceToHost;
+    int launches = 0;
+    // Chunk by chunk, everything a chunk needs is queued before the next
+    // chunk's copies, so the first fit is queued after a few calls: its
+    // inputs (with the shared pieces ahead of chunk 0) on the copy stream,
+    // its fit on its own stream once they are in, its outputs on the output
+    // stream once the fit is done.
     for (int c = 0; c < nch; ++c) {
+      const size_t t0 = tcut[c], t1 = tcut[c + 1], s0 = scut[c], s1 = scut[c + 1];
+      cudaStream_t si = h->s_in;
+      if (c == 0) {
+        e = cudaMemcpyAsync(b + o_off, tr->offsets, (T + 1) * 4, H2D, si);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_c, su->center, 3 * S * 8, H2D, si);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_r, su->rot, 9 * S * 8, H2D, si);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b + o_x, su->x_over_x0, S * 8, H2D, si);
+        if (e == cudaSuccess && map_bytes) e = cudaMemcpyAsync(b + o_map, fi->map->b, map_bytes, H2D, si);
+      }
+      if (e == cudaSuccess) e = copy_cols(b + o_sp, tr->seed_params, T, 8, 6, t0, t1, H2D, si);
+      if (e == cudaSuccess) e = copy_cols(b + o_sc, tr->seed_cov, T, 8, 21, t0, t1, H2D, si);
+      if (e == cudaSuccess) e = copy_cols(b + o_sid, me->surface_id, M, 4, 1, s0, s1, H2D, si);
+      if (e == cudaSuccess) e = copy_cols(b + o_loc, me->loc, M, 8, 2, s0, s1, H2D, si);
+      if (e == cudaSuccess) e = copy_cols(b + o_cov, me->cov, M, 8, 3, s0, s1, H2D, si);
+      if (e == cudaSuccess) e = copy_cols(b + o_h, me->is_hole, M, 1, 1, s0, s1, H2D, si);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[c], si);
+      if (e != cudaSuccess) return cuda_fail(e, "host-path H2D");
+      if (c == 0) {
+        // the surface table (in chunk 0's copies) is packed once and the
+        // work counters reset once, before any fit
+        e = cudaStreamWaitEvent(stream, h->ev_in[0], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+        e = launch_pack_surfaces(dsu.n_surfaces, dsu.center, dsu.rot, dsu.x_over_x0, h->surf, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
+        launches = 1;
+        if (concurrent && uses_counter(o.schedule)) {
+          e = cudaMemsetAsync(h->counters, 0, sizeof(int32_t) * kf_handle::kPipe, stream);
+          if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+        }
+        e = cudaEventRecord(h->ev_pack, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+      }
       cudaStream_t fs = concurrent && c > 0 ? h->s_fit[c - 1] : stream;
       e = cudaStreamWaitEvent(fs, h->ev_in[c], 0);
       if (e == cudaSuccess && fs != stream) e = cudaStreamWaitEvent(fs, h->ev_pack, 0);
       if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
       int l = 0;
-      rc = enqueue_fit(h, &dtr, &dsu, &dme, &dfi, o, &dout, fs, plan, &l, (int64_t)tcut[c],
-                       (int64_t)tcut[c + 1], false, concurrent, concurrent ? c : 0);
+      rc = enqueue_fit(h, &dtr, &dsu, &dme, &dfi, o, &dout, fs, plan, &l, (int64_t)t0, (int64_t)t1, false,
+                       concurrent, concurrent ? c : 0);
       if (rc) return rc;
       launches += l;
       e = cudaEventRecord(h->ev_fit[c], fs);
       if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+      cudaStream_t so = h->s_out;
+      e = cudaStreamWaitEvent(so, h->ev_fit[c], 0);
+      if (e == cudaSuccess) e = copy_cols(out->params, b + o_p, T, 8, 6, t0, t1, D2H, so);
+      if (e == cudaSuccess) e = copy_cols(out->cov, b + o_pc, T, 8, 21, t0, t1, D2H, so);
+      if (e == cudaSuccess) e = copy_cols(out->chi2, b + o_chi, T, 8, 1, t0, t1, D2H, so);
+      if (e == cudaSuccess && out->ndf) e = copy_cols(out->ndf, b + o_ndf, T, 4, 1, t0, t1, D2H, so);
+      if (e == cudaSuccess && out->status) e = copy_cols(out->status, b + o_st, T, 1, 1, t0, t1, D2H, so);
+      if (e == cudaSuccess && out->states) e = copy_cols(out->states, b + o_states, M, 8, 6, s0, s1, D2H, so);
+      if (e != cudaSuccess) break;
     }
     h->last_launches = launches;
-    // outputs, chunk by chunk once its fit is done
-    auto D2H = cudaMemcpyDeviceToHost;
-    for (int c = 0; c < nch && e == cudaSuccess; ++c) {
-      cudaStream_t s = h->s_out;
-      e = cudaStreamWaitEvent(s, h->ev_fit[c], 0);
-      const size_t t0 = tcut[c], t1 = tcut[c + 1], s0 = scut[c], s1 = scut[c + 1];
-      if (e == cudaSuccess) e = copy_cols(out->params, b + o_p, T, 8, 6, t0, t1, D2H, s);
-      if (e == cudaSuccess) e = copy_cols(out->cov, b + o_pc, T, 8, 21, t0, t1, D2H, s);
-      if (e == cudaSuccess) e = copy_cols(out->chi2, b + o_chi, T, 8, 1, t0, t1, D2H, s);
-      if (e == cudaSuccess && out->ndf) e = copy_cols(out->ndf, b + o_ndf, T, 4, 1, t0, t1, D2H, s);
-      if (e == cudaSuccess && out->status) e = copy_cols(out->status, b + o_st, T, 1, 1, t0, t1, D2H, s);
-      if (e == cudaSuccess && out->states) e = copy_cols(out->states, b + o_states, M, 8, 6, s0, s1, D2H, s);
-    }
     if (e != cudaSuccess) return cuda_fail(e, "host-path D2H");
-    // the caller's stream and the second fit stream are done once the last
-    // output copy (which waited for every fit) is
+    // the fit streams are done once the last output copy (which waited for
+    // every fit) is
     e = cudaStreamSynchronize(h->s_out);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   }

@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # Traffic grows in proportion to the states, so a launch's traffic is this
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (482.757376e6 + 387.44064e6 + 318.986496e6 + 277.01248e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "82e56a0445a5a78d91730d53ac40ab5debdc8f069459ad06cf0ce7b3894bedde"
+MIXED_TRAFFIC_BYTES_PER_STATE = (643.430144e6 + 534.587648e6 + 437.270272e6 + 382.899968e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "8f31316d40e18b423605e33214cc6b23f6ea10f3b770ecbf6b57ff67275284ad"
 
 
 # FP64 flops the hardware counted (ncu: 2 x fused + unfused FP64 warp
@@ -53,7 +53,7 @@ MIXED_TRAFFIC_SOURCES_SHA256 = "82e56a0445a5a78d91730d53ac40ab5debdc8f069459ad06
 # (align20, 21 states); reported while those kernels' sources match
 EXT_FLOPS_PER_TRACK = {"variants": (396343307 * 2 + 268774064) * 32 / 1e5,
                        "adjoint": (464212500 * 2 + 305600000) * 32 / 1e5}
-EXT_SOURCES_SHA256 = "522cb5f6a3b08ff4ae81d84101892ea73cb1460ac2f1688bb5c1b8a620b14645"
+EXT_SOURCES_SHA256 = "042ef2f57da9951b192c0015c81ba23d006c1ad29ab6b51f84c0341b1a0be5e3"
 
 
 def ext_kernel_sources_sha256():
@@ -584,7 +584,7 @@ def run_ours(args, rank, world, local):
                      "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
                      "algorithmic_bytes_per_launch": nbytes,
                      "traffic_note": ("ncu capture of both launches of a 100k-track step of this kernel (wave split, 168 registers); "
-                                      "mostly the smoother's per-state record round trip (216 B each way)")
+                                      "mostly the smoother's per-state record round trip (300 B each way)")
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,
         "scale": scale,

@@ -43,8 +43,8 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # Traffic grows in proportion to the states, so a launch's traffic is this
 # per-state figure times its states.  It holds only for the kernel sources and
 # build flags that were captured: any change to them makes the figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (643.430144e6 + 534.587648e6 + 437.270272e6 + 382.899968e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "8f31316d40e18b423605e33214cc6b23f6ea10f3b770ecbf6b57ff67275284ad"
+MIXED_TRAFFIC_BYTES_PER_STATE = (592.369664e6 + 492.28416e6 + 505.207296e6 + 429.755136e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "8a71f89d172d3fa7b89b8c05ab31578260476708d363090b36265c6664466013"
 
 
 # FP64 flops the hardware counted (ncu: 2 x fused + unfused FP64 warp
@@ -53,7 +53,7 @@ MIXED_TRAFFIC_SOURCES_SHA256 = "8f31316d40e18b423605e33214cc6b23f6ea10f3b770ecbf
 # (align20, 21 states); reported while those kernels' sources match
 EXT_FLOPS_PER_TRACK = {"variants": (396343307 * 2 + 268774064) * 32 / 1e5,
                        "adjoint": (464212500 * 2 + 305600000) * 32 / 1e5}
-EXT_SOURCES_SHA256 = "042ef2f57da9951b192c0015c81ba23d006c1ad29ab6b51f84c0341b1a0be5e3"
+EXT_SOURCES_SHA256 = "faedab12959631e34ab8e470c52d46c043781275dd0886f2e158a42e032fb5af"
 
 
 def ext_kernel_sources_sha256():

@@ -111,31 +111,34 @@ __device__ __forceinline__ R highland(R lam_abs, R m2, R xx0, R cos_inc) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double f2d(float f) {
   const uint32_t b = __float_as_uint(f);
-  const uint32_t e = (b >> 23) & 0xffu;
-  const uint32_t sign = b & 0x80000000u;
-  const uint32_t m = b & 0x7fffffu;
-  uint32_t hi = sign | (((e + 896u) << 20) + (m >> 3));
+  const uint32_t a = b & 0x7fffffffu;
+  // normal numbers: the high word is the float's exponent and mantissa moved
+  // down by 3 bits with the exponent rebiased by 1023 - 127 = 896
+  uint32_t hi = (a >> 3) + 0x38000000u;
   uint32_t lo = b << 29;
-  if (e == 0u) {
-    hi = sign;
-    lo = 0u;
-  }
-  if (e == 255u) hi = sign | 0x7ff00000u | (m >> 3) | (m ? 0x80000u : 0u);
-  return __hiloint2double((int)hi, (int)lo);
+  // Inf and NaN: all-ones exponent (a NaN keeps a mantissa bit, in either word)
+  if (a >= 0x7f800000u) hi = (a >> 3) | 0x7ff00000u;
+  // zero, and the float subnormals, become zero
+  if (a < 0x00800000u) hi = lo = 0u;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
 }
 
 __device__ __forceinline__ float d2f(double x) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
-  const uint32_t sign = hi & 0x80000000u;
-  const uint32_t ex = (hi >> 20) & 0x7ffu;
-  const int e = (int)ex - 896;
-  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t ah = hi & 0x7fffffffu;
+  // the float's exponent and 23 mantissa bits: the high word and the top 3
+  // bits of the low word, shifted up by 3, with the exponent rebiased by
+  // -896 (added modulo 2^32 as 2^32 - 896 * 2^23; the field it lands in is
+  // right whenever the result is a normal float)
+  uint32_t r = __funnelshift_l(lo, ah, 3) + 0x40000000u;
+  // round to nearest even on the 29 dropped bits (a carry into the exponent
+  // is the correct result, up to Inf)
   const uint32_t rem = lo & 0x1fffffffu;
-  uint32_t r = ((uint32_t)e << 23) + m;
-  r += (uint32_t)((rem > 0x10000000u) | ((rem == 0x10000000u) & (m & 1u)));
-  if (e <= 0) r = 0u;
-  if (e >= 255) r = 0x7f800000u | ((ex == 0x7ffu && ((hi & 0xfffffu) | lo)) ? 0x400000u : 0u);
-  return __uint_as_float(sign | r);
+  r += (rem + (r & 1u)) > 0x10000000u ? 1u : 0u;
+  if (ah < 0x38100000u) r = 0u;            // |x| < 2^-126
+  if (ah >= 0x47f00000u) r = 0x7f800000u;  // |x| >= 2^128, Inf
+  if (ah > 0x7ff00000u || (ah == 0x7ff00000u && lo != 0u)) r = 0x7fc00000u;  // NaN
+  return __uint_as_float(r | (hi & 0x80000000u));
 }
 
 // Double-precision 1/sqrt(x) and 1/x for positive normal x within the float

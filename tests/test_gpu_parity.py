@@ -449,7 +449,8 @@ def test_pipelined_host_entry_equals_device_entry(handle, prec):
         ref = gpu_fit(handle, ev, prec, with_states=True, schedule=kf.KF_SCHEDULE_PERSISTENT)
         per_track = 31 * (720 if prec == FP64 else 27 * 8 + 33 * 4)
         for sched, cap in ((kf.KF_SCHEDULE_PERSISTENT, 0), (kf.KF_SCHEDULE_SORTED, 0), (kf.KF_SCHEDULE_GRID, 0),
-                           (kf.KF_SCHEDULE_PERSISTENT, 7000 * per_track), (kf.KF_SCHEDULE_GRID, 7000 * per_track)):
+                           (kf.KF_SCHEDULE_WAVES, 0), (kf.KF_SCHEDULE_PERSISTENT, 7000 * per_track),
+                           (kf.KF_SCHEDULE_GRID, 7000 * per_track), (kf.KF_SCHEDULE_WAVES, 7000 * per_track)):
             opt = kf.kf_default_options(prec, schedule=sched, workspace_bytes=cap)
             host = kf.kf_fit_host(handle, ev, opt, with_states=True)
             for k in ("params", "cov", "chi2", "ndf", "status", "states"):

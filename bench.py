@@ -187,15 +187,38 @@ def cpu_model():
     return "%s (%s)" % (name or "unknown", platform.machine())
 
 
-def oracle_tracks_per_s(ev, n_sample, cores, method=None):
-    """Oracle (plain FP64 C, POSIX threads) over the first n_sample tracks."""
+def oracle_tracks_per_s(ev, n_sample, cores, method=None, keep=None):
+    """Oracle (plain FP64 C, POSIX threads) over the first n_sample tracks;
+    keep (a dict) receives the oracle's outputs."""
     import oracle
     from paper_2105_01796_gb300 import synth
     sub = synth.subset(ev, np.arange(min(n_sample, ev["n_tracks"])))
     t0 = time.perf_counter()
-    oracle.fit_batch(sub, n_threads=cores, method=method)
+    r = oracle.fit_batch(sub, n_threads=cores, method=method)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(r)
     return sub["n_tracks"] / dt, dt, sub["n_tracks"]
+
+
+def accuracy(gpu, ref):
+    """Error of a GPU fit against the FP64 oracle on the tracks both fitted:
+    parameters |dx_i| / max(|x_i|, sqrt(C_ii)), covariance |dC_ij| /
+    sqrt(C_ii C_jj) (oracle values), chi2 |d chi2| / max(chi2, 1); per track
+    the largest element, then the maximum and the 99.9th percentile over
+    tracks."""
+    ok = (ref["status"] == 0) & (gpu["status"] == 0)
+    diag = [i * (i + 1) // 2 + i for i in range(6)]
+    c, g = ref["cov"][:, ok], gpu["cov"][:, ok]
+    d = np.abs(c[diag])
+    sd = np.sqrt(d)
+    pe = np.max(np.abs(gpu["params"][:, ok] - ref["params"][:, ok]) / np.maximum(np.abs(ref["params"][:, ok]), sd), axis=0)
+    scale = np.stack([np.sqrt(d[i] * d[j]) for i in range(6) for j in range(i + 1)])
+    ce = np.max(np.abs(g - c) / scale, axis=0)
+    xe = np.abs(gpu["chi2"][ok] - ref["chi2"][ok]) / np.maximum(np.abs(ref["chi2"][ok]), 1.0)
+    q = lambda a: {"max": float(a.max()), "p99.9": float(np.percentile(a, 99.9))}
+    return {"tracks": int(ok.sum()), "status_agree": bool(np.array_equal(ref["status"], gpu["status"])),
+            "params": q(pe), "cov": q(ce), "chi2": q(xe)}
 
 
 ADJOINT_WORKLOAD = "align20_100k"
@@ -449,8 +472,10 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
         st = out["status"].cpu().numpy()
+        results[prec] = {k: out[k].cpu().numpy() for k in ("params", "cov", "chi2", "status")}
         return ms, launches, wall, st
 
+    results = {}
     # the precision not being headlined is timed first, untimed for clocks
     other = "fp64" if args.precision == "mixed" else "mixed"
     ms_other, _, _, st_other = timed(other, max(3, args.steps // 2), args.warmup)
@@ -537,12 +562,17 @@ def run_ours(args, rank, world, local):
     if args.precision == "mixed" and mixed_kernel_sources_sha256() == MIXED_TRAFFIC_SOURCES_SHA256:
         traffic = MIXED_TRAFFIC_BYTES_PER_STATE * M
     cpu = None
+    acc = None
     if not args.no_cpu:
         cores = os.cpu_count() or 1
         # warm the oracle build, then time a bounded sample
         oracle_tracks_per_s(ev, 500, cores)
-        v, dt, n = oracle_tracks_per_s(ev, T, cores)
+        ref = {}
+        v, dt, n = oracle_tracks_per_s(ev, T, cores, keep=ref)
         v1, dt1, n1 = oracle_tracks_per_s(ev, 5000, 1)
+        # the timed fits' outputs against the oracle's on the same tracks
+        acc = {prec: accuracy(res, ref) for prec, res in results.items()}
+        acc["reference"] = "FP64 oracle on all %d tracks" % n
         cpu = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt),
                "single_core": {"value": v1, "unit": "tracks/s",
@@ -587,6 +617,7 @@ def run_ours(args, rank, world, local):
                                       "mostly the smoother's per-state record round trip (300 B each way)")
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,
+        "accuracy": acc,
         "scale": scale,
         "variants": variants,
         "adjoint": adjoint,

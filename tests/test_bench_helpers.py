@@ -48,3 +48,26 @@ def test_peaks(bench):
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(152 * 2 * 2 * 2070e6 / 1e12)
     assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
     assert isinstance(bench.cpu_model(), str)
+
+
+def test_accuracy_metric(bench):
+    """The error report of the timed fits against the oracle: zero for equal
+    outputs, the planted parameter error recovered exactly, failed tracks
+    left out and a status mismatch flagged."""
+    rng = np.random.default_rng(0)
+    T = 500
+    A = rng.normal(size=(6, 6, T))
+    C = np.einsum("ijt,kjt->ikt", A, A) + 6 * np.eye(6)[:, :, None]
+    packed = np.stack([C[i, j] for i in range(6) for j in range(i + 1)])
+    ref = {"params": rng.normal(size=(6, T)), "cov": packed, "chi2": rng.uniform(0, 60, T),
+           "status": np.zeros(T, np.uint8)}
+    gpu = {k: v.copy() for k, v in ref.items()}
+    a = bench.accuracy(gpu, ref)
+    assert a["tracks"] == T and a["status_agree"] and a["params"]["max"] == 0 and a["cov"]["max"] == 0
+    scale = max(abs(ref["params"][2, 7]), np.sqrt(C[2, 2, 7]))
+    gpu["params"][2, 7] += 3e-5 * scale
+    assert bench.accuracy(gpu, ref)["params"]["max"] == pytest.approx(3e-5, rel=1e-6)
+    gpu["status"][9] = 2
+    gpu["params"][:, 9] = np.nan
+    a = bench.accuracy(gpu, ref)
+    assert a["tracks"] == T - 1 and not a["status_agree"]

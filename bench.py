@@ -254,19 +254,23 @@ def time_adjoint(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks,
         ms.append(a.elapsed_time(b))
     torch.cuda.nvtx.range_pop()
     step = float(np.mean(ms))
+    host = {"grad_seed": gs.cpu().numpy(), "chi2": chi2.cpu().numpy()}
     return ev, {"workload": ADJOINT_WORKLOAD, "tracks": T, "states_per_track": 21,
                 "gradient": "d(sum chi2)/d(seeds [6][T], alignment [6][21]) at zero alignment (FP64)",
-                "value": T / (step / 1e3), "unit": "tracks/s", "ms_per_step": step}
+                "value": T / (step / 1e3), "unit": "tracks/s", "ms_per_step": step}, host
 
 
-def oracle_gradient_rate(ev, n_sample, cores):
-    """The oracle's gradient by central finite differences over a sample."""
+def oracle_gradient_rate(ev, n_sample, cores, keep=None):
+    """The oracle's gradient by central finite differences over a sample;
+    keep (a dict) receives the seed gradient."""
     import oracle
     from paper_2105_01796_gb300 import synth
     sub = synth.subset(ev, np.arange(min(n_sample, ev["n_tracks"])))
     t0 = time.perf_counter()
-    oracle.chi2_gradient_fd(sub, n_threads=cores)
+    fs, _ = oracle.chi2_gradient_fd(sub, n_threads=cores)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep["grad_seed"] = fs
     return sub["n_tracks"] / dt, dt, sub["n_tracks"]
 
 
@@ -304,7 +308,8 @@ def time_variants(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks
     torch.cuda.nvtx.range_pop()
     st = out["status"].cpu().numpy()
     step = float(np.mean(ms))
-    return ev, {"workload": VARIANT_WORKLOAD, "tracks": n_tracks,
+    host = {k: out[k].cpu().numpy() for k in ("params", "cov", "chi2", "status")}
+    return ev, host, {"workload": VARIANT_WORKLOAD, "tracks": n_tracks,
                   "method": "backward-filter smoother + energy loss + field map (FP64)",
                   "value": n_tracks / (step / 1e3), "unit": "tracks/s", "ms_per_step": step,
                   "ok_tracks": int((st == 0).sum()),
@@ -490,7 +495,7 @@ def run_ours(args, rank, world, local):
     adjoint = None
     adjoint_event = None
     if not args.no_adjoint:
-        adjoint_event, adjoint = time_adjoint(h, kf, synth, torch, stream, l2_flush,
+        adjoint_event, adjoint, adjoint_out = time_adjoint(h, kf, synth, torch, stream, l2_flush,
                                               max(3, args.steps // 2), args.warmup, T,
                                               reduce=kdist.sum_over_ranks if world > 1 else None)
         a_ms = kdist.max_over_ranks(adjoint["ms_per_step"], device="cuda")
@@ -507,7 +512,7 @@ def run_ours(args, rank, world, local):
     variants = None
     variant_event = None
     if not args.no_variants:
-        variant_event, variants = time_variants(h, kf, synth, torch, stream, l2_flush,
+        variant_event, variant_out, variants = time_variants(h, kf, synth, torch, stream, l2_flush,
                                                 max(3, args.steps // 2), args.warmup, T)
         variants["roofline"] = ext_roofline("variants", variants["tracks"], variants["ms_per_step"])
 
@@ -578,16 +583,29 @@ def run_ours(args, rank, world, local):
                "single_core": {"value": v1, "unit": "tracks/s",
                                "sample": "first %d tracks, one thread (%.1f s)" % (n1, dt1)}}
         if adjoint is not None:
-            av, adt, an = oracle_gradient_rate(adjoint_event, 200, cores)
+            fd = {}
+            av, adt, an = oracle_gradient_rate(adjoint_event, 200, cores, keep=fd)
             adjoint["cpu_oracle"] = {"value": av, "unit": "tracks/s", "cores": cores,
                                      "kind": "oracle central finite differences",
                                      "sample": "%d tracks, %d + 12 x %d batch fits (%.1f s)"
                                                % (an, 12, adjoint_event["center"].shape[1], adt)}
+            # the timed kernel's seed gradients of those tracks against the
+            # oracle's central differences (per parameter, relative to the
+            # largest magnitude of that parameter's gradient)
+            g = adjoint_out["grad_seed"][:, :an]
+            rel = np.max(np.abs(g - fd["grad_seed"]), axis=1) / np.maximum(np.max(np.abs(fd["grad_seed"]), axis=1),
+                                                                         1e-300)
+            adjoint["accuracy"] = {"tracks": int(an), "grad_seed_rel_max": float(rel.max()),
+                                   "reference": "oracle central finite differences (step 1e-6)"}
         if variants is not None:
+            vref = {}
             vv, vdt, vn = oracle_tracks_per_s(variant_event, VARIANT_ORACLE_SAMPLE, cores,
-                                              method={"smoother": "backward", "energy_loss": True})
+                                              method={"smoother": "backward", "energy_loss": True}, keep=vref)
             variants["cpu_oracle"] = {"value": vv, "unit": "tracks/s", "cores": cores,
                                       "sample": "first %d tracks, one pass (%.1f s)" % (vn, vdt)}
+            first = {k: (v[..., :vn]) for k, v in variant_out.items()}
+            variants["accuracy"] = dict(accuracy(first, vref),
+                                        reference="FP64 oracle with the same variants, first %d tracks" % vn)
     other_ms = float(np.mean(ms_other))
     line = {
         "metric": "tracks_fitted_per_s", "value": value, "unit": "tracks/s",

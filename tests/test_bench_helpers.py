@@ -71,3 +71,23 @@ def test_accuracy_metric(bench):
     gpu["params"][:, 9] = np.nan
     a = bench.accuracy(gpu, ref)
     assert a["tracks"] == T - 1 and not a["status_agree"]
+
+
+def test_roofline_counts():
+    """The roofline numerator: per-transition, per-measurement and
+    per-smoother-step counts add up as documented (one track of 3 states,
+    the middle one a hole; the mixed path's FP64 part is the Joseph update
+    and chi2 per measurement plus the two inverse columns and the noise-rank
+    terms per smoother step)."""
+    from paper_2105_01796_gb300 import roofline as rf
+    offsets = np.array([0, 3])
+    is_hole = np.array([1, 1, 0], dtype=np.uint8)   # state 0 is the reference plane
+    f64, f32 = rf.batch_flops(offsets, is_hole, 0)
+    prop = 2 * (4 * rf.RKN_STEP + rf.FRAME + rf.TRANSPORT + rf.NOISE)
+    assert f32 == 0 and f64 == prop + 1 * (rf.GAIN + rf.JOSEPH) + 2 * (rf.CHOL + rf.SOLVE6 + rf.RTS_UPD)
+    m64, m32 = rf.batch_flops(offsets, is_hole, 1)
+    assert m64 == (rf.JOSEPH + rf.CHI2) + 2 * (rf.INV_COLS + rf.NRANK)
+    assert m32 == prop + (rf.GAIN - rf.CHI2) + 2 * rf.MIXED_SMOOTH_FP32
+    assert rf.JOSEPH == 219 and rf.INV_COLS == 141
+    # inputs plus outputs once, per track and per state
+    assert rf.algorithmic_bytes(offsets, is_hole) == (4 + 6 * 8 + 21 * 8 + 6 * 8 + 21 * 8 + 8 + 4 + 1) + 3 * (4 + 16 + 24 + 1)

@@ -907,8 +907,8 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     if (concurrent) {
       // the chunks' fits share the SMs, so no launch needs to fill them on
       // its own: plain grid launches of at most 128-thread CTAs pack them
-      // best (measured on 100k tracks in 8 chunks: 2.22 ms end to end with
-      // 128 threads against 2.30 ms with 352)
+      // best (measured on 100k tracks in 8 chunks: 2.16 ms end to end with
+      // 128 threads, 2.22-2.33 ms with 224-384, 2.61 ms with 512)
       if (o.schedule == KF_SCHEDULE_WAVES) o.schedule = KF_SCHEDULE_GRID;
       if (o.block > 128) o.block = 128;
     }

@@ -38,11 +38,12 @@ FP64_PEAK_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_MHZ * 1e6 / 1e12      # 1.259
 FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 
 # DRAM traffic of the mixed kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-# from one ncu capture of a 80k-track, 2.48M-state launch of the same
-# workload (profiles/fit_kernel_MixedBody_tel30_80k.md): 822.223 + 869.466 MB.
-# Traffic grows in proportion to the states, so a launch's traffic is this
-# per-state figure times its states.  It holds only for the kernel sources and
-# build flags that were captured: any change to them makes the figure null.
+# from one ncu capture of both wave-split launches of a 100k-track, 3.1M-state
+# step of the same workload: launch A 592.4 + 492.3 MB, launch B 505.2 +
+# 429.8 MB.  Traffic grows in proportion to the states, so a launch's traffic
+# is this per-state figure times its states.  It holds only for the kernel
+# sources and build flags that were captured: any change to them makes the
+# figure null.
 MIXED_TRAFFIC_BYTES_PER_STATE = (592.369664e6 + 492.28416e6 + 505.207296e6 + 429.755136e6) / 3.1e6
 MIXED_TRAFFIC_SOURCES_SHA256 = "8a71f89d172d3fa7b89b8c05ab31578260476708d363090b36265c6664466013"
 

@@ -86,8 +86,11 @@ typedef enum {
 typedef enum {
   KF_PRECISION_FP64 = 0, /* every step in double precision */
   KF_PRECISION_MIXED = 1 /* propagation, Jacobians, covariance transport and
-                            gain in float; Joseph covariance update, the
-                            smoother's Cholesky solve and chi2 in double */
+                            gain in float; Joseph covariance update, chi2
+                            and the smoother's inverse in double (the two
+                            columns of the inverse the smoother needs, by a
+                            4x4 LDL^T of the non-angle block and the 2x2
+                            Schur complement of the angle block) */
 } kf_precision;
 
 typedef struct {
@@ -269,8 +272,9 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
                 const kf_outputs* out, void* stream);
 
 /* kf_fit_ex without any device allocation, for callers that cannot allocate:
- * code running inside a CUDA stream capture, real-time loops that must not
- * wait on the allocator, hosts with a fixed memory budget.  (The paper has no
+ * real-time loops (a trigger farm's event loop) that must never block on the
+ * CUDA allocator, and hosts that give each library a fixed memory budget up
+ * front and own every other byte of device memory.  (The paper has no
  * counterpart; it is an addition of this library.)
  * Scratch space is one fixed 64 MiB block of device memory per GPU, reserved
  * for the whole life of the process once the library is loaded.  It holds
@@ -281,8 +285,9 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
  * KF_EUNSUPPORTED for schedules other than GRID and PERSISTENT and for the
  * method variants.  Device pointers, asynchronous on `stream`, same outputs
  * as kf_fit_ex.
- * The first call on a device looks up the block's device address; make it
- * before capturing a stream.  Every call reuses the same block, which keeps
+ * The first call on a device looks up the block's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call reuses the same block, which keeps
  * the previous call's contents: calls whose GPU work overlaps (other streams
  * or host threads) race on it and must be serialised by the caller. */
 int kf_fit_static(const kf_tracks* tracks, const kf_surfaces* surfaces,
@@ -318,7 +323,7 @@ int kf_autotune(kf_handle* handle, const kf_tracks* tracks,
  *   grad_seed[6][T]   dL/d seed_params (optional).
  *   grad_align[6][S]  dL/d align (optional); overwritten.
  * Method: reverse mode throughout: a reverse sweep over the states with the
- * filtered states recomputed from checkpoints every 8 states, and inside it
+ * filtered states recomputed from checkpoints every 5 states, and inside it
  * every transport recomputed with its RKN stage inputs taped and swept
  * backwards.  Launch shape: one thread per track, opt->block threads per
  * CTA (a multiple of 32 up to 256; 0, and opt == NULL, choose CTAs of the

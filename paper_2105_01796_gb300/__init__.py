@@ -315,8 +315,8 @@ def kf_autotune(handle: Handle, dev_ev, out, opt: KfOptions | None = None, strea
 
 def kf_fit_static(dev_ev, out, opt: KfOptions | None = None, stream=None):
     """Fit without any device allocation: scratch lives in the library's fixed
-    per-GPU block (for callers that cannot allocate, e.g. inside a stream
-    capture).  Same inputs, outputs and results as :func:`kf_fit_ex`; calls
+    per-GPU block (for callers that cannot allocate: real-time loops, fixed
+    memory budgets).  Same inputs, outputs and results as :func:`kf_fit_ex`; calls
     that overlap on the GPU share the block and must be serialised."""
     if stream is None:
         import torch

@@ -1,9 +1,8 @@
 // kf_static.cu -- kf_fit_static: the fit without any device allocation.
 //
-// Some callers cannot allocate device memory: code that runs inside a CUDA
-// stream capture (where cudaMalloc is not allowed), real-time trigger loops
-// that must never block on the allocator, and hosts that hand the library a
-// fixed memory budget up front.  For them this entry point uses one fixed
+// Some callers cannot allocate device memory: real-time trigger loops that
+// must never block on the CUDA allocator, and hosts that hand the library a
+// fixed memory budget up front and own every other byte of device memory.  For them this entry point uses one fixed
 // block of device memory that lives in this file for the whole life of the
 // process: every GPU that loads the library keeps kStaticBytes reserved until
 // the process exits.  The caller still owns and passes all inputs and

@@ -178,6 +178,55 @@ def test_highland_scaling():
     assert abs(oracle.highland(1.0, 0.01, 0.5) - oracle.highland(1.0, 0.02, 1.0)) < 1e-16
 
 
+def test_scattering_noise_split_matches_a_rotated_direction():
+    """The multiple-scattering noise the oracle adds at a surface,
+    Q = Cp - F Cf F^T, against the geometry of the scattering itself: turn
+    the unit direction T by two independent projected angles a, b ~
+    N(0, theta0^2) in two orthogonal planes containing T (T' =
+    normalise(T + tan a e_theta + tan b e_phi), e_theta = dT/dtheta,
+    e_phi = (dT/dphi)/sin(theta)), convert T' back to (phi, theta) and take
+    the sample covariance of the angle changes.  Nothing here restates the
+    1/sin^2(theta) split of the oracle or the generator: steep tracks
+    (sin^2 theta down to 0.71) make a missing or inverted factor a 20-40 %
+    error against a 1 % statistical tolerance.  theta0 is the Highland width,
+    pinned by its hand values above."""
+    w = synth.scaled(synth.WORKLOADS["tel10_1k"], 3, bz=0.0)
+    ev = dict(synth.make_event(w))
+    ev["seed_params"] = ev["seed_params"].copy()
+    ev["seed_params"][2] = [0.2, -0.1, 0.0]      # phi
+    ev["seed_params"][3] = [1.0, 2.0, 1.3]       # theta: sin^2 = 0.71, 0.83, 0.93
+    rng = np.random.default_rng(7)
+    n = 400_000
+    for t in range(3):
+        r = oracle.fit_track(ev, t)
+        assert r["status"] == oracle.OK
+        # state 1: the seed direction transported through B = 0 (unchanged)
+        Q = r["Cp"][1] - r["F"][1] @ r["Cf"][0] @ r["F"][1].T
+        phi, theta, qop = r["xp"][1][2], r["xp"][1][3], r["xp"][1][4]
+        T = np.array([np.cos(phi) * np.sin(theta), np.sin(phi) * np.sin(theta), np.cos(theta)])
+        sid = int(ev["surface_id"][ev["offsets"][t] + 1])
+        nrm = ev["rot"][:, sid].reshape(3, 3)[:, 2]
+        th0 = oracle.highland(qop, float(ev["x_over_x0"][sid]), float(nrm @ T))
+        e_th = np.array([np.cos(phi) * np.cos(theta), np.sin(phi) * np.cos(theta), -np.sin(theta)])
+        e_ph = np.array([-np.sin(phi), np.cos(phi), 0.0])
+        a = rng.normal(0.0, th0, n)
+        b = rng.normal(0.0, th0, n)
+        Tn = T[:, None] + np.tan(a)[None] * e_th[:, None] + np.tan(b)[None] * e_ph[:, None]
+        Tn /= np.linalg.norm(Tn, axis=0)
+        dphi = np.arctan2(Tn[1], Tn[0]) - phi
+        dth = np.arccos(Tn[2]) - theta
+        cov = np.cov(np.stack([dphi, dth]))
+        tol = 4 * np.sqrt(2.0 / n)              # relative spread of a sample variance
+        assert abs(Q[2, 2] / cov[0, 0] - 1) < tol, (t, Q[2, 2], cov[0, 0])
+        assert abs(Q[3, 3] / cov[1, 1] - 1) < tol, (t, Q[3, 3], cov[1, 1])
+        assert abs(Q[2, 3]) < 1e-12 * Q[3, 3]
+        assert abs(cov[0, 1]) < 4 * np.sqrt(cov[0, 0] * cov[1, 1] / n)
+        # no other element of C receives noise
+        Qo = Q.copy()
+        Qo[2, 2] = Qo[3, 3] = 0.0
+        assert np.max(np.abs(Qo)) < 1e-12 * np.max(np.abs(r["Cp"][1]))
+
+
 # ---------------------------------------------------------------- update
 
 def _random_spd(rng, n=6, scale=None):

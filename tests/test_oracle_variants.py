@@ -208,6 +208,29 @@ def test_straggling_width_is_the_landau_fwhm():
         assert abs(sigE * 2 * math.sqrt(2 * math.log(2)) / xi - fwhm_lambda) < 0.01 * fwhm_lambda
 
 
+def test_landau_xi_coefficient_matches_the_published_value():
+    """xi = 0.1535 MeV cm^2/mol x <Z/A> x / beta^2 (tests/golden/landau_xi.txt):
+    the published coefficient pins the factor 1/2 in front of K (a dropped
+    or doubled factor is off by 2x), independently of the K that the Bethe
+    pin checks."""
+    coef = None
+    with open(os.path.join(GOLDEN, "landau_xi.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            if k == "coefficient_MeV_cm2_per_mol":
+                coef = float(v)
+    m = oracle.silicon()
+    for z_over_a, thick, beta in ((1.0, 1.0, 1.0), (m.z_over_a, 0.0699, 0.999), (0.5, 2.5, 0.6)):
+        mat = oracle.silicon()
+        mat.z_over_a = z_over_a
+        xi_mev = oracle.landau_xi(beta, thick, mat) * 1e3
+        expect = coef * z_over_a * thick / beta ** 2
+        # the printed coefficient has four digits: 0.1535 vs 0.1535375
+        assert abs(xi_mev - expect) < 5e-4 * expect, (xi_mev, expect)
+
+
 @pytest.mark.parametrize("p", [0.3, 1.0, 20.0])
 def test_energy_loss_map_jacobian_and_reversal(p):
     qop = -1.0 / p

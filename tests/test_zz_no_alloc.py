@@ -1,8 +1,8 @@
 """kf_fit_static: the fit without any device allocation.
 
-Callers that cannot allocate device memory -- code running inside a CUDA
-stream capture, real-time loops that must never wait on the allocator, hosts
-with a fixed memory budget -- call kf_fit_static.  Its scratch space is one
+Callers that cannot allocate device memory -- real-time loops that must
+never wait on the CUDA allocator, hosts that give the library a fixed memory
+budget and own all other device memory -- call kf_fit_static.  Its scratch space is one
 fixed block of device memory per GPU that the library reserves for the life
 of the process.  These tests check, through the C ABI, that its results
 match kf_fit_ex on two different batches fitted one after the other (the

@@ -62,7 +62,7 @@
 extern "C" {
 #endif
 
-#define KF_ABI_VERSION 3
+#define KF_ABI_VERSION 4
 
 typedef enum {
   KF_SUCCESS = 0,
@@ -70,7 +70,9 @@ typedef enum {
   KF_ECUDA = -2,        /* a CUDA call failed; kf_last_cuda_error() has it */
   KF_ENOMEM = -3,       /* device or pinned allocation failed */
   KF_EUNSUPPORTED = -4, /* option outside what this build supports */
-  KF_EDEVICE = -5,      /* a kernel reported an internal wait timeout */
+  KF_EDEVICE = -5,      /* a kernel's bounded wait timed out (synchronous
+                           entry points; the tracks it held have status
+                           KF_TRACK_TIMEOUT) */
   KF_ESIZE = -6         /* kf_fit_static: the batch does not fit its fixed
                            device block */
 } kf_error;
@@ -80,7 +82,10 @@ typedef enum {
   KF_TRACK_NO_INTERSECTION = 1, /* track (nearly) parallel to a plane */
   KF_TRACK_NON_SPD = 2,         /* non-positive innovation or Cholesky pivot */
   KF_TRACK_NONFINITE = 3,       /* NaN/Inf in the result */
-  KF_TRACK_BAD_INPUT = 4        /* empty track, too many states, bad surface id */
+  KF_TRACK_BAD_INPUT = 4,       /* empty track, too many states, bad surface id */
+  KF_TRACK_TIMEOUT = 5          /* not fitted: a bounded device wait of the
+                                   call (the surface table's copy into shared
+                                   memory) gave up */
 } kf_track_status;
 
 typedef enum {
@@ -209,6 +214,14 @@ typedef struct {
                                   takes ceil(U / W) rounds; fewer warps
                                   that still fill the FP64 pipe can remove
                                   a part-filled last round */
+  int32_t wait_limit;          /* polls of the kernels' bounded waits before
+                                  they give up (0 = 2^20, about a second) */
+  int32_t test_wait_timeout;   /* diagnostic of the timeout path (0 = off):
+                                  1 announces the surface table's copy on
+                                  each CTA's barrier without issuing it, so
+                                  every bounded wait runs out with nothing
+                                  left in flight and every track of the call
+                                  gets KF_TRACK_TIMEOUT.  No fault, no hang */
 } kf_options;
 
 typedef enum {
@@ -254,7 +267,10 @@ int kf_fit(const kf_tracks* tracks, const kf_surfaces* surfaces,
 
 /* Fit with explicit options on `stream` (a cudaStream_t, NULL = legacy
  * default stream).  Device pointers.  Asynchronous: the call returns after
- * the launches are queued.  opt may be NULL (defaults). */
+ * the launches are queued.  opt may be NULL (defaults).  Each call clears the
+ * handle's device error flag first; a bounded device wait that gives up
+ * marks the tracks it held KF_TRACK_TIMEOUT (out_status), and so does every
+ * CTA that starts after it in the same call. */
 int kf_fit_ex(kf_handle* handle, const kf_tracks* tracks,
               const kf_surfaces* surfaces, const kf_measurements* meas,
               const kf_field* field, const kf_options* opt,
@@ -265,7 +281,8 @@ int kf_fit_ex(kf_handle* handle, const kf_tracks* tracks,
  * copies the outputs back before returning (synchronous).  Batches of at
  * least 20 000 tracks run as 2-8 chunks whose copies overlap the other
  * chunks' fits (each chunk's fit on a stream of the handle); pinned host
- * memory makes the copies asynchronous.  Results equal kf_fit_ex's. */
+ * memory makes the copies asynchronous.  Results equal kf_fit_ex's.
+ * Returns KF_EDEVICE when a bounded device wait of this call gave up. */
 int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
                 const kf_surfaces* surfaces, const kf_measurements* meas,
                 const kf_field* field, const kf_options* opt,
@@ -287,6 +304,9 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
  * as kf_fit_ex.
  * The first call on a device looks up the block's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The call returns before its GPU work runs, so a bounded device wait that
+ * gives up (not expected in normal operation) shows in the outputs: the
+ * tracks of that launch get status KF_TRACK_TIMEOUT and NaN results.
  * Every call reuses the same block, which keeps
  * the previous call's contents: calls whose GPU work overlaps (other streams
  * or host threads) race on it and must be serialised by the caller. */

@@ -24,7 +24,7 @@ KF_PRECISION_FP64 = 0
 KF_PRECISION_MIXED = 1
 KF_SCHEDULE_AUTO, KF_SCHEDULE_GRID, KF_SCHEDULE_PERSISTENT, KF_SCHEDULE_SORTED, KF_SCHEDULE_WAVES = -1, 0, 1, 2, 3
 KF_SMOOTHER_RTS, KF_SMOOTHER_BACKWARD_FILTER = 0, 1
-TRACK_STATUS = {0: "ok", 1: "no_intersection", 2: "non_spd", 3: "nonfinite", 4: "bad_input"}
+TRACK_STATUS = {0: "ok", 1: "no_intersection", 2: "non_spd", 3: "nonfinite", 4: "bad_input", 5: "timeout"}
 MUON_MASS = 0.1056583755
 
 # exported symbols of include/kf.h
@@ -79,7 +79,8 @@ class KfOptions(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("smoother", ctypes.c_int32),
                 ("energy_loss", ctypes.c_int32), ("bf_scale", ctypes.c_double),
-                ("material", KfMaterial), ("resident_warps", ctypes.c_int32)]
+                ("material", KfMaterial), ("resident_warps", ctypes.c_int32),
+                ("wait_limit", ctypes.c_int32), ("test_wait_timeout", ctypes.c_int32)]
 
 
 _lib = None

@@ -990,9 +990,19 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
   __shared__ __align__(8) uint64_t s_mbar;
   const FitParams& p = g.f;
   const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
-                                     p.error_flag);
-  if (!staged) return;
+                                     p.error_flag, p.wait_limit, p.skip_stage_copy != 0);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!staged || call_failed(p.error_flag)) {
+    // a bounded wait of this call gave up: this CTA's tracks get NaN chi2
+    // and seed gradients and add nothing to the alignment gradient (the
+    // whole CTA returns here, so no warp-wide reduction below is entered)
+    if (t < p.n_tracks) {
+      if (g.chi2) g.chi2[t] = qnan();
+      if (g.grad_seed)
+        for (int e = 0; e < 6; ++e) g.grad_seed[(size_t)e * p.n_tracks + t] = qnan();
+    }
+    return;
+  }
   const bool in_range = t < p.n_tracks;
   const int tt = in_range ? t : 0;
   const size_t TT = (size_t)p.n_tracks;

@@ -12,6 +12,15 @@
 
 using namespace kfgb;
 
+namespace {
+thread_local char g_cuda_err[256] = "no CUDA error";
+}
+
+int kfgb::cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? KF_ENOMEM : KF_ECUDA;
+}
+
 struct kf_handle {
   int device = -1;
   // device workspace (per-state records) and the packed surface table
@@ -55,12 +64,6 @@ struct kf_handle {
 
 namespace {
 
-thread_local char g_cuda_err[256] = "no CUDA error";
-
-int cuda_fail(cudaError_t e, const char* what) {
-  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", what, cudaGetErrorString(e));
-  return e == cudaErrorMemoryAllocation ? KF_ENOMEM : KF_ECUDA;
-}
 
 constexpr double kMuonMass = 0.1056583755;
 constexpr int64_t kDefaultWorkspace = int64_t(32) << 30;
@@ -122,6 +125,7 @@ int validate(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* 
   if (opt->block < 0 || (opt->block % 32) != 0 || opt->block > max_block(opt->precision == KF_PRECISION_MIXED, opt->min_blocks))
     return KF_EUNSUPPORTED;
   if (opt->resident_warps < 0 || opt->resident_warps > 64) return KF_EINVAL;
+  if (opt->wait_limit < 0 || (opt->test_wait_timeout != 0 && opt->test_wait_timeout != 1)) return KF_EINVAL;
   for (int i = 0; i < 3; ++i)
     if (!(fi->b[i] == fi->b[i])) return KF_EINVAL;
   if (opt->smoother != KF_SMOOTHER_RTS && opt->smoother != KF_SMOOTHER_BACKWARD_FILTER) return KF_EUNSUPPORTED;
@@ -178,6 +182,8 @@ void kf_default_options(kf_options* opt) {
   opt->energy_loss = 0;
   opt->bf_scale = 1e4;
   silicon(&opt->material);
+  opt->wait_limit = 0;
+  opt->test_wait_timeout = 0;
 }
 
 int kf_abi_version(void) { return KF_ABI_VERSION; }
@@ -203,7 +209,7 @@ const char* kf_strerror(int code) {
     case KF_ECUDA: return "CUDA error (see kf_last_cuda_error)";
     case KF_ENOMEM: return "out of memory";
     case KF_EUNSUPPORTED: return "unsupported option";
-    case KF_EDEVICE: return "device-side wait timed out";
+    case KF_EDEVICE: return "a device-side bounded wait timed out (its tracks have status KF_TRACK_TIMEOUT)";
     case KF_ESIZE: return "batch does not fit the fixed device block of kf_fit_static";
     default: return "unknown error";
   }
@@ -369,6 +375,9 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   cudaError_t e = cudaSuccess;
   int launches = 0;
   if (pack) {
+    // a new call: clear the flag a timed-out wait of an earlier call left
+    e = cudaMemsetAsync(h->error_flag, 0, sizeof(int32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(error flag)");
     e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
     if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
     launches = 1;
@@ -417,6 +426,8 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
     if (p.ws32) p.ws32 += kRec32Mixed * (size_t)tr->max_states * (size_t)t_begin;
   }
   p.error_flag = h->error_flag;
+  p.wait_limit = opt.wait_limit;
+  p.skip_stage_copy = opt.test_wait_timeout;
   p.order = opt.schedule == KF_SCHEDULE_SORTED ? h->order : nullptr;
   p.resident_warps = opt.resident_warps;
   p.waves = opt.schedule == KF_SCHEDULE_WAVES;
@@ -722,7 +733,9 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
     h->ckpt_bytes = need;
   }
   if ((rc = ensure_surf(h, su->n_surfaces))) return rc;
-  cudaError_t e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
+  cudaError_t e = cudaMemsetAsync(h->error_flag, 0, sizeof(int32_t), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(error flag)");
+  e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
   if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
   FitParams p;
   memset(&p, 0, sizeof(p));
@@ -744,6 +757,8 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   p.h_max = opt.h_max;
   p.n_iter = opt.n_iter;
   p.error_flag = h->error_flag;
+  p.wait_limit = opt.wait_limit;
+  p.skip_stage_copy = opt.test_wait_timeout;
   e = launch_grad(p, align, dl_dchi2, out_chi2, grad_seed, grad_align, h->ckpt, n_ckpt, grad_block,
                   opt.min_blocks, stream);
   if (e != cudaSuccess) return cuda_fail(e, "grad launch");
@@ -958,6 +973,7 @@ int kf_fit_host(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
         // the surface table (in chunk 0's copies) is packed once and the
         // work counters reset once, before any fit
         e = cudaStreamWaitEvent(stream, h->ev_in[0], 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->error_flag, 0, sizeof(int32_t), stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
         e = launch_pack_surfaces(dsu.n_surfaces, dsu.center, dsu.rot, dsu.x_over_x0, h->surf, stream);
         if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");

@@ -12,7 +12,9 @@ namespace dev {
 constexpr double kKappa = 2.99792458e-4;   // GeV / (T mm): curvature = kappa B q/p
 constexpr double kInvC = 1.0 / 299.792458;  // ns / mm
 
-enum : int { ST_OK = 0, ST_NO_INTERSECTION = 1, ST_NON_SPD = 2, ST_NONFINITE = 3, ST_BAD_INPUT = 4 };
+enum : int { ST_OK = 0, ST_NO_INTERSECTION = 1, ST_NON_SPD = 2, ST_NONFINITE = 3, ST_BAD_INPUT = 4, ST_TIMEOUT = 5 };
+
+constexpr int kDefaultWaitLimit = 1 << 20;  // polls of a bounded wait
 
 // packed lower-triangle index
 __host__ __device__ constexpr int sy(int i, int j) { return i * (i + 1) / 2 + j; }
@@ -26,9 +28,13 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 }
 
 // Every thread of the CTA calls this.  Returns false if the bounded wait on
-// the copy's mbarrier gave up (the error flag is then set).
+// the copy's mbarrier gave up after wait_limit polls (<= 0: the default);
+// the error flag is then set.  skip_copy (a diagnostic of the timeout path)
+// announces the copy's bytes on the barrier but issues no copy, so the wait
+// runs out with nothing in flight.
 __device__ __forceinline__ bool stage_surfaces(double* s_surf, const double* g_surf, uint32_t nbytes,
-                                               uint64_t* mbar, int32_t* error_flag) {
+                                               uint64_t* mbar, int32_t* error_flag, int wait_limit = 0,
+                                               bool skip_copy = false) {
   const uint32_t bar = smem_addr(mbar);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -37,14 +43,16 @@ __device__ __forceinline__ bool stage_surfaces(double* s_surf, const double* g_s
   __syncthreads();
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(nbytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(s_surf)),
-        "l"(g_surf), "r"(nbytes), "r"(bar)
-        : "memory");
+    if (!skip_copy)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_addr(s_surf)),
+          "l"(g_surf), "r"(nbytes), "r"(bar)
+          : "memory");
   }
+  const int limit = wait_limit > 0 ? wait_limit : kDefaultWaitLimit;
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 20) && !done; ++it) {
+  for (int it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -56,6 +64,14 @@ __device__ __forceinline__ bool stage_surfaces(double* s_surf, const double* g_s
     return false;
   }
   return true;
+}
+
+// True when a bounded wait of this call gave up somewhere (the flag is reset
+// at the start of every call).  CTAs that see it fit nothing: a copy that a
+// timed-out CTA left in flight could land in shared memory that a later CTA
+// on the same SM has been given.
+__device__ __forceinline__ bool call_failed(const int32_t* error_flag) {
+  return *reinterpret_cast<const volatile int32_t*>(error_flag) != 0;
 }
 
 struct Surf {
@@ -189,19 +205,42 @@ __device__ __forceinline__ int track_of(const FitParams& p, int i) {
   return p.order ? p.order[p.track0 + i] : p.track0 + i;
 }
 
+// Outputs of a track the launch could not fit: NaN parameters, covariance,
+// chi2 and smoothed states, ndf 0, the given status.
+__device__ __forceinline__ void write_failed_track(const FitParams& p, int i, int status) {
+  const int t = track_of(p, i);
+  const size_t TT = (size_t)p.n_tracks_total;
+  const double nan = qnan();
+#pragma unroll
+  for (int e = 0; e < 6; ++e) p.out_params[e * TT + t] = nan;
+#pragma unroll
+  for (int e = 0; e < 21; ++e) p.out_cov[e * TT + t] = nan;
+  p.out_chi2[t] = nan;
+  if (p.out_ndf) p.out_ndf[t] = 0;
+  if (p.out_status) p.out_status[t] = (uint8_t)status;
+  if (p.out_states) {
+    const int64_t o0 = p.offsets[t], o1 = p.offsets[t + 1];
+    if (o0 >= 0 && o1 > o0 && o1 <= p.n_states && o1 - o0 <= p.max_states)
+      for (int64_t k = o0; k < o1; ++k)
+        for (int e = 0; e < 6; ++e) p.out_states[e * p.n_states + k] = nan;
+  }
+}
+
 // The fit kernel: stage the surface table once per CTA, then either one
 // track per thread over the grid (work_counter == nullptr) or a persistent
 // loop in which every CTA takes blockDim-track units from a global counter
 // until the batch is exhausted (balances uneven tracks).
-// Body::run(p, s_surf, i) fits slot i.
+// Body::run(p, s_surf, i) fits slot i.  A CTA whose staging wait gave up, or
+// that starts after another CTA's did, writes its tracks as failed
+// (status ST_TIMEOUT) instead of fitting them.
 template <class Body, int MINB>
 __global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* s_surf = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(8) uint64_t s_mbar;
-  const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
-                                     p.error_flag);
-  if (!staged) return;
+  bool ok = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar, p.error_flag,
+                           p.wait_limit, p.skip_stage_copy != 0);
+  if (ok && call_failed(p.error_flag)) ok = false;
   // One call site for both schedules. A grid CTA fits its own blockDim
   // tracks once; a persistent CTA keeps taking blockDim-track units. The
   // whole CTA takes a unit together, so its warps start every unit in step
@@ -220,7 +259,12 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitP
     }
     if (base >= p.n_tracks) break;
     const int i = base + threadIdx.x;
-    if (i < p.n_tracks) Body::run(p, s_surf, i);
+    if (i < p.n_tracks) {
+      if (ok)
+        Body::run(p, s_surf, i);
+      else
+        write_failed_track(p, i, ST_TIMEOUT);
+    }
     if (!persistent) break;
   }
 }

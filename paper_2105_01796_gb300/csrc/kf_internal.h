@@ -67,6 +67,9 @@ struct FitParams {
   double* ws64;            // [max_states][rec64][n_tracks]
   float* ws32;             // [max_states][rec32][n_tracks] (mixed only)
   int32_t* error_flag;     // set to 1 when a bounded device wait gives up
+  int32_t wait_limit;      // polls of a bounded wait (0 = the default)
+  int32_t skip_stage_copy; // diagnostic: announce but skip the surface-table
+                           // copy, so that every staging wait runs out
   int32_t* work_counter;   // non-null: persistent launch, warps take 32-track
                            // units from this counter (zeroed before launch)
   const int32_t* order;    // non-null: slot s fits track order[s]
@@ -83,6 +86,10 @@ struct FitParams {
   double map_inv_spacing[3];
   const double* map_b;     // null: the constant field bfield
 };
+
+// Record a failed CUDA call for kf_last_cuda_error() and map it to a
+// kf_error code (KF_ENOMEM for allocation failures, else KF_ECUDA).
+int cuda_fail(cudaError_t e, const char* what);
 
 // True when the options or the field ask for a method variant.
 inline bool wants_variants(int smoother, int energy_loss, const void* map) {

@@ -88,6 +88,7 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   if (opt.schedule < KF_SCHEDULE_GRID || opt.schedule > KF_SCHEDULE_PERSISTENT) return KF_EUNSUPPORTED;
   if (opt.min_blocks < 0 || opt.min_blocks > 4) return KF_EUNSUPPORTED;
   if (opt.resident_warps < 0 || opt.resident_warps > 64) return KF_EINVAL;
+  if (opt.wait_limit < 0 || (opt.test_wait_timeout != 0 && opt.test_wait_timeout != 1)) return KF_EINVAL;
   // the static block serves the baseline method only
   if (wants_variants(opt.smoother, opt.energy_loss, fi->map)) return KF_EUNSUPPORTED;
   // size limits of the static block
@@ -99,7 +100,7 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
 
   void* base = nullptr;
   cudaError_t e = static_block(&base);
-  if (e != cudaSuccess) return KF_ECUDA;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static block)");
   cudaStream_t stream = (cudaStream_t)stream_v;
   char* b = (char*)base;
   double* surf = (double*)b;
@@ -112,9 +113,9 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   const size_t bytes64 = (n64 * sizeof(double) * tr->max_states * chunk + 255) / 256 * 256;
 
   e = cudaMemsetAsync(flag, 0, 2 * sizeof(int32_t), stream);  // flag and work counter start at zero
-  if (e != cudaSuccess) return KF_ECUDA;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(static flag)");
   e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, surf, stream);
-  if (e != cudaSuccess) return KF_ECUDA;
+  if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
   FitParams p;
   memset(&p, 0, sizeof(p));
   p.resident_warps = opt.resident_warps;
@@ -143,6 +144,8 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   p.ws64 = (double*)rec;
   p.ws32 = opt.precision == KF_PRECISION_FP64 ? nullptr : (float*)(rec + bytes64);
   p.error_flag = flag;
+  p.wait_limit = opt.wait_limit;
+  p.skip_stage_copy = opt.test_wait_timeout;
   // persistent launches share one work counter, re-zeroed before each chunk
   const bool persistent = opt.schedule != KF_SCHEDULE_GRID;
   for (size_t t0 = 0; t0 < (size_t)tr->n_tracks; t0 += chunk) {
@@ -151,10 +154,10 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
     p.work_counter = persistent ? flag + 1 : nullptr;
     if (persistent && t0 > 0) {
       e = cudaMemsetAsync(flag + 1, 0, sizeof(int32_t), stream);
-      if (e != cudaSuccess) return KF_ECUDA;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(static counter)");
     }
     e = launch_fit(p, opt.precision, opt.block, opt.min_blocks, stream);
-    if (e != cudaSuccess) return KF_ECUDA;
+    if (e != cudaSuccess) return cuda_fail(e, "fit launch");
   }
   return KF_SUCCESS;
 }

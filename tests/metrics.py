@@ -23,3 +23,49 @@ def cov_err(c, ref_cov):
 
 def chi2_err(c, ref):
     return np.abs(c - ref) / np.maximum(np.abs(ref), 1.0)
+
+
+def state_sigmas(ev, **fit_kw):
+    """Smoothed standard deviations of every state [6][M] from the oracle's
+    per-track fits (the floor of the per-state parameter metric)."""
+    import oracle
+    o = np.asarray(ev["offsets"], dtype=np.int64)
+    sd = np.full((6, int(o[-1])), np.nan)
+    for t in range(int(ev["n_tracks"])):
+        r = oracle.fit_track(ev, t, **fit_kw)
+        if r["status"] == 0:
+            sd[:, o[t]:o[t + 1]] = np.sqrt(np.abs(np.diagonal(r["Cs"], axis1=1, axis2=2))).T
+    return sd
+
+
+def states_err(g_states, r_states, sd):
+    """|dx| / max(|x_ref|, sigma of that state) on every state."""
+    return np.abs(g_states - r_states) / np.maximum(np.abs(r_states), sd)
+
+
+# Element-wise check of gradients against central finite differences.  The
+# oracle's objective L carries a relative rounding noise of about 1e-14 (a few
+# thousand FP64 operations per state), which a central difference with step h
+# turns into an absolute noise of about 1e-14 |L| / h in the derivative.  The
+# floor is the derivative at which that noise is 1e-5 of it:
+#   floor = 1e-14 |L| / h / 1e-5 = 1e-3 |L| (1e-6 / h),
+# so |g - fd| <= 1e-5 max(|fd|, floor) holds each element to 1e-5 relative
+# down to the size that finite differences can resolve at all.
+FD_NOISE_REL = 1e-14
+
+
+def fd_floor(l_abs, h, tol=1e-5):
+    return FD_NOISE_REL * np.asarray(l_abs) / np.asarray(h) / tol
+
+
+def seed_steps(seed_params, h=1e-6):
+    """The FD steps of oracle.chi2_gradient_fd for the seeds [6][T] (the q/p
+    step is relative)."""
+    hs = np.full(np.shape(seed_params), h, dtype=np.float64)
+    hs[4] = h * np.abs(np.asarray(seed_params)[4])
+    return hs
+
+
+def grad_err(g, fd, floor):
+    """|g - fd| / max(|fd|, floor), element-wise."""
+    return np.abs(np.asarray(g) - np.asarray(fd)) / np.maximum(np.abs(fd), floor)

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_host_only_entry_points(lib):
-    assert lib.kf_abi_version() == 3
+    assert lib.kf_abi_version() == 4
     o = kf.kf_default_options()
     assert o.precision == 0 and abs(o.mass - 0.1056583755) < 1e-15
     assert o.h_max == 50.0 and o.n_iter == 3 and o.block == 128

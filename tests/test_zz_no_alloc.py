@@ -5,8 +5,9 @@ never wait on the CUDA allocator, hosts that give the library a fixed memory
 budget and own all other device memory -- call kf_fit_static.  Its scratch space is one
 fixed block of device memory per GPU that the library reserves for the life
 of the process.  These tests check, through the C ABI, that its results
-match kf_fit_ex on two different batches fitted one after the other (the
-second call must not be affected by what the first left in the block), and
+equal kf_fit_ex's bit for bit on two different batches fitted one after the
+other (the second call must not be affected by what the first left in the
+block), with the grid and the persistent schedule, and
 that a batch too large for the block is refused with a clear error.
 
 This file is collected last so that a run stopping at the first failure has
@@ -17,11 +18,8 @@ import pytest
 
 import paper_2105_01796_gb300 as kf
 from paper_2105_01796_gb300 import synth
-from tests.metrics import chi2_err, cov_err, param_err
 
 pytestmark = pytest.mark.gpu
-
-TOL = {kf.KF_PRECISION_FP64: (1e-9, 1e-9, 1e-9), kf.KF_PRECISION_MIXED: (1e-4, 1e-3, 1e-4)}
 
 
 @pytest.fixture(scope="module")
@@ -39,10 +37,14 @@ def _host(out):
     return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
 
 
+@pytest.mark.parametrize("schedule", [kf.KF_SCHEDULE_GRID, kf.KF_SCHEDULE_PERSISTENT])
 @pytest.mark.parametrize("prec", [kf.KF_PRECISION_FP64, kf.KF_PRECISION_MIXED])
-def test_static_block_matches_fit_ex_on_two_calls_in_a_row(handle, prec):
+def test_static_block_matches_fit_ex_on_two_calls_in_a_row(handle, prec, schedule):
+    """Both entry points run the same kernel on every track (one thread per
+    track; how the batch is cut into launches does not enter a track's
+    arithmetic), so their outputs are equal bit for bit."""
     import torch
-    opt = kf.kf_default_options(prec)
+    opt = kf.kf_default_options(prec, schedule=schedule)
     # 7000 x 31 states needs several launches through the fixed block in FP64
     # (about 3000 tracks per launch) and in mixed precision (about 5800)
     events = [synth.make_event(synth.scaled(synth.WORKLOADS["tel30_100k"], 7000)),
@@ -54,19 +56,14 @@ def test_static_block_matches_fit_ex_on_two_calls_in_a_row(handle, prec):
         kf.kf_fit_static(dev, out, opt)
         outs.append(out)
     torch.cuda.synchronize()
-    tp, tc, tx = TOL[prec]
     for ev, dev, out in zip(events, devs, outs):
         ref = kf.alloc_outputs(ev["n_tracks"])
         kf.kf_fit_ex(handle, dev, ref, opt)
         torch.cuda.synchronize()
         a, r = _host(out), _host(ref)
-        assert np.array_equal(a["status"], r["status"])
-        assert np.array_equal(a["ndf"], r["ndf"])
-        ok = r["status"] == 0
-        assert ok.all()
-        assert param_err(a["params"][:, ok], r["params"][:, ok], r["cov"][:, ok]).max() < tp
-        assert cov_err(a["cov"][:, ok], r["cov"][:, ok]).max() < tc
-        assert chi2_err(a["chi2"][ok], r["chi2"][ok]).max() < tx
+        assert np.all(r["status"] == 0)
+        for k in ("params", "cov", "chi2", "ndf", "status"):
+            assert np.array_equal(a[k], r[k]), k
 
 
 def test_static_block_refuses_batches_that_do_not_fit(handle):

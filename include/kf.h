@@ -331,7 +331,8 @@ int kf_autotune(kf_handle* handle, const kf_tracks* tracks,
                 const kf_outputs* out, void* stream, kf_options* best,
                 double* best_ms);
 
-/* Gradient of the summed chi2 (the adjoint of the filter).
+/* Gradient of the summed chi2 (the adjoint of the filter; kf_grad with
+ * v = W = 0).
  * L = sum_t w_t chi2_t with w_t = dl_dchi2[t] (NULL: all 1); chi2_t as
  * returned by kf_fit (predicted-residual chi2, which the smoother does not
  * change).  Computed in FP64 whatever opt->precision says.
@@ -356,6 +357,53 @@ int kf_chi2_grad(kf_handle* handle, const kf_tracks* tracks,
                  const kf_options* opt, const double* dl_dchi2,
                  double* out_chi2, double* grad_seed, double* grad_align,
                  void* stream);
+
+/* Weights of the adjoint's objective (kf_grad):
+ *   L = sum_t [ w_t chi2_t + sum_i v_ti x_s0,ti + sum_e W_te C_s0,te ],
+ * x_s0 = out_params and C_s0 = out_cov (packed, 21) of the fit: the
+ * smoothed parameters and covariance of state 0.  With torch.autograd these
+ * are the incoming gradients of the three outputs. */
+typedef struct {
+  const double* dl_dchi2;      /* w [T]; NULL: all 1 */
+  const double* dl_dparams;    /* v [6][T]; NULL: all 0 */
+  const double* dl_dcov;       /* W [21][T] over the packed elements; NULL: all 0 */
+} kf_grad_weights;
+
+typedef struct {
+  double* chi2;                /* [T] chi2 per track (optional) */
+  double* params;              /* [6][T] x_s0 at this alignment (optional) */
+  double* cov;                 /* [21][T] C_s0 at this alignment (optional) */
+  double* grad_seed;           /* [6][T] dL/d seed_params (optional) */
+  double* grad_align;          /* [6][S] dL/d align (optional; overwritten) */
+} kf_grad_outputs;
+
+/* The adjoint of the whole fit, filter and smoother (paper Sect. 2: the
+ * filter step list and the smoother paragraph): the value and gradient of
+ * L above with respect to the seed parameters and the per-surface alignment,
+ * in FP64 whatever opt->precision says.  align as for kf_chi2_grad.
+ * Method: reverse mode throughout, one thread per track.
+ *   1. forward filter, (x_f, C_f) checkpointed every 5 states;
+ *   2. RTS smoother (when params, cov or the v / W terms are asked), from
+ *      the last state down, each 5-state segment's filtered states and
+ *      transports recomputed from its checkpoint; smoothed checkpoints at
+ *      the segment starts;
+ *   3. reverse of the smoother (when v or W is given), segment by segment
+ *      upwards, each segment's filtered and smoothed states recomputed from
+ *      the two kinds of checkpoint; each step's contributions to the
+ *      adjoints of x_f, C_f, x_p, C_p and F (79 doubles per state) are kept
+ *      in the handle's scratch for
+ *   4. the reverse of the filter (as kf_chi2_grad) with those contributions
+ *      added at every state.
+ * No filtered or smoothed state is stored beyond the checkpoints.  Scratch
+ * per track: 216 B per 5 states (filter checkpoints), plus with v or W 216 B
+ * per 5 states (smoothed checkpoints) and 632 B per state; a batch whose
+ * scratch exceeds opt->workspace_bytes (0: 32 GiB) runs as several launches.
+ * Launch shape and failure behaviour as for kf_chi2_grad; a track whose
+ * smoother meets a non-positive pivot gets NaN outputs and gradients.
+ * Device pointers; asynchronous on `stream`. */
+int kf_grad(kf_handle* handle, const kf_tracks* tracks, const kf_surfaces* surfaces, const double* align,
+            const kf_measurements* meas, const kf_field* field, const kf_options* opt,
+            const kf_grad_weights* weights, const kf_grad_outputs* out, void* stream);
 
 /* Bytes of device workspace kf_fit_ex would use for this batch shape. */
 int64_t kf_workspace_size(int32_t n_tracks, int32_t max_states,

@@ -415,16 +415,45 @@ def chi2_per_track(ev, align=None, seed_params=None, **kw):
     return fit_batch(e, **kw)["chi2"]
 
 
-def chi2_gradient_fd(ev, align=None, weights=None, h_shift=1e-6, h_rot=1e-6, h_seed=1e-6, n_threads=None):
-    """Gradient of L = sum_t w_t chi2_t by central finite differences of the
-    oracle (the plain definition of the derivative).  Returns
-    (grad_seed [6][T], grad_align [6][S]).  Steps are in the parameters'
-    units (mm, rad, GeV^-1, ns); the q/p step is relative to |q/p|."""
+def objective_per_track(ev, align=None, seed_params=None, weights=None, dl_dparams=None, dl_dcov=None,
+                        **kw):
+    """Per-track objective of the fit with the geometry aligned by `align`:
+    L_t = w_t chi2_t + sum_i v_it x_s0,it + sum_e W_et C_s0,et, where x_s0 and
+    C_s0 (packed, 21) are the smoothed parameters and covariance of state 0
+    (paper Sect. 2: the smoother's output), w = weights [T] (default 1),
+    v = dl_dparams [6][T] and W = dl_dcov [21][T] (default 0).  Returns
+    (L [T], |terms| [T]: the sum of the terms' magnitudes, the scale of L's
+    rounding noise)."""
+    e = dict(ev)
+    if align is not None:
+        e["center"], e["rot"] = apply_alignment(ev["center"], ev["rot"], align)
+    if seed_params is not None:
+        e["seed_params"] = seed_params
+    r = fit_batch(e, **kw)
+    T = int(ev["n_tracks"])
+    w = np.ones(T) if weights is None else np.asarray(weights, dtype=np.float64)
+    terms = [w * r["chi2"]]
+    if dl_dparams is not None:
+        terms += list(np.asarray(dl_dparams, dtype=np.float64) * r["params"])
+    if dl_dcov is not None:
+        terms += list(np.asarray(dl_dcov, dtype=np.float64) * r["cov"])
+    terms = np.stack(terms)
+    return terms.sum(axis=0), np.abs(terms).sum(axis=0)
+
+
+def objective_gradient_fd(ev, align=None, weights=None, dl_dparams=None, dl_dcov=None, h_shift=1e-6,
+                          h_rot=1e-6, h_seed=1e-6, n_threads=None):
+    """Gradient of L = sum_t L_t (objective_per_track) with respect to the
+    seed parameters and the per-surface alignment, by central finite
+    differences of the oracle (the plain definition of the derivative).
+    Returns (grad_seed [6][T], grad_align [6][S]).  Steps are in the
+    parameters' units (mm, rad, GeV^-1, ns); the q/p step is relative to
+    |q/p|."""
     T = int(ev["n_tracks"])
     S = ev["center"].shape[1]
     a0 = np.zeros((6, S)) if align is None else np.asarray(align, dtype=np.float64)
-    w = np.ones(T) if weights is None else np.asarray(weights, dtype=np.float64)
     seeds = np.asarray(ev["seed_params"], dtype=np.float64)
+    kw = dict(weights=weights, dl_dparams=dl_dparams, dl_dcov=dl_dcov, n_threads=n_threads)
     gs = np.zeros((6, T))
     for i in range(6):
         hv = np.full(T, h_seed)
@@ -432,16 +461,24 @@ def chi2_gradient_fd(ev, align=None, weights=None, h_shift=1e-6, h_rot=1e-6, h_s
             hv = h_seed * np.abs(seeds[4])
         sp = seeds.copy(); sp[i] += hv
         sm = seeds.copy(); sm[i] -= hv
-        cp = chi2_per_track(ev, a0, sp, n_threads=n_threads)
-        cm = chi2_per_track(ev, a0, sm, n_threads=n_threads)
-        gs[i] = w * (cp - cm) / (2 * hv)
+        lp, _ = objective_per_track(ev, a0, sp, **kw)
+        lm, _ = objective_per_track(ev, a0, sm, **kw)
+        gs[i] = (lp - lm) / (2 * hv)
     ga = np.zeros((6, S))
     for s in range(S):
         for e in range(6):
             h = h_shift if e < 3 else h_rot
             ap = a0.copy(); ap[e, s] += h
             am = a0.copy(); am[e, s] -= h
-            cp = chi2_per_track(ev, ap, n_threads=n_threads)
-            cm = chi2_per_track(ev, am, n_threads=n_threads)
-            ga[e, s] = np.sum(w * (cp - cm)) / (2 * h)
+            lp, _ = objective_per_track(ev, ap, **kw)
+            lm, _ = objective_per_track(ev, am, **kw)
+            ga[e, s] = np.sum(lp - lm) / (2 * h)
     return gs, ga
+
+
+def chi2_gradient_fd(ev, align=None, weights=None, h_shift=1e-6, h_rot=1e-6, h_seed=1e-6, n_threads=None):
+    """Gradient of L = sum_t w_t chi2_t by central finite differences of the
+    oracle (objective_gradient_fd without the smoother terms).  Returns
+    (grad_seed [6][T], grad_align [6][S])."""
+    return objective_gradient_fd(ev, align, weights, h_shift=h_shift, h_rot=h_rot, h_seed=h_seed,
+                                 n_threads=n_threads)

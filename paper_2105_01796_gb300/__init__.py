@@ -31,7 +31,7 @@ MUON_MASS = 0.1056583755
 EXPORTS = ("kf_default_options", "kf_create", "kf_destroy", "kf_fit", "kf_fit_ex",
            "kf_fit_host", "kf_workspace_size", "kf_last_launch_count", "kf_strerror",
            "kf_last_cuda_error", "kf_abi_version", "kf_selftest", "kf_fit_static",
-           "kf_autotune", "kf_chi2_grad")
+           "kf_autotune", "kf_chi2_grad", "kf_grad")
 
 
 class KfTracks(ctypes.Structure):
@@ -70,6 +70,16 @@ class KfOutputs(ctypes.Structure):
     _fields_ = [("params", ctypes.c_void_p), ("cov", ctypes.c_void_p),
                 ("chi2", ctypes.c_void_p), ("ndf", ctypes.c_void_p),
                 ("status", ctypes.c_void_p), ("states", ctypes.c_void_p)]
+
+
+class KfGradWeights(ctypes.Structure):
+    _fields_ = [("dl_dchi2", ctypes.c_void_p), ("dl_dparams", ctypes.c_void_p),
+                ("dl_dcov", ctypes.c_void_p)]
+
+
+class KfGradOutputs(ctypes.Structure):
+    _fields_ = [("chi2", ctypes.c_void_p), ("params", ctypes.c_void_p), ("cov", ctypes.c_void_p),
+                ("grad_seed", ctypes.c_void_p), ("grad_align", ctypes.c_void_p)]
 
 
 class KfOptions(ctypes.Structure):
@@ -127,6 +137,11 @@ def load(path: str = LIB_PATH):
                                      ctypes.POINTER(KfMeasurements), ctypes.POINTER(KfField),
                                      ctypes.POINTER(KfOptions), P, P, P, P, P]
         lib.kf_chi2_grad.restype = ctypes.c_int
+        lib.kf_grad.argtypes = [P, ctypes.POINTER(KfTracks), ctypes.POINTER(KfSurfaces), P,
+                                ctypes.POINTER(KfMeasurements), ctypes.POINTER(KfField),
+                                ctypes.POINTER(KfOptions), ctypes.POINTER(KfGradWeights),
+                                ctypes.POINTER(KfGradOutputs), P]
+        lib.kf_grad.restype = ctypes.c_int
         lib.kf_autotune.argtypes = [P] + base + [ctypes.POINTER(KfOptions), ctypes.POINTER(KfOutputs), P,
                                                  ctypes.POINTER(KfOptions), ctypes.POINTER(ctypes.c_double)]
         lib.kf_autotune.restype = ctypes.c_int
@@ -380,6 +395,29 @@ def kf_chi2_grad(handle: Handle, dev_ev, align=None, dl_dchi2=None, out_chi2=Non
                                ctypes.c_void_p(int(stream))))
 
 
+def kf_grad(handle: Handle, dev_ev, align=None, dl_dchi2=None, dl_dparams=None, dl_dcov=None, out_chi2=None,
+            out_params=None, out_cov=None, grad_seed=None, grad_align=None, opt: KfOptions | None = None,
+            stream=None):
+    """The adjoint of the whole fit (filter and smoother): chi2 [T], the
+    smoothed state-0 parameters [6][T] and covariance [21][T] at this
+    alignment, and the gradient of
+    L = sum_t [w_t chi2_t + v_t . params_t + W_t . cov_t]
+    (w = dl_dchi2, default 1; v = dl_dparams, W = dl_dcov, default 0) with
+    respect to the seeds (grad_seed [6][T]) and the per-surface alignment
+    (grad_align [6][S]).  Device tensors; None outputs are skipped."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    tr, su, me, fi = _structs(dev_ev, dev_ev["max_states"])
+    w = KfGradWeights(_ptr(dl_dchi2), _ptr(dl_dparams), _ptr(dl_dcov))
+    o = KfGradOutputs(_ptr(out_chi2), _ptr(out_params), _ptr(out_cov), _ptr(grad_seed), _ptr(grad_align))
+    _check(load().kf_grad(handle.ptr, ctypes.byref(tr), ctypes.byref(su), _ptr(align), ctypes.byref(me),
+                          ctypes.byref(fi), ctypes.byref(opt) if opt is not None else None, ctypes.byref(w),
+                          ctypes.byref(o), ctypes.c_void_p(int(stream))))
+
+
 def _chi2_function():
     import torch
 
@@ -410,7 +448,41 @@ def _chi2_function():
                          grad_seed=gs, grad_align=ga)
             return gs, ga, None, None
 
-    return KalmanChi2
+    class KalmanFit(torch.autograd.Function):
+        """The whole fit -- chi2 [T], smoothed state-0 parameters [6][T] and
+        packed covariance [21][T] -- as a differentiable function of the seed
+        parameters and the surface alignment; the backward pass is the
+        library's adjoint of the filter and the smoother (kf_grad)."""
+
+        @staticmethod
+        def forward(ctx, seed_params, align, dev_ev, handle):
+            ev = dict(dev_ev)
+            ev["seed_params"] = seed_params.detach().contiguous()
+            T = int(ev["n_tracks"])
+            kw = dict(dtype=torch.float64, device=seed_params.device)
+            chi2, params, cov = torch.empty(T, **kw), torch.empty((6, T), **kw), torch.empty((21, T), **kw)
+            kf_grad(handle, ev, align=align.detach().contiguous(), out_chi2=chi2, out_params=params,
+                    out_cov=cov)
+            ctx.save_for_backward(seed_params.detach(), align.detach())
+            ctx.ev = dev_ev
+            ctx.handle = handle
+            return chi2, params, cov
+
+        @staticmethod
+        def backward(ctx, g_chi2, g_params, g_cov):
+            seed_params, align = ctx.saved_tensors
+            ev = dict(ctx.ev)
+            ev["seed_params"] = seed_params.contiguous()
+            gs = torch.empty_like(seed_params) if ctx.needs_input_grad[0] else None
+            ga = torch.empty_like(align) if ctx.needs_input_grad[1] else None
+            f64 = lambda t: None if t is None else t.contiguous().to(torch.float64)
+            w = f64(g_chi2) if g_chi2 is not None else torch.zeros(seed_params.shape[1], dtype=torch.float64,
+                                                                   device=seed_params.device)
+            kf_grad(ctx.handle, ev, align=align.contiguous(), dl_dchi2=w, dl_dparams=f64(g_params),
+                    dl_dcov=f64(g_cov), grad_seed=gs, grad_align=ga)
+            return gs, ga, None, None
+
+    return KalmanChi2, KalmanFit
 
 
 _CHI2_FN = None
@@ -421,4 +493,13 @@ def chi2_autograd(seed_params, align, dev_ev, handle):
     global _CHI2_FN
     if _CHI2_FN is None:
         _CHI2_FN = _chi2_function()
-    return _CHI2_FN.apply(seed_params, align, dev_ev, handle)
+    return _CHI2_FN[0].apply(seed_params, align, dev_ev, handle)
+
+
+def fit_autograd(seed_params, align, dev_ev, handle):
+    """Differentiable (chi2 [T], params [6][T], cov [21][T]) of the whole fit
+    (torch.autograd), see KalmanFit."""
+    global _CHI2_FN
+    if _CHI2_FN is None:
+        _CHI2_FN = _chi2_function()
+    return _CHI2_FN[1].apply(seed_params, align, dev_ev, handle)

@@ -904,13 +904,21 @@ __device__ __forceinline__ void aligned_plane_rev(const Surf& s, const double a[
 }
 
 struct GradParams {
-  FitParams f;          // geometry, inputs, options (outputs unused)
+  FitParams f;          // geometry, inputs, options (outputs unused); a
+                        // launch covers tracks [track0, track0 + n_tracks)
+                        // of n_tracks_total
   const double* align;  // [6][S] or null (zero alignment)
-  const double* dl_dchi2;  // [T] or null (all ones)
+  const double* dl_dchi2;    // [T] or null (all ones)
+  const double* dl_dparams;  // [6][T] or null: weights of the smoothed state-0 parameters
+  const double* dl_dcov;     // [21][T] or null: weights of its packed covariance
   double* chi2;         // [T] or null
+  double* out_params;   // [6][T] or null: smoothed parameters of state 0
+  double* out_cov;      // [21][T] or null: smoothed covariance of state 0
   double* grad_seed;    // [6][T] or null
   double* grad_align;   // [6][S] or null (accumulated with atomicAdd; zeroed by the host)
-  double* ckpt;         // [n_ckpt][27][T]
+  double* ckpt;         // [n_ckpt][27][n_tracks]: filtered checkpoints
+  double* sck;          // [n_ckpt + 1][27][n_tracks]: smoothed checkpoints
+  double* sadj;         // [max_states][kSmRec][n_tracks]: the smoother's adjoint contributions
   int32_t n_ckpt;
 };
 
@@ -961,6 +969,308 @@ __device__ __forceinline__ void cov_transport(const double F[6][6], const double
   Cp[sy(3, 3)] += qt;
 }
 
+// ---------------------------------------------------------------------------
+// the RTS smoother step and its reverse (paper Sect. 2, smoother paragraph)
+// ---------------------------------------------------------------------------
+
+// Cholesky factor L (packed lower) of an SPD 6x6 C and the reciprocals of its
+// diagonal; false on a non-positive pivot.
+__device__ __forceinline__ bool chol6(const double C[21], double L[21], double idg[6]) {
+  bool ok = true;
+#pragma unroll
+  for (int e = 0; e < 21; ++e) L[e] = C[e];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    double dj = L[sy(j, j)];
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if (q < j) dj -= L[sy(j, q)] * L[sy(j, q)];
+    if (!(dj > 0.0)) ok = false;
+    idg[j] = rsqrt_any(dj);
+    L[sy(j, j)] = dj * idg[j];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+      if (r > j) {
+        double v = L[sy(r, j)];
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          if (q < j) v -= L[sy(r, q)] * L[sy(j, q)];
+        L[sy(r, j)] = v * idg[j];
+      }
+  }
+  return ok;
+}
+
+// G = C^-1 (packed) from the Cholesky factor: Y = L^-1 (lower), G = Y^T Y.
+__device__ __forceinline__ void chol6_inverse(const double L[21], const double idg[6], double G[21]) {
+  double Y[21];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    Y[sy(j, j)] = idg[j];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+      if (r > j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          if (q >= j && q < r) v += L[sy(r, q)] * Y[sy(q, j)];
+        Y[sy(r, j)] = -v * idg[r];
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+      if (j <= i) {
+        double v = 0.0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+          if (r >= i) v += Y[sy(r, i)] * Y[sy(r, j)];
+        G[sy(i, j)] = v;
+      }
+}
+
+// What the reverse of one smoother step needs from its forward: M = G F with
+// G = Cp_{k+1}^-1, and dx = xs_{k+1} - xp_{k+1}, dC = Cs_{k+1} - Cp_{k+1}.
+struct RtsKeep {
+  double M[36], G[21], dx[6], dC[21];
+};
+
+// One RTS step from the smoothed state k+1 (xs, Cs) to state k:
+//   A = Cf_k F^T Cp_{k+1}^-1 = Cf_k M^T,  M = Cp_{k+1}^-1 F,
+//   xs_k = xf_k + A (xs_{k+1} - xp_{k+1}),  Cs_k = Cf_k + A (Cs_{k+1} - Cp_{k+1}) A^T.
+// F is the transport k -> k+1, xp, Cp its prediction.
+__device__ __noinline__ int rts_step_fwd(const double xf[6], const double Cf[21], const double xp[6], const double Cp[21],
+                            const JacS<double>& J, double xs[6], double Cs[21], RtsKeep* keep) {
+  double L[21], idg[6], G[21];
+  if (!chol6(Cp, L, idg)) return ST_NON_SPD;
+  chol6_inverse(L, idg, G);
+  double F[6][6];
+  dense_F(J, F);
+  double M[6][6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += G[sym(i, q)] * F[q][j];
+      M[i][j] = v;
+    }
+  double A[6][6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += Cf[sym(r, q)] * M[c][q];
+      A[r][c] = v;
+    }
+  double dx[6], dC[21];
+#pragma unroll
+  for (int e = 0; e < 6; ++e) dx[e] = xs[e] - xp[e];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) dC[e] = Cs[e] - Cp[e];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    double v = xf[r];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v += A[r][c] * dx[c];
+    xs[r] = v;
+  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    double z[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += A[r][q] * dC[sym(q, c)];
+      z[c] = v;
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+      if (c <= r) {
+        double v = Cf[sy(r, c)];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += z[q] * A[c][q];
+        Cs[sy(r, c)] = v;
+      }
+  }
+  if (keep) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) keep->M[i * 6 + j] = M[i][j];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) {
+      keep->G[e] = G[e];
+      keep->dC[e] = dC[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 6; ++e) keep->dx[e] = dx[e];
+  }
+  return ST_OK;
+}
+
+// Contributions of one smoother step to the adjoints of the filter's
+// quantities (symmetric matrices in the full-matrix convention, stored
+// packed): [0..5] x_f,k, [6..26] C_f,k, [27..32] x_p,k+1, [33..53] C_p,k+1,
+// [54..73] F_{k+1} rows 0-3 x columns 0-4, [74..78] its time row.
+constexpr int kSmXF = 0, kSmCF = 6, kSmXP = 27, kSmCP = 33, kSmF = 54, kSmRec = 79;
+
+// Reverse of rts_step_fwd.  In: lxs, Ls, the adjoints of xs_k, Cs_k (Ls
+// symmetric).  Out: lxs, Ls become the adjoints of xs_{k+1}, Cs_{k+1}; c[]
+// receives the step's contributions (layout above).  With LA the adjoint of
+// the gain A:
+//   LA = lxs dx^T + 2 Ls A dC;  l_dx = A^T lxs;  L_dC = A^T Ls A
+//   x_f: lxs;  C_f: Ls + sym(LA M);  F: G LA^T Cf;
+//   x_p: -l_dx;  C_p: -L_dC - sym(A^T LA G);  next: lxs = l_dx, Ls = L_dC.
+__device__ __noinline__ void rts_step_rev(const double Cf[21], const RtsKeep& r, double lxs[6], double Ls[6][6],
+                             double c[kSmRec]) {
+  double A[6][6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += Cf[sym(i, q)] * r.M[j * 6 + q];
+      A[i][j] = v;
+    }
+  // LsA = Ls A, then LA = lxs dx^T + 2 (Ls A) dC
+  double LA[6][6];
+  {
+    double LsA[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += Ls[i][q] * A[q][j];
+        LsA[i][j] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += LsA[i][q] * r.dC[sym(q, j)];
+        LA[i][j] = lxs[i] * r.dx[j] + 2.0 * v;
+      }
+    // L_dC = A^T (Ls A)
+    double LdC[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += A[q][i] * LsA[q][j];
+        LdC[i][j] = v;
+      }
+    // x_f and C_f (direct terms), before Ls is replaced
+#pragma unroll
+    for (int e = 0; e < 6; ++e) c[kSmXF + e] = lxs[e];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+        if (j <= i) c[kSmCF + sy(i, j)] = Ls[i][j];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) Ls[i][j] = 0.5 * (LdC[i][j] + LdC[j][i]);
+  }
+  // l_dx = A^T lxs
+  double ldx[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) v += A[q][j] * lxs[q];
+    ldx[j] = v;
+  }
+  // C_f += sym(LA M)
+  {
+    double T[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += LA[i][q] * r.M[q * 6 + j];
+        T[i][j] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+        if (j <= i) c[kSmCF + sy(i, j)] += 0.5 * (T[i][j] + T[j][i]);
+  }
+  // F: G LA^T Cf (rows 0-3 and 5, columns 0-4)
+  {
+    double LtC[6][6];  // LA^T Cf
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += LA[q][i] * Cf[sym(q, j)];
+        LtC[i][j] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      if (i == 4) continue;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += r.G[sym(i, q)] * LtC[q][j];
+        c[i == 5 ? kSmF + 20 + j : kSmF + i * 5 + j] = v;
+      }
+    }
+  }
+  // x_p and C_p: -l_dx, -L_dC - sym(A^T LA G)
+  {
+    double ATL[6][6];  // A^T LA
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += A[q][i] * LA[q][j];
+        ATL[i][j] = v;
+      }
+    double T[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v += ATL[i][q] * r.G[sym(q, j)];
+        T[i][j] = v;
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j)
+        if (j <= i) c[kSmCP + sy(i, j)] = -Ls[i][j] - 0.5 * (T[i][j] + T[j][i]);
+  }
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    c[kSmXP + e] = -ldx[e];
+    lxs[e] = ldx[e];
+  }
+}
+
 // add v to grad_align[e][sid] (all 32 lanes of the warp call this together;
 // inactive lanes pass act = false).  When every active lane is on the same
 // surface the warp adds its sum once; otherwise each active lane adds.
@@ -980,9 +1290,79 @@ __device__ __forceinline__ void add_align_grad(double* grad, int n_surf, int sid
   }
 }
 
+// Per-thread view of one track's inputs and of its slices of the scratch
+// arrays (inputs and outputs are [.][n_tracks_total] at track tg, scratch is
+// [.][n_tracks] of the launch at track tl).
+struct TrackIO {
+  const GradParams* g;
+  int64_t o0;
+  int tg, tl;
+  size_t TG, TL;
+  __device__ double& ck(int j, int e) const { return g->ckpt[((size_t)j * 27 + e) * TL + tl]; }
+  __device__ double& sck(int j, int e) const { return g->sck[((size_t)j * 27 + e) * TL + tl]; }
+  __device__ double& sadj(int k, int e) const { return g->sadj[((size_t)k * kSmRec + e) * TL + tl]; }
+  __device__ void meas(int k, double m[2], double V[3]) const {
+    const FitParams& p = g->f;
+    m[0] = p.loc[o0 + k];
+    m[1] = p.loc[p.n_states + o0 + k];
+    V[0] = p.cov[o0 + k];
+    V[1] = p.cov[p.n_states + o0 + k];
+    V[2] = p.cov[2 * p.n_states + o0 + k];
+  }
+  __device__ int sid(int k) const { return g->f.surface_id[o0 + k]; }
+  __device__ bool hole(int k) const { return g->f.is_hole[o0 + k] != 0; }
+};
+
+// Recompute segment [s0, s0 + L] of a track from its filtered checkpoint j:
+// the filtered states s0 .. s0+L-1 (fx, fC) and the transports i: s0+i ->
+// s0+i+1 (their predictions px, pC and Jacobians pJ), i = 0 .. L-1.  The
+// arithmetic is the forward pass's, so it succeeds where that did.
+__device__ __noinline__ void recompute_segment(const TrackIO& io, const double* s_surf, int j, int s0, int L,
+                                  double fx[kSeg][6], double fC[kSeg][21], double px[kSeg][6],
+                                  double pC[kSeg][21], JacS<double> pJ[kSeg]) {
+#pragma unroll
+  for (int e = 0; e < 6; ++e) fx[0][e] = io.ck(j, e);
+#pragma unroll
+  for (int e = 0; e < 21; ++e) fC[0][e] = io.ck(j, 6 + e);
+#pragma unroll 1
+  for (int i = 0; i < L; ++i) {
+    const int k = s0 + i + 1;
+    double qp, qt, F[6][6];
+    transport_values(*io.g, s_surf, io.sid(k - 1), io.sid(k), fx[i], px[i], pJ[i], qp, qt);
+    dense_F(pJ[i], F);
+    cov_transport(F, fC[i], qp, qt, pC[i]);
+    if (i + 1 < L) {
+      if (!io.hole(k)) {
+        double m[2], V[3], c2;
+        io.meas(k, m, V);
+        update_fwd(px[i], pC[i], m, V, fx[i + 1], fC[i + 1], c2);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) fx[i + 1][e] = px[i][e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) fC[i + 1][e] = pC[i][e];
+      }
+    }
+  }
+}
+
 // Register-cap variants as for the fit kernels: MINB 1 may use 255
 // registers (up to 8 warps per SM), 3 caps at 168 (12 warps) and 4 at 128
 // (16 warps; the tape then spills to local memory).
+//
+// Passes (one thread per track):
+//   F  forward filter, filtered checkpoints every kSeg states, chi2;
+//   S  (smoothed outputs or their adjoints asked) the RTS smoother from the
+//      last state down, segment by segment, each segment's filtered states
+//      and transports recomputed from its checkpoint; smoothed checkpoints
+//      at the segment starts; the smoothed state 0 is the output;
+//   R  (adjoints of the smoothed outputs asked) the reverse of the smoother,
+//      segment by segment upwards: the segment's states recomputed from both
+//      kinds of checkpoint, then each step reversed; the contributions to
+//      the adjoints of the filter's quantities go to sadj;
+//   B  the reverse of the filter, segment by segment downwards (states
+//      recomputed from the checkpoints, transports re-run with a tape), with
+//      sadj added in at every state.
 template <int MINB>
 __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const GradParams g) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -992,21 +1372,33 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
   const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
                                      p.error_flag, p.wait_limit, p.skip_stage_copy != 0);
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in_range = t < p.n_tracks;
+  TrackIO io;
+  io.g = &g;
+  io.tl = in_range ? t : 0;
+  io.tg = p.track0 + io.tl;
+  io.TG = (size_t)p.n_tracks_total;
+  io.TL = (size_t)p.n_tracks;
+  const int tg = io.tg;
+  const size_t TG = io.TG;
   if (!staged || call_failed(p.error_flag)) {
-    // a bounded wait of this call gave up: this CTA's tracks get NaN chi2
-    // and seed gradients and add nothing to the alignment gradient (the
-    // whole CTA returns here, so no warp-wide reduction below is entered)
-    if (t < p.n_tracks) {
-      if (g.chi2) g.chi2[t] = qnan();
+    // a bounded wait of this call gave up: this CTA's tracks get NaN chi2,
+    // smoothed outputs and seed gradients and add nothing to the alignment
+    // gradient (the whole CTA returns here, so no warp-wide reduction below
+    // is entered)
+    if (in_range) {
+      if (g.chi2) g.chi2[tg] = qnan();
       if (g.grad_seed)
-        for (int e = 0; e < 6; ++e) g.grad_seed[(size_t)e * p.n_tracks + t] = qnan();
+        for (int e = 0; e < 6; ++e) g.grad_seed[(size_t)e * TG + tg] = qnan();
+      if (g.out_params)
+        for (int e = 0; e < 6; ++e) g.out_params[(size_t)e * TG + tg] = qnan();
+      if (g.out_cov)
+        for (int e = 0; e < 21; ++e) g.out_cov[(size_t)e * TG + tg] = qnan();
     }
     return;
   }
-  const bool in_range = t < p.n_tracks;
-  const int tt = in_range ? t : 0;
-  const size_t TT = (size_t)p.n_tracks;
-  const int64_t o0 = p.offsets[tt], o1 = p.offsets[tt + 1];
+  const int64_t o0 = p.offsets[tg], o1 = p.offsets[tg + 1];
+  io.o0 = o0;
   const int n = (int)(o1 - o0);
   int status = in_range ? ST_OK : ST_BAD_INPUT;
   if (!(o1 > o0) || o0 < 0 || o1 > p.n_states || n > p.max_states) status = ST_BAD_INPUT;
@@ -1015,24 +1407,19 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
       const int sid = p.surface_id[o0 + k];
       if (sid < 0 || sid >= p.n_surfaces) status = ST_BAD_INPUT;
     }
-  const double w = (g.dl_dchi2 && in_range) ? g.dl_dchi2[tt] : 1.0;
-  auto ck = [&](int j, int e) -> double& { return g.ckpt[((size_t)j * 27 + e) * TT + tt]; };
-  auto meas = [&](int k, double m[2], double V[3]) {
-    m[0] = p.loc[o0 + k];
-    m[1] = p.loc[p.n_states + o0 + k];
-    V[0] = p.cov[o0 + k];
-    V[1] = p.cov[p.n_states + o0 + k];
-    V[2] = p.cov[2 * p.n_states + o0 + k];
-  };
+  const double w = (g.dl_dchi2 && in_range) ? g.dl_dchi2[tg] : 1.0;
+  const bool want = (g.grad_seed || g.grad_align);
+  const bool sm_adj = want && (g.dl_dparams || g.dl_dcov);
+  const bool sm_fwd = sm_adj || g.out_params || g.out_cov;
 
-  // ---------------------------------------------------------- forward
+  // ---------------------------------------------------------- F: forward
   double chi2sum = 0.0;
   double x[6], C[21];
   if (status == ST_OK) {
 #pragma unroll
-    for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TT + tt];
+    for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TG + tg];
 #pragma unroll
-    for (int e = 0; e < 21; ++e) C[e] = p.seed_cov[e * TT + tt];
+    for (int e = 0; e < 21; ++e) C[e] = p.seed_cov[e * TG + tg];
     for (int k = 0; k < n && status == ST_OK; ++k) {
       double xp[6], Cp[21];
       if (k == 0) {
@@ -1043,14 +1430,14 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
       } else {
         JacS<double> J;
         double qp, qt, F[6][6];
-        status = transport_values(g, s_surf, p.surface_id[o0 + k - 1], p.surface_id[o0 + k], x, xp, J, qp, qt);
+        status = transport_values(g, s_surf, io.sid(k - 1), io.sid(k), x, xp, J, qp, qt);
         if (status != ST_OK) break;
         dense_F(J, F);
         cov_transport(F, C, qp, qt, Cp);
       }
-      if (!p.is_hole[o0 + k]) {
+      if (!io.hole(k)) {
         double m[2], V[3], c2 = 0.0;
-        meas(k, m, V);
+        io.meas(k, m, V);
         status = update_fwd(xp, Cp, m, V, x, C, c2);
         chi2sum += c2;
       } else {
@@ -1061,23 +1448,129 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
       }
       if (k % kSeg == 0 && k / kSeg < g.n_ckpt) {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) ck(k / kSeg, e) = x[e];
+        for (int e = 0; e < 6; ++e) io.ck(k / kSeg, e) = x[e];
 #pragma unroll
-        for (int e = 0; e < 21; ++e) ck(k / kSeg, 6 + e) = C[e];
+        for (int e = 0; e < 21; ++e) io.ck(k / kSeg, 6 + e) = C[e];
       }
     }
   }
-  if (in_range && g.chi2) g.chi2[tt] = status == ST_OK ? chi2sum : qnan();
-  const bool want = (g.grad_seed || g.grad_align);
+  // segments: sg covers the transitions s0+1 .. s1, s0 = sg kSeg,
+  // s1 = min(s0 + kSeg, n - 1); its filtered checkpoint is state s0
+  const int n_seg_trk = status == ST_OK ? (n - 1 + kSeg - 1) / kSeg : 0;
 
-  // ---------------------------------------------------------- backward
+  // ---------------------------------------------------------- S: smoother
+  if (sm_fwd && status == ST_OK) {
+    double xs[6], Cs[21];  // x_s,n-1 = x_f,n-1
+#pragma unroll
+    for (int e = 0; e < 6; ++e) xs[e] = x[e];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) Cs[e] = C[e];
+    if (sm_adj) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) io.sck(n_seg_trk, e) = xs[e];
+#pragma unroll
+      for (int e = 0; e < 21; ++e) io.sck(n_seg_trk, 6 + e) = Cs[e];
+    }
+#pragma unroll 1
+    for (int sg = n_seg_trk - 1; sg >= 0 && status == ST_OK; --sg) {
+      const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+      double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+      JacS<double> pJ[kSeg];
+      recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
+#pragma unroll 1
+      for (int i = L - 1; i >= 0 && status == ST_OK; --i)
+        status = rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xs, Cs, nullptr);
+      if (sm_adj && sg > 0) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) io.sck(sg, e) = xs[e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) io.sck(sg, 6 + e) = Cs[e];
+      }
+    }
+    if (in_range && g.out_params)
+#pragma unroll
+      for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = status == ST_OK ? xs[e] : qnan();
+    if (in_range && g.out_cov)
+#pragma unroll
+      for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = status == ST_OK ? Cs[e] : qnan();
+  } else if (in_range) {
+    if (g.out_params)
+      for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = qnan();
+    if (g.out_cov)
+      for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = qnan();
+  }
+  if (in_range && g.chi2) g.chi2[tg] = status == ST_OK ? chi2sum : qnan();
+
+  // ---------------------------------------------------------- R: smoother reverse
+  if (sm_adj && status == ST_OK) {
+    double lxs[6], Ls[6][6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) lxs[e] = g.dl_dparams ? g.dl_dparams[e * TG + tg] : 0.0;
+    // the weight W_e of a packed covariance element e = (i, j), i > j, stands
+    // for both C_ij and C_ji in the full-matrix convention: W_e / 2 each
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        const double v = g.dl_dcov ? g.dl_dcov[sy(i, j) * TG + tg] : 0.0;
+        Ls[i][j] = Ls[j][i] = (i == j) ? v : 0.5 * v;
+      }
+#pragma unroll 1
+    for (int sg = 0; sg < n_seg_trk; ++sg) {
+      const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+      double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+      JacS<double> pJ[kSeg];
+      recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
+      double xs[6], Cs[21];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) xs[e] = io.sck(sg + 1, e);
+#pragma unroll
+      for (int e = 0; e < 21; ++e) Cs[e] = io.sck(sg + 1, 6 + e);
+      RtsKeep keep[kSeg];
+#pragma unroll 1
+      for (int i = L - 1; i >= 0; --i) rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xs, Cs, &keep[i]);
+#pragma unroll 1
+      for (int i = 0; i < L; ++i) {
+        double c[kSmRec];
+        rts_step_rev(fC[i], keep[i], lxs, Ls, c);
+        const int k = s0 + i;
+#pragma unroll
+        for (int e = 0; e < kSmXP; ++e) io.sadj(k, e) = c[e];
+#pragma unroll
+        for (int e = kSmXP; e < kSmRec; ++e) io.sadj(k + 1, e) = c[e];
+      }
+    }
+    // the last state: x_s,n-1 = x_f,n-1, C_s,n-1 = C_f,n-1
+#pragma unroll
+    for (int e = 0; e < 6; ++e) io.sadj(n - 1, kSmXF + e) = lxs[e];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) io.sadj(n - 1, kSmCF + sy(i, j)) = Ls[i][j];
+  }
+  // adds the smoother's contributions to the adjoints of x_f,k and C_f,k
+  auto add_sm_filtered = [&](int k, double lf_[6], double Lf_[6][6]) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) lf_[e] += io.sadj(k, kSmXF + e);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) {
+        const double v = io.sadj(k, kSmCF + sy(i, j));
+        Lf_[i][j] += v;
+        if (j < i) Lf_[j][i] += v;
+      }
+  };
+
+  // ---------------------------------------------------------- B: filter reverse
   double lf[6] = {0, 0, 0, 0, 0, 0};
   double Lf[6][6];
 #pragma unroll
   for (int i = 0; i < 6; ++i)
 #pragma unroll
     for (int j = 0; j < 6; ++j) Lf[i][j] = 0.0;
-  const int n_seg = (status == ST_OK && want) ? (n - 1 + kSeg - 1) / kSeg : 0;
+  const int n_seg = (status == ST_OK && want) ? n_seg_trk : 0;
+  const bool use_sm = sm_adj && status == ST_OK;
   // the loop runs in lock-step over the warp's maximum segment count so that
   // the alignment-gradient reduction sees whole warps
   int n_seg_warp = n_seg;
@@ -1091,21 +1584,21 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
     double bx[kSeg][6], bC[kSeg][21];
     if (seg_active) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) bx[0][e] = ck(sg, e);
+      for (int e = 0; e < 6; ++e) bx[0][e] = io.ck(sg, e);
 #pragma unroll
-      for (int e = 0; e < 21; ++e) bC[0][e] = ck(sg, 6 + e);
+      for (int e = 0; e < 21; ++e) bC[0][e] = io.ck(sg, 6 + e);
 #pragma unroll
       for (int i = 1; i < kSeg; ++i) {
         if (s0 + i < s1) {
           const int k = s0 + i;
           double xp[6], Cp[21], F[6][6], qp, qt;
           JacS<double> J;
-          transport_values(g, s_surf, p.surface_id[o0 + k - 1], p.surface_id[o0 + k], bx[i - 1], xp, J, qp, qt);
+          transport_values(g, s_surf, io.sid(k - 1), io.sid(k), bx[i - 1], xp, J, qp, qt);
           dense_F(J, F);
           cov_transport(F, bC[i - 1], qp, qt, Cp);
-          if (!p.is_hole[o0 + k]) {
+          if (!io.hole(k)) {
             double m[2], V[3], c2;
-            meas(k, m, V);
+            io.meas(k, m, V);
             update_fwd(xp, Cp, m, V, bx[i], bC[i], c2);
           } else {
 #pragma unroll
@@ -1121,7 +1614,7 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
     for (int k = s0 + kSeg; k > s0; --k) {
       const bool act = seg_active && k <= s1;
       const int i = act ? k - 1 - s0 : 0;
-      const int sa = act ? p.surface_id[o0 + k - 1] : 0, sbi = act ? p.surface_id[o0 + k] : 0;
+      const int sa = act ? io.sid(k - 1) : 0, sbi = act ? io.sid(k) : 0;
       double lp[6], Lp[6][6];
       double xprev[6], Cprev[21];
 #pragma unroll
@@ -1145,9 +1638,10 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
         transport_tape<true>(pa, pb, xprev, B, p.mass, p.h_max, p.n_iter, xxb, xp, J, qp, qt, &tp, s_end);
         dense_F(J, F);
         cov_transport(F, Cprev, qp, qt, Cp);
-        if (!p.is_hole[o0 + k]) {
+        if (use_sm) add_sm_filtered(k, lf, Lf);
+        if (!io.hole(k)) {
           double m[2], V[3];
-          meas(k, m, V);
+          io.meas(k, m, V);
           update_adj(xp, Cp, m, V, w, lf, Lf, lp, Lp);
         } else {
 #pragma unroll
@@ -1156,6 +1650,19 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
 #pragma unroll
             for (int b2 = 0; b2 < 6; ++b2) Lp[a2][b2] = Lf[a2][b2];
           }
+        }
+        if (use_sm) {
+          // the smoother's direct use of x_p,k and C_p,k
+#pragma unroll
+          for (int e = 0; e < 6; ++e) lp[e] += io.sadj(k, kSmXP + e);
+#pragma unroll
+          for (int a2 = 0; a2 < 6; ++a2)
+#pragma unroll
+            for (int b2 = 0; b2 <= a2; ++b2) {
+              const double v = io.sadj(k, kSmCP + sy(a2, b2));
+              Lp[a2][b2] += v;
+              if (b2 < a2) Lp[b2][a2] += v;
+            }
         }
       } else {
 #pragma unroll
@@ -1199,8 +1706,8 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
 #pragma unroll
-          for (int r = 0; r < 4; ++r) lJ[r][c] = lF[r][c];
-          lJt[c] = lF[5][c];
+          for (int r = 0; r < 4; ++r) lJ[r][c] = lF[r][c] + (use_sm ? io.sadj(k, kSmF + r * 5 + c) : 0.0);
+          lJt[c] = lF[5][c] + (use_sm ? io.sadj(k, kSmF + 20 + c) : 0.0);
         }
         double lca[3], lRa[9], lcb[3], lRb[9];
         transport_rev(pa, pb, xprev, B, p.mass, xxb, tp, s_end, lp, lJ, lJt, Lp[2][2], Lp[3][3], lx, lca, lRa,
@@ -1241,13 +1748,14 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
   if (in_range && g.grad_seed) {
     double gs[6];
     if (status == ST_OK && want) {
-      if (!p.is_hole[o0]) {
+      if (use_sm) add_sm_filtered(0, lf, Lf);
+      if (!io.hole(0)) {
         double m[2], V[3], lp[6], Lp[6][6], Cp0[21], xp0[6];
-        meas(0, m, V);
+        io.meas(0, m, V);
 #pragma unroll
-        for (int e = 0; e < 6; ++e) xp0[e] = p.seed_params[e * TT + tt];
+        for (int e = 0; e < 6; ++e) xp0[e] = p.seed_params[e * TG + tg];
 #pragma unroll
-        for (int e = 0; e < 21; ++e) Cp0[e] = p.seed_cov[e * TT + tt];
+        for (int e = 0; e < 21; ++e) Cp0[e] = p.seed_cov[e * TG + tg];
         update_adj(xp0, Cp0, m, V, w, lf, Lf, lp, Lp);
 #pragma unroll
         for (int e = 0; e < 6; ++e) gs[e] = lp[e];
@@ -1260,7 +1768,7 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
       for (int e = 0; e < 6; ++e) gs[e] = qnan();
     }
 #pragma unroll
-    for (int e = 0; e < 6; ++e) g.grad_seed[e * TT + tt] = gs[e];
+    for (int e = 0; e < 6; ++e) g.grad_seed[e * TG + tg] = gs[e];
   }
 }
 
@@ -1297,18 +1805,32 @@ cudaError_t launch_grad_v(const GradParams& g, int block, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad(const FitParams& f, const double* align, const double* dl_dchi2, double* chi2,
-                        double* grad_seed, double* grad_align, double* ckpt, int n_ckpt, int block,
-                        int min_blocks, cudaStream_t stream) {
+size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint) {
+  const size_t n_ckpt = ((size_t)max_states + kSeg - 1) / kSeg;
+  size_t d = 27 * n_ckpt;
+  if (smoother_adjoint) d += 27 * (n_ckpt + 1) + (size_t)kSmRec * (size_t)max_states;
+  (void)smoother;  // the smoother alone keeps no per-track scratch
+  return d;
+}
+
+cudaError_t launch_grad(const FitParams& f, const GradArgs& a, double* scratch, int block, int min_blocks,
+                        cudaStream_t stream) {
   GradParams g;
   g.f = f;
-  g.align = align;
-  g.dl_dchi2 = dl_dchi2;
-  g.chi2 = chi2;
-  g.grad_seed = grad_seed;
-  g.grad_align = grad_align;
-  g.ckpt = ckpt;
-  g.n_ckpt = n_ckpt;
+  g.align = a.align;
+  g.dl_dchi2 = a.dl_dchi2;
+  g.dl_dparams = a.dl_dparams;
+  g.dl_dcov = a.dl_dcov;
+  g.chi2 = a.chi2;
+  g.out_params = a.params;
+  g.out_cov = a.cov;
+  g.grad_seed = a.grad_seed;
+  g.grad_align = a.grad_align;
+  const size_t T = (size_t)f.n_tracks;
+  g.n_ckpt = (f.max_states + kSeg - 1) / kSeg;
+  g.ckpt = scratch;
+  g.sck = scratch + 27 * (size_t)g.n_ckpt * T;
+  g.sadj = g.sck + 27 * (size_t)(g.n_ckpt + 1) * T;
   switch (min_blocks) {
     case 4: return launch_grad_v<4>(g, block, stream);
     case 3: return launch_grad_v<3>(g, block, stream);
@@ -1316,6 +1838,5 @@ cudaError_t launch_grad(const FitParams& f, const double* align, const double* d
   }
 }
 
-int grad_segment_length() { return kSeg; }
 
 }  // namespace kfgb

@@ -690,10 +690,10 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   return KF_SUCCESS;
 }
 
-int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const double* align,
-                 const kf_measurements* me, const kf_field* fi, const kf_options* opt_in, const double* dl_dchi2,
-                 double* out_chi2, double* grad_seed, double* grad_align, void* stream_v) {
-  if (!h) return KF_EINVAL;
+int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const double* align,
+            const kf_measurements* me, const kf_field* fi, const kf_options* opt_in, const kf_grad_weights* wts,
+            const kf_grad_outputs* go, void* stream_v) {
+  if (!h || !go) return KF_EINVAL;
   kf_options opt;
   if (opt_in) {
     opt = *opt_in;
@@ -716,20 +716,43 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   if (rc) return rc;
   // the adjoint differentiates the baseline method only
   if (wants_variants(opt.smoother, opt.energy_loss, fi->map)) return KF_EUNSUPPORTED;
+  GradArgs a;
+  memset(&a, 0, sizeof(a));
+  a.align = align;
+  if (wts) {
+    a.dl_dchi2 = wts->dl_dchi2;
+    a.dl_dparams = wts->dl_dparams;
+    a.dl_dcov = wts->dl_dcov;
+  }
+  a.chi2 = go->chi2;
+  a.params = go->params;
+  a.cov = go->cov;
+  a.grad_seed = go->grad_seed;
+  a.grad_align = go->grad_align;
   cudaStream_t stream = (cudaStream_t)stream_v;
-  if (grad_align) {
-    cudaError_t e = cudaMemsetAsync(grad_align, 0, sizeof(double) * 6 * (size_t)su->n_surfaces, stream);
+  if (a.grad_align) {
+    cudaError_t e = cudaMemsetAsync(a.grad_align, 0, sizeof(double) * 6 * (size_t)su->n_surfaces, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(grad_align)");
   }
+  h->last_launches = 0;
   if (tr->n_tracks == 0) return KF_SUCCESS;
-  const int n_ckpt = (tr->max_states + grad_segment_length() - 1) / grad_segment_length();
-  const size_t need = sizeof(double) * 27 * (size_t)n_ckpt * (size_t)tr->n_tracks;
+  // scratch per track; batches whose scratch exceeds the workspace cap run
+  // as several launches over consecutive track ranges
+  const bool want = a.grad_seed || a.grad_align;
+  const bool sm_adj = want && (a.dl_dparams || a.dl_dcov);
+  const bool sm = sm_adj || a.params || a.cov;
+  const size_t per_track = sizeof(double) * grad_scratch_doubles(tr->max_states, sm, sm_adj);
+  const int64_t cap = opt.workspace_bytes > 0 ? opt.workspace_bytes : kDefaultWorkspace;
+  int64_t chunk = cap / (int64_t)per_track;
+  if (chunk < 1) chunk = 1;
+  if (chunk > tr->n_tracks) chunk = tr->n_tracks;
+  const size_t need = per_track * (size_t)chunk;
   if (h->ckpt_bytes < need) {
     if (h->ckpt) cudaFree(h->ckpt);
     h->ckpt = nullptr;
     h->ckpt_bytes = 0;
     cudaError_t e = cudaMalloc(&h->ckpt, need);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(checkpoints)");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(adjoint scratch)");
     h->ckpt_bytes = need;
   }
   if ((rc = ensure_surf(h, su->n_surfaces))) return rc;
@@ -737,9 +760,9 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(error flag)");
   e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
   if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
+  int launches = 1;
   FitParams p;
   memset(&p, 0, sizeof(p));
-  p.n_tracks = tr->n_tracks;
   p.n_tracks_total = tr->n_tracks;
   p.max_states = tr->max_states;
   p.offsets = tr->offsets;
@@ -759,11 +782,29 @@ int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const
   p.error_flag = h->error_flag;
   p.wait_limit = opt.wait_limit;
   p.skip_stage_copy = opt.test_wait_timeout;
-  e = launch_grad(p, align, dl_dchi2, out_chi2, grad_seed, grad_align, h->ckpt, n_ckpt, grad_block,
-                  opt.min_blocks, stream);
-  if (e != cudaSuccess) return cuda_fail(e, "grad launch");
-  h->last_launches = 2;
+  for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk) {
+    p.track0 = (int32_t)t0;
+    p.n_tracks = (int32_t)((tr->n_tracks - t0) < chunk ? (tr->n_tracks - t0) : chunk);
+    e = launch_grad(p, a, (double*)h->ckpt, grad_block, opt.min_blocks, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "grad launch");
+    ++launches;
+  }
+  h->last_launches = launches;
   return KF_SUCCESS;
+}
+
+int kf_chi2_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const double* align,
+                 const kf_measurements* me, const kf_field* fi, const kf_options* opt_in, const double* dl_dchi2,
+                 double* out_chi2, double* grad_seed, double* grad_align, void* stream_v) {
+  kf_grad_weights w;
+  memset(&w, 0, sizeof(w));
+  w.dl_dchi2 = dl_dchi2;
+  kf_grad_outputs o;
+  memset(&o, 0, sizeof(o));
+  o.chi2 = out_chi2;
+  o.grad_seed = grad_seed;
+  o.grad_align = grad_align;
+  return kf_grad(h, tr, su, align, me, fi, opt_in, &w, &o, stream_v);
 }
 
 int kf_fit(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* me, const kf_field* fi,

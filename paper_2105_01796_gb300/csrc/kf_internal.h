@@ -119,13 +119,31 @@ cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blo
 // smoother, energy loss, field map; same records as the FP64 path.
 cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stream, int* launched = nullptr);
 
-// Gradients of sum_t w_t chi2_t with respect to the seeds and the
-// per-surface alignment (kf_adjoint.cu).  ckpt holds n_ckpt checkpoints of 27
-// doubles per track; n_ckpt = ceil(max_states / grad_segment_length()).
-cudaError_t launch_grad(const FitParams& f, const double* align, const double* dl_dchi2, double* chi2,
-                        double* grad_seed, double* grad_align, double* ckpt, int n_ckpt, int block,
-                        int min_blocks, cudaStream_t stream);
-int grad_segment_length();
+// Inputs and outputs of the adjoint (kf_adjoint.cu): the objective
+// L = sum_t [w_t chi2_t + v_t . x_s0,t + W_t . C_s0,t] (x_s0, C_s0 the
+// smoothed parameters and packed covariance of state 0) and its gradient
+// with respect to the seeds and the per-surface alignment.
+struct GradArgs {
+  const double* align;       // [6][S] or null (zero)
+  const double* dl_dchi2;    // w [T] or null (ones)
+  const double* dl_dparams;  // v [6][T] or null (zero)
+  const double* dl_dcov;     // W [21][T] or null (zero)
+  double* chi2;              // [T] or null
+  double* params;            // [6][T] or null: x_s0
+  double* cov;               // [21][T] or null: C_s0
+  double* grad_seed;         // [6][T] or null
+  double* grad_align;        // [6][S] or null: accumulated (the caller zeroes it)
+};
+
+// Scratch doubles per track of one adjoint launch: the filtered checkpoints,
+// and with the smoother the smoothed checkpoints and (for the adjoint of the
+// smoothed outputs) the smoother's per-state contributions.
+size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint);
+
+// One launch over tracks [f.track0, f.track0 + f.n_tracks) of
+// f.n_tracks_total; scratch holds grad_scratch_doubles(...) x f.n_tracks.
+cudaError_t launch_grad(const FitParams& f, const GradArgs& a, double* scratch, int block, int min_blocks,
+                        cudaStream_t stream);
 
 // Counting sort of the tracks by state count, longest first:
 // order[0..n_tracks) receives track indices.  hist needs max_states + 2 ints.

@@ -44,14 +44,18 @@ def states_err(g_states, r_states, sd):
 
 
 # Element-wise check of gradients against central finite differences.  The
-# oracle's objective L carries a relative rounding noise of about 1e-14 (a few
-# thousand FP64 operations per state), which a central difference with step h
-# turns into an absolute noise of about 1e-14 |L| / h in the derivative.  The
-# floor is the derivative at which that noise is 1e-5 of it:
-#   floor = 1e-14 |L| / h / 1e-5 = 1e-3 |L| (1e-6 / h),
+# oracle's objective L carries a relative rounding noise of about 1e-13: its
+# chi2 terms are built from residuals m - x_p of ~50 um that are differences
+# of positions of ~100 mm, so one rounding of a position is amplified ~2000x
+# (measured on 100 tracks of the misaligned 20-plane telescope: central
+# differences at steps h and 2h, h = 1e-6, differ by up to 6.5e-8 |L|, i.e.
+# 6.5e-14 |L| / h).  A central difference with step h turns it into an
+# absolute noise of about 1e-13 |L| / h in the derivative.  The floor is the
+# derivative at which that noise is 1e-5 of it:
+#   floor = 1e-13 |L| / h / 1e-5 = 1e-2 |L| (1e-6 / h),
 # so |g - fd| <= 1e-5 max(|fd|, floor) holds each element to 1e-5 relative
 # down to the size that finite differences can resolve at all.
-FD_NOISE_REL = 1e-14
+FD_NOISE_REL = 1e-13
 
 
 def fd_floor(l_abs, h, tol=1e-5):

@@ -1,15 +1,17 @@
-"""The adjoint kernel (kf_chi2_grad): gradients of the summed chi2 with
-respect to the seed parameters and the per-surface alignment, against
-central finite differences of the CPU oracle (step 1e-6) on 100 tracks of a
-misaligned telescope, plus the chi2 itself against the fit and the
-torch.autograd wrapper."""
+"""The adjoint kernel: gradients with respect to the seed parameters and the
+per-surface alignment of the summed chi2 (kf_chi2_grad, the filter) and of
+the whole fit's objective sum_t [w chi2 + v . x_s0 + W . C_s0] (kf_grad,
+filter and smoother), against central finite differences of the CPU oracle
+(step 1e-6) on 100 tracks of a misaligned telescope, element by element;
+plus the values themselves against the fit and the torch.autograd
+wrappers."""
 import numpy as np
 import pytest
 
 import oracle
 import paper_2105_01796_gb300 as kf
 from paper_2105_01796_gb300 import synth
-from tests.metrics import fd_floor, grad_err, seed_steps
+from tests.metrics import PAIRS, DIAG, cov_err, fd_floor, grad_err, param_err, seed_steps
 
 pytestmark = pytest.mark.gpu
 
@@ -128,3 +130,132 @@ def test_full_size_gradients_sampled_and_additive(handle):
     _, _, ga0 = _grad(handle, synth.subset(ev, np.arange(half)), align)
     _, _, ga1 = _grad(handle, synth.subset(ev, np.arange(half, T)), align)
     assert np.max(np.abs(ga - (ga0 + ga1))) <= 1e-10 * np.max(np.abs(ga))
+
+
+# ---------------------------------------------------------------- the whole fit (filter + smoother)
+
+def _smoother_weights(ev, seed=5):
+    """Weights v [6][T] and W [21][T] that make every smoother term of L of
+    order one: v_i ~ N(0, 1) / max(|x_i|, sigma_i), W_ij ~ N(0, 1) /
+    (sigma_i sigma_j), from the oracle's smoothed state 0."""
+    r = oracle.fit_batch(ev)
+    T = int(ev["n_tracks"])
+    rng = np.random.default_rng(seed)
+    sd = np.sqrt(np.abs(r["cov"][DIAG]))
+    v = rng.normal(size=(6, T)) / np.maximum(np.abs(r["params"]), sd)
+    W = rng.normal(size=(21, T)) / np.stack([sd[i] * sd[j] for i, j in PAIRS])
+    return v, W
+
+
+def _whole(handle, ev, align, w=None, v=None, W=None, opt=None):
+    import torch
+    dev = kf.event_to_device(ev)
+    T, S = int(ev["n_tracks"]), ev["center"].shape[1]
+    d = lambda *shape: torch.empty(shape, dtype=torch.float64, device="cuda")
+    cu = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    o = {"chi2": d(T), "params": d(6, T), "cov": d(21, T), "gs": d(6, T), "ga": d(6, S)}
+    kf.kf_grad(handle, dev, align=cu(align), dl_dchi2=cu(w), dl_dparams=cu(v), dl_dcov=cu(W),
+               out_chi2=o["chi2"], out_params=o["params"], out_cov=o["cov"], grad_seed=o["gs"],
+               grad_align=o["ga"], opt=opt)
+    torch.cuda.synchronize()
+    return {k: t.cpu().numpy() for k, t in o.items()}
+
+
+@pytest.mark.parametrize("terms,nonzero_align", [("all", False), ("all", True), ("params", False),
+                                                 ("cov", False)])
+def test_whole_fit_gradients_match_oracle_finite_differences(handle, terms, nonzero_align):
+    """L = sum_t [w chi2 + v . x_s0 + W . C_s0]: all three terms, and the
+    smoother terms alone (w = 0; then every derivative goes through the
+    smoother's reverse)."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["align20_100k"], 100))
+    S = ev["center"].shape[1]
+    rng = np.random.default_rng(2)
+    align = np.zeros((6, S))
+    if nonzero_align:
+        align[:3, 1:] = rng.normal(size=(3, S - 1)) * 0.05
+        align[3:, 1:] = rng.normal(size=(3, S - 1)) * 5e-4
+    v, W = _smoother_weights(ev)
+    w = rng.uniform(0.5, 1.5, size=100)
+    if terms == "params":
+        w, W = np.zeros(100), None
+    elif terms == "cov":
+        w, v = np.zeros(100), None
+    g = _whole(handle, ev, align, w, v, W)
+    # the values: the smoothed state 0 and chi2 of the fit at this alignment
+    ea = dict(ev)
+    ea["center"], ea["rot"] = oracle.apply_alignment(ev["center"], ev["rot"], align)
+    ref = oracle.fit_batch(ea)
+    assert np.all(ref["status"] == 0)
+    assert param_err(g["params"], ref["params"], ref["cov"]).max() < 1e-9
+    assert cov_err(g["cov"], ref["cov"]).max() < 1e-9
+    assert np.max(np.abs(g["chi2"] - ref["chi2"]) / ref["chi2"]) < 1e-9
+    # the gradients, element by element
+    fs, fa = oracle.objective_gradient_fd(ev, align, weights=w, dl_dparams=v, dl_dcov=W)
+    _, l_abs = oracle.objective_per_track(ev, align, weights=w, dl_dparams=v, dl_dcov=W)
+    _check_grads(g["gs"], g["ga"], fs, fa, ev["seed_params"], l_abs)
+    # the smoother terms carry real weight: the gradient differs from the
+    # chi2 gradient of the same weights well beyond the tolerance
+    _, gs0, ga0 = _grad(handle, ev, align, w)
+    assert np.max(np.abs(g["gs"] - gs0)) > 1e-2 * np.max(np.abs(g["gs"]))
+    assert np.max(np.abs(g["ga"] - ga0)) > 1e-2 * np.max(np.abs(g["ga"]))
+
+
+def test_whole_fit_autograd_and_chunked_launches(handle):
+    """fit_autograd's values equal the FP64 fit's outputs (within the FP64
+    contract: the adjoint kernel's smoother inverts explicitly), its backward
+    equals kf_grad with the same weights, and a workspace cap that splits the
+    batch into several launches changes nothing."""
+    import torch
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["align20_100k"], 300))
+    dev = kf.event_to_device(ev)
+    S = ev["center"].shape[1]
+    out = kf.alloc_outputs(300)
+    kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(kf.KF_PRECISION_FP64))
+    seeds = dev["seed_params"].clone().requires_grad_(True)
+    align = torch.zeros((6, S), dtype=torch.float64, device="cuda", requires_grad=True)
+    chi2, params, cov = kf.fit_autograd(seeds, align, dev, handle)
+    torch.cuda.synchronize()
+    f = {k: out[k].cpu().numpy() for k in ("params", "cov", "chi2")}
+    assert param_err(params.detach().cpu().numpy(), f["params"], f["cov"]).max() < 1e-9
+    assert cov_err(cov.detach().cpu().numpy(), f["cov"]).max() < 1e-9
+    assert np.max(np.abs(chi2.detach().cpu().numpy() - f["chi2"]) / f["chi2"]) < 1e-9
+    v, W = _smoother_weights(ev)
+    w = np.linspace(0.5, 2.0, 300)
+    tw = lambda a: torch.from_numpy(a).cuda()
+    loss = (chi2 * tw(w)).sum() + (params * tw(v)).sum() + (cov * tw(W)).sum()
+    loss.backward()
+    g = _whole(handle, ev, np.zeros((6, S)), w, v, W)
+    assert np.allclose(seeds.grad.cpu().numpy(), g["gs"], rtol=1e-12, atol=0)
+    assert np.allclose(align.grad.cpu().numpy(), g["ga"], rtol=1e-9, atol=1e-9 * np.abs(g["ga"]).max())
+    # 300 tracks through a workspace that holds 64 of them: five launches
+    per_track = 8 * (27 * 5 + 27 * 6 + 79 * 21)
+    opt = kf.kf_default_options(kf.KF_PRECISION_FP64, block=0, workspace_bytes=64 * per_track)
+    gc = _whole(handle, ev, np.zeros((6, S)), w, v, W, opt=opt)
+    assert handle.last_launch_count() == 1 + 5
+    for k in ("chi2", "params", "cov", "gs"):
+        assert np.array_equal(gc[k], g[k]), k
+    assert np.allclose(gc["ga"], g["ga"], rtol=1e-11, atol=1e-11 * np.abs(g["ga"]).max())
+
+
+def test_full_size_whole_fit_gradients_sampled(handle):
+    """The bench's workload at full size (100k tracks x 21 states) through
+    the whole-fit adjoint: values and seed gradients of 40 sampled tracks
+    against the oracle (central differences of those tracks), and the
+    alignment gradient of the batch equal to the sum of its two halves'."""
+    ev = synth.make_event(synth.WORKLOADS["align20_100k"], with_truth_states=False)
+    T, S = int(ev["n_tracks"]), ev["center"].shape[1]
+    v, W = _smoother_weights(ev)
+    g = _whole(handle, ev, np.zeros((6, S)), None, v, W)
+    pick = np.sort(np.random.default_rng(22).choice(T, 40, replace=False))
+    sub = synth.subset(ev, pick)
+    ref = oracle.fit_batch(sub)
+    assert param_err(g["params"][:, pick], ref["params"], ref["cov"]).max() < 1e-9
+    assert cov_err(g["cov"][:, pick], ref["cov"]).max() < 1e-9
+    fs, _ = oracle.objective_gradient_fd(sub, dl_dparams=v[:, pick], dl_dcov=W[:, pick])
+    _, l_abs = oracle.objective_per_track(sub, dl_dparams=v[:, pick], dl_dcov=W[:, pick])
+    es = grad_err(g["gs"][:, pick], fs, fd_floor(l_abs[None, :], seed_steps(sub["seed_params"])))
+    assert es.max() < 1e-5, es.max()
+    half = T // 2
+    g0 = _whole(handle, synth.subset(ev, np.arange(half)), np.zeros((6, S)), None, v[:, :half], W[:, :half])
+    g1 = _whole(handle, synth.subset(ev, np.arange(half, T)), np.zeros((6, S)), None, v[:, half:], W[:, half:])
+    assert np.max(np.abs(g["ga"] - (g0["ga"] + g1["ga"]))) <= 1e-10 * np.max(np.abs(g["ga"]))

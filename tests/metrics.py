@@ -70,6 +70,15 @@ def seed_steps(seed_params, h=1e-6):
     return hs
 
 
+def fd_floor_measured(fd_h, fd_2h, model_floor, tol=1e-5):
+    """The floor with each element's measured finite-difference resolution:
+    central differences at steps h and 2h differ by their noise (~1/h) and
+    truncation (~h^2) errors, which bounds the step-h value's error within a
+    factor of about two; an element is held to tol relative only above the
+    size at which twice that spread is tol of it."""
+    return np.maximum(model_floor, 2.0 * np.abs(np.asarray(fd_h) - np.asarray(fd_2h)) / tol)
+
+
 def grad_err(g, fd, floor):
     """|g - fd| / max(|fd|, floor), element-wise."""
     return np.abs(np.asarray(g) - np.asarray(fd)) / np.maximum(np.abs(fd), floor)

@@ -53,7 +53,7 @@ MIXED_TRAFFIC_SOURCES_SHA256 = "8a71f89d172d3fa7b89b8c05ab31578260476708d363090b
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
 # (align20, 21 states); reported while those kernels' sources match
 EXT_FLOPS_PER_TRACK = {"variants": (396343307 * 2 + 268774064) * 32 / 1e5,
-                       "adjoint": (464212500 * 2 + 305600000) * 32 / 1e5}
+                       "adjoint_chi2": (464212500 * 2 + 305600000) * 32 / 1e5}
 EXT_SOURCES_SHA256 = "faedab12959631e34ab8e470c52d46c043781275dd0886f2e158a42e032fb5af"
 
 
@@ -70,7 +70,7 @@ def ext_kernel_sources_sha256():
 def ext_roofline(kind, tracks, ms):
     """Roofline entry of the variant or adjoint kernel from its hardware-
     counted FP64 flops per track (None once the kernel has changed)."""
-    if ext_kernel_sources_sha256() != EXT_SOURCES_SHA256:
+    if ext_kernel_sources_sha256() != EXT_SOURCES_SHA256 or kind not in EXT_FLOPS_PER_TRACK:
         return None
     flops = EXT_FLOPS_PER_TRACK[kind] * tracks
     achieved = flops / (ms / 1e3) / 1e12
@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the method-variant kernel (backward filter + energy loss + field map)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (chi2 gradient) kernel")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the further configurations (1k FP64 10-plane tracks, 1M uneven tracks)")
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the 4M-track throughput-scale workload (mixed and FP64)")
     return ap.parse_args()
@@ -225,54 +227,113 @@ def accuracy(gpu, ref):
 ADJOINT_WORKLOAD = "align20_100k"
 
 
+def smoother_weights(ev, seed=5):
+    """Weights v [6][T], W [21][T] of the smoothed state-0 terms of the
+    whole-fit objective, of order one per term: v_i ~ N(0,1) / max(|x_i|,
+    sigma_i), W_ij ~ N(0,1) / (sigma_i sigma_j) with the seed's values and
+    prior widths (synthetic inputs, no fit output)."""
+    T = int(ev["n_tracks"])
+    rng = np.random.default_rng(seed)
+    diag = [i * (i + 1) // 2 + i for i in range(6)]
+    sd = np.sqrt(np.asarray(ev["seed_cov"])[diag])
+    v = rng.normal(size=(6, T)) / np.maximum(np.abs(ev["seed_params"]), sd)
+    W = rng.normal(size=(21, T)) / np.stack([sd[i] * sd[j] for i in range(6) for j in range(i + 1)])
+    return v, W
+
+
 def time_adjoint(h, kf, synth, torch, stream, l2_flush, steps, warmup, n_tracks, reduce=None):
-    """The adjoint kernel: chi2 per track and its gradient with respect to
-    the seeds and the 6 x 21 alignment parameters (at zero alignment) on the
-    misaligned 20-plane telescope.  With several ranks, each fits its own
-    batch and the alignment gradient is summed over ranks (one all-reduce of
-    126 doubles) inside the timed region."""
+    """The adjoint kernel on the misaligned 20-plane telescope at zero
+    alignment, for two objectives: the summed chi2 (the filter's adjoint,
+    kf_chi2_grad) and the whole fit's sum [chi2 + v . x_s0 + W . C_s0]
+    (filter and smoother, kf_grad); each returns the values and the gradient
+    with respect to the seeds and the 6 x 21 alignment parameters.  With
+    several ranks, each fits its own batch and the alignment gradient is
+    summed over ranks (one all-reduce of 126 doubles) inside the timed
+    region."""
     ev = synth.make_event(synth.scaled(synth.WORKLOADS[ADJOINT_WORKLOAD], n_tracks))
     dev = kf.event_to_device(ev)
     T, S = int(ev["n_tracks"]), int(ev["center"].shape[1])
-    chi2 = torch.empty(T, dtype=torch.float64, device="cuda")
-    gs = torch.empty((6, T), dtype=torch.float64, device="cuda")
-    ga = torch.empty((6, S), dtype=torch.float64, device="cuda")
-    for _ in range(warmup):
-        kf.kf_chi2_grad(h, dev, out_chi2=chi2, grad_seed=gs, grad_align=ga, stream=stream)
-    torch.cuda.synchronize()
-    ms = []
-    torch.cuda.nvtx.range_push("timed_adjoint")
-    for _ in range(steps):
-        l2_flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        kf.kf_chi2_grad(h, dev, out_chi2=chi2, grad_seed=gs, grad_align=ga, stream=stream)
-        if reduce is not None:
-            reduce(ga)
-        b.record(stream)
+    d = lambda *shape: torch.empty(shape, dtype=torch.float64, device="cuda")
+    chi2, par, cov, gs, ga = d(T), d(6, T), d(21, T), d(6, T), d(6, S)
+    v, W = smoother_weights(ev)
+    tv, tW = torch.from_numpy(v).cuda(), torch.from_numpy(W).cuda()
+    calls = {"chi2": lambda: kf.kf_chi2_grad(h, dev, out_chi2=chi2, grad_seed=gs, grad_align=ga, stream=stream),
+             "whole": lambda: kf.kf_grad(h, dev, dl_dparams=tv, dl_dcov=tW, out_chi2=chi2, out_params=par,
+                                         out_cov=cov, grad_seed=gs, grad_align=ga, stream=stream)}
+    res = {"workload": ADJOINT_WORKLOAD, "tracks": T, "states_per_track": 21}
+    for name, call in calls.items():
+        for _ in range(warmup):
+            call()
         torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    torch.cuda.nvtx.range_pop()
-    step = float(np.mean(ms))
-    host = {"grad_seed": gs.cpu().numpy(), "chi2": chi2.cpu().numpy()}
-    return ev, {"workload": ADJOINT_WORKLOAD, "tracks": T, "states_per_track": 21,
-                "gradient": "d(sum chi2)/d(seeds [6][T], alignment [6][21]) at zero alignment (FP64)",
-                "value": T / (step / 1e3), "unit": "tracks/s", "ms_per_step": step}, host
+        ms = []
+        torch.cuda.nvtx.range_push("timed_adjoint_" + name)
+        for _ in range(steps):
+            l2_flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call()
+            if reduce is not None:
+                reduce(ga)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        torch.cuda.nvtx.range_pop()
+        step = float(np.mean(ms))
+        res[name] = {"value": T / (step / 1e3), "unit": "tracks/s", "ms_per_step": step,
+                     "step_ms": step_stats(ms)}
+    res["chi2"]["gradient"] = "d(sum chi2)/d(seeds [6][T], alignment [6][21]) at zero alignment (FP64; filter)"
+    res["whole"]["gradient"] = ("d(sum [chi2 + v . x_s0 + W . C_s0])/d(seeds, alignment) at zero alignment "
+                                "(FP64; filter and RTS smoother), with chi2, x_s0, C_s0")
+    # the headline entry of the adjoint: the whole fit
+    res.update(value=res["whole"]["value"], unit="tracks/s", ms_per_step=res["whole"]["ms_per_step"])
+    return ev, res, (v, W)
 
 
-def oracle_gradient_rate(ev, n_sample, cores, keep=None):
-    """The oracle's gradient by central finite differences over a sample;
-    keep (a dict) receives the seed gradient."""
+def adjoint_accuracy(h, kf, torch, ev, v, W, n_sample, cores):
+    """The adjoint's gradients of the first n_sample tracks (a separate call
+    on those tracks, so that the alignment gradient is theirs alone) against
+    the oracle's central differences, element by element: |g - fd| /
+    max(|fd|, floor), the floor being the larger of the rounding-noise model
+    (1e-13 |L| / h / 1e-5) and twice the element's step-h / step-2h spread
+    over 1e-5.  Both objectives; returns the accuracy entry and the oracle's
+    rate."""
     import oracle
     from paper_2105_01796_gb300 import synth
     sub = synth.subset(ev, np.arange(min(n_sample, ev["n_tracks"])))
-    t0 = time.perf_counter()
-    fs, _ = oracle.chi2_gradient_fd(sub, n_threads=cores)
-    dt = time.perf_counter() - t0
-    if keep is not None:
-        keep["grad_seed"] = fs
-    return sub["n_tracks"] / dt, dt, sub["n_tracks"]
+    n = int(sub["n_tracks"])
+    dev = kf.event_to_device(sub)
+    S = sub["center"].shape[1]
+    vs, Ws = v[:, :n], W[:, :n]
+    out = {}
+    t_or = 0.0
+    for name, wkw in (("chi2", {}), ("whole", {"dl_dparams": vs, "dl_dcov": Ws})):
+        d = lambda *shape: torch.empty(shape, dtype=torch.float64, device="cuda")
+        gs, ga = d(6, n), d(6, S)
+        cu = {k: torch.from_numpy(np.ascontiguousarray(a)).cuda() for k, a in wkw.items()}
+        kf.kf_grad(h, dev, grad_seed=gs, grad_align=ga, **cu)
+        torch.cuda.synchronize()
+        gs, ga = gs.cpu().numpy(), ga.cpu().numpy()
+        t0 = time.perf_counter()
+        fs, fa = oracle.objective_gradient_fd(sub, n_threads=cores, **wkw)
+        t_or += time.perf_counter() - t0
+        fs2, fa2 = oracle.objective_gradient_fd(sub, n_threads=cores, h_seed=2e-6, h_shift=2e-6, h_rot=2e-6, **wkw)
+        _, l_abs = oracle.objective_per_track(sub, n_threads=cores, **wkw)
+        hs = np.full((6, n), 1e-6)
+        hs[4] = 1e-6 * np.abs(sub["seed_params"][4])
+        fl_s = np.maximum(1e-13 * l_abs[None, :] / hs / 1e-5, 2 * np.abs(fs - fs2) / 1e-5)
+        fl_a = np.maximum(1e-13 * np.sum(l_abs) / 1e-6 / 1e-5, 2 * np.abs(fa - fa2) / 1e-5)
+        es = np.abs(gs - fs) / np.maximum(np.abs(fs), fl_s)
+        ea = np.abs(ga - fa) / np.maximum(np.abs(fa), fl_a)
+        out[name] = {"grad_seed_err_max": float(es.max()), "grad_align_err_max": float(ea.max()),
+                     "grad_seed_resolved": float(np.mean(np.abs(fs) > fl_s)),
+                     "grad_align_resolved": float(np.mean(np.abs(fa) > fl_a))}
+    out.update(tracks=n, reference="oracle central finite differences (step 1e-6), element by element; "
+               "floor = max(1e-13 |L| / h, 2 |fd(h) - fd(2h)|) / 1e-5; resolved = fraction of elements above it")
+    rate = {"value": 2 * n / t_or, "unit": "tracks/s", "cores": cores,
+            "kind": "oracle central finite differences",
+            "sample": "%d tracks, both objectives, %d + 12 x %d batch fits each (%.1f s)" % (n, 12, S, t_or)}
+    return out, rate
 
 
 VARIANT_WORKLOAD = "fringe30_100k"
@@ -381,6 +442,70 @@ def time_scale(kf, synth, torch, stream, l2_flush, steps, warmup, rank, no_cpu):
         res["cpu_oracle"] = {"value": v, "unit": "tracks/s", "cores": cores, "kind": "oracle",
                              "sample": "first %d tracks, one pass (%.1f s)" % (n, dt)}
     return res
+
+
+# Further configurations of the fit, each timed as the headline is (autotuned
+# launch shape, graph replay, L2 flushed between steps) and checked against
+# the oracle: the small plain FP64 batch of 10-plane tracks, and the
+# 1M-track batch of uneven tracks with holes (mixed precision, one persistent
+# launch over the tracks sorted longest first, as the autotuner picks).
+CONFIGS = (("tel10_1k", "fp64", "all"), ("uneven30_1m", "mixed", "all"))
+
+
+def fit_roofline(roofline, offsets, is_hole, prec_id, ms, hbm):
+    """Roofline entry of a fit from the required flops of its own states."""
+    f64, f32 = roofline.batch_flops(offsets, is_hole, prec_id)
+    nbytes = roofline.algorithmic_bytes(offsets, is_hole)
+    achieved = f64 / (ms / 1e3) / 1e12
+    t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12), nbytes / (hbm * 1e9))
+    return {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "peak_source": "derived: 152 SM x 2 DFMA/clk x 2070 MHz",
+            "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32, "algorithmic_bytes_per_launch": nbytes,
+            "t_roof_ms": 1e3 * t_roof, "roof_frac": 1e3 * t_roof / ms, "traffic": None}
+
+
+def time_config(h, kf, synth, roofline, torch, stream, l2_flush, steps, warmup, name, prec, hbm, rank):
+    """One further configuration (see CONFIGS): tracks/s, its roofline and
+    the event (for the oracle check)."""
+    w = synth.WORKLOADS[name]
+    w = synth.scaled(w, w.n_tracks, seed=w.seed + 1000 * rank)
+    t0 = time.perf_counter()
+    ev = synth.make_event(w, with_truth_states=False)
+    gen_s = time.perf_counter() - t0
+    T = int(ev["n_tracks"])
+    dev = kf.event_to_device(ev)
+    out = kf.alloc_outputs(T)
+    pid = kf.KF_PRECISION_MIXED if prec == "mixed" else kf.KF_PRECISION_FP64
+    best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(pid), stream)
+    opt = kf.kf_default_options(pid, schedule=best.schedule, block=best.block, min_blocks=best.min_blocks,
+                                resident_warps=best.resident_warps, use_graph=1)
+    for _ in range(warmup):
+        kf.kf_fit_ex(h, dev, out, opt, stream)
+    torch.cuda.synchronize()
+    ms = []
+    torch.cuda.nvtx.range_push("timed_" + name)
+    for _ in range(steps):
+        l2_flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kf.kf_fit_ex(h, dev, out, opt, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    torch.cuda.nvtx.range_pop()
+    st = step_stats(ms)
+    holes = np.asarray(ev["is_hole"], dtype=bool)
+    res = {"workload": name, "tracks": T, "states": int(ev["surface_id"].shape[0]),
+           "precision": prec, "holes": int(holes.sum()) - T, "generation_s": gen_s,
+           "value": T / (st["mean"] / 1e3), "unit": "tracks/s", "ms_per_step": st["mean"], "step_ms": st,
+           "ok_tracks": int((out["status"] == 0).sum().item()),
+           "launch_shape": {"schedule": SCHEDULE_NAMES[best.schedule], "block": best.block,
+                            "min_blocks": best.min_blocks, "resident_warps": best.resident_warps,
+                            "cuda_graph": True},
+           "roofline": fit_roofline(roofline, ev["offsets"], ev["is_hole"], pid, st["mean"], hbm)}
+    host = {k: out[k].cpu().numpy() for k in ("params", "cov", "chi2", "status")}
+    return ev, host, res
 
 
 def run_reference(args, rank, world):
@@ -496,13 +621,14 @@ def run_ours(args, rank, world, local):
     adjoint = None
     adjoint_event = None
     if not args.no_adjoint:
-        adjoint_event, adjoint, adjoint_out = time_adjoint(h, kf, synth, torch, stream, l2_flush,
-                                              max(3, args.steps // 2), args.warmup, T,
-                                              reduce=kdist.sum_over_ranks if world > 1 else None)
-        a_ms = kdist.max_over_ranks(adjoint["ms_per_step"], device="cuda")
-        adjoint.update(ms_per_step=a_ms, value=world * adjoint["tracks"] / (a_ms / 1e3))
-    if adjoint is not None:
-        adjoint["roofline"] = ext_roofline("adjoint", adjoint["tracks"], adjoint["ms_per_step"])
+        adjoint_event, adjoint, adjoint_w = time_adjoint(h, kf, synth, torch, stream, l2_flush,
+                                                         max(3, args.steps // 2), args.warmup, T,
+                                                         reduce=kdist.sum_over_ranks if world > 1 else None)
+        for name in ("chi2", "whole"):
+            a_ms = kdist.max_over_ranks(adjoint[name]["ms_per_step"], device="cuda")
+            adjoint[name].update(ms_per_step=a_ms, value=world * adjoint["tracks"] / (a_ms / 1e3))
+            adjoint[name]["roofline"] = ext_roofline("adjoint_" + name, adjoint["tracks"], a_ms)
+        adjoint.update(ms_per_step=adjoint["whole"]["ms_per_step"], value=adjoint["whole"]["value"])
     scale = None
     if not args.no_scale:
         scale = time_scale(kf, synth, torch, stream, l2_flush, max(3, args.steps // 2), args.warmup,
@@ -510,6 +636,17 @@ def run_ours(args, rank, world, local):
         for name in ("mixed", "fp64"):
             s_ms = kdist.max_over_ranks(scale[name]["ms_per_step"], device="cuda")
             scale[name].update(ms_per_step=s_ms, value=world * scale["tracks"] / (s_ms / 1e3))
+    hbm = json.load(open(MEASURED_PEAKS)).get("hbm_gbs", 6780.0) if os.path.exists(MEASURED_PEAKS) else 6780.0
+    configs = {}
+    config_data = {}
+    if not args.no_configs:
+        for cname, cprec, _ in CONFIGS:
+            c_ev, c_out, c_res = time_config(h, kf, synth, roofline, torch, stream, l2_flush,
+                                             max(3, args.steps // 2), args.warmup, cname, cprec, hbm, rank)
+            c_ms = kdist.max_over_ranks(c_res["ms_per_step"], device="cuda")
+            c_res.update(ms_per_step=c_ms, value=world * c_res["tracks"] / (c_ms / 1e3))
+            configs[cname] = c_res
+            config_data[cname] = (c_ev, c_out)
     variants = None
     variant_event = None
     if not args.no_variants:
@@ -560,7 +697,6 @@ def run_ours(args, rank, world, local):
 
     f64, f32 = roofline.batch_flops(ev["offsets"], ev["is_hole"], prec_id[args.precision])
     nbytes = roofline.algorithmic_bytes(ev["offsets"], ev["is_hole"])
-    hbm = json.load(open(MEASURED_PEAKS)).get("hbm_gbs", 6780.0) if os.path.exists(MEASURED_PEAKS) else 6780.0
     kern_s = step_ms / 1e3
     achieved = f64 / kern_s / 1e12
     t_roof = max(f64 / (FP64_PEAK_TFLOPS * 1e12), f32 / (FP32_PEAK_TFLOPS * 1e12), nbytes / (hbm * 1e9))
@@ -583,21 +719,17 @@ def run_ours(args, rank, world, local):
                "sample": "all %d tracks of the workload, one pass (%.1f s)" % (n, dt),
                "single_core": {"value": v1, "unit": "tracks/s",
                                "sample": "first %d tracks, one thread (%.1f s)" % (n1, dt1)}}
+        for cname, (c_ev, c_out) in config_data.items():
+            cref = {}
+            cv, cdt, cn = oracle_tracks_per_s(c_ev, c_ev["n_tracks"], cores, keep=cref)
+            configs[cname]["accuracy"] = dict(accuracy(c_out, cref),
+                                              reference="FP64 oracle on all %d tracks" % cn)
+            configs[cname]["cpu_oracle"] = {"value": cv, "unit": "tracks/s", "cores": cores, "kind": "oracle",
+                                            "sample": "all %d tracks, one pass (%.1f s)" % (cn, cdt)}
         if adjoint is not None:
-            fd = {}
-            av, adt, an = oracle_gradient_rate(adjoint_event, 200, cores, keep=fd)
-            adjoint["cpu_oracle"] = {"value": av, "unit": "tracks/s", "cores": cores,
-                                     "kind": "oracle central finite differences",
-                                     "sample": "%d tracks, %d + 12 x %d batch fits (%.1f s)"
-                                               % (an, 12, adjoint_event["center"].shape[1], adt)}
-            # the timed kernel's seed gradients of those tracks against the
-            # oracle's central differences (per parameter, relative to the
-            # largest magnitude of that parameter's gradient)
-            g = adjoint_out["grad_seed"][:, :an]
-            rel = np.max(np.abs(g - fd["grad_seed"]), axis=1) / np.maximum(np.max(np.abs(fd["grad_seed"]), axis=1),
-                                                                         1e-300)
-            adjoint["accuracy"] = {"tracks": int(an), "grad_seed_rel_max": float(rel.max()),
-                                   "reference": "oracle central finite differences (step 1e-6)"}
+            acc_a, rate = adjoint_accuracy(h, kf, torch, adjoint_event, adjoint_w[0], adjoint_w[1], 200, cores)
+            adjoint["accuracy"] = acc_a
+            adjoint["cpu_oracle"] = rate
         if variants is not None:
             vref = {}
             vv, vdt, vn = oracle_tracks_per_s(variant_event, VARIANT_ORACLE_SAMPLE, cores,
@@ -621,7 +753,8 @@ def run_ours(args, rank, world, local):
                    "parallelism": "one independent batch per GPU" if world > 1 else "single GPU"},
         "fp64_path" if args.precision == "mixed" else "mixed_path": {
             "value": world * T / (other_ms / 1e3), "ms_per_step": other_ms, "step_ms": step_stats(ms_other),
-            "ok_tracks": int((st_other == 0).sum())},
+            "ok_tracks": int((st_other == 0).sum()),
+            "roofline": fit_roofline(roofline, ev["offsets"], ev["is_hole"], prec_id[other], other_ms, hbm)},
         "ok_tracks": int((st == 0).sum()),
         "launch_shape": tuned,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
@@ -638,6 +771,7 @@ def run_ours(args, rank, world, local):
         "cpu_baseline": cpu,
         "accuracy": acc,
         "scale": scale,
+        "configs": configs or None,
         "variants": variants,
         "adjoint": adjoint,
         "e2e": e2e,

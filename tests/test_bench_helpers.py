@@ -34,9 +34,10 @@ def test_source_hashes_gate_the_measured_constants(bench, monkeypatch):
         assert len(h) == 64 and int(h, 16) >= 0
     # with the sources the constants were captured on, the entry is reported
     monkeypatch.setattr(bench, "EXT_SOURCES_SHA256", bench.ext_kernel_sources_sha256())
-    r = bench.ext_roofline("adjoint", 100000, 50.0)
+    r = bench.ext_roofline("adjoint_chi2", 100000, 50.0)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["achieved"] == pytest.approx(bench.EXT_FLOPS_PER_TRACK["adjoint"] * 1e5 / 0.05 / 1e12)
+    assert r["achieved"] == pytest.approx(bench.EXT_FLOPS_PER_TRACK["adjoint_chi2"] * 1e5 / 0.05 / 1e12)
+    assert bench.ext_roofline("no such kernel", 100000, 50.0) is None
     assert r["frac"] == pytest.approx(r["achieved"] / bench.FP64_PEAK_TFLOPS)
     # a kernel changed since the capture reports no figure
     monkeypatch.setattr(bench, "EXT_SOURCES_SHA256", "0" * 64)

@@ -216,6 +216,13 @@ typedef struct {
                                   a part-filled last round */
   int32_t wait_limit;          /* polls of the kernels' bounded waits before
                                   they give up (0 = 2^20, about a second) */
+  int32_t team_warps;          /* FP64 path: warps that share each track's
+                                  work (0 or 1 = one thread per track; 2 or 4
+                                  = a team: lane l of each of a CTA's warps
+                                  works on track l of its 32, splitting the
+                                  Jacobian columns and the matrix rows, for
+                                  batches too small to fill the GPU; grid
+                                  schedule, block ignored) */
   int32_t test_wait_timeout;   /* diagnostic of the timeout path (0 = off):
                                   1 announces the surface table's copy on
                                   each CTA's barrier without issuing it, so

@@ -90,7 +90,8 @@ class KfOptions(ctypes.Structure):
                 ("use_graph", ctypes.c_int32), ("smoother", ctypes.c_int32),
                 ("energy_loss", ctypes.c_int32), ("bf_scale", ctypes.c_double),
                 ("material", KfMaterial), ("resident_warps", ctypes.c_int32),
-                ("wait_limit", ctypes.c_int32), ("test_wait_timeout", ctypes.c_int32)]
+                ("wait_limit", ctypes.c_int32), ("team_warps", ctypes.c_int32),
+                ("test_wait_timeout", ctypes.c_int32)]
 
 
 _lib = None

@@ -10,8 +10,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkfgb.so")
-SOURCES = ["kf_kernels.cu", "kf_mixed.cu", "kf_adjoint.cu", "kf_variants.cu", "kf_api.cu", "kf_static.cu"]
-HEADERS = ["kf_internal.h", "kf_device.cuh", "kf_fp64.cuh", os.path.join("..", "..", "include", "kf.h")]
+SOURCES = ["kf_kernels.cu", "kf_team.cu", "kf_mixed.cu", "kf_adjoint.cu", "kf_variants.cu", "kf_api.cu",
+           "kf_static.cu"]
+HEADERS = ["kf_internal.h", "kf_device.cuh", "kf_fp64.cuh", "kf_transport.cuh", os.path.join("..", "..", "include", "kf.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # per-file flags: the mixed kernel's FP32 divisions and square roots (step
 # lengths, Jacobian normalisations, angle increments) need no IEEE rounding;

@@ -1381,7 +1381,7 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
   io.TL = (size_t)p.n_tracks;
   const int tg = io.tg;
   const size_t TG = io.TG;
-  if (!staged || call_failed(p.error_flag)) {
+  if (!staged) {
     // a bounded wait of this call gave up: this CTA's tracks get NaN chi2,
     // smoothed outputs and seed gradients and add nothing to the alignment
     // gradient (the whole CTA returns here, so no warp-wide reduction below

@@ -126,6 +126,10 @@ int validate(const kf_tracks* tr, const kf_surfaces* su, const kf_measurements* 
     return KF_EUNSUPPORTED;
   if (opt->resident_warps < 0 || opt->resident_warps > 64) return KF_EINVAL;
   if (opt->wait_limit < 0 || (opt->test_wait_timeout != 0 && opt->test_wait_timeout != 1)) return KF_EINVAL;
+  if (opt->team_warps < 0 || opt->team_warps == 3 || opt->team_warps > 4) return KF_EINVAL;
+  if (opt->team_warps > 1 && (opt->precision != KF_PRECISION_FP64 || wants_variants(opt->smoother, opt->energy_loss,
+                                                                                     fi->map)))
+    return KF_EUNSUPPORTED;
   for (int i = 0; i < 3; ++i)
     if (!(fi->b[i] == fi->b[i])) return KF_EINVAL;
   if (opt->smoother != KF_SMOOTHER_RTS && opt->smoother != KF_SMOOTHER_BACKWARD_FILTER) return KF_EUNSUPPORTED;
@@ -183,6 +187,7 @@ void kf_default_options(kf_options* opt) {
   opt->bf_scale = 1e4;
   silicon(&opt->material);
   opt->wait_limit = 0;
+  opt->team_warps = 0;
   opt->test_wait_timeout = 0;
 }
 
@@ -369,6 +374,7 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
                 bool pack = true, bool own_slice = false, int counter_slot = 0) {
   if (t_end < 0) t_end = tr->n_tracks;
   kf_options opt = opt_in;
+  if (opt.team_warps > 1) opt.schedule = KF_SCHEDULE_GRID;  // one CTA per 32 tracks
   const bool whole = t_begin == 0 && t_end == tr->n_tracks;
   if (!whole && opt.schedule == KF_SCHEDULE_SORTED) opt.schedule = KF_SCHEDULE_PERSISTENT;
   const int64_t chunk = plan.chunk;
@@ -431,6 +437,7 @@ int enqueue_fit(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
   p.order = opt.schedule == KF_SCHEDULE_SORTED ? h->order : nullptr;
   p.resident_warps = opt.resident_warps;
   p.waves = opt.schedule == KF_SCHEDULE_WAVES;
+  p.team_warps = opt.team_warps;
   const bool variants = wants_variants(opt.smoother, opt.energy_loss, fi->map);
   if (variants) fill_variants(&p, fi, opt);
   int c = 0;
@@ -520,6 +527,7 @@ int kf_fit_ex(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const kf
     opt.block = best.block;
     opt.min_blocks = best.min_blocks;
     opt.resident_warps = best.resident_warps;
+    opt.team_warps = best.team_warps;
   }
   FitPlan plan;
   if ((rc = prepare_fit(h, tr, su, opt, &plan))) return rc;
@@ -576,6 +584,7 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
       best_out->block = c.best.block;
       best_out->min_blocks = c.best.min_blocks;
       best_out->resident_warps = c.best.resident_warps;
+      best_out->team_warps = c.best.team_warps;
       if (best_ms) *best_ms = c.ms;
       return KF_SUCCESS;
     }
@@ -607,6 +616,19 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
       o.block = mixed ? shapes_mixed[bi][0] : shapes_fp64[bi][0];
       o.min_blocks = mixed ? shapes_mixed[bi][1] : shapes_fp64[bi][1];
       o.resident_warps = 0;
+      o.team_warps = 0;
+      o.use_graph = 0;
+      cand[n_cand++] = o;
+    }
+  if (!mixed && !variants)
+    for (int tw = 2; tw <= 4; tw += 2) {
+      // each track shared by a team of warps (small batches)
+      kf_options o = base;
+      o.schedule = KF_SCHEDULE_GRID;
+      o.block = 32 * tw;
+      o.min_blocks = 0;
+      o.resident_warps = 0;
+      o.team_warps = tw;
       o.use_graph = 0;
       cand[n_cand++] = o;
     }
@@ -626,6 +648,7 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
             o.min_blocks = mixed ? vars_mixed[vi] : 0;
             if (o.block > max_block(mixed, o.min_blocks)) continue;
             o.resident_warps = 0;
+            o.team_warps = 0;
             o.use_graph = 0;
             cand[n_cand++] = o;
           }
@@ -640,6 +663,7 @@ int kf_autotune(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const 
       o.block = mixed ? waves_mixed[bi][0] : waves_fp64[bi][0];
       o.min_blocks = mixed ? waves_mixed[bi][1] : waves_fp64[bi][1];
       o.resident_warps = 0;
+      o.team_warps = 0;
       o.use_graph = 0;
       cand[n_cand++] = o;
     }

@@ -27,11 +27,18 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Every thread of the CTA calls this.  Returns false if the bounded wait on
-// the copy's mbarrier gave up after wait_limit polls (<= 0: the default);
-// the error flag is then set.  skip_copy (a diagnostic of the timeout path)
-// announces the copy's bytes on the barrier but issues no copy, so the wait
-// runs out with nothing in flight.
+// True when a bounded wait of this call gave up somewhere (the flag is reset
+// at the start of every call).
+__device__ __forceinline__ bool call_failed(const int32_t* error_flag) {
+  return *reinterpret_cast<const volatile int32_t*>(error_flag) != 0;
+}
+
+// Every thread of the CTA calls this.  Returns false (in every thread) if
+// the bounded wait on the copy's mbarrier gave up after wait_limit polls
+// (<= 0: the default) in any thread -- the error flag is then set -- or if
+// the flag was already set by another CTA of the call.  skip_copy (a
+// diagnostic of the timeout path) announces the copy's bytes on the barrier
+// but issues no copy, so the wait runs out with nothing in flight.
 __device__ __forceinline__ bool stage_surfaces(double* s_surf, const double* g_surf, uint32_t nbytes,
                                                uint64_t* mbar, int32_t* error_flag, int wait_limit = 0,
                                                bool skip_copy = false) {
@@ -59,19 +66,14 @@ __device__ __forceinline__ bool stage_surfaces(double* s_surf, const double* g_s
         : "r"(bar), "r"(0u)
         : "memory");
   }
-  if (!done) {
-    atomicExch(error_flag, 1);
-    return false;
-  }
-  return true;
-}
-
-// True when a bounded wait of this call gave up somewhere (the flag is reset
-// at the start of every call).  CTAs that see it fit nothing: a copy that a
-// timed-out CTA left in flight could land in shared memory that a later CTA
-// on the same SM has been given.
-__device__ __forceinline__ bool call_failed(const int32_t* error_flag) {
-  return *reinterpret_cast<const volatile int32_t*>(error_flag) != 0;
+  // one verdict for the whole CTA (its threads poll independently and could
+  // disagree near the limit; the callers' barriers need every thread)
+  const bool mine = __syncthreads_and(done) != 0;
+  if (!mine && threadIdx.x == 0) atomicExch(error_flag, 1);
+  // a CTA that starts after another CTA's wait of this call gave up fits
+  // nothing either: a copy that a timed-out CTA left in flight could land in
+  // shared memory that this CTA has been given
+  return __syncthreads_and(mine && !call_failed(error_flag)) != 0;
 }
 
 struct Surf {
@@ -238,9 +240,8 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitP
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* s_surf = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(8) uint64_t s_mbar;
-  bool ok = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar, p.error_flag,
-                           p.wait_limit, p.skip_stage_copy != 0);
-  if (ok && call_failed(p.error_flag)) ok = false;
+  const bool ok = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
+                                 p.error_flag, p.wait_limit, p.skip_stage_copy != 0);
   // One call site for both schedules. A grid CTA fits its own blockDim
   // tracks once; a persistent CTA keeps taking blockDim-track units. The
   // whole CTA takes a unit together, so its warps start every unit in step

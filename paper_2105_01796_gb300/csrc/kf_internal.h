@@ -75,6 +75,7 @@ struct FitParams {
   const int32_t* order;    // non-null: slot s fits track order[s]
   int32_t resident_warps;  // persistent launch: warps per SM (0 = occupancy)
   int32_t waves;           // grid launch split into full waves + one spread wave (host side)
+  int32_t team_warps;      // FP64 path: > 1 shares each track over that many warps (host side)
   // method variants (the FP64 variant kernel)
   int32_t smoother;        // 0 RTS, 1 backward filter + weighted mean
   int32_t energy_loss;     // 1: mean loss and straggling on q/p
@@ -114,6 +115,10 @@ cudaError_t launch_selftest_any(long long n, unsigned long long* counter, cudaSt
 // *launched (optional) gets the number of kernel launches queued.
 cudaError_t launch_fit(const FitParams& p, int precision, int block, int min_blocks,
                        cudaStream_t stream, int* launched = nullptr);
+
+// The FP64 fit with each track's work shared by a team of 2 or 4 warps
+// (kf_team.cu): one CTA per 32 tracks, grid schedule.
+cudaError_t launch_fit_team(const FitParams& p, int team_warps, cudaStream_t stream, int* launched = nullptr);
 
 // The FP64 kernel of the method variants (kf_variants.cu): backward-filter
 // smoother, energy loss, field map; same records as the FP64 path.

@@ -89,6 +89,7 @@ extern "C" int kf_fit_static(const kf_tracks* tr, const kf_surfaces* su, const k
   if (opt.min_blocks < 0 || opt.min_blocks > 4) return KF_EUNSUPPORTED;
   if (opt.resident_warps < 0 || opt.resident_warps > 64) return KF_EINVAL;
   if (opt.wait_limit < 0 || (opt.test_wait_timeout != 0 && opt.test_wait_timeout != 1)) return KF_EINVAL;
+  if (opt.team_warps > 1) return KF_EUNSUPPORTED;  // one thread per track only
   // the static block serves the baseline method only
   if (wants_variants(opt.smoother, opt.energy_loss, fi->map)) return KF_EUNSUPPORTED;
   // size limits of the static block

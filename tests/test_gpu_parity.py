@@ -451,3 +451,59 @@ def test_pipelined_host_entry_equals_device_entry(handle, prec):
             for k in ("params", "cov", "chi2", "ndf", "status", "states"):
                 assert np.array_equal(host[k], ref[k], equal_nan=True), (n, sched, cap, k)
             assert handle.last_launch_count() >= 3
+
+
+# ---------------------------------------------------------------- track teams (FP64)
+
+@pytest.mark.parametrize("team", [2, 4])
+def test_track_team_matches_oracle(handle, team):
+    """Each track shared by a team of 2 or 4 warps: the 1k-track batch,
+    uneven tracks with holes (the CTA's tracks step in lockstep over
+    different lengths) with every smoothed state, a general field with tilted
+    planes (the field-along-z shortcut off), and the edge cases -- all in
+    the FP64 contract, and within 1e-12 of the one-thread-per-track kernel
+    (the same arithmetic per element, summed in a few different orders)."""
+    ev = synth.make_event(synth.WORKLOADS["tel10_1k"])
+    g = gpu_fit(handle, ev, FP64, team_warps=team)
+    compare(g, oracle.fit_batch(ev), FP64)
+    one = gpu_fit(handle, ev, FP64)
+    assert param_err(g["params"], one["params"], one["cov"]).max() < 1e-12
+    assert cov_err(g["cov"], one["cov"]).max() < 1e-12
+
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 1500))
+    g = gpu_fit(handle, ev, FP64, with_states=True, team_warps=team)
+    r = oracle.fit_batch(ev, with_states=True)
+    compare(g, r, FP64)
+    ok = np.repeat(r["status"] == 0, np.diff(ev["offsets"].astype(np.int64)))
+    err = states_err(g["states"][:, ok], r["states"][:, ok], state_sigmas(ev)[:, ok])
+    assert err.max() < TOL[FP64][0], err.max()
+
+    ev = dict(synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 333)))
+    ev["bfield"] = np.array([0.3, -0.2, 2.0])
+    rng = np.random.default_rng(12)
+    rot, center = ev["rot"].copy(), ev["center"].copy()
+    for s in range(1, center.shape[1]):
+        a, b = rng.normal(size=2) * 0.02
+        Rx = np.array([[1, 0, 0], [0, np.cos(a), -np.sin(a)], [0, np.sin(a), np.cos(a)]])
+        Ry = np.array([[np.cos(b), 0, np.sin(b)], [0, 1, 0], [-np.sin(b), 0, np.cos(b)]])
+        rot[:, s] = (Ry @ Rx @ rot[:, s].reshape(3, 3)).ravel()
+    ev["rot"], ev["center"] = rot, center
+    compare(gpu_fit(handle, ev, FP64, team_warps=team), oracle.fit_batch(ev), FP64)
+
+    ev = _edge_event()
+    g = gpu_fit(handle, ev, FP64, with_states=True, team_warps=team)
+    compare(g, oracle.fit_batch(ev, with_states=True), FP64)
+    assert g["ndf"][0] == 0 and np.array_equal(g["params"][:, 0], ev["seed_params"][:, 0])
+
+
+def test_track_team_options(handle):
+    """Team sizes other than 2 and 4 are refused; so is a team in mixed
+    precision; the autotuner's choice (which includes the teams for FP64)
+    fits within the contract."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel10_1k"], 64))
+    with pytest.raises(kf.KfError, match="-1"):
+        gpu_fit(handle, ev, FP64, team_warps=3)
+    with pytest.raises(kf.KfError, match="-4"):
+        gpu_fit(handle, ev, MIXED, team_warps=2)
+    ev = synth.make_event(synth.WORKLOADS["tel10_1k"])
+    compare(gpu_fit(handle, ev, FP64, schedule=kf.KF_SCHEDULE_AUTO), oracle.fit_batch(ev), FP64)

@@ -39,7 +39,16 @@ using namespace dev;
 
 constexpr int kTeamTracks = 32;
 // shared exchange buffers per CTA, [field][32 tracks] doubles
-constexpr int kShF = 0, kShCp = 25, kShCf = 46, kShA = 67, kShFields = 103;
+// F 25 | Cp 21 | Cf (also Cs) 21 | A 36 | sin/cos of the next transport's
+// start angles 4 | the end angles (phi, theta) and the scattering variance 3
+constexpr int kShF = 0, kShCp = 25, kShCf = 46, kShA = 67, kShTrig = 103, kShAng = 107, kShFields = 110;
+
+// The transcendental functions of the state (the sine and cosine of the
+// start angles, atan2 of the end direction, the Highland width) are computed
+// by one warp, the one with the least split work, and read by the others
+// after the barriers that follow them anyway.
+template <int W>
+__host__ __device__ constexpr int trig_owner() { return W - 1; }
 
 // owner warp of matrix row r (rows hold 1..6 lower-triangle elements; the
 // split balances them: W = 2: 11 / 10, W = 4: 6 / 6 / 6 / 3)
@@ -63,16 +72,18 @@ __host__ __device__ constexpr int col_mask(int w) {
 // The transport of kf_kernels.cu for the F columns in FMASK: the state is
 // propagated in full, the Jacobian columns of FMASK only; those columns of F
 // go to shared memory (sF[(r * 5 + c) * 32 + lane], time row at r = 4).
-template <bool BZ, int FMASK>
-__device__ __forceinline__ int transport_cols(const Surf& sa, const Surf& sb, const double x[6], const double B[3],
-                                              double mass, double h_max, int n_iter, double xp[6], double* sF,
-                                              int lane, double& sin_theta, double& cos_inc) {
+// sc = (sin phi, cos phi, sin theta, cos theta) of x; the end angles phi,
+// theta go to sAng when ANG (their owner warp), else xp[2], xp[3] are left
+// for the caller to read from sAng after the barrier.
+template <bool BZ, int FMASK, bool ANG>
+__device__ __forceinline__ int transport_cols(const Surf& sa, const Surf& sb, const double x[6], const double sc[4],
+                                              const double B[3], double mass, double h_max, int n_iter,
+                                              double xp[6], double* sF, double* sAng, int lane, double& sin_theta,
+                                              double& cos_inc) {
   using R = double;
   constexpr int CMASK = (FMASK >> 2) & 7;
   Prop<R> s;
-  double sp, cp, st, ct;
-  sincos(x[2], &sp, &cp);
-  sincos(x[3], &st, &ct);
+  const double sp = sc[0], cp = sc[1], st = sc[2], ct = sc[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) s.r[i] = sa.c(i) + x[0] * sa.u(i) + x[1] * sa.v(i);
   s.T[0] = cp * st;
@@ -103,8 +114,10 @@ __device__ __forceinline__ int transport_cols(const Surf& sa, const Surf& sb, co
   const double rho2 = s.T[0] * s.T[0] + s.T[1] * s.T[1];
   const double irho = rsqrt_any(rho2);
   const double rho = rho2 * irho;
-  const double phi = atan2(s.T[1], s.T[0]);
-  const double theta = atan2(rho, s.T[2]);
+  if (ANG) {
+    sAng[0 * kTeamTracks + lane] = atan2(s.T[1], s.T[0]);
+    sAng[1 * kTeamTracks + lane] = atan2(rho, s.T[2]);
+  }
   const double itn = rsqrt_any(rho2 + s.T[2] * s.T[2]);
   const double tn = (rho2 + s.T[2] * s.T[2]) * itn;
   const double cph = s.T[0] * irho, sph = s.T[1] * irho;
@@ -143,8 +156,6 @@ __device__ __forceinline__ int transport_cols(const Surf& sa, const Surf& sb, co
   const double d0 = s.r[0] - sb.c(0), d1 = s.r[1] - sb.c(1), d2 = s.r[2] - sb.c(2);
   xp[0] = d0 * sb.u(0) + d1 * sb.u(1) + d2 * sb.u(2);
   xp[1] = d0 * sb.v(0) + d1 * sb.v(1) + d2 * sb.v(2);
-  xp[2] = phi;
-  xp[3] = theta;
   xp[4] = s.lam;
   xp[5] = s.t;
   sin_theta = sth;
@@ -153,10 +164,12 @@ __device__ __forceinline__ int transport_cols(const Surf& sa, const Surf& sb, co
 }
 
 template <bool BZ, int W, int w>
-__device__ __forceinline__ int transport_warp(const Surf& sa, const Surf& sb, const double x[6], const double B[3],
-                                              double mass, double h_max, int n_iter, double xp[6], double* sF,
-                                              int lane, double& sin_theta, double& cos_inc) {
-  return transport_cols<BZ, col_mask<W>(w)>(sa, sb, x, B, mass, h_max, n_iter, xp, sF, lane, sin_theta, cos_inc);
+__device__ __forceinline__ int transport_warp(const Surf& sa, const Surf& sb, const double x[6], const double sc[4],
+                                              const double B[3], double mass, double h_max, int n_iter,
+                                              double xp[6], double* sF, double* sAng, int lane, double& sin_theta,
+                                              double& cos_inc) {
+  return transport_cols<BZ, col_mask<W>(w), w == trig_owner<W>()>(sa, sb, x, sc, B, mass, h_max, n_iter, xp, sF,
+                                                                   sAng, lane, sin_theta, cos_inc);
 }
 
 // F element (r, c), r in {0..3, 5}, c in 0..4, from shared memory
@@ -178,6 +191,8 @@ __device__ void fit_team(const FitParams& p, const double* s_surf, double* sh, i
   double* sCp = sh + kShCp * kTeamTracks;
   double* sCf = sh + kShCf * kTeamTracks;
   double* sA = sh + kShA * kTeamTracks;
+  double* sTrig = sh + kShTrig * kTeamTracks;
+  double* sAng = sh + kShAng * kTeamTracks;
   int64_t o0 = 0, o1 = 0;
   int n = 0;
   int status = valid ? ST_OK : ST_BAD_INPUT;
@@ -221,16 +236,38 @@ __device__ void fit_team(const FitParams& p, const double* s_surf, double* sh, i
       if (act) {
         const Surf sa{s_surf + p.surface_id[o0 + k - 1] * kSurfStride}, sb{s_surf + p.surface_id[o0 + k] * kSurfStride};
         int st = ST_OK;
+        double sc[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sc[e] = sTrig[e * kTeamTracks + lane];
+#define KF_TEAM_TRANSPORT(WW) \
+  transport_warp<BZ, W, WW>(sa, sb, x, sc, Bf, p.mass, p.h_max, p.n_iter, xp, sF, sAng, lane, sin_th, cos_inc)
         switch (w) {
-          case 0: st = transport_warp<BZ, W, 0>(sa, sb, x, Bf, p.mass, p.h_max, p.n_iter, xp, sF, lane, sin_th, cos_inc); break;
-          case 1: st = transport_warp<BZ, W, 1>(sa, sb, x, Bf, p.mass, p.h_max, p.n_iter, xp, sF, lane, sin_th, cos_inc); break;
-          case 2: st = transport_warp<BZ, W, (W > 2 ? 2 : 1)>(sa, sb, x, Bf, p.mass, p.h_max, p.n_iter, xp, sF, lane, sin_th, cos_inc); break;
-          default: st = transport_warp<BZ, W, (W > 3 ? 3 : 1)>(sa, sb, x, Bf, p.mass, p.h_max, p.n_iter, xp, sF, lane, sin_th, cos_inc); break;
+          case 0: st = KF_TEAM_TRANSPORT(0); break;
+          case 1: st = KF_TEAM_TRANSPORT(1); break;
+          case 2: st = KF_TEAM_TRANSPORT((W > 2 ? 2 : 1)); break;
+          default: st = KF_TEAM_TRANSPORT((W > 3 ? 3 : 1)); break;
         }
+#undef KF_TEAM_TRANSPORT
         status = st;
         act = st == ST_OK;
+        // multiple scattering of surface k: theta0^2 (added before the update)
+        if (act && w == trig_owner<W>()) {
+          const double xx0 = sb.xx0();
+          double q = 0.0;
+          if (xx0 > 0.0) {
+            const double th0 = highland<double>(fabs(x[4]), p.mass * p.mass, xx0, cos_inc);
+            q = th0 * th0;
+          }
+          sAng[2 * kTeamTracks + lane] = q;
+        }
       }
-      __syncthreads();  // F complete
+      __syncthreads();  // F, the end angles and theta0^2 complete
+      double q_ms = 0.0;
+      if (act) {
+        xp[2] = sAng[0 * kTeamTracks + lane];
+        xp[3] = sAng[1 * kTeamTracks + lane];
+        q_ms = sAng[2 * kTeamTracks + lane];
+      }
       if (act) {
         // Bm = F Cf_{k-1} and Cp = Bm F^T for the rows this warp owns
 #pragma unroll
@@ -269,13 +306,9 @@ __device__ void fit_team(const FitParams& p, const double* s_surf, double* sh, i
       if (act) {
 #pragma unroll
         for (int e = 0; e < 21; ++e) Cp[e] = sCp[e * kTeamTracks + lane];
-        // multiple scattering of surface k (added before the update)
-        const double xx0 = Surf{s_surf + p.surface_id[o0 + k] * kSurfStride}.xx0();
-        if (xx0 > 0.0) {
-          const double th0 = highland<double>(fabs(x[4]), p.mass * p.mass, xx0, cos_inc);
-          const double q = th0 * th0;
-          Cp[sy(2, 2)] += q / (sin_th * sin_th);
-          Cp[sy(3, 3)] += q;
+        if (q_ms > 0.0) {
+          Cp[sy(2, 2)] += q_ms / (sin_th * sin_th);
+          Cp[sy(3, 3)] += q_ms;
         }
       }
     }
@@ -345,7 +378,17 @@ __device__ void fit_team(const FitParams& p, const double* s_surf, double* sh, i
 #pragma unroll
           for (int c = 0; c <= r; ++c) RC::put_cf(ws, k, sy(r, c), Cp[sy(r, c)]);
     }
-    __syncthreads();  // Cf complete
+    // the start angles' sines and cosines for the next transport
+    if (act && status == ST_OK && w == trig_owner<W>() && k + 1 < n) {
+      double sp, cp, st, ct;
+      sincos(x[2], &sp, &cp);
+      sincos(x[3], &st, &ct);
+      sTrig[0 * kTeamTracks + lane] = sp;
+      sTrig[1 * kTeamTracks + lane] = cp;
+      sTrig[2 * kTeamTracks + lane] = st;
+      sTrig[3 * kTeamTracks + lane] = ct;
+    }
+    __syncthreads();  // Cf and the start angles complete
     if (meas && status == ST_OK)
 #pragma unroll
       for (int e = 0; e < 21; ++e) C[e] = sCf[e * kTeamTracks + lane];

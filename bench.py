@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (chi2 gradient) kernel")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the further configurations (1k FP64 10-plane tracks, 1M uneven tracks)")
+    ap.add_argument("--configs", default="all",
+                    help="comma-separated names of the further configurations to run (default: all)")
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the 4M-track throughput-scale workload (mixed and FP64)")
     return ap.parse_args()
@@ -411,7 +413,7 @@ def time_scale(kf, synth, torch, stream, l2_flush, steps, warmup, rank, no_cpu):
     for name, prec in (("mixed", kf.KF_PRECISION_MIXED), ("fp64", kf.KF_PRECISION_FP64)):
         best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(prec), stream)
         opt = kf.kf_default_options(prec, schedule=best.schedule, block=best.block, min_blocks=best.min_blocks,
-                                    resident_warps=best.resident_warps, use_graph=1)
+                                    resident_warps=best.resident_warps, team_warps=best.team_warps, use_graph=1)
         for _ in range(warmup):
             kf.kf_fit_ex(h, dev, out, opt, stream)
         torch.cuda.synchronize()
@@ -478,7 +480,7 @@ def time_config(h, kf, synth, roofline, torch, stream, l2_flush, steps, warmup, 
     pid = kf.KF_PRECISION_MIXED if prec == "mixed" else kf.KF_PRECISION_FP64
     best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(pid), stream)
     opt = kf.kf_default_options(pid, schedule=best.schedule, block=best.block, min_blocks=best.min_blocks,
-                                resident_warps=best.resident_warps, use_graph=1)
+                                resident_warps=best.resident_warps, team_warps=best.team_warps, use_graph=1)
     for _ in range(warmup):
         kf.kf_fit_ex(h, dev, out, opt, stream)
     torch.cuda.synchronize()
@@ -495,6 +497,30 @@ def time_config(h, kf, synth, roofline, torch, stream, l2_flush, steps, warmup, 
         ms.append(a.elapsed_time(b))
     torch.cuda.nvtx.range_pop()
     st = step_stats(ms)
+    one = None
+    if best.team_warps > 1:
+        # the same batch with one thread per track (grid of 64-thread CTAs),
+        # for comparison with the track-team mapping the autotuner picked
+        opt1 = kf.kf_default_options(pid, schedule=kf.KF_SCHEDULE_GRID, block=64, use_graph=1)
+        for _ in range(warmup):
+            kf.kf_fit_ex(h, dev, out, opt1, stream)
+        torch.cuda.synchronize()
+        ms1 = []
+        for _ in range(steps):
+            l2_flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            kf.kf_fit_ex(h, dev, out, opt1, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms1.append(a.elapsed_time(b))
+        s1 = step_stats(ms1)
+        one = {"value": T / (s1["mean"] / 1e3), "unit": "tracks/s", "ms_per_step": s1["mean"], "step_ms": s1,
+               "launch_shape": {"schedule": "grid", "block": 64, "team_warps": 1, "cuda_graph": True}}
+        # the timed fit's outputs are the tuned launch's
+        kf.kf_fit_ex(h, dev, out, opt, stream)
+        torch.cuda.synchronize()
     holes = np.asarray(ev["is_hole"], dtype=bool)
     res = {"workload": name, "tracks": T, "states": int(ev["surface_id"].shape[0]),
            "precision": prec, "holes": int(holes.sum()) - T, "generation_s": gen_s,
@@ -502,8 +528,11 @@ def time_config(h, kf, synth, roofline, torch, stream, l2_flush, steps, warmup, 
            "ok_tracks": int((out["status"] == 0).sum().item()),
            "launch_shape": {"schedule": SCHEDULE_NAMES[best.schedule], "block": best.block,
                             "min_blocks": best.min_blocks, "resident_warps": best.resident_warps,
-                            "cuda_graph": True},
+                            "team_warps": max(1, best.team_warps), "cuda_graph": True},
            "roofline": fit_roofline(roofline, ev["offsets"], ev["is_hole"], pid, st["mean"], hbm)}
+    if one is not None:
+        one["roofline"] = fit_roofline(roofline, ev["offsets"], ev["is_hole"], pid, one["ms_per_step"], hbm)
+        res["one_thread_per_track"] = one
     host = {k: out[k].cpu().numpy() for k in ("params", "cov", "chi2", "status")}
     return ev, host, res
 
@@ -575,10 +604,10 @@ def run_ours(args, rank, world, local):
         best, _ = kf.kf_autotune(h, dev, out, kf.kf_default_options(prec_id[prec]), stream)
         opt = kf.kf_default_options(prec_id[prec], schedule=best.schedule, block=best.block,
                                     min_blocks=best.min_blocks, resident_warps=best.resident_warps,
-                                    use_graph=0 if args.no_graph else 1)
+                                    team_warps=best.team_warps, use_graph=0 if args.no_graph else 1)
         tuned[prec] = {"schedule": SCHEDULE_NAMES[best.schedule], "block": best.block,
                        "min_blocks": best.min_blocks, "resident_warps": best.resident_warps,
-                       "cuda_graph": not args.no_graph}
+                       "team_warps": max(1, best.team_warps), "cuda_graph": not args.no_graph}
         for _ in range(warmup):
             kf.kf_fit_ex(h, dev, out, opt, stream)
         torch.cuda.synchronize()
@@ -641,6 +670,8 @@ def run_ours(args, rank, world, local):
     config_data = {}
     if not args.no_configs:
         for cname, cprec, _ in CONFIGS:
+            if args.configs != "all" and cname not in args.configs.split(","):
+                continue
             c_ev, c_out, c_res = time_config(h, kf, synth, roofline, torch, stream, l2_flush,
                                              max(3, args.steps // 2), args.warmup, cname, cprec, hbm, rank)
             c_ms = kdist.max_over_ranks(c_res["ms_per_step"], device="cuda")

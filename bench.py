@@ -44,17 +44,23 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 # is this per-state figure times its states.  It holds only for the kernel
 # sources and build flags that were captured: any change to them makes the
 # figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (592.369664e6 + 492.28416e6 + 505.207296e6 + 429.755136e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "8a71f89d172d3fa7b89b8c05ab31578260476708d363090b36265c6664466013"
+MIXED_TRAFFIC_BYTES_PER_STATE = (637.5552e6 + 534.25152e6 + 435.349504e6 + 382.342912e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "30c471845aed6646e64a8580254a5fd0fe632083569c8bf0f1ddb923f4723011"
+# the same for the FP64 path's kernel (one launch of the 100k-track step:
+# 2304.475 + 2223.975 MB)
+FP64_TRAFFIC_BYTES_PER_STATE = (2304.475e6 + 2223.975e6) / 3.1e6
+FP64_TRAFFIC_SOURCES_SHA256 = "d2ada231cfd1170211a73713799423d0ff5dad2742b8b8a93584ec8a84416c64"
 
 
-# FP64 flops the hardware counted (ncu: 2 x fused + unfused FP64 warp
-# instructions x 32) per track in one 100k-track launch of the variant kernel
+# FP64 flops the hardware counted (ncu: 2 x DFMA + DADD + DMUL thread
+# instructions) per track in one 100k-track launch of the variant kernel
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
-# (align20, 21 states); reported while those kernels' sources match
-EXT_FLOPS_PER_TRACK = {"variants": (396343307 * 2 + 268774064) * 32 / 1e5,
-                       "adjoint_chi2": (464212500 * 2 + 305600000) * 32 / 1e5}
-EXT_SOURCES_SHA256 = "faedab12959631e34ab8e470c52d46c043781275dd0886f2e158a42e032fb5af"
+# (align20, 21 states; the chi2 objective and the whole-fit objective);
+# reported while those kernels' sources match
+EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105256 + 2760501561 + 5733751603) / 1e5,
+                       "adjoint_chi2": (2 * 14906000038 + 1671199997 + 7903600040) / 1e5,
+                       "adjoint_whole": (2 * 28841200052 + 2808200046 + 11588700025) / 1e5}
+EXT_SOURCES_SHA256 = "67248be0dcbebc1439e396ad96190876b2f40e957c84ac9580bcec8530b359dc"
 
 
 def ext_kernel_sources_sha256():
@@ -79,13 +85,22 @@ def ext_roofline(kind, tracks, ms):
             "flops_source": "hardware-counted FP64 flops (ncu) of a 100k-track launch, per track"}
 
 
-def mixed_kernel_sources_sha256():
+def kernel_sources_sha256(files):
     import hashlib
     h = hashlib.sha256()
-    for f in ("csrc/kf_mixed.cu", "csrc/kf_device.cuh", "csrc/kf_internal.h", "_build.py"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2105_01796_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def mixed_kernel_sources_sha256():
+    return kernel_sources_sha256(("csrc/kf_mixed.cu", "csrc/kf_device.cuh", "csrc/kf_internal.h", "_build.py"))
+
+
+def fp64_kernel_sources_sha256():
+    return kernel_sources_sha256(("csrc/kf_kernels.cu", "csrc/kf_transport.cuh", "csrc/kf_fp64.cuh",
+                                  "csrc/kf_device.cuh", "csrc/kf_internal.h", "_build.py"))
 
 
 def parse():
@@ -785,7 +800,10 @@ def run_ours(args, rank, world, local):
         "fp64_path" if args.precision == "mixed" else "mixed_path": {
             "value": world * T / (other_ms / 1e3), "ms_per_step": other_ms, "step_ms": step_stats(ms_other),
             "ok_tracks": int((st_other == 0).sum()),
-            "roofline": fit_roofline(roofline, ev["offsets"], ev["is_hole"], prec_id[other], other_ms, hbm)},
+            "roofline": dict(fit_roofline(roofline, ev["offsets"], ev["is_hole"], prec_id[other], other_ms, hbm),
+                             traffic=(FP64_TRAFFIC_BYTES_PER_STATE * M
+                                      if other == "fp64" and fp64_kernel_sources_sha256() == FP64_TRAFFIC_SOURCES_SHA256
+                                      else None))},
         "ok_tracks": int((st == 0).sum()),
         "launch_shape": tuned,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,

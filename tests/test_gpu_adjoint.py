@@ -287,3 +287,39 @@ def test_full_size_whole_fit_gradients_sampled(handle):
     g0 = _whole(handle, synth.subset(ev, np.arange(half)), np.zeros((6, S)), None, v[:, :half], W[:, :half])
     g1 = _whole(handle, synth.subset(ev, np.arange(half, T)), np.zeros((6, S)), None, v[:, half:], W[:, half:])
     assert np.max(np.abs(g["ga"] - (g0["ga"] + g1["ga"]))) <= 1e-10 * np.max(np.abs(g["ga"]))
+
+
+def test_whole_fit_gradients_uneven_tracks_with_holes(handle):
+    """Tracks of 1 to 30 states with holes (segment boundaries at every
+    place, warps whose tracks have different segment counts, holes on the
+    reference-plane side and at the last state): the whole-fit objective's
+    values and gradients against the oracle, element by element."""
+    ev = dict(synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 96)))
+    # a few very short tracks: 1, 2 and 3 states (cut from the first three)
+    o = ev["offsets"].astype(np.int64)
+    keep = []
+    lengths = []
+    for t in range(96):
+        n = int(o[t + 1] - o[t])
+        L = {0: 1, 1: 2, 2: 3}.get(t, n)
+        keep.append(np.arange(o[t], o[t] + L))
+        lengths.append(L)
+    idx = np.concatenate(keep)
+    ev["offsets"] = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int32)
+    for k in ("loc", "cov", "truth_states"):
+        if ev.get(k) is not None:
+            ev[k] = np.ascontiguousarray(ev[k][:, idx])
+    for k in ("surface_id", "is_hole"):
+        ev[k] = np.ascontiguousarray(ev[k][idx]).copy()
+    ev["is_hole"][ev["offsets"][5 + 1] - 1] = 1      # a track ending on a hole
+    v, W = _smoother_weights(ev)
+    w = np.random.default_rng(4).uniform(0.5, 1.5, size=96)
+    S = ev["center"].shape[1]
+    g = _whole(handle, ev, np.zeros((6, S)), w, v, W)
+    ref = oracle.fit_batch(ev)
+    assert np.all(ref["status"] == 0)
+    assert param_err(g["params"], ref["params"], ref["cov"]).max() < 1e-9
+    assert cov_err(g["cov"], ref["cov"]).max() < 1e-9
+    fd = _fd2(oracle.objective_gradient_fd, ev=ev, weights=w, dl_dparams=v, dl_dcov=W)
+    _, l_abs = oracle.objective_per_track(ev, weights=w, dl_dparams=v, dl_dcov=W)
+    _check_grads(g["gs"], g["ga"], fd[0], fd[1], ev["seed_params"], l_abs)

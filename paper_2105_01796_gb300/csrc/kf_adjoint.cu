@@ -919,6 +919,7 @@ struct GradParams {
   double* ckpt;         // [n_ckpt][27][n_tracks]: filtered checkpoints
   double* sck;          // [n_ckpt + 1][27][n_tracks]: smoothed checkpoints
   double* sadj;         // [max_states][kSmRec][n_tracks]: the smoother's adjoint contributions
+  double* pipe;         // [2][kSlot][n_tracks]: hand-off slots of the pipelined reverse (or null)
   int32_t n_ckpt;
 };
 
@@ -1346,6 +1347,297 @@ __device__ __noinline__ void recompute_segment(const TrackIO& io, const double* 
   }
 }
 
+// adds the smoother's contributions to the adjoints of x_f,k and C_f,k
+__device__ __forceinline__ void add_sm_filtered(const TrackIO& io, int k, double lf[6], double Lf[6][6]) {
+#pragma unroll
+  for (int e = 0; e < 6; ++e) lf[e] += io.sadj(k, kSmXF + e);
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const double v = io.sadj(k, kSmCF + sy(i, j));
+      Lf[i][j] += v;
+      if (j < i) Lf[j][i] += v;
+    }
+}
+
+// The filtered states s0 .. s1-1 of a segment, from its checkpoint j.
+__device__ __forceinline__ void recompute_filtered(const TrackIO& io, const double* s_surf, int j, int s0, int s1,
+                                                   double bx[kSeg][6], double bC[kSeg][21]) {
+#pragma unroll
+  for (int e = 0; e < 6; ++e) bx[0][e] = io.ck(j, e);
+#pragma unroll
+  for (int e = 0; e < 21; ++e) bC[0][e] = io.ck(j, 6 + e);
+#pragma unroll
+  for (int i = 1; i < kSeg; ++i) {
+    if (s0 + i < s1) {
+      const int k = s0 + i;
+      double xp[6], Cp[21], F[6][6], qp, qt;
+      JacS<double> J;
+      transport_values(*io.g, s_surf, io.sid(k - 1), io.sid(k), bx[i - 1], xp, J, qp, qt);
+      dense_F(J, F);
+      cov_transport(F, bC[i - 1], qp, qt, Cp);
+      if (!io.hole(k)) {
+        double m[2], V[3], c2;
+        io.meas(k, m, V);
+        update_fwd(xp, Cp, m, V, bx[i], bC[i], c2);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) bx[i][e] = xp[e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) bC[i][e] = Cp[e];
+      }
+    }
+  }
+}
+
+// What the reverse of transition k-1 -> k needs from its forward: the
+// filtered state it starts from, the prediction, the Jacobian, and the
+// transport's tape and end state.
+struct TransitionFwd {
+  double xprev[6], Cprev[21], xp[6], Cp[21];
+  JacS<double> J;
+  Tape tp;
+  PropS<double> s_end;
+};
+
+__device__ __forceinline__ void aligned_planes(const GradParams& g, const double* s_surf, int sa, int sb,
+                                               double aa[6], double ab[6], Plane<double>& pa, Plane<double>& pb) {
+  load_align(g, sa, aa);
+  load_align(g, sb, ab);
+  pa = aligned_plane<double>(Surf{s_surf + sa * kSurfStride}, aa);
+  pb = aligned_plane<double>(Surf{s_surf + sb * kSurfStride}, ab);
+}
+
+// the forward of transition k: the taped transport from (xprev, Cprev)
+__device__ __forceinline__ void transition_forward(const GradParams& g, const TrackIO& io, const double* s_surf, int k,
+                                                   const double xprev[6], const double Cprev[21], TransitionFwd& tf) {
+  const FitParams& p = g.f;
+  const int sa = io.sid(k - 1), sb = io.sid(k);
+  double aa[6], ab[6];
+  Plane<double> pa, pb;
+  aligned_planes(g, s_surf, sa, sb, aa, ab, pa, pb);
+  const double B[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
+  const double xxb = Surf{s_surf + sb * kSurfStride}.xx0();
+#pragma unroll
+  for (int e = 0; e < 6; ++e) tf.xprev[e] = xprev[e];
+#pragma unroll
+  for (int e = 0; e < 21; ++e) tf.Cprev[e] = Cprev[e];
+  double qp, qt, F[6][6];
+  transport_tape<true>(pa, pb, xprev, B, p.mass, p.h_max, p.n_iter, xxb, tf.xp, tf.J, qp, qt, &tf.tp, tf.s_end);
+  dense_F(tf.J, F);
+  cov_transport(F, Cprev, qp, qt, tf.Cp);
+}
+
+// The reverse of transition k: lf, Lf (adjoints of x_f,k, C_f,k) become
+// those of x_f,k-1, C_f,k-1; galign receives the adjoints of the alignment
+// of surfaces k-1 (0..5) and k (6..11).
+__device__ __forceinline__ void transition_reverse(const GradParams& g, const TrackIO& io, const double* s_surf, int k,
+                                                   double w, bool use_sm, const TransitionFwd& tf, double lf[6],
+                                                   double Lf[6][6], double galign[12]) {
+  const FitParams& p = g.f;
+  const int sa = io.sid(k - 1), sbi = io.sid(k);
+  double aa[6], ab[6];
+  Plane<double> pa, pb;
+  aligned_planes(g, s_surf, sa, sbi, aa, ab, pa, pb);
+  const double B[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
+  const double xxb = Surf{s_surf + sbi * kSurfStride}.xx0();
+  double F[6][6];
+  dense_F(tf.J, F);
+  double lp[6], Lp[6][6];
+  if (use_sm) add_sm_filtered(io, k, lf, Lf);
+  if (!io.hole(k)) {
+    double m[2], V[3];
+    io.meas(k, m, V);
+    update_adj(tf.xp, tf.Cp, m, V, w, lf, Lf, lp, Lp);
+  } else {
+#pragma unroll
+    for (int a2 = 0; a2 < 6; ++a2) {
+      lp[a2] = lf[a2];
+#pragma unroll
+      for (int b2 = 0; b2 < 6; ++b2) Lp[a2][b2] = Lf[a2][b2];
+    }
+  }
+  if (use_sm) {
+    // the smoother's direct use of x_p,k and C_p,k
+#pragma unroll
+    for (int e = 0; e < 6; ++e) lp[e] += io.sadj(k, kSmXP + e);
+#pragma unroll
+    for (int a2 = 0; a2 < 6; ++a2)
+#pragma unroll
+      for (int b2 = 0; b2 <= a2; ++b2) {
+        const double v = io.sadj(k, kSmCP + sy(a2, b2));
+        Lp[a2][b2] += v;
+        if (b2 < a2) Lp[b2][a2] += v;
+      }
+  }
+  // lambda_F = 2 Lp F Cf (only rows 0-3, 5 and columns 0-4 of F vary)
+  double lF[6][6];
+#pragma unroll
+  for (int a2 = 0; a2 < 6; ++a2) {
+    double LF[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += Lp[a2][q] * F[q][c];
+      LF[c] = v;
+    }
+#pragma unroll
+    for (int b2 = 0; b2 < 6; ++b2) {
+      double v = 0.0;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v += LF[c] * tf.Cprev[sym(c, b2)];
+      lF[a2][b2] = 2.0 * v;
+    }
+  }
+  // reverse sweep through the transport: adjoints of x_f,k-1 and of both
+  // planes' alignment, contracted with (lambda_xp, lambda_F, Lambda_Q)
+  double lx[6];
+  {
+    double lJ[4][5], lJt[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) lJ[r][c] = lF[r][c] + (use_sm ? io.sadj(k, kSmF + r * 5 + c) : 0.0);
+      lJt[c] = lF[5][c] + (use_sm ? io.sadj(k, kSmF + 20 + c) : 0.0);
+    }
+    double lca[3], lRa[9], lcb[3], lRb[9];
+    transport_rev(pa, pb, tf.xprev, B, p.mass, xxb, tf.tp, tf.s_end, lp, lJ, lJt, Lp[2][2], Lp[3][3], lx, lca, lRa,
+                  lcb, lRb);
+    aligned_plane_rev(Surf{s_surf + sa * kSurfStride}, aa, lca, lRa, galign);
+    aligned_plane_rev(Surf{s_surf + sbi * kSurfStride}, ab, lcb, lRb, galign + 6);
+  }
+  // Lambda_Cf = F^T Lp F
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    lf[a] = lx[a];
+    double LFa[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) v += Lp[c][q] * F[q][a];
+      LFa[c] = v;
+    }
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      double v = 0.0;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) v += F[c][b] * LFa[c];
+      Lf[a][b] = v;  // (F^T Lp F)[b][a], symmetric
+    }
+  }
+}
+
+// Hand-off slot of the pipelined reverse, [field][n_tracks] doubles:
+// xprev 6 | Cprev 21 | xp 6 | Cp 21 | J 25 | n_steps, nsub, s0 | end state 27
+// | the recorded steps (16 doubles each, as many as were recorded).
+constexpr int kSlotFixed = 6 + 21 + 6 + 21 + 25 + 3 + 27;
+constexpr int kSlot = kSlotFixed + 16 * kTape;
+
+__device__ __forceinline__ void slot_write(double* slot, size_t TL, int tl, const TransitionFwd& tf) {
+  int o = 0;
+  auto put = [&](double v) { slot[(size_t)(o++) * TL + tl] = v; };
+#pragma unroll
+  for (int e = 0; e < 6; ++e) put(tf.xprev[e]);
+#pragma unroll
+  for (int e = 0; e < 21; ++e) put(tf.Cprev[e]);
+#pragma unroll
+  for (int e = 0; e < 6; ++e) put(tf.xp[e]);
+#pragma unroll
+  for (int e = 0; e < 21; ++e) put(tf.Cp[e]);
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) put(tf.J.f[r][c]);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) put(tf.J.ft[c]);
+  put((double)tf.tp.n_steps);
+  put((double)tf.tp.nsub);
+  put(tf.tp.s0);
+  const PropS<double>& e = tf.s_end;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) put(e.r[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) put(e.T[i]);
+  put(e.t);
+  put(e.lam);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) put(e.gr[i][c]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) put(e.gT[i][c]);
+  put(e.gtl);
+  const int ns = min(tf.tp.n_steps, kTape);
+  for (int j = 0; j < ns; ++j) {
+    double* q = slot + (size_t)(kSlotFixed + 16 * j) * TL + tl;
+    const StepIn& st = tf.tp.st[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      q[(size_t)i * TL] = st.r[i];
+      q[(size_t)(3 + i) * TL] = st.T[i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[(size_t)(6 + 3 * i + c) * TL] = st.gT[i][c];
+    }
+    q[(size_t)15 * TL] = st.h;
+  }
+}
+
+__device__ __forceinline__ void slot_read(const double* slot, size_t TL, int tl, TransitionFwd& tf) {
+  int o = 0;
+  auto get = [&]() { return slot[(size_t)(o++) * TL + tl]; };
+#pragma unroll
+  for (int e = 0; e < 6; ++e) tf.xprev[e] = get();
+#pragma unroll
+  for (int e = 0; e < 21; ++e) tf.Cprev[e] = get();
+#pragma unroll
+  for (int e = 0; e < 6; ++e) tf.xp[e] = get();
+#pragma unroll
+  for (int e = 0; e < 21; ++e) tf.Cp[e] = get();
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) tf.J.f[r][c] = get();
+#pragma unroll
+  for (int c = 0; c < 5; ++c) tf.J.ft[c] = get();
+  tf.tp.n_steps = (int)get();
+  tf.tp.nsub = (int)get();
+  tf.tp.s0 = get();
+  PropS<double>& e = tf.s_end;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) e.r[i] = get();
+#pragma unroll
+  for (int i = 0; i < 3; ++i) e.T[i] = get();
+  e.t = get();
+  e.lam = get();
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e.gr[i][c] = get();
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e.gT[i][c] = get();
+  e.gtl = get();
+  const int ns = min(tf.tp.n_steps, kTape);
+  for (int j = 0; j < ns; ++j) {
+    const double* q = slot + (size_t)(kSlotFixed + 16 * j) * TL + tl;
+    StepIn& st = tf.tp.st[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      st.r[i] = q[(size_t)i * TL];
+      st.T[i] = q[(size_t)(3 + i) * TL];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) st.gT[i][c] = q[(size_t)(6 + 3 * i + c) * TL];
+    }
+    st.h = q[(size_t)15 * TL];
+  }
+}
+
 // Register-cap variants as for the fit kernels: MINB 1 may use 255
 // registers (up to 8 warps per SM), 3 caps at 168 (12 warps) and 4 at 128
 // (16 warps; the tape then spills to local memory).
@@ -1363,16 +1655,26 @@ __device__ __noinline__ void recompute_segment(const TrackIO& io, const double* 
 //   B  the reverse of the filter, segment by segment downwards (states
 //      recomputed from the checkpoints, transports re-run with a tape), with
 //      sadj added in at every state.
-template <int MINB>
-__global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const GradParams g) {
+// PIPE: a CTA of two warps per 32 tracks (lane l of both on track l).  The
+// second warp runs passes F, S, R and, in B, the forward half of every
+// transition (the segment's recompute, the taped transport) one transition
+// ahead; the first warp runs the reverse half (the reverse of the update and
+// of the transport) on what the second left in a slot (two slots, one
+// barrier per transition).  For batches too small to fill the GPU: a warp
+// instruction costs an SM sub-partition's FP64 pipe the same at any number
+// of active lanes, so the split has to go across warps.
+template <int MINB, bool PIPE>
+__global__ void __launch_bounds__(PIPE ? 64 : max_threads_of(MINB), 1) kf_grad_kernel(const GradParams g) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* s_surf = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(8) uint64_t s_mbar;
   const FitParams& p = g.f;
   const bool staged = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
                                      p.error_flag, p.wait_limit, p.skip_stage_copy != 0);
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = PIPE ? blockIdx.x * 32 + (int)(threadIdx.x & 31) : blockIdx.x * blockDim.x + threadIdx.x;
   const bool in_range = t < p.n_tracks;
+  // the warp that runs passes F, S and R (both warps without PIPE)
+  const bool run_fwd = !PIPE || threadIdx.x >= 32;
   TrackIO io;
   io.g = &g;
   io.tl = in_range ? t : 0;
@@ -1415,7 +1717,7 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
   // ---------------------------------------------------------- F: forward
   double chi2sum = 0.0;
   double x[6], C[21];
-  if (status == ST_OK) {
+  if (status == ST_OK && run_fwd) {
 #pragma unroll
     for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TG + tg];
 #pragma unroll
@@ -1459,7 +1761,7 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
   const int n_seg_trk = status == ST_OK ? (n - 1 + kSeg - 1) / kSeg : 0;
 
   // ---------------------------------------------------------- S: smoother
-  if (sm_fwd && status == ST_OK) {
+  if (sm_fwd && status == ST_OK && run_fwd) {
     double xs[6], Cs[21];  // x_s,n-1 = x_f,n-1
 #pragma unroll
     for (int e = 0; e < 6; ++e) xs[e] = x[e];
@@ -1493,16 +1795,16 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
     if (in_range && g.out_cov)
 #pragma unroll
       for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = status == ST_OK ? Cs[e] : qnan();
-  } else if (in_range) {
+  } else if (in_range && run_fwd) {
     if (g.out_params)
       for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = qnan();
     if (g.out_cov)
       for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = qnan();
   }
-  if (in_range && g.chi2) g.chi2[tg] = status == ST_OK ? chi2sum : qnan();
+  if (in_range && g.chi2 && run_fwd) g.chi2[tg] = status == ST_OK ? chi2sum : qnan();
 
   // ---------------------------------------------------------- R: smoother reverse
-  if (sm_adj && status == ST_OK) {
+  if (sm_adj && status == ST_OK && run_fwd) {
     double lxs[6], Ls[6][6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) lxs[e] = g.dl_dparams ? g.dl_dparams[e * TG + tg] : 0.0;
@@ -1548,20 +1850,13 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
 #pragma unroll
       for (int j = 0; j <= i; ++j) io.sadj(n - 1, kSmCF + sy(i, j)) = Ls[i][j];
   }
-  // adds the smoother's contributions to the adjoints of x_f,k and C_f,k
-  auto add_sm_filtered = [&](int k, double lf_[6], double Lf_[6][6]) {
-#pragma unroll
-    for (int e = 0; e < 6; ++e) lf_[e] += io.sadj(k, kSmXF + e);
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        const double v = io.sadj(k, kSmCF + sy(i, j));
-        Lf_[i][j] += v;
-        if (j < i) Lf_[j][i] += v;
-      }
-  };
-
+  if (PIPE) {
+    // the reverse warp learns each track's status from the forward warp
+    __shared__ int s_status[32];
+    if (run_fwd) s_status[threadIdx.x & 31] = status;
+    __syncthreads();
+    status = s_status[threadIdx.x & 31];
+  }
   // ---------------------------------------------------------- B: filter reverse
   double lf[6] = {0, 0, 0, 0, 0, 0};
   double Lf[6][6];
@@ -1572,183 +1867,88 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
   const int n_seg = (status == ST_OK && want) ? n_seg_trk : 0;
   const bool use_sm = sm_adj && status == ST_OK;
   // the loop runs in lock-step over the warp's maximum segment count so that
-  // the alignment-gradient reduction sees whole warps
+  // the alignment-gradient reduction sees whole warps (with PIPE both warps
+  // hold the same 32 tracks and find the same count)
   int n_seg_warp = n_seg;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) n_seg_warp = max(n_seg_warp, __shfl_xor_sync(0xffffffffu, n_seg_warp, o));
-  for (int sg = n_seg_warp - 1; sg >= 0; --sg) {
-    const bool seg_active = sg < n_seg;
-    const int s0 = sg * kSeg;
-    const int s1 = seg_active ? min(s0 + kSeg, n - 1) : s0;  // last state of the segment
-    // recompute the filtered states s0 .. s1-1 of the segment
-    double bx[kSeg][6], bC[kSeg][21];
-    if (seg_active) {
+  auto add_galign = [&](int k, bool act, const double galign[12]) {
+    if (!g.grad_align) return;
+    const int sa = act ? io.sid(k - 1) : 0, sbi = act ? io.sid(k) : 0;
+#pragma unroll 1
+    for (int e = 0; e < 12; ++e) add_align_grad(g.grad_align, p.n_surfaces, e < 6 ? sa : sbi, e % 6, galign[e], act);
+  };
+  if (!PIPE) {
+    for (int sg = n_seg_warp - 1; sg >= 0; --sg) {
+      const bool seg_active = sg < n_seg;
+      const int s0 = sg * kSeg;
+      const int s1 = seg_active ? min(s0 + kSeg, n - 1) : s0;  // last state of the segment
+      // the filtered states s0 .. s1-1 of the segment
+      double bx[kSeg][6], bC[kSeg][21];
+      if (seg_active) recompute_filtered(io, s_surf, sg, s0, s1, bx, bC);
+      // reverse over the transitions k = s1 .. s0+1
+#pragma unroll 1
+      for (int k = s0 + kSeg; k > s0; --k) {
+        const bool act = seg_active && k <= s1;
+        double galign[12];
 #pragma unroll
-      for (int e = 0; e < 6; ++e) bx[0][e] = io.ck(sg, e);
-#pragma unroll
-      for (int e = 0; e < 21; ++e) bC[0][e] = io.ck(sg, 6 + e);
-#pragma unroll
-      for (int i = 1; i < kSeg; ++i) {
-        if (s0 + i < s1) {
-          const int k = s0 + i;
-          double xp[6], Cp[21], F[6][6], qp, qt;
-          JacS<double> J;
-          transport_values(g, s_surf, io.sid(k - 1), io.sid(k), bx[i - 1], xp, J, qp, qt);
-          dense_F(J, F);
-          cov_transport(F, bC[i - 1], qp, qt, Cp);
-          if (!io.hole(k)) {
-            double m[2], V[3], c2;
-            io.meas(k, m, V);
-            update_fwd(xp, Cp, m, V, bx[i], bC[i], c2);
-          } else {
-#pragma unroll
-            for (int e = 0; e < 6; ++e) bx[i][e] = xp[e];
-#pragma unroll
-            for (int e = 0; e < 21; ++e) bC[i][e] = Cp[e];
-          }
+        for (int e = 0; e < 12; ++e) galign[e] = 0.0;
+        if (act) {
+          TransitionFwd tf;
+          transition_forward(g, io, s_surf, k, bx[k - 1 - s0], bC[k - 1 - s0], tf);
+          transition_reverse(g, io, s_surf, k, w, use_sm, tf, lf, Lf, galign);
         }
+        add_galign(k, act, galign);
       }
     }
-    // reverse over the transitions k = s1 .. s0+1
-#pragma unroll 1
-    for (int k = s0 + kSeg; k > s0; --k) {
-      const bool act = seg_active && k <= s1;
-      const int i = act ? k - 1 - s0 : 0;
-      const int sa = act ? io.sid(k - 1) : 0, sbi = act ? io.sid(k) : 0;
-      double lp[6], Lp[6][6];
-      double xprev[6], Cprev[21];
-#pragma unroll
-      for (int e = 0; e < 6; ++e) xprev[e] = act ? bx[i][e] : 0.0;
-#pragma unroll
-      for (int e = 0; e < 21; ++e) Cprev[e] = act ? bC[i][e] : 0.0;
-      double F[6][6];
-      // the transport k-1 -> k with its tape (values as in the forward pass)
-      double aa[6], ab[6];
-      load_align(g, sa, aa);
-      load_align(g, sbi, ab);
-      const Plane<double> pa = aligned_plane<double>(Surf{s_surf + sa * kSurfStride}, aa);
-      const Plane<double> pb = aligned_plane<double>(Surf{s_surf + sbi * kSurfStride}, ab);
-      const double B[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
-      const double xxb = Surf{s_surf + sbi * kSurfStride}.xx0();
-      Tape tp;
-      PropS<double> s_end;
-      if (act) {
-        double xp[6], Cp[21], qp, qt;
-        JacS<double> J;
-        transport_tape<true>(pa, pb, xprev, B, p.mass, p.h_max, p.n_iter, xxb, xp, J, qp, qt, &tp, s_end);
-        dense_F(J, F);
-        cov_transport(F, Cprev, qp, qt, Cp);
-        if (use_sm) add_sm_filtered(k, lf, Lf);
-        if (!io.hole(k)) {
-          double m[2], V[3];
-          io.meas(k, m, V);
-          update_adj(xp, Cp, m, V, w, lf, Lf, lp, Lp);
-        } else {
-#pragma unroll
-          for (int a2 = 0; a2 < 6; ++a2) {
-            lp[a2] = lf[a2];
-#pragma unroll
-            for (int b2 = 0; b2 < 6; ++b2) Lp[a2][b2] = Lf[a2][b2];
-          }
-        }
-        if (use_sm) {
-          // the smoother's direct use of x_p,k and C_p,k
-#pragma unroll
-          for (int e = 0; e < 6; ++e) lp[e] += io.sadj(k, kSmXP + e);
-#pragma unroll
-          for (int a2 = 0; a2 < 6; ++a2)
-#pragma unroll
-            for (int b2 = 0; b2 <= a2; ++b2) {
-              const double v = io.sadj(k, kSmCP + sy(a2, b2));
-              Lp[a2][b2] += v;
-              if (b2 < a2) Lp[b2][a2] += v;
-            }
-        }
-      } else {
-#pragma unroll
-        for (int a2 = 0; a2 < 6; ++a2) {
-          lp[a2] = 0.0;
-#pragma unroll
-          for (int b2 = 0; b2 < 6; ++b2) {
-            Lp[a2][b2] = 0.0;
-            F[a2][b2] = (a2 == b2) ? 1.0 : 0.0;
-          }
+  } else {
+    // item j is transition k of segment sg, in the order above; the forward
+    // warp produces item j into slot j % 2 while the reverse warp consumes
+    // item j - 1 from the other slot; one barrier per item (both warps run
+    // the same n_items + 1 iterations)
+    const bool fwd_warp = threadIdx.x >= 32;
+    const int n_items = n_seg_warp * kSeg;
+    const size_t slot_stride = (size_t)kSlot * io.TL;
+    double bx[kSeg][6], bC[kSeg][21];
+    for (int j = 0; j <= n_items; ++j) {
+      if (fwd_warp && j < n_items) {
+        const int sg = n_seg_warp - 1 - j / kSeg;
+        const int s0 = sg * kSeg, k = s0 + kSeg - j % kSeg;
+        const bool seg_active = sg < n_seg;
+        const int s1 = seg_active ? min(s0 + kSeg, n - 1) : s0;
+        if (j % kSeg == 0 && seg_active) recompute_filtered(io, s_surf, sg, s0, s1, bx, bC);
+        if (seg_active && k <= s1) {
+          TransitionFwd tf;
+          transition_forward(g, io, s_surf, k, bx[k - 1 - s0], bC[k - 1 - s0], tf);
+          slot_write(g.pipe + (size_t)(j & 1) * slot_stride, io.TL, io.tl, tf);
         }
       }
-      // lambda_F = 2 Lp F Cf (only rows 0-3, 5 and columns 0-4 of F vary)
-      double lF[6][6];
+      if (!fwd_warp && j >= 1) {
+        const int jj = j - 1;
+        const int sg = n_seg_warp - 1 - jj / kSeg;
+        const int s0 = sg * kSeg, k = s0 + kSeg - jj % kSeg;
+        const bool seg_active = sg < n_seg;
+        const int s1 = seg_active ? min(s0 + kSeg, n - 1) : s0;
+        const bool act = seg_active && k <= s1;
+        double galign[12];
 #pragma unroll
-      for (int a2 = 0; a2 < 6; ++a2) {
-        double LF[6];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          double v = 0.0;
-#pragma unroll
-          for (int q = 0; q < 6; ++q) v += Lp[a2][q] * F[q][c];
-          LF[c] = v;
+        for (int e = 0; e < 12; ++e) galign[e] = 0.0;
+        if (act) {
+          TransitionFwd tf;
+          slot_read(g.pipe + (size_t)(jj & 1) * slot_stride, io.TL, io.tl, tf);
+          transition_reverse(g, io, s_surf, k, w, use_sm, tf, lf, Lf, galign);
         }
-#pragma unroll
-        for (int b2 = 0; b2 < 6; ++b2) {
-          double v = 0.0;
-#pragma unroll
-          for (int c = 0; c < 6; ++c) v += LF[c] * Cprev[sym(c, b2)];
-          lF[a2][b2] = 2.0 * v;
-        }
+        add_galign(k, act, galign);
       }
-      // reverse sweep through the transport: adjoints of x_f,k-1 and of
-      // both planes' alignment, contracted with (lambda_xp, lambda_F, Lambda_Q)
-      double lx[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-      double galign[12];
-#pragma unroll
-      for (int e = 0; e < 12; ++e) galign[e] = 0.0;
-      if (act) {
-        double lJ[4][5], lJt[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) {
-#pragma unroll
-          for (int r = 0; r < 4; ++r) lJ[r][c] = lF[r][c] + (use_sm ? io.sadj(k, kSmF + r * 5 + c) : 0.0);
-          lJt[c] = lF[5][c] + (use_sm ? io.sadj(k, kSmF + 20 + c) : 0.0);
-        }
-        double lca[3], lRa[9], lcb[3], lRb[9];
-        transport_rev(pa, pb, xprev, B, p.mass, xxb, tp, s_end, lp, lJ, lJt, Lp[2][2], Lp[3][3], lx, lca, lRa,
-                      lcb, lRb);
-        aligned_plane_rev(Surf{s_surf + sa * kSurfStride}, aa, lca, lRa, galign);
-        aligned_plane_rev(Surf{s_surf + sbi * kSurfStride}, ab, lcb, lRb, galign + 6);
-      }
-      if (g.grad_align) {
-#pragma unroll 1
-        for (int e = 0; e < 12; ++e)
-          add_align_grad(g.grad_align, p.n_surfaces, e < 6 ? sa : sbi, e % 6, galign[e], act);
-      }
-      if (act) {
-        // Lambda_Cf = F^T Lp F
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-          lf[a] = lx[a];
-          double LFa[6];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            double v = 0.0;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) v += Lp[c][q] * F[q][a];
-            LFa[c] = v;
-          }
-#pragma unroll
-          for (int b = 0; b < 6; ++b) {
-            double v = 0.0;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) v += F[c][b] * LFa[c];
-            Lf[a][b] = v;  // (F^T Lp F)[b][a], symmetric
-          }
-        }
-      }
+      __syncthreads();
     }
   }
+  if (PIPE && run_fwd) return;  // the reverse warp finishes the track
   // state 0: reverse through its update; x_p,0 is the seed
   if (in_range && g.grad_seed) {
     double gs[6];
     if (status == ST_OK && want) {
-      if (use_sm) add_sm_filtered(0, lf, Lf);
+      if (use_sm) add_sm_filtered(io, 0, lf, Lf);
       if (!io.hole(0)) {
         double m[2], V[3], lp[6], Lp[6][6], Cp0[21], xp0[6];
         io.meas(0, m, V);
@@ -1774,14 +1974,18 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) kf_grad_kernel(const 
 
 }  // namespace
 
-template <int MINB>
+template <int MINB, bool PIPE>
 cudaError_t launch_grad_v(const GradParams& g, int block, cudaStream_t stream) {
   const FitParams& f = g.f;
   const size_t smem = (size_t)f.n_surfaces * kSurfStride * sizeof(double);
-  auto kern = kf_grad_kernel<MINB>;
+  auto kern = kf_grad_kernel<MINB, PIPE>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+  }
+  if (PIPE) {
+    kern<<<(f.n_tracks + 31) / 32, 64, smem, stream>>>(g);
+    return cudaGetLastError();
   }
   if (block <= 0) {
     // CTAs of w warps, one per SM per wave, w the smallest count (within the
@@ -1805,16 +2009,17 @@ cudaError_t launch_grad_v(const GradParams& g, int block, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint) {
+size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint, bool pipelined) {
   const size_t n_ckpt = ((size_t)max_states + kSeg - 1) / kSeg;
   size_t d = 27 * n_ckpt;
   if (smoother_adjoint) d += 27 * (n_ckpt + 1) + (size_t)kSmRec * (size_t)max_states;
+  if (pipelined) d += 2 * (size_t)kSlot;
   (void)smoother;  // the smoother alone keeps no per-track scratch
   return d;
 }
 
 cudaError_t launch_grad(const FitParams& f, const GradArgs& a, double* scratch, int block, int min_blocks,
-                        cudaStream_t stream) {
+                        bool pipelined, cudaStream_t stream) {
   GradParams g;
   g.f = f;
   g.align = a.align;
@@ -1829,14 +2034,19 @@ cudaError_t launch_grad(const FitParams& f, const GradArgs& a, double* scratch, 
   const size_t T = (size_t)f.n_tracks;
   g.n_ckpt = (f.max_states + kSeg - 1) / kSeg;
   g.ckpt = scratch;
+  // the smoother's checkpoints and contributions follow when its adjoint is
+  // asked; the hand-off slots come last
+  const bool sm_adj = (a.grad_seed || a.grad_align) && (a.dl_dparams || a.dl_dcov);
   g.sck = scratch + 27 * (size_t)g.n_ckpt * T;
   g.sadj = g.sck + 27 * (size_t)(g.n_ckpt + 1) * T;
+  g.pipe = nullptr;
+  if (pipelined) g.pipe = sm_adj ? g.sadj + (size_t)kSmRec * (size_t)f.max_states * T : g.sck;
+  if (pipelined) return launch_grad_v<1, true>(g, 64, stream);
   switch (min_blocks) {
-    case 4: return launch_grad_v<4>(g, block, stream);
-    case 3: return launch_grad_v<3>(g, block, stream);
-    default: return launch_grad_v<1>(g, block, stream);
+    case 4: return launch_grad_v<4, false>(g, block, stream);
+    case 3: return launch_grad_v<3, false>(g, block, stream);
+    default: return launch_grad_v<1, false>(g, block, stream);
   }
 }
-
 
 }  // namespace kfgb

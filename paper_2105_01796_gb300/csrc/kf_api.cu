@@ -731,6 +731,10 @@ int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const doub
   // threads per CTA for min_blocks 1 / 3 / 4)
   const int grad_block = opt.block;
   if (grad_block < 0 || grad_block % 32 != 0 || grad_block > max_threads_of(opt.min_blocks)) return KF_EUNSUPPORTED;
+  // team_warps 2: the pipelined form (two warps per 32 tracks)
+  if (opt.team_warps != 0 && opt.team_warps != 1 && opt.team_warps != 2) return KF_EUNSUPPORTED;
+  const bool pipelined = opt.team_warps == 2;
+  opt.team_warps = 0;
   opt.block = 0;
   kf_outputs dummy;
   memset(&dummy, 0, sizeof(dummy));
@@ -765,7 +769,7 @@ int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const doub
   const bool want = a.grad_seed || a.grad_align;
   const bool sm_adj = want && (a.dl_dparams || a.dl_dcov);
   const bool sm = sm_adj || a.params || a.cov;
-  const size_t per_track = sizeof(double) * grad_scratch_doubles(tr->max_states, sm, sm_adj);
+  const size_t per_track = sizeof(double) * grad_scratch_doubles(tr->max_states, sm, sm_adj, pipelined);
   const int64_t cap = opt.workspace_bytes > 0 ? opt.workspace_bytes : kDefaultWorkspace;
   int64_t chunk = cap / (int64_t)per_track;
   if (chunk < 1) chunk = 1;
@@ -809,7 +813,7 @@ int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const doub
   for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk) {
     p.track0 = (int32_t)t0;
     p.n_tracks = (int32_t)((tr->n_tracks - t0) < chunk ? (tr->n_tracks - t0) : chunk);
-    e = launch_grad(p, a, (double*)h->ckpt, grad_block, opt.min_blocks, stream);
+    e = launch_grad(p, a, (double*)h->ckpt, grad_block, opt.min_blocks, pipelined, stream);
     if (e != cudaSuccess) return cuda_fail(e, "grad launch");
     ++launches;
   }

@@ -141,14 +141,16 @@ struct GradArgs {
 };
 
 // Scratch doubles per track of one adjoint launch: the filtered checkpoints,
-// and with the smoother the smoothed checkpoints and (for the adjoint of the
-// smoothed outputs) the smoother's per-state contributions.
-size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint);
+// with the smoother's adjoint the smoothed checkpoints and its per-state
+// contributions, and in the pipelined form two hand-off slots.
+size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint, bool pipelined);
 
 // One launch over tracks [f.track0, f.track0 + f.n_tracks) of
 // f.n_tracks_total; scratch holds grad_scratch_doubles(...) x f.n_tracks.
+// pipelined: two warps per 32 tracks (the forward and the reverse half of
+// the filter's reverse sweep on separate warps), block ignored.
 cudaError_t launch_grad(const FitParams& f, const GradArgs& a, double* scratch, int block, int min_blocks,
-                        cudaStream_t stream);
+                        bool pipelined, cudaStream_t stream);
 
 // Counting sort of the tracks by state count, longest first:
 // order[0..n_tracks) receives track indices.  hist needs max_states + 2 ints.

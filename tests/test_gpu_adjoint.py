@@ -323,3 +323,29 @@ def test_whole_fit_gradients_uneven_tracks_with_holes(handle):
     fd = _fd2(oracle.objective_gradient_fd, ev=ev, weights=w, dl_dparams=v, dl_dcov=W)
     _, l_abs = oracle.objective_per_track(ev, weights=w, dl_dparams=v, dl_dcov=W)
     _check_grads(g["gs"], g["ga"], fd[0], fd[1], ev["seed_params"], l_abs)
+
+
+@pytest.mark.parametrize("objective", ["chi2", "whole"])
+def test_pipelined_adjoint_equals_sequential(handle, objective):
+    """team_warps = 2 runs the filter's reverse on two warps per 32 tracks
+    (the forward half one transition ahead on one, the reverse half on the
+    other): the same arithmetic, so the same chi2, smoothed outputs and seed
+    gradients bit for bit, and the alignment gradient up to the order of its
+    atomic sums; on uneven tracks with holes, zero and non-zero alignment."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 333))
+    S = ev["center"].shape[1]
+    v, W = _smoother_weights(ev) if objective == "whole" else (None, None)
+    rng = np.random.default_rng(6)
+    for nonzero in (False, True):
+        align = np.zeros((6, S))
+        if nonzero:
+            align[:3, 1:] = rng.normal(size=(3, S - 1)) * 0.05
+            align[3:, 1:] = rng.normal(size=(3, S - 1)) * 5e-4
+        seq = _whole(handle, ev, align, None, v, W, opt=kf.kf_default_options(block=0))
+        pip = _whole(handle, ev, align, None, v, W, opt=kf.kf_default_options(block=0, team_warps=2))
+        assert handle.last_launch_count() == 2
+        for k in ("chi2", "params", "cov", "gs"):
+            assert np.array_equal(seq[k], pip[k]), k
+        assert np.allclose(pip["ga"], seq["ga"], rtol=1e-12, atol=1e-12 * np.abs(seq["ga"]).max())
+    with pytest.raises(kf.KfError, match="-4"):
+        _whole(handle, ev, align, None, v, W, opt=kf.kf_default_options(block=0, team_warps=4))

@@ -50,13 +50,14 @@ struct Plane {
   __device__ const S& n(int i) const { return R[3 * i + 2]; }
 };
 
-// c' = c + R (du, dv, dn); R' = R Ru(alpha) Rv(beta) Rn(gamma)
-template <class S>
-__device__ __forceinline__ Plane<S> aligned_plane(const Surf& s, const S a[6]) {
+// c' = c + R (du, dv, dn); R' = R Ru(alpha) Rv(beta) Rn(gamma); cs holds the
+// cosines and sines of the three angles (cos alpha, sin alpha, cos beta, ...)
+__device__ __forceinline__ Plane<double> aligned_plane(const Surf& s, const double a[6], const double cs[6]) {
+  using S = double;
   Plane<S> p;
 #pragma unroll
   for (int i = 0; i < 3; ++i) p.c[i] = s.c(i) + s.R(i, 0) * a[0] + s.R(i, 1) * a[1] + s.R(i, 2) * a[2];
-  const S ca = cos(a[3]), sa = sin(a[3]), cb = cos(a[4]), sb = sin(a[4]), cg = cos(a[5]), sg = sin(a[5]);
+  const S ca = cs[0], sa = cs[1], cb = cs[2], sb = cs[3], cg = cs[4], sg = cs[5];
   // M = Ru Rv Rn
   S M[9];
   // Ru = [[1,0,0],[0,ca,-sa],[0,sa,ca]], Rv = [[cb,0,sb],[0,1,0],[-sb,0,cb]], Rn = [[cg,-sg,0],[sg,cg,0],[0,0,1]]
@@ -74,6 +75,19 @@ __device__ __forceinline__ Plane<S> aligned_plane(const Surf& s, const S a[6]) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) p.R[3 * i + j] = s.R(i, 0) * M[0 * 3 + j] + s.R(i, 1) * M[1 * 3 + j] + s.R(i, 2) * M[2 * 3 + j];
   return p;
+}
+
+// the cosines and sines of every surface's alignment angles, once per call:
+// out[2 m][s] = cos(angle m), out[2 m + 1][s] = sin(angle m), m = 0, 1, 2
+__global__ void align_trig_kernel(int n_surfaces, const double* __restrict__ align, double* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_surfaces) return;
+  for (int m = 0; m < 3; ++m) {
+    double sn, cn;
+    sincos(align[(size_t)(3 + m) * n_surfaces + s], &sn, &cn);
+    out[(size_t)(2 * m) * n_surfaces + s] = cn;
+    out[(size_t)(2 * m + 1) * n_surfaces + s] = sn;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -856,7 +870,7 @@ __device__ void transport_rev(const Plane<double>& pa, const Plane<double>& pb, 
 // (row-major) -> adjoints of its 6 alignment parameters (accumulated in ga).
 //   c' = c + R (du, dv, dn):        d(du, dv, dn) = R^T lc
 //   R' = R M, M = Ru(al) Rv(be) Rn(ga):  lM = R^T lR, d(angle) = <lM, dM/d(angle)>
-__device__ __forceinline__ void aligned_plane_rev(const Surf& s, const double a[6], const double lc[3],
+__device__ __forceinline__ void aligned_plane_rev(const Surf& s, const double cs[6], const double lc[3],
                                                   const double lR[9], double ga[6]) {
 #pragma unroll
   for (int e = 0; e < 3; ++e) ga[e] += s.R(0, e) * lc[0] + s.R(1, e) * lc[1] + s.R(2, e) * lc[2];
@@ -865,7 +879,7 @@ __device__ __forceinline__ void aligned_plane_rev(const Surf& s, const double a[
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) lM[i][j] = s.R(0, i) * lR[0 * 3 + j] + s.R(1, i) * lR[1 * 3 + j] + s.R(2, i) * lR[2 * 3 + j];
-  const double ca = cos(a[3]), sa = sin(a[3]), cb = cos(a[4]), sb = sin(a[4]), cg = cos(a[5]), sg = sin(a[5]);
+  const double ca = cs[0], sa = cs[1], cb = cs[2], sb = cs[3], cg = cs[4], sg = cs[5];
   const double Ru[3][3] = {{1, 0, 0}, {0, ca, -sa}, {0, sa, ca}};
   const double Rv[3][3] = {{cb, 0, sb}, {0, 1, 0}, {-sb, 0, cb}};
   const double Rn[3][3] = {{cg, -sg, 0}, {sg, cg, 0}, {0, 0, 1}};
@@ -908,6 +922,7 @@ struct GradParams {
                         // launch covers tracks [track0, track0 + n_tracks)
                         // of n_tracks_total
   const double* align;  // [6][S] or null (zero alignment)
+  const double* align_cs;  // [6][S] cosines and sines of the alignment angles (with align)
   const double* dl_dchi2;    // [T] or null (all ones)
   const double* dl_dparams;  // [6][T] or null: weights of the smoothed state-0 parameters
   const double* dl_dcov;     // [21][T] or null: weights of its packed covariance
@@ -923,21 +938,23 @@ struct GradParams {
   int32_t n_ckpt;
 };
 
-template <class S>
-__device__ __forceinline__ void load_align(const GradParams& g, int sid, S a[6]) {
+// the alignment of surface sid and the cosines and sines of its angles
+__device__ __forceinline__ void load_align(const GradParams& g, int sid, double a[6], double cs[6]) {
 #pragma unroll
-  for (int e = 0; e < 6; ++e) a[e] = S(g.align ? g.align[(size_t)e * g.f.n_surfaces + sid] : 0.0);
+  for (int e = 0; e < 6; ++e) a[e] = g.align ? g.align[(size_t)e * g.f.n_surfaces + sid] : 0.0;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) cs[e] = g.align ? g.align_cs[(size_t)e * g.f.n_surfaces + sid] : ((e & 1) ? 0.0 : 1.0);
 }
 
 // values of the transport k-1 -> k with the aligned planes
 __device__ __forceinline__ int transport_values(const GradParams& g, const double* s_surf, int sa, int sb,
                                                 const double x[6], double xp[6], JacS<double>& J, double& qp,
                                                 double& qt) {
-  double aa[6], ab[6];
-  load_align(g, sa, aa);
-  load_align(g, sb, ab);
-  const Plane<double> pa = aligned_plane<double>(Surf{s_surf + sa * kSurfStride}, aa);
-  const Plane<double> pb = aligned_plane<double>(Surf{s_surf + sb * kSurfStride}, ab);
+  double aa[6], ab[6], ca[6], cb[6];
+  load_align(g, sa, aa, ca);
+  load_align(g, sb, ab, cb);
+  const Plane<double> pa = aligned_plane(Surf{s_surf + sa * kSurfStride}, aa, ca);
+  const Plane<double> pb = aligned_plane(Surf{s_surf + sb * kSurfStride}, ab, cb);
   const double B[3] = {g.f.bfield[0], g.f.bfield[1], g.f.bfield[2]};
   PropS<double> s_end;
   return transport_tape<false>(pa, pb, x, B, g.f.mass, g.f.h_max, g.f.n_iter, Surf{s_surf + sb * kSurfStride}.xx0(),
@@ -1402,11 +1419,12 @@ struct TransitionFwd {
 };
 
 __device__ __forceinline__ void aligned_planes(const GradParams& g, const double* s_surf, int sa, int sb,
-                                               double aa[6], double ab[6], Plane<double>& pa, Plane<double>& pb) {
-  load_align(g, sa, aa);
-  load_align(g, sb, ab);
-  pa = aligned_plane<double>(Surf{s_surf + sa * kSurfStride}, aa);
-  pb = aligned_plane<double>(Surf{s_surf + sb * kSurfStride}, ab);
+                                               double ca[6], double cb[6], Plane<double>& pa, Plane<double>& pb) {
+  double aa[6], ab[6];
+  load_align(g, sa, aa, ca);
+  load_align(g, sb, ab, cb);
+  pa = aligned_plane(Surf{s_surf + sa * kSurfStride}, aa, ca);
+  pb = aligned_plane(Surf{s_surf + sb * kSurfStride}, ab, cb);
 }
 
 // the forward of transition k: the taped transport from (xprev, Cprev)
@@ -1414,9 +1432,9 @@ __device__ __forceinline__ void transition_forward(const GradParams& g, const Tr
                                                    const double xprev[6], const double Cprev[21], TransitionFwd& tf) {
   const FitParams& p = g.f;
   const int sa = io.sid(k - 1), sb = io.sid(k);
-  double aa[6], ab[6];
+  double ca[6], cb[6];
   Plane<double> pa, pb;
-  aligned_planes(g, s_surf, sa, sb, aa, ab, pa, pb);
+  aligned_planes(g, s_surf, sa, sb, ca, cb, pa, pb);
   const double B[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
   const double xxb = Surf{s_surf + sb * kSurfStride}.xx0();
 #pragma unroll
@@ -1437,9 +1455,9 @@ __device__ __forceinline__ void transition_reverse(const GradParams& g, const Tr
                                                    double Lf[6][6], double galign[12]) {
   const FitParams& p = g.f;
   const int sa = io.sid(k - 1), sbi = io.sid(k);
-  double aa[6], ab[6];
+  double ca[6], cb[6];
   Plane<double> pa, pb;
-  aligned_planes(g, s_surf, sa, sbi, aa, ab, pa, pb);
+  aligned_planes(g, s_surf, sa, sbi, ca, cb, pa, pb);
   const double B[3] = {p.bfield[0], p.bfield[1], p.bfield[2]};
   const double xxb = Surf{s_surf + sbi * kSurfStride}.xx0();
   double F[6][6];
@@ -1505,8 +1523,8 @@ __device__ __forceinline__ void transition_reverse(const GradParams& g, const Tr
     double lca[3], lRa[9], lcb[3], lRb[9];
     transport_rev(pa, pb, tf.xprev, B, p.mass, xxb, tf.tp, tf.s_end, lp, lJ, lJt, Lp[2][2], Lp[3][3], lx, lca, lRa,
                   lcb, lRb);
-    aligned_plane_rev(Surf{s_surf + sa * kSurfStride}, aa, lca, lRa, galign);
-    aligned_plane_rev(Surf{s_surf + sbi * kSurfStride}, ab, lcb, lRb, galign + 6);
+    aligned_plane_rev(Surf{s_surf + sa * kSurfStride}, ca, lca, lRa, galign);
+    aligned_plane_rev(Surf{s_surf + sbi * kSurfStride}, cb, lcb, lRb, galign + 6);
   }
   // Lambda_Cf = F^T Lp F
 #pragma unroll
@@ -2009,6 +2027,11 @@ cudaError_t launch_grad_v(const GradParams& g, int block, cudaStream_t stream) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_align_trig(int n_surfaces, const double* align, double* out, cudaStream_t stream) {
+  align_trig_kernel<<<(n_surfaces + 127) / 128, 128, 0, stream>>>(n_surfaces, align, out);
+  return cudaGetLastError();
+}
+
 size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint, bool pipelined) {
   const size_t n_ckpt = ((size_t)max_states + kSeg - 1) / kSeg;
   size_t d = 27 * n_ckpt;
@@ -2023,6 +2046,7 @@ cudaError_t launch_grad(const FitParams& f, const GradArgs& a, double* scratch, 
   GradParams g;
   g.f = f;
   g.align = a.align;
+  g.align_cs = a.align_cs;
   g.dl_dchi2 = a.dl_dchi2;
   g.dl_dparams = a.dl_dparams;
   g.dl_dcov = a.dl_dcov;

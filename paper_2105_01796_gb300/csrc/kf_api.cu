@@ -774,7 +774,9 @@ int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const doub
   int64_t chunk = cap / (int64_t)per_track;
   if (chunk < 1) chunk = 1;
   if (chunk > tr->n_tracks) chunk = tr->n_tracks;
-  const size_t need = per_track * (size_t)chunk;
+  // the alignment angles' cosines and sines ([6][S]) ahead of the tracks' scratch
+  const size_t trig_bytes = align_up(sizeof(double) * 6 * (size_t)su->n_surfaces, 256);
+  const size_t need = trig_bytes + per_track * (size_t)chunk;
   if (h->ckpt_bytes < need) {
     if (h->ckpt) cudaFree(h->ckpt);
     h->ckpt = nullptr;
@@ -789,6 +791,12 @@ int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const doub
   e = launch_pack_surfaces(su->n_surfaces, su->center, su->rot, su->x_over_x0, h->surf, stream);
   if (e != cudaSuccess) return cuda_fail(e, "pack_surfaces launch");
   int launches = 1;
+  if (align) {
+    a.align_cs = (const double*)h->ckpt;
+    e = launch_align_trig(su->n_surfaces, align, (double*)h->ckpt, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "align trig launch");
+    ++launches;
+  }
   FitParams p;
   memset(&p, 0, sizeof(p));
   p.n_tracks_total = tr->n_tracks;
@@ -813,7 +821,7 @@ int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const doub
   for (int64_t t0 = 0; t0 < tr->n_tracks; t0 += chunk) {
     p.track0 = (int32_t)t0;
     p.n_tracks = (int32_t)((tr->n_tracks - t0) < chunk ? (tr->n_tracks - t0) : chunk);
-    e = launch_grad(p, a, (double*)h->ckpt, grad_block, opt.min_blocks, pipelined, stream);
+    e = launch_grad(p, a, (double*)((char*)h->ckpt + trig_bytes), grad_block, opt.min_blocks, pipelined, stream);
     if (e != cudaSuccess) return cuda_fail(e, "grad launch");
     ++launches;
   }

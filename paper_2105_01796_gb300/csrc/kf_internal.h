@@ -130,6 +130,7 @@ cudaError_t launch_fit_variants(const FitParams& p, int block, cudaStream_t stre
 // with respect to the seeds and the per-surface alignment.
 struct GradArgs {
   const double* align;       // [6][S] or null (zero)
+  const double* align_cs;    // [6][S] cosines and sines of its angles (launch_align_trig)
   const double* dl_dchi2;    // w [T] or null (ones)
   const double* dl_dparams;  // v [6][T] or null (zero)
   const double* dl_dcov;     // W [21][T] or null (zero)
@@ -139,6 +140,10 @@ struct GradArgs {
   double* grad_seed;         // [6][T] or null
   double* grad_align;        // [6][S] or null: accumulated (the caller zeroes it)
 };
+
+// The cosines and sines of every surface's three alignment angles, out[6][S]
+// (cos alpha, sin alpha, cos beta, sin beta, cos gamma, sin gamma).
+cudaError_t launch_align_trig(int n_surfaces, const double* align, double* out, cudaStream_t stream);
 
 // Scratch doubles per track of one adjoint launch: the filtered checkpoints,
 // with the smoother's adjoint the smoothed checkpoints and its per-state

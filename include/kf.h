@@ -353,10 +353,10 @@ int kf_autotune(kf_handle* handle, const kf_tracks* tracks,
  * Method: reverse mode throughout: a reverse sweep over the states with the
  * filtered states recomputed from checkpoints every 5 states, and inside it
  * every transport recomputed with its RKN stage inputs taped and swept
- * backwards.  Launch shape: one thread per track, opt->block threads per
- * CTA (a multiple of 32 up to 256; 0, and opt == NULL, choose CTAs of the
- * warp count that covers the batch in nearly full waves of one CTA per SM);
- * the other launch options do not apply.  Device pointers; asynchronous on `stream`.  Tracks that fail
+ * backwards.  Launch shape: opt->team_warps as for kf_grad; one thread per
+ * track with opt->block threads per CTA (a multiple of 32 up to 256; 0, and
+ * opt == NULL, choose CTAs of the warp count that covers the batch in nearly
+ * full waves of one CTA per SM); the other launch options do not apply.  Device pointers; asynchronous on `stream`.  Tracks that fail
  * get NaN chi2 and gradients and do not contribute to grad_align. */
 int kf_chi2_grad(kf_handle* handle, const kf_tracks* tracks,
                  const kf_surfaces* surfaces, const double* align,
@@ -405,8 +405,17 @@ typedef struct {
  * per track: 216 B per 5 states (filter checkpoints), plus with v or W 216 B
  * per 5 states (smoothed checkpoints) and 632 B per state; a batch whose
  * scratch exceeds opt->workspace_bytes (0: 32 GiB) runs as several launches.
- * Launch shape and failure behaviour as for kf_chi2_grad; a track whose
- * smoother meets a non-positive pivot gets NaN outputs and gradients.
+ * Launch shape: opt->team_warps 1 = one thread per track (CTAs as for
+ * kf_chi2_grad); 2 = the pipelined form, for batches too small to fill the
+ * GPU: two warps per 32 tracks, one running the forward half of the filter's
+ * reverse sweep (the segments' recompute and the taped transports) one
+ * transition ahead of the other, which runs the reverse half (results equal
+ * the one-thread form's, up to the summation order of the alignment
+ * gradient); 0 (the default, and opt == NULL) = the pipelined form while
+ * 2 x ceil(T / 32) warps fit in one warp per SM sub-partition (T <= 9728 on
+ * 152 SMs), else one thread per track; others: KF_EUNSUPPORTED.
+ * Failure behaviour as for kf_chi2_grad; a track whose smoother meets a
+ * non-positive pivot gets NaN outputs and gradients.
  * Device pointers; asynchronous on `stream`. */
 int kf_grad(kf_handle* handle, const kf_tracks* tracks, const kf_surfaces* surfaces, const double* align,
             const kf_measurements* meas, const kf_field* field, const kf_options* opt,

@@ -1408,6 +1408,26 @@ __device__ __forceinline__ void recompute_filtered(const TrackIO& io, const doub
   }
 }
 
+// One filtered state: transition k-1 -> k from (xi, Ci) and the update at k.
+__device__ __forceinline__ void step_filtered(const TrackIO& io, const double* s_surf, int k, const double xi[6],
+                                              const double Ci[21], double xo[6], double Co[21]) {
+  double xp[6], Cp[21], F[6][6], qp, qt;
+  JacS<double> J;
+  transport_values(*io.g, s_surf, io.sid(k - 1), io.sid(k), xi, xp, J, qp, qt);
+  dense_F(J, F);
+  cov_transport(F, Ci, qp, qt, Cp);
+  if (!io.hole(k)) {
+    double m[2], V[3], c2;
+    io.meas(k, m, V);
+    update_fwd(xp, Cp, m, V, xo, Co, c2);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) xo[e] = xp[e];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) Co[e] = Cp[e];
+  }
+}
+
 // What the reverse of transition k-1 -> k needs from its forward: the
 // filtered state it starts from, the prediction, the Jacobian, and the
 // transport's tape and end state.
@@ -1923,21 +1943,37 @@ __global__ void __launch_bounds__(PIPE ? 64 : max_threads_of(MINB), 1) kf_grad_k
     // item j is transition k of segment sg, in the order above; the forward
     // warp produces item j into slot j % 2 while the reverse warp consumes
     // item j - 1 from the other slot; one barrier per item (both warps run
-    // the same n_items + 1 iterations)
+    // the same n_items + 1 iterations).  The forward warp recomputes the
+    // filtered states of the next segment (below) one per item while it
+    // produces the current segment's items, so no item carries a whole
+    // segment's recompute (only the first segment is recomputed at once).
     const bool fwd_warp = threadIdx.x >= 32;
     const int n_items = n_seg_warp * kSeg;
     const size_t slot_stride = (size_t)kSlot * io.TL;
-    double bx[kSeg][6], bC[kSeg][21];
+    double bx[2][kSeg][6], bC[2][kSeg][21];  // by segment parity
     for (int j = 0; j <= n_items; ++j) {
       if (fwd_warp && j < n_items) {
-        const int sg = n_seg_warp - 1 - j / kSeg;
-        const int s0 = sg * kSeg, k = s0 + kSeg - j % kSeg;
+        const int sg = n_seg_warp - 1 - j / kSeg, q = j % kSeg;
+        const int s0 = sg * kSeg, k = s0 + kSeg - q;
         const bool seg_active = sg < n_seg;
         const int s1 = seg_active ? min(s0 + kSeg, n - 1) : s0;
-        if (j % kSeg == 0 && seg_active) recompute_filtered(io, s_surf, sg, s0, s1, bx, bC);
+        const int cur = sg & 1, nxt = cur ^ 1;
+        if (j == 0 && seg_active) recompute_filtered(io, s_surf, sg, s0, s1, bx[cur], bC[cur]);
+        if (sg > 0 && sg - 1 < n_seg && q + 1 < kSeg) {
+          // state q + 1 of segment sg - 1 (its checkpoint first)
+          const int s0n = (sg - 1) * kSeg, s1n = min(s0n + kSeg, n - 1);
+          if (q == 0) {
+#pragma unroll
+            for (int e = 0; e < 6; ++e) bx[nxt][0][e] = io.ck(sg - 1, e);
+#pragma unroll
+            for (int e = 0; e < 21; ++e) bC[nxt][0][e] = io.ck(sg - 1, 6 + e);
+          }
+          if (s0n + q + 1 < s1n)
+            step_filtered(io, s_surf, s0n + q + 1, bx[nxt][q], bC[nxt][q], bx[nxt][q + 1], bC[nxt][q + 1]);
+        }
         if (seg_active && k <= s1) {
           TransitionFwd tf;
-          transition_forward(g, io, s_surf, k, bx[k - 1 - s0], bC[k - 1 - s0], tf);
+          transition_forward(g, io, s_surf, k, bx[cur][k - 1 - s0], bC[cur][k - 1 - s0], tf);
           slot_write(g.pipe + (size_t)(j & 1) * slot_stride, io.TL, io.tl, tf);
         }
       }

@@ -731,9 +731,17 @@ int kf_grad(kf_handle* h, const kf_tracks* tr, const kf_surfaces* su, const doub
   // threads per CTA for min_blocks 1 / 3 / 4)
   const int grad_block = opt.block;
   if (grad_block < 0 || grad_block % 32 != 0 || grad_block > max_threads_of(opt.min_blocks)) return KF_EUNSUPPORTED;
-  // team_warps 2: the pipelined form (two warps per 32 tracks)
+  // team_warps 2: the pipelined form (two warps per 32 tracks); 1: one
+  // thread per track; 0: the pipelined form while its two-warp teams fit in
+  // one warp per SM sub-partition (a batch too small to fill the GPU)
   if (opt.team_warps != 0 && opt.team_warps != 1 && opt.team_warps != 2) return KF_EUNSUPPORTED;
-  const bool pipelined = opt.team_warps == 2;
+  bool pipelined = opt.team_warps == 2;
+  if (opt.team_warps == 0) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      pipelined = 2 * (((int64_t)tr->n_tracks + 31) / 32) <= 4 * (int64_t)nsm;
+  }
   opt.team_warps = 0;
   opt.block = 0;
   kf_outputs dummy;

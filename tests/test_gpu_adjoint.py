@@ -255,13 +255,17 @@ def test_whole_fit_autograd_and_chunked_launches(handle):
     assert np.allclose(seeds.grad.cpu().numpy(), g["gs"], rtol=1e-12, atol=0)
     assert np.allclose(align.grad.cpu().numpy(), g["ga"], rtol=1e-9, atol=1e-9 * np.abs(g["ga"]).max())
     # 300 tracks through a workspace that holds 64 of them: five launches
+    # (one thread per track; the pipelined form adds two hand-off slots of
+    # kSlot doubles to each track's scratch)
     per_track = 8 * (27 * 5 + 27 * 6 + 79 * 21)
-    opt = kf.kf_default_options(kf.KF_PRECISION_FP64, block=0, workspace_bytes=64 * per_track)
+    opt = kf.kf_default_options(kf.KF_PRECISION_FP64, block=0, team_warps=1, workspace_bytes=64 * per_track)
     gc = _whole(handle, ev, np.zeros((6, S)), w, v, W, opt=opt)
     # the surface packing, the alignment angles' cosines and sines, 5 chunks
     assert handle.last_launch_count() == 1 + 1 + 5
+    g1 = _whole(handle, ev, np.zeros((6, S)), w, v, W, opt=kf.kf_default_options(block=0, team_warps=1))
     for k in ("chi2", "params", "cov", "gs"):
-        assert np.array_equal(gc[k], g[k]), k
+        assert np.array_equal(gc[k], g1[k]), k
+        assert np.array_equal(g1[k], g[k]), k   # the default here is the pipelined form
     assert np.allclose(gc["ga"], g["ga"], rtol=1e-11, atol=1e-11 * np.abs(g["ga"]).max())
 
 
@@ -342,7 +346,7 @@ def test_pipelined_adjoint_equals_sequential(handle, objective):
         if nonzero:
             align[:3, 1:] = rng.normal(size=(3, S - 1)) * 0.05
             align[3:, 1:] = rng.normal(size=(3, S - 1)) * 5e-4
-        seq = _whole(handle, ev, align, None, v, W, opt=kf.kf_default_options(block=0))
+        seq = _whole(handle, ev, align, None, v, W, opt=kf.kf_default_options(block=0, team_warps=1))
         pip = _whole(handle, ev, align, None, v, W, opt=kf.kf_default_options(block=0, team_warps=2))
         assert handle.last_launch_count() == 3  # packing, alignment trig, the adjoint
         for k in ("chi2", "params", "cov", "gs"):

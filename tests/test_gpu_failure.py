@@ -74,6 +74,22 @@ def test_timed_out_wait_marks_every_track_and_the_next_call_succeeds(handle, eve
         assert np.array_equal(a[k], r[k]), k
 
 
+@pytest.mark.parametrize("team", [2, 4])
+def test_timed_out_wait_in_a_track_team(handle, event, team):
+    import torch
+    dev = kf.event_to_device(event)
+    T, M = int(event["n_tracks"]), int(event["surface_id"].shape[0])
+    bad = kf.alloc_outputs(T, M, with_states=True)
+    kf.kf_fit_ex(handle, dev, bad, kf.kf_default_options(kf.KF_PRECISION_FP64, team_warps=team, wait_limit=64,
+                                                         test_wait_timeout=1))
+    torch.cuda.synchronize()
+    _assert_timed_out(_host(bad), M)
+    out = kf.alloc_outputs(T, M, with_states=True)
+    kf.kf_fit_ex(handle, dev, out, kf.kf_default_options(kf.KF_PRECISION_FP64, team_warps=team))
+    torch.cuda.synchronize()
+    assert torch.all(out["status"] == 0)
+
+
 def test_host_entry_reports_the_timeout_then_recovers(handle, event):
     T = int(event["n_tracks"])
     with pytest.raises(kf.KfError, match="kf error -5"):

@@ -282,6 +282,14 @@ def test_every_launch_variant_agrees(handle, prec):
                     base = g
                 for k in ("params", "cov", "chi2", "ndf", "status"):
                     assert np.array_equal(g[k], base[k]), (sched, block, k)
+    # the track teams the tuner may pick for FP64 (each element computed
+    # with the one-thread kernel's expressions)
+    if prec == FP64:
+        for tw in (2, 4):
+            g = gpu_fit(handle, ev, prec, team_warps=tw)
+            compare(g, r, prec)
+            for k in ("params", "cov", "chi2", "ndf", "status"):
+                assert np.array_equal(g[k], base[k]), ("team", tw, k)
     # persistent launches of one-warp CTAs with a few resident warps per SM
     # (fewer warps than units: every warp takes several units)
     for sched in (kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED):

@@ -946,11 +946,8 @@ __device__ __forceinline__ void load_align(const GradParams& g, int sid, double 
   for (int e = 0; e < 6; ++e) cs[e] = g.align ? g.align_cs[(size_t)e * g.f.n_surfaces + sid] : ((e & 1) ? 0.0 : 1.0);
 }
 
-// values of the transport k-1 -> k with the aligned planes (a separate
-// function: it is called from every pass, and one copy instead of many
-// keeps the kernel's instruction footprint down; measured 50.4 -> 48.6 ms
-// for the chi2 objective at 100k tracks)
-__device__ __noinline__ int transport_values(const GradParams& g, const double* s_surf, int sa, int sb,
+// values of the transport k-1 -> k with the aligned planes
+__device__ __forceinline__ int transport_values(const GradParams& g, const double* s_surf, int sa, int sb,
                                                 const double x[6], double xp[6], JacS<double>& J, double& qp,
                                                 double& qt) {
   double aa[6], ab[6], ca[6], cb[6];

@@ -282,14 +282,20 @@ def test_every_launch_variant_agrees(handle, prec):
                     base = g
                 for k in ("params", "cov", "chi2", "ndf", "status"):
                     assert np.array_equal(g[k], base[k]), (sched, block, k)
-    # the track teams the tuner may pick for FP64 (each element computed
-    # with the one-thread kernel's expressions)
+    # the track teams the tuner may pick for FP64: the same status and ndf,
+    # and values within 1e-11 of the one-thread kernel (a team sums some
+    # matrix products in a different order, so not bit for bit; measured
+    # 1.0e-12 on these 30-state tracks)
     if prec == FP64:
+        ok = base["status"] == 0
         for tw in (2, 4):
             g = gpu_fit(handle, ev, prec, team_warps=tw)
             compare(g, r, prec)
-            for k in ("params", "cov", "chi2", "ndf", "status"):
+            for k in ("ndf", "status"):
                 assert np.array_equal(g[k], base[k]), ("team", tw, k)
+            assert param_err(g["params"][:, ok], base["params"][:, ok], base["cov"][:, ok]).max() < 1e-11
+            assert cov_err(g["cov"][:, ok], base["cov"][:, ok]).max() < 1e-11
+            assert chi2_err(g["chi2"][ok], base["chi2"][ok]).max() < 1e-11
     # persistent launches of one-warp CTAs with a few resident warps per SM
     # (fewer warps than units: every warp takes several units)
     for sched in (kf.KF_SCHEDULE_PERSISTENT, kf.KF_SCHEDULE_SORTED):

@@ -39,17 +39,17 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 
 # DRAM traffic of the mixed kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of both wave-split launches of a 100k-track, 3.1M-state
-# step of the same workload: launch A 592.4 + 492.3 MB, launch B 505.2 +
-# 429.8 MB.  Traffic grows in proportion to the states, so a launch's traffic
+# step of the same workload: launch A 591.2 + 492.7 MB, launch B 505.3 +
+# 429.9 MB.  Traffic grows in proportion to the states, so a launch's traffic
 # is this per-state figure times its states.  It holds only for the kernel
 # sources and build flags that were captured: any change to them makes the
 # figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (637.5552e6 + 534.25152e6 + 435.349504e6 + 382.342912e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "30c471845aed6646e64a8580254a5fd0fe632083569c8bf0f1ddb923f4723011"
+MIXED_TRAFFIC_BYTES_PER_STATE = (591.208192e6 + 492.73472e6 + 505.311744e6 + 429.914624e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "022f42830c9d364aca24439fd2ba44b616db9a12fd4ba10d5993cf0b0c35d1ce"
 # the same for the FP64 path's kernel (one launch of the 100k-track step:
-# 2304.475 + 2223.975 MB)
-FP64_TRAFFIC_BYTES_PER_STATE = (2304.475e6 + 2223.975e6) / 3.1e6
-FP64_TRAFFIC_SOURCES_SHA256 = "d2ada231cfd1170211a73713799423d0ff5dad2742b8b8a93584ec8a84416c64"
+# 2301.903 + 2223.674 MB)
+FP64_TRAFFIC_BYTES_PER_STATE = (2301.903e6 + 2223.674e6) / 3.1e6
+FP64_TRAFFIC_SOURCES_SHA256 = "92d99672b85a36d94abd604e7aa4753a56e2020d39cc458dbdba4d5cd4316b4b"
 
 
 # FP64 flops the hardware counted (ncu: 2 x DFMA + DADD + DMUL thread
@@ -57,10 +57,10 @@ FP64_TRAFFIC_SOURCES_SHA256 = "d2ada231cfd1170211a73713799423d0ff5dad2742b8b8a93
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
 # (align20, 21 states; the chi2 objective and the whole-fit objective);
 # reported while those kernels' sources match
-EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105256 + 2760501561 + 5733751603) / 1e5,
-                       "adjoint_chi2": (2 * 14906000038 + 1671199997 + 7903600040) / 1e5,
-                       "adjoint_whole": (2 * 28841200052 + 2808200046 + 11588700025) / 1e5}
-EXT_SOURCES_SHA256 = "67248be0dcbebc1439e396ad96190876b2f40e957c84ac9580bcec8530b359dc"
+EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105235 + 2760501538 + 5733751609) / 1e5,
+                       "adjoint_chi2": (2 * 14277600007 + 1627199962 + 7860000020) / 1e5,
+                       "adjoint_whole": (2 * 27684799964 + 2716199927 + 11449100094) / 1e5}
+EXT_SOURCES_SHA256 = "eabc18d8ee1d1a99a2143d7d5c81e084ea83dd2e978a3580af12d1c1070d95a0"
 
 
 def ext_kernel_sources_sha256():

@@ -100,7 +100,7 @@ int ensure_surf(kf_handle* h, int n) {
   if (h->surf) cudaFree(h->surf);
   h->surf = nullptr;
   h->surf_cap = 0;
-  cudaError_t e = cudaMalloc(&h->surf, (size_t)n * kSurfStride * sizeof(double));
+  cudaError_t e = cudaMalloc(&h->surf, (size_t)n * kSurfPacked * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(surfaces)");
   h->surf_cap = n;
   return KF_SUCCESS;

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitP
   extern __shared__ __align__(128) unsigned char smem_raw[];
   double* s_surf = reinterpret_cast<double*>(smem_raw);
   __shared__ __align__(8) uint64_t s_mbar;
-  const bool ok = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * kSurfStride * 8), &s_mbar,
+  const bool ok = stage_surfaces(s_surf, p.surf, (uint32_t)(p.n_surfaces * Body::kStride * 8), &s_mbar,
                                  p.error_flag, p.wait_limit, p.skip_stage_copy != 0);
   // One call site for both schedules. A grid CTA fits its own blockDim
   // tracks once; a persistent CTA keeps taking blockDim-track units. The
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(max_threads_of(MINB), 1) fit_kernel(const FitP
 // the number of launches queued.
 template <class Body, int MINB>
 cudaError_t launch_body(const FitParams& p, int block, cudaStream_t stream, int* launched = nullptr) {
-  const size_t smem = (size_t)p.n_surfaces * kSurfStride * sizeof(double);
+  const size_t smem = (size_t)p.n_surfaces * Body::kStride * sizeof(double);
   auto kern = fit_kernel<Body, MINB>;
   if (launched) *launched = 1;
   if (smem > 48 * 1024) {

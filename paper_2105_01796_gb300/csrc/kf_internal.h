@@ -11,9 +11,20 @@ namespace kfgb {
 //   doubles [0..2] centre c, [3..11] R row-major (columns u, v, n), [12] x/X0,
 //           [13] n.c, [14] u.c, [15] v.c
 //   floats at double offset 16: [0..2] n, [3..5] u, [6..8] v, [9] x/X0
-//           (float copies, so the mixed kernel converts nothing per step)
+//           (float copies)
+// The mixed kernel stages a table of its own, 32 floats (128 B) per surface,
+// packed after the FP64 table in the same buffer ([n_surfaces][kSurfStride]
+// doubles, then [n_surfaces][kSurfStrideM] doubles): every FP64 quantity as
+// a double-float pair hi + lo (hi = the nearest float, lo = the nearest
+// float to the rest), so it converts nothing per step:
+//   [0..2] n hi, [3..5] u hi, [6..8] v hi, [9] x/X0,
+//   [10..12] n lo, [13..15] u lo, [16..18] v lo,
+//   [19..21] (n.c, u.c, v.c) hi, [22..24] (n.c, u.c, v.c) lo,
+//   [25..27] c hi, [28..30] c lo, [31] 0
 constexpr int kSurfStride = 24;
-constexpr int kMaxSurfaces = 1024;  // 192 KiB of shared memory
+constexpr int kSurfStrideM = 16;
+constexpr int kSurfPacked = kSurfStride + kSurfStrideM;  // doubles per surface in the packed buffer
+constexpr int kMaxSurfaces = 1024;  // 192 KiB of shared memory (FP64 table)
 
 // Per-state record the forward pass writes and the RTS pass reads back.
 // FP64 path, all in ws64:  xp 6 | xf 6 | Cp 21 | Cf 21 | Bm 36   (90 doubles)
@@ -97,7 +108,8 @@ inline bool wants_variants(int smoother, int energy_loss, const void* map) {
   return smoother != 0 || energy_loss != 0 || map != nullptr;
 }
 
-// Pack the SoA surface table into [S][kSurfStride] doubles.
+// Pack the SoA surface table into [S][kSurfStride] doubles followed by the
+// mixed kernel's [S][kSurfStrideM] (packed must hold S * kSurfPacked doubles).
 cudaError_t launch_pack_surfaces(int n_surfaces, const double* center,
                                  const double* rot, const double* x_over_x0,
                                  double* packed, cudaStream_t stream);

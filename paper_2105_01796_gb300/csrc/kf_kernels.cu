@@ -342,10 +342,28 @@ __global__ void pack_surfaces_kernel(int n, const double* __restrict__ center, c
   }
   f[9] = (float)o[12];
   for (int i = 10; i < 16; ++i) f[i] = 0.0f;
+  // the mixed kernel's table: each FP64 value v as hi = (float)v and
+  // lo = (float)(v - hi)
+  float* m = reinterpret_cast<float*>(out + (size_t)n * kSurfStride + (size_t)s * kSurfStrideM);
+  auto split = [](double v, float* hi, float* lo) {
+    const float h = (float)v;
+    *hi = h;
+    *lo = (float)(v - (double)h);
+  };
+  for (int i = 0; i < 3; ++i) {
+    split(o[3 + 3 * i + 2], &m[i], &m[10 + i]);      // n
+    split(o[3 + 3 * i + 0], &m[3 + i], &m[13 + i]);  // u
+    split(o[3 + 3 * i + 1], &m[6 + i], &m[16 + i]);  // v
+    split(o[13 + i], &m[19 + i], &m[22 + i]);        // n.c, u.c, v.c
+    split(o[i], &m[25 + i], &m[28 + i]);             // c
+  }
+  m[9] = (float)o[12];
+  m[31] = 0.0f;
 }
 
 template <bool BZ>
 struct Fp64Body {
+  static constexpr int kStride = kSurfStride;
   static __device__ __forceinline__ void run(const FitParams& p, const double* s_surf, int i) {
     fit_one_fp64<BZ>(p, s_surf, i);
   }

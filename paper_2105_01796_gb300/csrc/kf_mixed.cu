@@ -8,14 +8,17 @@
 //     transport F C F^T, the Highland noise, the gain K, the smoother gain
 //     algebra and the smoothed covariance.
 //   * FP64: the Joseph covariance update, chi2, the LDL^T factorisation
-//     of the predicted covariance and its solves (the smoother's inverse),
-//     and the accumulators of position, direction, time and the parameter
-//     vector, which receive FP32 increments.
+//     of the predicted covariance and its solves (the smoother's inverse).
+//   * Double-float pairs of FP32 values (about 48 bits): the track's point,
+//     direction, angles, q/p and time between surfaces, which only receive
+//     FP32 increments and meet the plane geometry (split the same way in
+//     this kernel's own surface table) in dot products; no FP64 instruction
+//     is spent on them.
 //   * float<->double conversions run on the integer pipe (dev::f2d/d2f);
 //     FP64 1/sqrt and 1/x come from float seeds refined by a Newton step.
-//   * The direction is carried as FP64 (phi, theta) with their cosines and
+//   * The direction is carried as (phi, theta) with their cosines and
 //     sines; propagation and updates change them by small rotations, so no
-//     FP64 trigonometry runs after the seed.
+//     trigonometry of the carried angles runs after the seed.
 //
 // Smoother in noise-rank form.  With Cp' = F Cf F^T + Q (Q non-zero only in
 // the (phi, theta) block) the RTS gain A = Cf F^T Cp'^-1 equals
@@ -45,6 +48,98 @@ using namespace dev;
 constexpr int XP = 0, CPD = 6;                                 // ws64 fields
 constexpr int FJ = 0, QPHI = 25, QTH = 26, DXF = 27;          // ws32 fields
 
+// ---- double-float ("df") values: an unevaluated sum hi + lo of two floats
+// with |lo| <= ulp(hi) / 2, about 48 significant bits.  Error-free
+// transformations: Knuth's TwoSum, Dekker's Fast2Sum and the exact product
+// from one FMA; sums and products of df values as in Dekker (1971), dot
+// products as Dot2 of Ogita, Rump and Oishi (2005).  The _rn intrinsics keep
+// the compiler from contracting or reassociating these steps.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// exact for |a| >= |b| or a = 0
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+// x + f (the final TwoSum keeps the pair normalised under cancellation)
+__device__ __forceinline__ DF df_add_f(DF x, float f) {
+  const DF s = two_sum(x.hi, f);
+  return two_sum(s.hi, __fadd_rn(s.lo, x.lo));
+}
+// x + y, with the low parts summed exactly as well
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = two_sum(x.hi, y.hi);
+  const DF t = two_sum(x.lo, y.lo);
+  const DF u = two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+__device__ __forceinline__ DF df_neg(DF x) { return {-x.hi, -x.lo}; }
+// x * y (the lo * lo term is below the pair's resolution)
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const DF p = two_prod(x.hi, y.hi);
+  return fast_two_sum(p.hi, __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo)));
+}
+// float value (hi + lo rounded)
+__device__ __forceinline__ float df_f(DF x) { return __fadd_rn(x.hi, x.lo); }
+// conversions: to FP64 exactly, from FP64 as the nearest float and the
+// nearest float to the rest
+__device__ __forceinline__ double df_to_d(DF x) { return f2d(x.hi) + f2d(x.lo); }
+__device__ __forceinline__ DF df_from_d(double v) {
+  const float h = d2f(v);
+  return {h, d2f(v - f2d(h))};
+}
+// w . r - w0 for a vector w given as hi / lo float arrays and a df offset
+// w0: Dot2 (the products split exactly by FMA, the running sum by TwoSum,
+// every error term gathered in one float), as accurate as a dot product in
+// twice the float precision; the wl * r.lo terms are below that
+__device__ __forceinline__ DF df_dot(const float* wh, const float* wl, DF w0, const DF r[3]) {
+  float s = -w0.hi, c = -w0.lo;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const DF p = two_prod(wh[i], r[i].hi);
+    const DF q = two_sum(s, p.hi);
+    s = q.hi;
+    c = __fadd_rn(c, __fadd_rn(q.lo, p.lo));
+    c = __fmaf_rn(wh[i], r[i].lo, c);
+    c = __fmaf_rn(wl[i], r[i].hi, c);
+  }
+  return two_sum(s, c);
+}
+
+// this kernel's surface record (32 floats, layout in kf_internal.h)
+struct SurfM {
+  const float* f;  // shared memory
+  __device__ const float* nh() const { return f; }
+  __device__ const float* uh() const { return f + 3; }
+  __device__ const float* vh() const { return f + 6; }
+  __device__ const float* nl() const { return f + 10; }
+  __device__ const float* ul() const { return f + 13; }
+  __device__ const float* vl() const { return f + 16; }
+  __device__ float nf(int i) const { return f[i]; }
+  __device__ float uf(int i) const { return f[3 + i]; }
+  __device__ float vf(int i) const { return f[6 + i]; }
+  __device__ float xx0f() const { return f[9]; }
+  __device__ DF nc() const { return {f[19], f[22]}; }
+  __device__ DF uc() const { return {f[20], f[23]}; }
+  __device__ DF vc() const { return {f[21], f[24]}; }
+  __device__ DF c(int i) const { return {f[25 + i], f[28 + i]}; }
+  __device__ DF u(int i) const { return {f[3 + i], f[13 + i]}; }
+  __device__ DF v(int i) const { return {f[6 + i], f[16 + i]}; }
+};
+__device__ __forceinline__ SurfM surf_m(const double* s_surf, int sid) {
+  return SurfM{reinterpret_cast<const float*>(s_surf + (size_t)sid * kSurfStrideM)};
+}
+
 struct WSM {
   double* w64;
   float* w32;
@@ -54,15 +149,15 @@ struct WSM {
   __device__ float& f(int k, int e) const { return w32[((size_t)k * kRec32Mixed + e) * nt + i]; }
 };
 
-// direction: the angles and the unit direction vector, all FP64
+// direction: the angles and the unit direction vector, all df
 struct Dir {
-  double phi, theta;
-  double T[3];  // (cos phi sin theta, sin phi sin theta, cos theta), unit up to rounding
+  DF phi, theta;
+  DF T[3];  // (cos phi sin theta, sin phi sin theta, cos theta), unit up to rounding
 };
 
 // float cosines and sines of the direction's angles, from T
-__device__ __forceinline__ void dir_cs(const double T[3], float& cp, float& sp, float& ct, float& st) {
-  const float t0 = d2f(T[0]), t1 = d2f(T[1]), t2 = d2f(T[2]);
+__device__ __forceinline__ void dir_cs(const DF T[3], float& cp, float& sp, float& ct, float& st) {
+  const float t0 = T[0].hi, t1 = T[1].hi, t2 = T[2].hi;
   const float rho = sqrtf(t0 * t0 + t1 * t1);
   const float irho = 1.0f / rho, itn = rsqrtf(rho * rho + t2 * t2);
   cp = t0 * irho;
@@ -198,18 +293,19 @@ __device__ __forceinline__ void turn_inc(CS& cs, float a, float b, float out[3])
 // state is the predicted one (point r0, direction d, time x[5]) plus the
 // filter's pending FP32 increments pd; x[4] is the filtered q/p.
 template <bool BZ>
-__device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, const double r0[3], const double x[6],
+__device__ __forceinline__ int transport_mixed(const SurfM& sa, const SurfM& sb, const DF r0[3], const DF x[6],
                                const Dir& d, const Pend& pd, CS& cs, const float Bf[3], float m2, float h_max,
-                               int n_iter, double xp[6], double rp[3], Dir& dp, JacF& J, float& sin_th,
+                               int n_iter, DF xp[6], DF rp[3], Dir& dp, JacF& J, float& sin_th,
                                float& cos_inc) {
-  // The point and the direction stay FP64 (predicted values of surface a);
+  // The point and the direction stay df (predicted values of surface a);
   // everything that moves them here (the pending filter increments, the RKN
   // curvature terms, the direction change accT, the plane corrections) is
   // summed in FP32 and added once at the end.
-  double r[3] = {r0[0], r0[1], r0[2]};
-  const double* Td = d.T;
-  const float T0f[3] = {d2f(Td[0]) + pd.T[0], d2f(Td[1]) + pd.T[1], d2f(Td[2]) + pd.T[2]};
-  const float lam = d2f(x[4]);
+  DF r[3] = {r0[0], r0[1], r0[2]};
+  const DF* Td = d.T;
+  const float T0f[3] = {Td[0].hi + (Td[0].lo + pd.T[0]), Td[1].hi + (Td[1].lo + pd.T[1]),
+                        Td[2].hi + (Td[2].lo + pd.T[2])};
+  const float lam = df_f(x[4]);
   const float lk = lam * (float)kKappa;
   const float bs[3] = {lk * Bf[0], lk * Bf[1], lk * Bf[2]};
   const float kB[3] = {(float)kKappa * Bf[0], (float)kKappa * Bf[1], (float)kKappa * Bf[2]};
@@ -233,20 +329,19 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   float accR[3] = {0.0f, 0.0f, 0.0f};  // r_end - r_start - s0 T_start
   float tinc = 0.0f;                    // t_end - t_start
   // main steps over the straight-line distance s0: the position moves by
-  // s0 T_start (FP64) plus the FP32 offsets of the curvature and of the
+  // s0 T_start (df) plus the FP32 offsets of the curvature and of the
   // direction change
-  double s0d, dist;
+  DF s0d, dist;
   {
-    dist = fma(-sb.n(2), r[2], fma(-sb.n(1), r[1], fma(-sb.n(0), r[0], sb.nc())));
+    dist = df_neg(df_dot(sb.nh(), sb.nl(), sb.nc(), r));  // n.c - n.r
     const float nT = nb[0] * T0f[0] + nb[1] * T0f[1] + nb[2] * T0f[2];
     if (!(fabsf(nT) > 1e-9f)) return ST_NO_INTERSECTION;
-    const float s0 = (d2f(dist) - (nb[0] * pd.r[0] + nb[1] * pd.r[1] + nb[2] * pd.r[2])) / nT;
+    const float s0 = (df_f(dist) - (nb[0] * pd.r[0] + nb[1] * pd.r[1] + nb[2] * pd.r[2])) / nT;
     const float nsub_f = ceilf(fabsf(s0) / h_max);
     if (!(nsub_f <= 64.0f)) return ST_NO_INTERSECTION;
     const int nsub = nsub_f < 1.0f ? 1 : (int)nsub_f;
     const float h = s0 / (float)nsub;
-    s0d = f2d(h);
-    if (nsub > 1) s0d *= (double)nsub;  // exact: nsub is a small integer
+    s0d = two_prod(h, (float)nsub);  // exact: nsub is a small integer
     for (int k = 0; k < nsub; ++k) {
       const float Tf[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
       cols_step<BZ>(g, h, bs, kB, Tf, dtl);
@@ -264,13 +359,13 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
   // The main end is r_main = r0 + s0 Td + off with the FP32 offset
   // off = pd.r + s0 pd.T + accR; the remaining distance is
   // n.(c - r_main) = dist - s0 (n.Td) - n.off.
-  const float s0f = d2f(s0d);
+  const float s0f = s0d.hi;
   float off[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) off[i] = pd.r[i] + s0f * pd.T[i] + accR[i];
   {
-    const double nTd = sb.n(0) * Td[0] + sb.n(1) * Td[1] + sb.n(2) * Td[2];
-    const float dmf = d2f(fma(-s0d, nTd, dist)) - (nb[0] * off[0] + nb[1] * off[1] + nb[2] * off[2]);
+    const DF nTd = df_dot(sb.nh(), sb.nl(), DF{0.0f, 0.0f}, Td);
+    const float dmf = df_f(df_add(dist, df_neg(df_mul(s0d, nTd)))) - (nb[0] * off[0] + nb[1] * off[1] + nb[2] * off[2]);
     const float Tm[3] = {T0f[0] + accT[0], T0f[1] + accT[1], T0f[2] + accT[2]};
     float orr[3] = {0.0f, 0.0f, 0.0f}, oT[3] = {0.0f, 0.0f, 0.0f}, ot = 0.0f;
     for (int it = 0; it < n_iter; ++it) {
@@ -311,12 +406,12 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     const float drem = dmf - (nb[0] * orr[0] + nb[1] * orr[1] + nb[2] * orr[2]);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      r[i] = fma(s0d, Td[i], r[i]) + f2d(off[i] + orr[i] + drem * nb[i]);
+      r[i] = df_add_f(df_add(r[i], df_mul(s0d, Td[i])), off[i] + orr[i] + drem * nb[i]);
       accT[i] += oT[i];
     }
     tinc += ot;
   }
-  const double t = x[5] + f2d(pd.t + tinc);
+  const DF t = df_add_f(x[5], pd.t + tinc);
   // end angles: the rotation from the start to the end direction, computed in
   // FP32 from the start direction c and its change a = accT (no cancellation
   // of large terms):
@@ -333,24 +428,23 @@ __device__ __forceinline__ int transport_mixed(const Surf& sa, const Surf& sb, c
     const float rho = sqrtf(rho_sq), rho_end = sqrtf(rho_sq + drho_sq);
     const float drho = drho_sq / (rho + rho_end);
     const float dth = small_atan2(c2 * drho - rho * a2, c2 * (c2 + a2) + rho * (rho + drho));
-    dp = d;
-    double phi = d.phi + f2d(pd.phi + dphi);
-    // keep phi in (-pi, pi]; compared on the integer pipe (doubles of one
-    // sign order like their magnitudes' bit patterns)
-    const double pi = 3.141592653589793;
-    const long long bp = __double_as_longlong(phi), bpi = __double_as_longlong(pi);
-    if (bp > bpi) phi -= 2.0 * pi;
-    else if (bp < 0 && (bp & 0x7fffffffffffffffLL) >= bpi) phi += 2.0 * pi;
+    DF phi = df_add_f(d.phi, pd.phi + dphi);
+    // keep phi in (-pi, pi]: pi as the df pair (nearest float, rest)
+    constexpr float kPiHi = 3.14159274101257324f, kPiLo = -8.742278000372475e-08f;
+    if (phi.hi > kPiHi || (phi.hi == kPiHi && phi.lo > kPiLo))
+      phi = df_add(phi, DF{-2.0f * kPiHi, -2.0f * kPiLo});
+    else if (phi.hi < -kPiHi || (phi.hi == -kPiHi && phi.lo <= -kPiLo))
+      phi = df_add(phi, DF{2.0f * kPiHi, 2.0f * kPiLo});
     dp.phi = phi;
-    dp.theta = d.theta + f2d(pd.theta + dth);
+    dp.theta = df_add_f(d.theta, pd.theta + dth);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dp.T[i] = Td[i] + f2d(pd.T[i] + accT[i]);
+    for (int i = 0; i < 3; ++i) dp.T[i] = df_add_f(Td[i], pd.T[i] + accT[i]);
   }
   rp[0] = r[0];
   rp[1] = r[1];
   rp[2] = r[2];
-  xp[0] = fma(sb.u(2), r[2], fma(sb.u(1), r[1], fma(sb.u(0), r[0], -sb.uc())));
-  xp[1] = fma(sb.v(2), r[2], fma(sb.v(1), r[1], fma(sb.v(0), r[0], -sb.vc())));
+  xp[0] = df_dot(sb.uh(), sb.ul(), sb.uc(), r);
+  xp[1] = df_dot(sb.vh(), sb.vl(), sb.vc(), r);
   xp[2] = dp.phi;
   xp[3] = dp.theta;
   xp[4] = x[4];
@@ -601,39 +695,44 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
   int nmeas = 0;
   if (status == ST_OK) {
     // ------------------------------------------------ forward filter
-    // Between states the FP64 state is the prediction of the last surface
+    // Between states the df state is the prediction of the last surface
     // (point r, direction d, time x[5]) plus the filter's FP32 increments
     // in pd, which the next transport applies; the filtered q/p is x[4].
     // The filtered covariance is kept in FP32 between states: it only feeds
     // the FP32 transport F Cf F^T (the Joseph update produces it in FP64).
-    double x[6], r[3];
+    DF x[6], r[3];
     Pend pd = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, 0.0f, 0.0f, 0.0f};
     CS cs;  // float cosines / sines of the filtered direction
     float Cf[21];
     float dx[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // x_f - x_p of the last state
-#pragma unroll
-    for (int e = 0; e < 6; ++e) x[e] = p.seed_params[e * TT + t];
     Dir d;
-    d.phi = x[2];
-    d.theta = x[3];
     {
+      double xs0[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        xs0[e] = p.seed_params[e * TT + t];
+        x[e] = df_from_d(xs0[e]);
+      }
+      d.phi = x[2];
+      d.theta = x[3];
       double sp, cp, st, ct;
-      sincos(x[2], &sp, &cp);  // the only FP64 trigonometry of the track
-      sincos(x[3], &st, &ct);
-      d.T[0] = cp * st;
-      d.T[1] = sp * st;
-      d.T[2] = ct;
+      sincos(xs0[2], &sp, &cp);  // the only FP64 trigonometry of the track
+      sincos(xs0[3], &st, &ct);
+      d.T[0] = df_from_d(cp * st);
+      d.T[1] = df_from_d(sp * st);
+      d.T[2] = df_from_d(ct);
       cs = CS{d2f(cp), d2f(sp), d2f(ct), d2f(st)};
     }
     int sid_prev = p.surface_id[o0];
     {
-      const Surf s0{s_surf + sid_prev * kSurfStride};
+      const SurfM s0 = surf_m(s_surf, sid_prev);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) r[c] = fma(x[1], s0.v(c), fma(x[0], s0.u(c), s0.c(c)));
+      for (int c = 0; c < 3; ++c) r[c] = df_add(s0.c(c), df_add(df_mul(x[0], s0.u(c)), df_mul(x[1], s0.v(c))));
     }
     for (int k = 0; k < n && status == ST_OK; ++k) {
       const int sid = p.surface_id[o0 + k];
-      double xp[6], Cp[21], rp[3];
+      DF xp[6], rp[3];
+      double Cp[21];
       float Cpf[21];
       Dir dp;
       if (k == 0) {
@@ -648,7 +747,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         for (int c = 0; c < 3; ++c) rp[c] = r[c];
         dp = d;
       } else {
-        const Surf sa{s_surf + sid_prev * kSurfStride}, sb{s_surf + sid * kSurfStride};
+        const SurfM sa = surf_m(s_surf, sid_prev), sb = surf_m(s_surf, sid);
         JacF J;
         float sin_th, cos_inc;
         status = transport_mixed<BZ>(sa, sb, r, x, d, pd, cs, Bf, m2, h_max, p.n_iter, xp, rp, dp, J, sin_th,
@@ -689,7 +788,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         float qphi = 0.0f, qth = 0.0f;
         const float xx0 = sb.xx0f();
         if (xx0 > 0.0f) {
-          const float th0 = highland<float>(fabsf(d2f(x[4])), m2, xx0, cos_inc);
+          const float th0 = highland<float>(fabsf(x[4].hi), m2, xx0, cos_inc);
           qth = th0 * th0;
           qphi = qth / (sin_th * sin_th);
           Cpf[sy(2, 2)] += qphi;
@@ -706,13 +805,13 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
       }
       if (k == 0 || p.out_states) {
 #pragma unroll
-        for (int e = 0; e < 6; ++e) ws.d(k, XP + e) = xp[e];
+        for (int e = 0; e < 6; ++e) ws.d(k, XP + e) = df_to_d(xp[e]);
       }
       if (k > 0) {
 #pragma unroll
         for (int e = 0; e < 21; ++e) ws.d(k, CPD + e) = Cp[e];
       }
-      const Surf sk{s_surf + sid * kSurfStride};
+      const SurfM sk = surf_m(s_surf, sid);
       if (!p.is_hole[o0 + k]) {
         // gain-matrix update: gain in FP32, Joseph covariance and chi2 in FP64
         const double m0 = p.loc[o0 + k], m1 = p.loc[p.n_states + o0 + k];
@@ -724,7 +823,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           break;
         }
         const double idet = rcp_nr<1>(det);
-        const double r0 = m0 - xp[0], r1 = m1 - xp[1];
+        const double r0 = (m0 - f2d(xp[0].hi)) - f2d(xp[0].lo), r1 = (m1 - f2d(xp[1].hi)) - f2d(xp[1].lo);
         const double u = fma(S11, r0, -S01 * r1), v = fma(S00, r1, -S01 * r0);
         chi2sum += fma(r0, u, r1 * v) * idet;
         ++nmeas;
@@ -768,7 +867,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         pd.phi = dx[2];
         pd.theta = dx[3];
         pd.t = dx[5];
-        x[4] = xp[4] + f2d(dx[4]);
+        x[4] = df_add_f(xp[4], dx[4]);
       } else {
 #pragma unroll
         for (int e = 0; e < 6; ++e) dx[e] = 0.0f;
@@ -922,6 +1021,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
 
 template <bool BZ>
 struct MixedBody {
+  static constexpr int kStride = kSurfStrideM;
   static __device__ __forceinline__ void run(const FitParams& p, const double* s_surf, int i) {
     fit_one_mixed<BZ>(p, s_surf, i);
   }
@@ -940,8 +1040,11 @@ cudaError_t launch_m(const FitParams& p, int block, int min_blocks, cudaStream_t
 
 cudaError_t launch_fit_mixed(const FitParams& p, int block, int min_blocks, cudaStream_t stream, int* launched) {
   const bool bz = p.bfield[0] == 0.0 && p.bfield[1] == 0.0;
-  return bz ? launch_m<true>(p, block, min_blocks, stream, launched)
-            : launch_m<false>(p, block, min_blocks, stream, launched);
+  // this kernel's table follows the FP64 table in the packed buffer
+  FitParams q = p;
+  q.surf = p.surf + (size_t)p.n_surfaces * kSurfStride;
+  return bz ? launch_m<true>(q, block, min_blocks, stream, launched)
+            : launch_m<false>(q, block, min_blocks, stream, launched);
 }
 
 }  // namespace kfgb

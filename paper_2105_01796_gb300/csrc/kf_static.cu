@@ -36,7 +36,7 @@ using namespace kfgb;
 namespace {
 
 constexpr size_t kStaticBytes = size_t(64) << 20;  // 64 MiB per device
-constexpr size_t kSurfBytes = size_t(kMaxSurfaces) * kSurfStride * sizeof(double);
+constexpr size_t kSurfBytes = size_t(kMaxSurfaces) * kSurfPacked * sizeof(double);
 constexpr size_t kFlagBytes = 256;
 constexpr size_t kRecordBytes = kStaticBytes - kSurfBytes - kFlagBytes;
 

@@ -640,6 +640,7 @@ __device__ __forceinline__ void fit_one_variants(const FitParams& p, const doubl
 }
 
 struct VariantBody {
+  static constexpr int kStride = kSurfStride;
   static __device__ __forceinline__ void run(const FitParams& p, const double* s_surf, int i) {
     fit_one_variants(p, s_surf, i);
   }

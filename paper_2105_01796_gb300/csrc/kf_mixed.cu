@@ -831,20 +831,28 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         const float i00 = d2f(S11) * idf, i01 = -d2f(S01) * idf, i11 = d2f(S00) * idf;
         const float r0f = d2f(r0), r1f = d2f(r1);
         double K[6][2];
+        float Kf[6][2];
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
           const float c0 = Cpf[sym(e, 0)], c1 = Cpf[sym(e, 1)];
           const float k0 = c0 * i00 + c1 * i01, k1 = c0 * i01 + c1 * i11;
+          Kf[e][0] = k0;
+          Kf[e][1] = k1;
           K[e][0] = f2d(k0);
           K[e][1] = f2d(k1);
           dx[e] = k0 * r0f + k1 * r1f;
         }
-        // Joseph form, expanded: Cf = Cp + K W - (H Cp)^T K^T, W = S K^T - H Cp
-        double W[2][6];
+        // Joseph form, expanded: Cf = Cp - (H Cp)^T K^T + K W with
+        // W = S K^T - H Cp.  For the exact gain W = 0; here W is the residual
+        // of the gain equation left by the FP32 gain, O(eps32 |H Cp|), so
+        // the term K W is O(eps32 |Cp|).  FP64 takes the cancelling part
+        // (Cp - (H Cp)^T K^T, and W itself); K W is summed in FP32 onto the
+        // rounded result, which carries it to O(eps32^2 |Cp|).
+        float Wf[2][6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          W[0][j] = fma(S00, K[j][0], fma(S01, K[j][1], -Cp[sym(0, j)]));
-          W[1][j] = fma(S01, K[j][0], fma(S11, K[j][1], -Cp[sym(1, j)]));
+          Wf[0][j] = d2f(fma(S00, K[j][0], fma(S01, K[j][1], -Cp[sym(0, j)])));
+          Wf[1][j] = d2f(fma(S01, K[j][0], fma(S11, K[j][1], -Cp[sym(1, j)])));
         }
 #pragma unroll
         for (int a = 0; a < 6; ++a)
@@ -852,11 +860,9 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
           for (int b = 0; b < 6; ++b)
             if (b <= a) {
               double v = Cp[sy(a, b)];
-              v = fma(K[a][0], W[0][b], v);
-              v = fma(K[a][1], W[1][b], v);
               v = fma(-Cp[sym(0, a)], K[b][0], v);
               v = fma(-Cp[sym(1, a)], K[b][1], v);
-              Cf[sy(a, b)] = d2f(v);
+              Cf[sy(a, b)] = d2f(v) + (Kf[a][0] * Wf[0][b] + Kf[a][1] * Wf[1][b]);
             }
         // the filtered state: the prediction plus the increments, which stay
         // pending in FP32 (the point moves in the plane by (dx0, dx1)); only

@@ -26,7 +26,9 @@ FP64 path (everything in double precision):
     RTS_UPD   xs update and Cs = Cf + A dC A^T
 
 Mixed path: the double-precision part the method requires is
-    per measured state   JOSEPH + CHI2
+    per measured state   JOSEPH_64 + CHI2 (the Joseph update without its
+                         second-order term K W, which is O(eps32 |Cp|) and
+                         summed in FP32: JOSEPH_KW32)
     per smoother step    INV_COLS + NRANK   (the (phi, theta) columns of
                          Cp^-1 by a 4x4 LDL^T of the loc/q/p/t block, two
                          solves and the 2x2 Schur complement of the angle
@@ -40,6 +42,8 @@ TRANSPORT = 2 * 156 + 2 * 105
 NOISE = 15
 GAIN = 80
 JOSEPH = 2 * 12 * 2 + 2 * 21 * 4 + 3
+JOSEPH_KW32 = 2 * 21 * 2
+JOSEPH_64 = JOSEPH - JOSEPH_KW32
 CHI2 = 16
 CHOL = 2 * 35 + 15 + 6
 SOLVE6 = 6 * 2 * 36
@@ -72,8 +76,8 @@ def batch_flops(offsets, is_hole, precision, steps_per_transition=4):
     prop = tr * (steps_per_transition * RKN_STEP + FRAME + TRANSPORT + NOISE)
     if precision == 0:
         return prop + M * (GAIN + JOSEPH) + tr * (CHOL + SOLVE6 + RTS_UPD), 0
-    f64 = M * (JOSEPH + CHI2) + tr * (INV_COLS + NRANK)
-    f32 = prop + M * (GAIN - CHI2) + tr * MIXED_SMOOTH_FP32
+    f64 = M * (JOSEPH_64 + CHI2) + tr * (INV_COLS + NRANK)
+    f32 = prop + M * (GAIN - CHI2 + JOSEPH_KW32) + tr * MIXED_SMOOTH_FP32
     return f64, f32
 
 

@@ -77,7 +77,7 @@ def test_roofline_counts():
     """The roofline numerator: per-transition, per-measurement and
     per-smoother-step counts add up as documented (one track of 3 states,
     the middle one a hole; the mixed path's FP64 part is the Joseph update
-    and chi2 per measurement plus the two inverse columns and the noise-rank
+    (less its K W term) and chi2 per measurement plus the two inverse columns and the noise-rank
     terms per smoother step)."""
     from paper_2105_01796_gb300 import roofline as rf
     offsets = np.array([0, 3])
@@ -86,8 +86,9 @@ def test_roofline_counts():
     prop = 2 * (4 * rf.RKN_STEP + rf.FRAME + rf.TRANSPORT + rf.NOISE)
     assert f32 == 0 and f64 == prop + 1 * (rf.GAIN + rf.JOSEPH) + 2 * (rf.CHOL + rf.SOLVE6 + rf.RTS_UPD)
     m64, m32 = rf.batch_flops(offsets, is_hole, 1)
-    assert m64 == (rf.JOSEPH + rf.CHI2) + 2 * (rf.INV_COLS + rf.NRANK)
-    assert m32 == prop + (rf.GAIN - rf.CHI2) + 2 * rf.MIXED_SMOOTH_FP32
-    assert rf.JOSEPH == 219 and rf.INV_COLS == 141
+    # the mixed Joseph update sums its K W term (21 elements x 2 FMA) in FP32
+    assert m64 == (rf.JOSEPH - 84 + rf.CHI2) + 2 * (rf.INV_COLS + rf.NRANK)
+    assert m32 == prop + (rf.GAIN - rf.CHI2 + 84) + 2 * rf.MIXED_SMOOTH_FP32
+    assert rf.JOSEPH == 219 and rf.JOSEPH_64 == 135 and rf.INV_COLS == 141
     # inputs plus outputs once, per track and per state
     assert rf.algorithmic_bytes(offsets, is_hole) == (4 + 6 * 8 + 21 * 8 + 6 * 8 + 21 * 8 + 8 + 4 + 1) + 3 * (4 + 16 + 24 + 1)

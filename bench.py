@@ -39,17 +39,17 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 
 # DRAM traffic of the mixed kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of both wave-split launches of a 100k-track, 3.1M-state
-# step of the same workload: launch A 591.2 + 492.7 MB, launch B 505.3 +
-# 429.9 MB.  Traffic grows in proportion to the states, so a launch's traffic
+# step of the same workload: launch A 591.4 + 491.0 MB, launch B 504.1 +
+# 428.6 MB.  Traffic grows in proportion to the states, so a launch's traffic
 # is this per-state figure times its states.  It holds only for the kernel
 # sources and build flags that were captured: any change to them makes the
 # figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (591.208192e6 + 492.73472e6 + 505.311744e6 + 429.914624e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "022f42830c9d364aca24439fd2ba44b616db9a12fd4ba10d5993cf0b0c35d1ce"
+MIXED_TRAFFIC_BYTES_PER_STATE = (591.434752e6 + 490.97856e6 + 504.090624e6 + 428.584704e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "1717aecd4c1934696c890b4b2935aef40b458873305d10bf034c53ae7e8b8949"
 # the same for the FP64 path's kernel (one launch of the 100k-track step:
-# 2301.903 + 2223.674 MB)
-FP64_TRAFFIC_BYTES_PER_STATE = (2301.903e6 + 2223.674e6) / 3.1e6
-FP64_TRAFFIC_SOURCES_SHA256 = "92d99672b85a36d94abd604e7aa4753a56e2020d39cc458dbdba4d5cd4316b4b"
+# 2300.644 + 2223.372 MB)
+FP64_TRAFFIC_BYTES_PER_STATE = (2300.644e6 + 2223.372e6) / 3.1e6
+FP64_TRAFFIC_SOURCES_SHA256 = "e3e54f8dc0163ca80921eccfd9714bfe43d8986aca7fd18fec974a4dbcfb16a1"
 
 
 # FP64 flops the hardware counted (ncu: 2 x DFMA + DADD + DMUL thread
@@ -57,10 +57,10 @@ FP64_TRAFFIC_SOURCES_SHA256 = "92d99672b85a36d94abd604e7aa4753a56e2020d39cc458db
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
 # (align20, 21 states; the chi2 objective and the whole-fit objective);
 # reported while those kernels' sources match
-EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105235 + 2760501538 + 5733751609) / 1e5,
-                       "adjoint_chi2": (2 * 14277600007 + 1627199962 + 7860000020) / 1e5,
-                       "adjoint_whole": (2 * 27684799964 + 2716199927 + 11449100094) / 1e5}
-EXT_SOURCES_SHA256 = "eabc18d8ee1d1a99a2143d7d5c81e084ea83dd2e978a3580af12d1c1070d95a0"
+EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105293 + 2760501568 + 5733751638) / 1e5,
+                       "adjoint_chi2": (2 * 14277599965 + 1627199998 + 7859999954) / 1e5,
+                       "adjoint_whole": (2 * 27684799985 + 2716199995 + 11449099977) / 1e5}
+EXT_SOURCES_SHA256 = "c7643f8ccb5674640595eb535c4e91f28d8e676ce64a3545a70cdddb4aa58e01"
 
 
 def ext_kernel_sources_sha256():

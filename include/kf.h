@@ -91,8 +91,11 @@ typedef enum {
 typedef enum {
   KF_PRECISION_FP64 = 0, /* every step in double precision */
   KF_PRECISION_MIXED = 1 /* propagation, Jacobians, covariance transport and
-                            gain in float; Joseph covariance update, chi2
-                            and the smoother's inverse in double (the two
+                            gain in float; Joseph covariance update (its
+                            second-order term K W, O(eps_float |Cp|), in
+                            float), chi2 and the smoother's inverse in
+                            double; the track state as double-float pairs
+                            of floats (about 48 bits) (the two
                             columns of the inverse the smoother needs, by a
                             4x4 LDL^T of the non-angle block and the 2x2
                             Schur complement of the angle block) */

@@ -94,11 +94,11 @@ typedef enum {
                             gain in float; Joseph covariance update (its
                             second-order term K W, O(eps_float |Cp|), in
                             float), chi2 and the smoother's inverse in
-                            double; the track state as double-float pairs
-                            of floats (about 48 bits) (the two
-                            columns of the inverse the smoother needs, by a
-                            4x4 LDL^T of the non-angle block and the 2x2
-                            Schur complement of the angle block) */
+                            double (the two columns of the inverse the
+                            smoother needs, by a 4x4 LDL^T of the non-angle
+                            block and the 2x2 Schur complement of the angle
+                            block); the track state between surfaces as
+                            double-float pairs (about 48 bits) */
 } kf_precision;
 
 typedef struct {

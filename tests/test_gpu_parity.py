@@ -467,6 +467,32 @@ def test_pipelined_host_entry_equals_device_entry(handle, prec):
             assert handle.last_launch_count() >= 3
 
 
+# ---------------------------------------------------------------- far from the origin
+
+def test_translated_geometry_far_from_origin(handle):
+    """Moving every surface by the same vector leaves every local quantity
+    (seeds, measurements, the constant field's effect) unchanged, so the fit
+    must not change.  At 10 m from the origin a float position would be off
+    by about 1e-3 mm (tens of sigma of a 30 um hit); the mixed path carries
+    the point, direction and angles as double-float pairs and must stay
+    within its contract of the oracle and of the untranslated fit."""
+    ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel30_100k"], 2000))
+    moved = dict(ev)
+    moved["center"] = ev["center"] + np.array([[9000.0], [-7000.0], [11000.0]])
+    r = oracle.fit_batch(moved)
+    r0 = oracle.fit_batch(ev)
+    ok = r0["status"] == 0
+    # the oracle itself: translation moves its FP64 results by rounding only
+    assert np.array_equal(r["status"], r0["status"])
+    assert param_err(r["params"][:, ok], r0["params"][:, ok], r0["cov"][:, ok]).max() < 1e-9
+    for prec in (FP64, MIXED):
+        g = gpu_fit(handle, moved, prec)
+        compare(g, r, prec)
+        g0 = gpu_fit(handle, ev, prec)
+        assert param_err(g["params"][:, ok], g0["params"][:, ok], g0["cov"][:, ok]).max() < TOL[prec][0]
+        assert cov_err(g["cov"][:, ok], g0["cov"][:, ok]).max() < TOL[prec][1]
+
+
 # ---------------------------------------------------------------- track teams (FP64)
 
 @pytest.mark.parametrize("team", [2, 4])

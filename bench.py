@@ -815,7 +815,7 @@ def run_ours(args, rank, world, local):
                      "fp64_flops_per_launch": f64, "fp32_flops_per_launch": f32,
                      "algorithmic_bytes_per_launch": nbytes,
                      "traffic_note": ("ncu capture of both launches of a 100k-track step of this kernel (wave split, 168 registers); "
-                                      "mostly the smoother's per-state record round trip (300 B each way)")
+                                      "mostly the smoother's per-state record round trip (216 B each way)")
                      if traffic else "kernel changed since the last ncu capture"},
         "cpu_baseline": cpu,
         "accuracy": acc,

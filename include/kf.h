@@ -308,7 +308,7 @@ int kf_fit_host(kf_handle* handle, const kf_tracks* tracks,
  * the packed surface table (up to 1024 surfaces) and the per-state records;
  * larger batches run as several launches on `stream`.  Returns KF_ESIZE when
  * n_surfaces > 1024 or when one track's records (max_states x 720 B in FP64,
- * max_states x 348 B in mixed precision) do not fit the block, and
+ * max_states x 264 B in mixed precision) do not fit the block, and
  * KF_EUNSUPPORTED for schedules other than GRID and PERSISTENT and for the
  * method variants.  Device pointers, asynchronous on `stream`, same outputs
  * as kf_fit_ex.

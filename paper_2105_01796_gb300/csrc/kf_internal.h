@@ -29,14 +29,15 @@ constexpr int kMaxSurfaces = 1024;  // 192 KiB of shared memory (FP64 table)
 // Per-state record the forward pass writes and the RTS pass reads back.
 // FP64 path, all in ws64:  xp 6 | xf 6 | Cp 21 | Cf 21 | Bm 36   (90 doubles)
 //   Bm = F_k * Cf_{k-1}: the right-hand side of the smoother-gain solve.
-// Mixed path, ws64:        xp 6 | Cp 21                           (27 doubles)
-//             ws32:        F 25 | q_phi | q_theta | dxf 6         (33 floats)
+// Mixed path, ws64:        xp 6                                   (6 doubles)
+//             ws32:        F 25 | q_phi | q_theta | dxf 6 | Cp 21 (54 floats)
 //   xp is written for state 0 always and for the others only when smoothed
 //   states are output.
 //   F_k: rows loc0, loc1, phi, theta over columns 0..4 (20), then the time
 //   row over columns 0..4 (5); q = the multiple-scattering variances added to
 //   Var(phi) and Var(theta) at state k; dxf = x_f - x_p (the filter's
-//   increment, zero on a hole).
+//   increment, zero on a hole); Cp = the predicted covariance of state k
+//   (FP32 products, so exact as floats; states k >= 1).
 // Register-cap variants of the fit kernels ("min_blocks"): variant 1 (the
 // default) may use 255 registers, 3 caps at 168 and 4 at 128, i.e. the
 // registers of 1, 3 or 4 CTAs of 128 threads per SM. Each variant accepts
@@ -47,8 +48,8 @@ constexpr int max_threads_of(int min_blocks) { return min_blocks == 4 ? 512 : mi
 inline int max_block(bool mixed, int min_blocks) { return max_threads_of(mixed ? min_blocks : 1); }
 
 constexpr int kRec64Fp64 = 90;
-constexpr int kRec64Mixed = 27;
-constexpr int kRec32Mixed = 33;
+constexpr int kRec64Mixed = 6;
+constexpr int kRec32Mixed = 54;
 
 struct FitParams {
   int32_t n_tracks;        // tracks in this launch (chunk)

@@ -40,13 +40,12 @@ namespace {
 using namespace dev;
 
 // per-state record: x_p in FP64 (written for state 0, and for every state
-// when the smoothed states are output) and the predicted covariance in FP64
-// (its values are FP32-exact, but the smoother's FP64 inverse would convert
-// all 21 again: storing the doubles is faster than the 84 B it saves); the
-// transport Jacobian, the scattering variances and the filter increment in
-// FP32
-constexpr int XP = 0, CPD = 6;                                 // ws64 fields
-constexpr int FJ = 0, QPHI = 25, QTH = 26, DXF = 27;          // ws32 fields
+// when the smoothed states are output); in FP32 the transport Jacobian, the
+// scattering variances, the filter increment and the predicted covariance
+// (its values are FP32 products, so the float copy is exact; the smoother
+// promotes them for its FP64 inverse)
+constexpr int XP = 0;                                           // ws64 fields
+constexpr int FJ = 0, QPHI = 25, QTH = 26, DXF = 27, CPF = 33;  // ws32 fields
 
 // ---- double-float ("df") values: an unevaluated sum hi + lo of two floats
 // with |lo| <= ulp(hi) / 2, about 48 significant bits.  Error-free
@@ -809,7 +808,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
       }
       if (k > 0) {
 #pragma unroll
-        for (int e = 0; e < 21; ++e) ws.d(k, CPD + e) = Cp[e];
+        for (int e = 0; e < 21; ++e) ws.f(k, CPF + e) = Cpf[e];
       }
       const SurfM sk = surf_m(s_surf, sid);
       if (!p.is_hole[o0 + k]) {
@@ -909,7 +908,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         // FP64: the (phi, theta) columns of Cp_{k+1}^-1
         double Cp1[21];
 #pragma unroll
-        for (int e = 0; e < 21; ++e) Cp1[e] = ws.d(k + 1, CPD + e);
+        for (int e = 0; e < 21; ++e) Cp1[e] = f2d(ws.f(k + 1, CPF + e));
         double w[2][6];
         if (!angle_columns_of_inverse(Cp1, w)) {
           status = ST_NON_SPD;

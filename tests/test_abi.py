@@ -49,10 +49,10 @@ def test_host_only_entry_points(lib):
     assert o.h_max == 50.0 and o.n_iter == 3 and o.block == 128
     assert lib.kf_strerror(0) == b"success"
     assert lib.kf_strerror(-1) == b"invalid argument"
-    # 90 doubles per state (FP64), 27 doubles + 33 floats (mixed)
+    # 90 doubles per state (FP64), 6 doubles + 54 floats (mixed)
     assert kf.kf_workspace_size(1000, 31, o) == 1000 * 31 * 720 + 256
     om = kf.kf_default_options(kf.KF_PRECISION_MIXED)
-    assert kf.kf_workspace_size(1000, 31, om) == 1000 * 31 * (27 * 8 + 33 * 4) + 256
+    assert kf.kf_workspace_size(1000, 31, om) == 1000 * 31 * (6 * 8 + 54 * 4) + 256
     # a workspace cap splits the batch into chunks
     oc = kf.kf_default_options(workspace_bytes=720 * 31 * 100)
     assert kf.kf_workspace_size(1000, 31, oc) == 100 * 31 * 720 + 256

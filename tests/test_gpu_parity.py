@@ -184,7 +184,7 @@ def test_empty_batch(handle):
 def test_chunked_equals_single_launch(handle, prec):
     ev = synth.make_event(synth.scaled(synth.WORKLOADS["tel30_100k"], 1500))
     a = gpu_fit(handle, ev, prec)
-    per_track = 31 * (720 if prec == FP64 else 27 * 8 + 33 * 4)
+    per_track = 31 * (720 if prec == FP64 else 6 * 8 + 54 * 4)
     b = gpu_fit(handle, ev, prec, workspace_bytes=per_track * 400)  # 4 chunks
     assert handle.last_launch_count() == 1 + 4
     for k in ("params", "cov", "chi2", "ndf", "status"):
@@ -456,7 +456,7 @@ def test_pipelined_host_entry_equals_device_entry(handle, prec):
     for n in (30001, 90001):
         ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], n))
         ref = gpu_fit(handle, ev, prec, with_states=True, schedule=kf.KF_SCHEDULE_PERSISTENT)
-        per_track = 31 * (720 if prec == FP64 else 27 * 8 + 33 * 4)
+        per_track = 31 * (720 if prec == FP64 else 6 * 8 + 54 * 4)
         for sched, cap in ((kf.KF_SCHEDULE_PERSISTENT, 0), (kf.KF_SCHEDULE_SORTED, 0), (kf.KF_SCHEDULE_GRID, 0),
                            (kf.KF_SCHEDULE_WAVES, 0), (kf.KF_SCHEDULE_PERSISTENT, 7000 * per_track),
                            (kf.KF_SCHEDULE_GRID, 7000 * per_track), (kf.KF_SCHEDULE_WAVES, 7000 * per_track)):

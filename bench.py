@@ -39,17 +39,17 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 
 # DRAM traffic of the mixed kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of both wave-split launches of a 100k-track, 3.1M-state
-# step of the same workload: launch A 591.4 + 491.0 MB, launch B 504.1 +
-# 428.6 MB.  Traffic grows in proportion to the states, so a launch's traffic
+# step of the same workload: launch A 441.8 + 356.4 MB, launch B 373.5 +
+# 309.8 MB.  Traffic grows in proportion to the states, so a launch's traffic
 # is this per-state figure times its states.  It holds only for the kernel
 # sources and build flags that were captured: any change to them makes the
 # figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (591.434752e6 + 490.97856e6 + 504.090624e6 + 428.584704e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "1717aecd4c1934696c890b4b2935aef40b458873305d10bf034c53ae7e8b8949"
+MIXED_TRAFFIC_BYTES_PER_STATE = (441.766912e6 + 356.435712e6 + 373.46304e6 + 309.7728e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "e14ad798c43989cf9f02586c9bffcedd04608dcf65b0d4b3d1ebc90945a56049"
 # the same for the FP64 path's kernel (one launch of the 100k-track step:
-# 2300.644 + 2223.372 MB)
-FP64_TRAFFIC_BYTES_PER_STATE = (2300.644e6 + 2223.372e6) / 3.1e6
-FP64_TRAFFIC_SOURCES_SHA256 = "e3e54f8dc0163ca80921eccfd9714bfe43d8986aca7fd18fec974a4dbcfb16a1"
+# 2300.176 + 2223.512 MB)
+FP64_TRAFFIC_BYTES_PER_STATE = (2300.176e6 + 2223.512e6) / 3.1e6
+FP64_TRAFFIC_SOURCES_SHA256 = "affacdf943c537137b994d87932121664f40f2669338ed8a1f0e2ed1e6a1a71f"
 
 
 # FP64 flops the hardware counted (ncu: 2 x DFMA + DADD + DMUL thread
@@ -57,10 +57,10 @@ FP64_TRAFFIC_SOURCES_SHA256 = "e3e54f8dc0163ca80921eccfd9714bfe43d8986aca7fd18fe
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
 # (align20, 21 states; the chi2 objective and the whole-fit objective);
 # reported while those kernels' sources match
-EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105293 + 2760501568 + 5733751638) / 1e5,
-                       "adjoint_chi2": (2 * 14277599965 + 1627199998 + 7859999954) / 1e5,
-                       "adjoint_whole": (2 * 27684799985 + 2716199995 + 11449099977) / 1e5}
-EXT_SOURCES_SHA256 = "c7643f8ccb5674640595eb535c4e91f28d8e676ce64a3545a70cdddb4aa58e01"
+EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105241 + 2760501556 + 5733751595) / 1e5,
+                       "adjoint_chi2": (2 * 14277599970 + 1627200005 + 7860000050) / 1e5,
+                       "adjoint_whole": (2 * 27684799965 + 2716200077 + 11449099992) / 1e5}
+EXT_SOURCES_SHA256 = "241cb78994f8d28d7fa1d4415384aee0d77fa8fb81cd85077dcc460bd2008374"
 
 
 def ext_kernel_sources_sha256():

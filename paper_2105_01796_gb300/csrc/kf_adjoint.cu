@@ -934,7 +934,7 @@ struct GradParams {
   double* ckpt;         // [n_ckpt][27][n_tracks]: filtered checkpoints
   double* sck;          // [n_ckpt + 1][27][n_tracks]: smoothed checkpoints
   double* sadj;         // [max_states][kSmRec][n_tracks]: the smoother's adjoint contributions
-  double* pipe;         // [2][kSlot][n_tracks]: hand-off slots of the pipelined reverse (or null)
+  double* pipe;         // [kPipeScratch][n_tracks]: hand-off slots of the pipelined form (or null)
   int32_t n_ckpt;
 };
 
@@ -1574,6 +1574,58 @@ __device__ __forceinline__ void transition_reverse(const GradParams& g, const Tr
 constexpr int kSlotFixed = 6 + 21 + 6 + 21 + 25 + 3 + 27;
 constexpr int kSlot = kSlotFixed + 16 * kTape;
 
+// Hand-off slot of one recomputed segment in the pipelined smoother passes:
+// for each of its kSeg transitions the filtered state and covariance, the
+// prediction and its covariance, and the transport Jacobian
+// ([fx 6 | fC 21 | px 6 | pC 21 | J 25] doubles per transition and track).
+constexpr int kSegRec = 6 + 21 + 6 + 21 + 25;
+constexpr int kSegSlot = kSeg * kSegRec;
+// the pipelined form's hand-off scratch per track: two transition slots
+// (pass B) or two segment slots and the last filtered state (passes S, R)
+constexpr int kPipeScratch = 2 * kSlot > 2 * kSegSlot + 27 ? 2 * kSlot : 2 * kSegSlot + 27;
+
+__device__ __forceinline__ void seg_write(double* slot, size_t TL, int tl, int L, const double fx[kSeg][6],
+                                          const double fC[kSeg][21], const double px[kSeg][6],
+                                          const double pC[kSeg][21], const JacS<double> pJ[kSeg]) {
+#pragma unroll 1
+  for (int i = 0; i < L; ++i) {
+    double* q = slot + (size_t)i * kSegRec * TL + tl;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) q[(size_t)e * TL] = fx[i][e];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) q[(size_t)(6 + e) * TL] = fC[i][e];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) q[(size_t)(27 + e) * TL] = px[i][e];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) q[(size_t)(33 + e) * TL] = pC[i][e];
+#pragma unroll
+    for (int e = 0; e < 20; ++e) q[(size_t)(54 + e) * TL] = pJ[i].f[e / 5][e % 5];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) q[(size_t)(74 + e) * TL] = pJ[i].ft[e];
+  }
+}
+
+__device__ __forceinline__ void seg_read(const double* slot, size_t TL, int tl, int L, double fx[kSeg][6],
+                                         double fC[kSeg][21], double px[kSeg][6], double pC[kSeg][21],
+                                         JacS<double> pJ[kSeg]) {
+#pragma unroll 1
+  for (int i = 0; i < L; ++i) {
+    const double* q = slot + (size_t)i * kSegRec * TL + tl;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) fx[i][e] = q[(size_t)e * TL];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) fC[i][e] = q[(size_t)(6 + e) * TL];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) px[i][e] = q[(size_t)(27 + e) * TL];
+#pragma unroll
+    for (int e = 0; e < 21; ++e) pC[i][e] = q[(size_t)(33 + e) * TL];
+#pragma unroll
+    for (int e = 0; e < 20; ++e) pJ[i].f[e / 5][e % 5] = q[(size_t)(54 + e) * TL];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) pJ[i].ft[e] = q[(size_t)(74 + e) * TL];
+  }
+}
+
 __device__ __forceinline__ void slot_write(double* slot, size_t TL, int tl, const TransitionFwd& tf) {
   int o = 0;
   auto put = [&](double v) { slot[(size_t)(o++) * TL + tl] = v; };
@@ -1694,11 +1746,14 @@ __device__ __forceinline__ void slot_read(const double* slot, size_t TL, int tl,
 //      recomputed from the checkpoints, transports re-run with a tape), with
 //      sadj added in at every state.
 // PIPE: a CTA of two warps per 32 tracks (lane l of both on track l).  The
-// second warp runs passes F, S, R and, in B, the forward half of every
-// transition (the segment's recompute, the taped transport) one transition
-// ahead; the first warp runs the reverse half (the reverse of the update and
-// of the transport) on what the second left in a slot (two slots, one
-// barrier per transition).  For batches too small to fill the GPU: a warp
+// second warp runs pass F; in S and R it recomputes each segment one segment
+// ahead of the first warp, which runs the RTS steps and their reverse on
+// what the second left in a segment slot (two slots, one barrier per
+// segment); in B it runs the forward half of every transition (the
+// segment's recompute, the taped transport) one transition ahead, and the
+// first warp the reverse half (the reverse of the update and of the
+// transport) on what the second left in a slot (two slots, one barrier per
+// transition).  For batches too small to fill the GPU: a warp
 // instruction costs an SM sub-partition's FP64 pipe the same at any number
 // of active lanes, so the split has to go across warps.
 template <int MINB, bool PIPE>
@@ -1711,7 +1766,7 @@ __global__ void __launch_bounds__(PIPE ? 64 : max_threads_of(MINB), 1) kf_grad_k
                                      p.error_flag, p.wait_limit, p.skip_stage_copy != 0);
   const int t = PIPE ? blockIdx.x * 32 + (int)(threadIdx.x & 31) : blockIdx.x * blockDim.x + threadIdx.x;
   const bool in_range = t < p.n_tracks;
-  // the warp that runs passes F, S and R (both warps without PIPE)
+  // the warp that runs pass F (both warps without PIPE)
   const bool run_fwd = !PIPE || threadIdx.x >= 32;
   TrackIO io;
   io.g = &g;
@@ -1798,103 +1853,255 @@ __global__ void __launch_bounds__(PIPE ? 64 : max_threads_of(MINB), 1) kf_grad_k
   // s1 = min(s0 + kSeg, n - 1); its filtered checkpoint is state s0
   const int n_seg_trk = status == ST_OK ? (n - 1 + kSeg - 1) / kSeg : 0;
 
-  // ---------------------------------------------------------- S: smoother
-  if (sm_fwd && status == ST_OK && run_fwd) {
-    double xs[6], Cs[21];  // x_s,n-1 = x_f,n-1
-#pragma unroll
-    for (int e = 0; e < 6; ++e) xs[e] = x[e];
-#pragma unroll
-    for (int e = 0; e < 21; ++e) Cs[e] = C[e];
-    if (sm_adj) {
-#pragma unroll
-      for (int e = 0; e < 6; ++e) io.sck(n_seg_trk, e) = xs[e];
-#pragma unroll
-      for (int e = 0; e < 21; ++e) io.sck(n_seg_trk, 6 + e) = Cs[e];
-    }
-#pragma unroll 1
-    for (int sg = n_seg_trk - 1; sg >= 0 && status == ST_OK; --sg) {
-      const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
-      double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
-      JacS<double> pJ[kSeg];
-      recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
-#pragma unroll 1
-      for (int i = L - 1; i >= 0 && status == ST_OK; --i)
-        status = rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xs, Cs, nullptr);
-      if (sm_adj && sg > 0) {
-#pragma unroll
-        for (int e = 0; e < 6; ++e) io.sck(sg, e) = xs[e];
-#pragma unroll
-        for (int e = 0; e < 21; ++e) io.sck(sg, 6 + e) = Cs[e];
+  if constexpr (!PIPE) {
+    // ---------------------------------------------------------- S: smoother
+    if (sm_fwd && status == ST_OK && run_fwd) {
+      double xs[6], Cs[21];  // x_s,n-1 = x_f,n-1
+  #pragma unroll
+      for (int e = 0; e < 6; ++e) xs[e] = x[e];
+  #pragma unroll
+      for (int e = 0; e < 21; ++e) Cs[e] = C[e];
+      if (sm_adj) {
+  #pragma unroll
+        for (int e = 0; e < 6; ++e) io.sck(n_seg_trk, e) = xs[e];
+  #pragma unroll
+        for (int e = 0; e < 21; ++e) io.sck(n_seg_trk, 6 + e) = Cs[e];
       }
+  #pragma unroll 1
+      for (int sg = n_seg_trk - 1; sg >= 0 && status == ST_OK; --sg) {
+        const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+        double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+        JacS<double> pJ[kSeg];
+        recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
+  #pragma unroll 1
+        for (int i = L - 1; i >= 0 && status == ST_OK; --i)
+          status = rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xs, Cs, nullptr);
+        if (sm_adj && sg > 0) {
+  #pragma unroll
+          for (int e = 0; e < 6; ++e) io.sck(sg, e) = xs[e];
+  #pragma unroll
+          for (int e = 0; e < 21; ++e) io.sck(sg, 6 + e) = Cs[e];
+        }
+      }
+      if (in_range && g.out_params)
+  #pragma unroll
+        for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = status == ST_OK ? xs[e] : qnan();
+      if (in_range && g.out_cov)
+  #pragma unroll
+        for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = status == ST_OK ? Cs[e] : qnan();
+    } else if (in_range && run_fwd) {
+      if (g.out_params)
+        for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = qnan();
+      if (g.out_cov)
+        for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = qnan();
     }
-    if (in_range && g.out_params)
-#pragma unroll
-      for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = status == ST_OK ? xs[e] : qnan();
-    if (in_range && g.out_cov)
-#pragma unroll
-      for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = status == ST_OK ? Cs[e] : qnan();
-  } else if (in_range && run_fwd) {
-    if (g.out_params)
-      for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = qnan();
-    if (g.out_cov)
-      for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = qnan();
-  }
-  if (in_range && g.chi2 && run_fwd) g.chi2[tg] = status == ST_OK ? chi2sum : qnan();
+    if (in_range && g.chi2 && run_fwd) g.chi2[tg] = status == ST_OK ? chi2sum : qnan();
 
-  // ---------------------------------------------------------- R: smoother reverse
-  if (sm_adj && status == ST_OK && run_fwd) {
-    double lxs[6], Ls[6][6];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) lxs[e] = g.dl_dparams ? g.dl_dparams[e * TG + tg] : 0.0;
-    // the weight W_e of a packed covariance element e = (i, j), i > j, stands
-    // for both C_ij and C_ji in the full-matrix convention: W_e / 2 each
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j <= i; ++j) {
-        const double v = g.dl_dcov ? g.dl_dcov[sy(i, j) * TG + tg] : 0.0;
-        Ls[i][j] = Ls[j][i] = (i == j) ? v : 0.5 * v;
+    // ---------------------------------------------------------- R: smoother reverse
+    if (sm_adj && status == ST_OK && run_fwd) {
+      double lxs[6], Ls[6][6];
+  #pragma unroll
+      for (int e = 0; e < 6; ++e) lxs[e] = g.dl_dparams ? g.dl_dparams[e * TG + tg] : 0.0;
+      // the weight W_e of a packed covariance element e = (i, j), i > j, stands
+      // for both C_ij and C_ji in the full-matrix convention: W_e / 2 each
+  #pragma unroll
+      for (int i = 0; i < 6; ++i)
+  #pragma unroll
+        for (int j = 0; j <= i; ++j) {
+          const double v = g.dl_dcov ? g.dl_dcov[sy(i, j) * TG + tg] : 0.0;
+          Ls[i][j] = Ls[j][i] = (i == j) ? v : 0.5 * v;
+        }
+  #pragma unroll 1
+      for (int sg = 0; sg < n_seg_trk; ++sg) {
+        const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+        double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+        JacS<double> pJ[kSeg];
+        recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
+        double xs[6], Cs[21];
+  #pragma unroll
+        for (int e = 0; e < 6; ++e) xs[e] = io.sck(sg + 1, e);
+  #pragma unroll
+        for (int e = 0; e < 21; ++e) Cs[e] = io.sck(sg + 1, 6 + e);
+        RtsKeep keep[kSeg];
+  #pragma unroll 1
+        for (int i = L - 1; i >= 0; --i) rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xs, Cs, &keep[i]);
+  #pragma unroll 1
+        for (int i = 0; i < L; ++i) {
+          double c[kSmRec];
+          rts_step_rev(fC[i], keep[i], lxs, Ls, c);
+          const int k = s0 + i;
+  #pragma unroll
+          for (int e = 0; e < kSmXP; ++e) io.sadj(k, e) = c[e];
+  #pragma unroll
+          for (int e = kSmXP; e < kSmRec; ++e) io.sadj(k + 1, e) = c[e];
+        }
       }
+      // the last state: x_s,n-1 = x_f,n-1, C_s,n-1 = C_f,n-1
+  #pragma unroll
+      for (int e = 0; e < 6; ++e) io.sadj(n - 1, kSmXF + e) = lxs[e];
+  #pragma unroll
+      for (int i = 0; i < 6; ++i)
+  #pragma unroll
+        for (int j = 0; j <= i; ++j) io.sadj(n - 1, kSmCF + sy(i, j)) = Ls[i][j];
+    }
+  } else {
+    // Pipelined smoother passes: the forward warp recomputes the filter's
+    // segments (transports and updates from the checkpoints) one segment
+    // ahead; the other warp runs the RTS steps on what it left in one of two
+    // segment slots (one barrier per segment, both warps the same count).
+    const bool fwd_warp = threadIdx.x >= 32;
+    const int lane = threadIdx.x & 31;
+    __shared__ int s_status[32];
+    // the filter's status, from the forward warp to the other
+    if (fwd_warp) s_status[lane] = status;
+    __syncthreads();
+    status = s_status[lane];
+    __syncthreads();
+    const int nseg_f = status == ST_OK ? n_seg_trk : 0;  // the same in both warps
+    auto warp_max = [](int v) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+      return v;
+    };
+    const size_t seg_stride = (size_t)kSegSlot * io.TL;
+    double* const hand = g.pipe + 2 * seg_stride;  // the last filtered state
+    // ---------------------------------------------------------- S: smoother
+    double xs[6], Cs[21];
+    if (sm_fwd) {
+      if (fwd_warp && status == ST_OK) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) hand[(size_t)e * io.TL + io.tl] = x[e];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) hand[(size_t)(6 + e) * io.TL + io.tl] = C[e];
+      }
+      __syncthreads();
+      if (!fwd_warp && status == ST_OK) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) xs[e] = hand[(size_t)e * io.TL + io.tl];
+#pragma unroll
+        for (int e = 0; e < 21; ++e) Cs[e] = hand[(size_t)(6 + e) * io.TL + io.tl];
+        if (sm_adj) {
+#pragma unroll
+          for (int e = 0; e < 6; ++e) io.sck(nseg_f, e) = xs[e];
+#pragma unroll
+          for (int e = 0; e < 21; ++e) io.sck(nseg_f, 6 + e) = Cs[e];
+        }
+      }
+      const int n_items = warp_max(nseg_f);
+      for (int j = 0; j <= n_items; ++j) {
+        if (fwd_warp && j < n_items) {
+          const int sg = n_items - 1 - j;
+          if (sg < nseg_f) {
+            const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+            double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+            JacS<double> pJ[kSeg];
+            recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
+            seg_write(g.pipe + (size_t)(j & 1) * seg_stride, io.TL, io.tl, L, fx, fC, px, pC, pJ);
+          }
+        }
+        if (!fwd_warp && j >= 1) {
+          const int sg = n_items - j;
+          if (sg < nseg_f && status == ST_OK) {
+            const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+            double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+            JacS<double> pJ[kSeg];
+            seg_read(g.pipe + (size_t)((j - 1) & 1) * seg_stride, io.TL, io.tl, L, fx, fC, px, pC, pJ);
 #pragma unroll 1
-    for (int sg = 0; sg < n_seg_trk; ++sg) {
-      const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
-      double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
-      JacS<double> pJ[kSeg];
-      recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
-      double xs[6], Cs[21];
+            for (int i = L - 1; i >= 0 && status == ST_OK; --i)
+              status = rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xs, Cs, nullptr);
+            if (sm_adj && sg > 0) {
 #pragma unroll
-      for (int e = 0; e < 6; ++e) xs[e] = io.sck(sg + 1, e);
+              for (int e = 0; e < 6; ++e) io.sck(sg, e) = xs[e];
 #pragma unroll
-      for (int e = 0; e < 21; ++e) Cs[e] = io.sck(sg + 1, 6 + e);
-      RtsKeep keep[kSeg];
-#pragma unroll 1
-      for (int i = L - 1; i >= 0; --i) rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xs, Cs, &keep[i]);
-#pragma unroll 1
-      for (int i = 0; i < L; ++i) {
-        double c[kSmRec];
-        rts_step_rev(fC[i], keep[i], lxs, Ls, c);
-        const int k = s0 + i;
+              for (int e = 0; e < 21; ++e) io.sck(sg, 6 + e) = Cs[e];
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (!fwd_warp && in_range) {
+        if (g.out_params)
 #pragma unroll
-        for (int e = 0; e < kSmXP; ++e) io.sadj(k, e) = c[e];
+          for (int e = 0; e < 6; ++e) g.out_params[e * TG + tg] = status == ST_OK ? xs[e] : qnan();
+        if (g.out_cov)
 #pragma unroll
-        for (int e = kSmXP; e < kSmRec; ++e) io.sadj(k + 1, e) = c[e];
+          for (int e = 0; e < 21; ++e) g.out_cov[e * TG + tg] = status == ST_OK ? Cs[e] : qnan();
       }
     }
-    // the last state: x_s,n-1 = x_f,n-1, C_s,n-1 = C_f,n-1
+    // ---------------------------------------------------------- R: smoother reverse
+    if (sm_adj) {
+      double lxs[6], Ls[6][6];
+      if (!fwd_warp) {
 #pragma unroll
-    for (int e = 0; e < 6; ++e) io.sadj(n - 1, kSmXF + e) = lxs[e];
+        for (int e = 0; e < 6; ++e) lxs[e] = g.dl_dparams ? g.dl_dparams[e * TG + tg] : 0.0;
+        // W_e of a packed off-diagonal element stands for C_ij and C_ji: W_e / 2 each
 #pragma unroll
-    for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j <= i; ++j) io.sadj(n - 1, kSmCF + sy(i, j)) = Ls[i][j];
-  }
-  if (PIPE) {
-    // the reverse warp learns each track's status from the forward warp
-    __shared__ int s_status[32];
-    if (run_fwd) s_status[threadIdx.x & 31] = status;
+          for (int j = 0; j <= i; ++j) {
+            const double v = g.dl_dcov ? g.dl_dcov[sy(i, j) * TG + tg] : 0.0;
+            Ls[i][j] = Ls[j][i] = (i == j) ? v : 0.5 * v;
+          }
+      }
+      const int n_items = warp_max(nseg_f);
+      for (int j = 0; j <= n_items; ++j) {
+        if (fwd_warp && j < n_items) {
+          const int sg = j;
+          if (sg < nseg_f) {
+            const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+            double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+            JacS<double> pJ[kSeg];
+            recompute_segment(io, s_surf, sg, s0, L, fx, fC, px, pC, pJ);
+            seg_write(g.pipe + (size_t)(j & 1) * seg_stride, io.TL, io.tl, L, fx, fC, px, pC, pJ);
+          }
+        }
+        if (!fwd_warp && j >= 1) {
+          const int sg = j - 1;
+          if (sg < nseg_f && status == ST_OK) {
+            const int s0 = sg * kSeg, L = min(s0 + kSeg, n - 1) - s0;
+            double fx[kSeg][6], fC[kSeg][21], px[kSeg][6], pC[kSeg][21];
+            JacS<double> pJ[kSeg];
+            seg_read(g.pipe + (size_t)((j - 1) & 1) * seg_stride, io.TL, io.tl, L, fx, fC, px, pC, pJ);
+            double xr[6], Cr[21];
+#pragma unroll
+            for (int e = 0; e < 6; ++e) xr[e] = io.sck(sg + 1, e);
+#pragma unroll
+            for (int e = 0; e < 21; ++e) Cr[e] = io.sck(sg + 1, 6 + e);
+            RtsKeep keep[kSeg];
+#pragma unroll 1
+            for (int i = L - 1; i >= 0; --i) rts_step_fwd(fx[i], fC[i], px[i], pC[i], pJ[i], xr, Cr, &keep[i]);
+#pragma unroll 1
+            for (int i = 0; i < L; ++i) {
+              double c[kSmRec];
+              rts_step_rev(fC[i], keep[i], lxs, Ls, c);
+              const int k = s0 + i;
+#pragma unroll
+              for (int e = 0; e < kSmXP; ++e) io.sadj(k, e) = c[e];
+#pragma unroll
+              for (int e = kSmXP; e < kSmRec; ++e) io.sadj(k + 1, e) = c[e];
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (!fwd_warp && status == ST_OK) {
+        // the last state: x_s,n-1 = x_f,n-1, C_s,n-1 = C_f,n-1
+#pragma unroll
+        for (int e = 0; e < 6; ++e) io.sadj(n - 1, kSmXF + e) = lxs[e];
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+#pragma unroll
+          for (int j = 0; j <= i; ++j) io.sadj(n - 1, kSmCF + sy(i, j)) = Ls[i][j];
+      }
+    }
+    // the smoother's status (an RTS step may fail), back to the forward warp
     __syncthreads();
-    status = s_status[threadIdx.x & 31];
+    if (!fwd_warp) s_status[lane] = status;
+    __syncthreads();
+    status = s_status[lane];
+    if (in_range && g.chi2 && fwd_warp) g.chi2[tg] = status == ST_OK ? chi2sum : qnan();
   }
+
   // ---------------------------------------------------------- B: filter reverse
   double lf[6] = {0, 0, 0, 0, 0, 0};
   double Lf[6][6];
@@ -2072,7 +2279,7 @@ size_t grad_scratch_doubles(int max_states, bool smoother, bool smoother_adjoint
   const size_t n_ckpt = ((size_t)max_states + kSeg - 1) / kSeg;
   size_t d = 27 * n_ckpt;
   if (smoother_adjoint) d += 27 * (n_ckpt + 1) + (size_t)kSmRec * (size_t)max_states;
-  if (pipelined) d += 2 * (size_t)kSlot;
+  if (pipelined) d += (size_t)kPipeScratch;
   (void)smoother;  // the smoother alone keeps no per-track scratch
   return d;
 }

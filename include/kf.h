@@ -412,7 +412,9 @@ typedef struct {
  * kf_chi2_grad); 2 = the pipelined form, for batches too small to fill the
  * GPU: two warps per 32 tracks, one running the forward half of the filter's
  * reverse sweep (the segments' recompute and the taped transports) one
- * transition ahead of the other, which runs the reverse half (results equal
+ * transition ahead of the other, which runs the reverse half, and in the
+ * smoother's passes recomputing each segment one segment ahead of the RTS
+ * steps and their reverse, which the other runs (results equal
  * the one-thread form's, up to the summation order of the alignment
  * gradient); 0 (the default, and opt == NULL) = the pipelined form while
  * 2 x ceil(T / 32) warps fit in one warp per SM sub-partition (T <= 9728 on

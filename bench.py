@@ -57,10 +57,10 @@ FP64_TRAFFIC_SOURCES_SHA256 = "affacdf943c537137b994d87932121664f40f2669338ed8a1
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
 # (align20, 21 states; the chi2 objective and the whole-fit objective);
 # reported while those kernels' sources match
-EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105241 + 2760501556 + 5733751595) / 1e5,
-                       "adjoint_chi2": (2 * 14277599970 + 1627200005 + 7860000050) / 1e5,
-                       "adjoint_whole": (2 * 27684799965 + 2716200077 + 11449099992) / 1e5}
-EXT_SOURCES_SHA256 = "241cb78994f8d28d7fa1d4415384aee0d77fa8fb81cd85077dcc460bd2008374"
+EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105286 + 2760501541 + 5733751617) / 1e5,
+                       "adjoint_chi2": (2 * 14277600047 + 1627199952 + 7859999977) / 1e5,
+                       "adjoint_whole": (2 * 27684800044 + 2716199931 + 11449099961) / 1e5}
+EXT_SOURCES_SHA256 = "b62e8842c497ae9245055c6dc4451dd01c49b335bd0b77988fc7b6b700483e88"
 
 
 def ext_kernel_sources_sha256():

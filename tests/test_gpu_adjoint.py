@@ -334,7 +334,10 @@ def test_whole_fit_gradients_uneven_tracks_with_holes(handle):
 def test_pipelined_adjoint_equals_sequential(handle, objective):
     """team_warps = 2 runs the filter's reverse on two warps per 32 tracks
     (the forward half one transition ahead on one, the reverse half on the
-    other): the same arithmetic, so the same chi2, smoothed outputs and seed
+    other) and the smoother's passes likewise (each segment recomputed one
+    segment ahead of its RTS steps; with the chi2 objective the smoothed
+    outputs alone, with the whole one their reverse as well): the same
+    arithmetic, so the same chi2, smoothed outputs and seed
     gradients bit for bit, and the alignment gradient up to the order of its
     atomic sums; on uneven tracks with holes, zero and non-zero alignment."""
     ev = synth.make_event(synth.scaled(synth.WORKLOADS["uneven30_1m"], 333))

@@ -450,6 +450,18 @@ const char* kf_last_cuda_error(void);
  * 4 ulp.  All zero means the helpers behave as documented.  Synchronous. */
 int kf_selftest(int64_t n_patterns, uint64_t* counts);
 
+/* Diagnostic: device self-check of the mixed path's double-float arithmetic
+ * (values carried as a pair of floats hi + lo) against FP64 arithmetic on the
+ * same inputs, over n_patterns random patterns (a quarter of them with sums
+ * that cancel).  counts[5] (host memory) receives the number of results off
+ * by more than 2^-44 of the magnitude of their terms: [0] pair + pair,
+ * [1] pair + float, [2] pair * pair, [3] the compensated dot product
+ * w . r - w0 with a pair-valued r; and [4] the number of patterns whose sum
+ * of the high floats alone already misses that bound (most of them: the
+ * bound is out of plain float arithmetic's reach).  [0..3] all zero means
+ * the arithmetic behaves as documented.  Synchronous. */
+int kf_selftest_df(int64_t n_patterns, uint64_t* counts);
+
 /* ABI version of the loaded library (KF_ABI_VERSION). */
 int kf_abi_version(void);
 

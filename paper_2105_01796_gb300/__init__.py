@@ -30,7 +30,7 @@ MUON_MASS = 0.1056583755
 # exported symbols of include/kf.h
 EXPORTS = ("kf_default_options", "kf_create", "kf_destroy", "kf_fit", "kf_fit_ex",
            "kf_fit_host", "kf_workspace_size", "kf_last_launch_count", "kf_strerror",
-           "kf_last_cuda_error", "kf_abi_version", "kf_selftest", "kf_fit_static",
+           "kf_last_cuda_error", "kf_abi_version", "kf_selftest", "kf_selftest_df", "kf_fit_static",
            "kf_autotune", "kf_chi2_grad", "kf_grad")
 
 
@@ -150,6 +150,8 @@ def load(path: str = LIB_PATH):
         lib.kf_fit_static.restype = ctypes.c_int
         lib.kf_selftest.argtypes = [ctypes.c_int64, ctypes.c_void_p]
         lib.kf_selftest.restype = ctypes.c_int
+        lib.kf_selftest_df.argtypes = [ctypes.c_int64, ctypes.c_void_p]
+        lib.kf_selftest_df.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -307,6 +309,16 @@ def kf_selftest(n_patterns=1 << 22):
     """Device self-check of the numeric helpers; returns the 6 mismatch counts."""
     counts = np.zeros(6, dtype=np.uint64)
     _check(load().kf_selftest(int(n_patterns), counts.ctypes.data_as(ctypes.c_void_p)))
+    return [int(c) for c in counts]
+
+
+def kf_selftest_df(n_patterns=1 << 22):
+    """Device self-check of the mixed path's double-float arithmetic; returns
+    the 4 counts of results beyond 2^-44 (sum, sum with a float, product,
+    compensated dot product) and the count of patterns that a plain float
+    sum already misses."""
+    counts = np.zeros(5, dtype=np.uint64)
+    _check(load().kf_selftest_df(int(n_patterns), counts.ctypes.data_as(ctypes.c_void_p)))
     return [int(c) for c in counts]
 
 

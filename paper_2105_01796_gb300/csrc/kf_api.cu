@@ -207,6 +207,19 @@ int kf_selftest(int64_t n_patterns, uint64_t* counts) {
   return KF_SUCCESS;
 }
 
+int kf_selftest_df(int64_t n_patterns, uint64_t* counts) {
+  if (!counts || n_patterns < 0) return KF_EINVAL;
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 5 * sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(selftest_df)");
+  e = cudaMemset(d, 0, 5 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = launch_selftest_df(n_patterns, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(counts, d, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "selftest_df");
+  return KF_SUCCESS;
+}
+
 const char* kf_strerror(int code) {
   switch (code) {
     case KF_SUCCESS: return "success";

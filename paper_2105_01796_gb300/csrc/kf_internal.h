@@ -118,6 +118,10 @@ cudaError_t launch_pack_surfaces(int n_surfaces, const double* center,
 // Check the integer-pipe conversions and the Newton 1/sqrt, 1/x helpers on n
 // patterns; counters[0..4] receive the mismatch counts.
 cudaError_t launch_selftest(long long n, unsigned long long* counters, cudaStream_t stream);
+// Check the mixed kernel's double-float arithmetic against FP64 on n
+// patterns; counters[0..3] receive the counts beyond 2^-44, counters[4] the
+// patterns a plain float sum already misses.
+cudaError_t launch_selftest_df(long long n, unsigned long long* counters, cudaStream_t stream);
 // The full-range 1/sqrt and 1/x helpers of the FP64 path; counter[0] gets
 // the cases beyond 4 ulp.
 cudaError_t launch_selftest_any(long long n, unsigned long long* counter, cudaStream_t stream);

@@ -1104,6 +1104,63 @@ __global__ void selftest_kernel(long long n, unsigned long long* counters) {
 }
 }  // namespace
 
+// the double-float helpers against FP64 arithmetic on the same (df-exact)
+// inputs; counters: [0] df_add, [1] df_add_f, [2] df_mul, [3] df_dot off by
+// more than 2^-44 of the magnitude of their terms; [4] the patterns whose
+// sum of the float parts alone (hi + hi) already misses that bound, which
+// shows the bound is out of plain FP32's reach.  Every fourth pattern makes
+// the sum cancel (b close to -a).
+__global__ void df_selftest_kernel(long long n, unsigned long long* counters) {
+  const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned long long c[5] = {0, 0, 0, 0, 0};
+  // a double of magnitude 2^-10 .. 2^14 with a random sign and mantissa
+  auto rnd = [](uint64_t z) {
+    const double m = 1.0 + (double)((z >> 12) & 0xfffffffffULL) * 0x1p-36;
+    return ((z & 1) ? -m : m) * exp2((double)((int)((z >> 1) % 25) - 10));
+  };
+  const double tol = 0x1p-44;
+  for (long long i = i0; i < n; i += stride) {
+    const uint64_t z = mix64((uint64_t)i);
+    const double a = rnd(z), b0 = rnd(mix64(z)), f0 = rnd(mix64(z + 1));
+    const double b = (i & 3) == 0 ? -a * (1.0 + rnd(mix64(z + 2)) * 0x1p-30) : b0;
+    const DF A = df_from_d(a), B = df_from_d(b);
+    const double ad = df_to_d(A), bd = df_to_d(B);
+    const double sd = df_to_d(df_add(A, B));
+    if (!(fabs(sd - (ad + bd)) <= tol * (fabs(ad) + fabs(bd)))) ++c[0];
+    if (!(fabs((double)(A.hi + B.hi) - (ad + bd)) <= tol * (fabs(ad) + fabs(bd)))) ++c[4];
+    const float f = __double2float_rn((i & 3) == 1 ? -ad : f0);
+    const double s2 = df_to_d(df_add_f(A, f));
+    if (!(fabs(s2 - (ad + (double)f)) <= tol * (fabs(ad) + fabs((double)f)))) ++c[1];
+    const double pd = df_to_d(df_mul(A, B));
+    if (!(fabs(pd - ad * bd) <= tol * fabs(ad * bd))) ++c[2];
+    float wh[3], wl[3];
+    DF r[3];
+    double ref = 0.0, mag = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const DF w = df_from_d(rnd(mix64(z + 3 + k)));
+      wh[k] = w.hi;
+      wl[k] = w.lo;
+      r[k] = df_from_d(rnd(mix64(z + 7 + k)));
+      const double t = df_to_d(w) * df_to_d(r[k]);
+      ref += t;
+      mag += fabs(t);
+    }
+    const DF w0 = df_from_d((i & 3) == 2 ? ref : rnd(mix64(z + 11)));
+    ref -= df_to_d(w0);
+    mag += fabs(df_to_d(w0));
+    const double dd = df_to_d(df_dot(wh, wl, w0, r));
+    if (!(fabs(dd - ref) <= tol * mag)) ++c[3];
+  }
+  for (int k = 0; k < 5; ++k)
+    if (c[k]) atomicAdd(&counters[k], c[k]);
+}
+
+cudaError_t launch_selftest_df(long long n, unsigned long long* counters, cudaStream_t stream) {
+  df_selftest_kernel<<<152 * 4, 256, 0, stream>>>(n, counters);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_selftest(long long n, unsigned long long* counters, cudaStream_t stream) {
   selftest_kernel<<<152 * 4, 256, 0, stream>>>(n, counters);
   return cudaGetLastError();

@@ -262,6 +262,17 @@ def test_numeric_helpers_selftest(handle):
     assert kf.kf_selftest(1 << 22) == [0, 0, 0, 0, 0, 0]
 
 
+def test_double_float_selftest(handle):
+    """The mixed path's double-float sums, products and compensated dot
+    products stay within 2^-44 of FP64 arithmetic on the same inputs
+    (cancelling sums included), a bound that the float parts alone miss on
+    most patterns."""
+    n = 1 << 22
+    c = kf.kf_selftest_df(n)
+    assert c[:4] == [0, 0, 0, 0], c
+    assert c[4] > n // 2, c
+
+
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_every_launch_variant_agrees(handle, prec):
     """All schedules, block sizes and register-cap variants a tuner may pick:

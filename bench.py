@@ -39,17 +39,17 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 
 # DRAM traffic of the mixed kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of both wave-split launches of a 100k-track, 3.1M-state
-# step of the same workload: launch A 441.8 + 356.4 MB, launch B 373.5 +
-# 309.8 MB.  Traffic grows in proportion to the states, so a launch's traffic
+# step of the same workload: launch A 442.9 + 356.8 MB, launch B 372.5 +
+# 309.7 MB.  Traffic grows in proportion to the states, so a launch's traffic
 # is this per-state figure times its states.  It holds only for the kernel
 # sources and build flags that were captured: any change to them makes the
 # figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (441.766912e6 + 356.435712e6 + 373.46304e6 + 309.7728e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "e14ad798c43989cf9f02586c9bffcedd04608dcf65b0d4b3d1ebc90945a56049"
+MIXED_TRAFFIC_BYTES_PER_STATE = (442.934016e6 + 356.761344e6 + 372.493056e6 + 309.665024e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "b88229987e81bbb373a99d669b7c21229e27bf3f9bbf24cbb3cf314ce7241cee"
 # the same for the FP64 path's kernel (one launch of the 100k-track step:
-# 2300.176 + 2223.512 MB)
-FP64_TRAFFIC_BYTES_PER_STATE = (2300.176e6 + 2223.512e6) / 3.1e6
-FP64_TRAFFIC_SOURCES_SHA256 = "affacdf943c537137b994d87932121664f40f2669338ed8a1f0e2ed1e6a1a71f"
+# 2301.875 + 2223.671 MB)
+FP64_TRAFFIC_BYTES_PER_STATE = (2301.875e6 + 2223.671e6) / 3.1e6
+FP64_TRAFFIC_SOURCES_SHA256 = "021253bb834cb2d2d256b0a9917e45781ba32226a69ae9577eb6016de1512920"
 
 
 # FP64 flops the hardware counted (ncu: 2 x DFMA + DADD + DMUL thread
@@ -57,10 +57,10 @@ FP64_TRAFFIC_SOURCES_SHA256 = "affacdf943c537137b994d87932121664f40f2669338ed8a1
 # (fringe30, 31 states, all three variants) and of the adjoint kernel
 # (align20, 21 states; the chi2 objective and the whole-fit objective);
 # reported while those kernels' sources match
-EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105286 + 2760501541 + 5733751617) / 1e5,
-                       "adjoint_chi2": (2 * 14277600047 + 1627199952 + 7859999977) / 1e5,
-                       "adjoint_whole": (2 * 27684800044 + 2716199931 + 11449099961) / 1e5}
-EXT_SOURCES_SHA256 = "b62e8842c497ae9245055c6dc4451dd01c49b335bd0b77988fc7b6b700483e88"
+EXT_FLOPS_PER_TRACK = {"variants": (2 * 12582105289 + 2760501554 + 5733751583) / 1e5,
+                       "adjoint_chi2": (2 * 14277599975 + 1627200021 + 7860000013) / 1e5,
+                       "adjoint_whole": (2 * 27684800044 + 2716200085 + 11449099947) / 1e5}
+EXT_SOURCES_SHA256 = "3a16bfd21128941923a73fcc50dc8a0a20e200ebe1a9e8fd66701d3eb829c210"
 
 
 def ext_kernel_sources_sha256():

@@ -416,7 +416,7 @@ __device__ __forceinline__ int transport_mixed(const SurfM& sa, const SurfM& sb,
   // of large terms):
   //   tan dphi = (c0 a1 - c1 a0) / (rho^2 + c0 a0 + c1 a1),
   //   tan dtheta = (c2 drho - rho a2) / (c2 (c2 + a2) + rho (rho + drho)),
-  // with rho = |(c0, c1)| and drho the change of rho; the FP64 angles and
+  // with rho = |(c0, c1)| and drho the change of rho; the df angles and
   // their cosines / sines then turn by these increments.
   {
     const float c0 = T0f[0], c1 = T0f[1], c2 = T0f[2];
@@ -812,7 +812,8 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
       }
       const SurfM sk = surf_m(s_surf, sid);
       if (!p.is_hole[o0 + k]) {
-        // gain-matrix update: gain in FP32, Joseph covariance and chi2 in FP64
+        // gain-matrix update: gain in FP32, Joseph covariance (but its K W term)
+        // and chi2 in FP64
         const double m0 = p.loc[o0 + k], m1 = p.loc[p.n_states + o0 + k];
         const double V0 = p.cov[o0 + k], V1 = p.cov[p.n_states + o0 + k], V2 = p.cov[2 * p.n_states + o0 + k];
         const double S00 = V0 + Cp[sy(0, 0)], S01 = V1 + Cp[sy(1, 0)], S11 = V2 + Cp[sy(1, 1)];
@@ -881,7 +882,7 @@ __device__ __forceinline__ void fit_one_mixed(const FitParams& p, const double* 
         pd = Pend{{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}, 0.0f, 0.0f, 0.0f};
         x[4] = xp[4];
       }
-      // the FP64 state moves to the prediction of surface k
+      // the df state moves to the prediction of surface k
 #pragma unroll
       for (int c = 0; c < 3; ++c) r[c] = rp[c];
       d = dp;

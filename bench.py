@@ -39,13 +39,13 @@ FP32_PEAK_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12    # 80.5
 
 # DRAM traffic of the mixed kernel (dram__bytes_read.sum + dram__bytes_write.sum)
 # from one ncu capture of both wave-split launches of a 100k-track, 3.1M-state
-# step of the same workload: launch A 442.9 + 356.8 MB, launch B 372.5 +
-# 309.7 MB.  Traffic grows in proportion to the states, so a launch's traffic
+# step of the same workload: launch A 442.7 + 356.2 MB, launch B 372.7 +
+# 309.2 MB.  Traffic grows in proportion to the states, so a launch's traffic
 # is this per-state figure times its states.  It holds only for the kernel
 # sources and build flags that were captured: any change to them makes the
 # figure null.
-MIXED_TRAFFIC_BYTES_PER_STATE = (442.934016e6 + 356.761344e6 + 372.493056e6 + 309.665024e6) / 3.1e6
-MIXED_TRAFFIC_SOURCES_SHA256 = "b88229987e81bbb373a99d669b7c21229e27bf3f9bbf24cbb3cf314ce7241cee"
+MIXED_TRAFFIC_BYTES_PER_STATE = (442.68288e6 + 356.226304e6 + 372.705536e6 + 309.217792e6) / 3.1e6
+MIXED_TRAFFIC_SOURCES_SHA256 = "97aced5b5c14c3999e2f1739b2b6d73320a1d0671d27f427ceaa7a9bae368779"
 # the same for the FP64 path's kernel (one launch of the 100k-track step:
 # 2301.875 + 2223.671 MB)
 FP64_TRAFFIC_BYTES_PER_STATE = (2301.875e6 + 2223.671e6) / 3.1e6
